@@ -1,0 +1,209 @@
+"""CPU oracle for sampled betweenness centrality -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package. The product path (``paper_1608_04472_gb300``) never
+does, and this package never imports the product path.
+
+The arithmetic lives in ``bc_oracle.c`` (plain single-threaded C, compiled with
+``-ffp-contract=off`` so every double operation rounds once). This module only
+marshals numpy arrays through ctypes. Function-by-function citations of the
+paper are in the C file.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bc_oracle.c")
+_LIB = os.path.join(_HERE, "_bc_oracle.so")
+_lib = None
+
+STOPPED = 0
+CAPPED = 1
+SIGMA_OVERFLOW = 1
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_i32, _i64, _u64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+
+
+def build(force: bool = False) -> str:
+    """Compile bc_oracle.c into _bc_oracle.so (in-tree) and return its path."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    sig = {
+        "orc_philox4x64_10": (None, [_u64p, _u64p, _u64p]),
+        "orc_draw_source": (_i32, [_u64, _u64, _u64, _i32]),
+        "orc_draw_pair": (None, [_u64, _u64, _u64, _i32, _i32p, _i32p]),
+        "orc_exact_sum": (_f64, [_f64p, _i64]),
+        "orc_bfs": (ctypes.c_int, [_i32, _i32p, _i32p, _i32, _i32p, _u64p, _i32p, _i32p]),
+        "orc_source_dependencies": (ctypes.c_int, [_i32, _i32p, _i32p, _i32, _f64p, _i32p, _u64p]),
+        "orc_exact_bc": (ctypes.c_int, [_i32, _i32p, _i32p, _f64p]),
+        "orc_uniform_sources": (ctypes.c_int, [_i32, _i32p, _i32p, _i64, _u64, _u64, _f64p]),
+        "orc_adaptive_sources": (ctypes.c_int, [_i32, _i32p, _i32p, _i32, _i32p, _f64, _i64, _u64,
+                                                _u64, _f64p, _i64p, _f64p, _i32p]),
+        "orc_adaptive_pairs": (ctypes.c_int, [_i32, _i32p, _i32p, _i32, _i32p, _f64, _i64, _u64,
+                                              _u64, _f64, _f64p, _i64p, _f64p, _i32p]),
+        "orc_pair_value": (_f64, [_i32, _i32, _i32, _i32p, _u64p, _i32, _u64]),
+        "orc_pair_sequence": (ctypes.c_int, [_i32, _i32p, _i32p, _i32, _u64, _u64, _i64, _i64,
+                                             _f64p, _i32p, _i32p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _csr(g):
+    rp = np.ascontiguousarray(g.row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(g.col, dtype=np.int32)
+    if col.size == 0:
+        col = np.zeros(1, np.int32)
+    return rp.shape[0] - 1, rp, col
+
+
+def _check(rc):
+    if rc < 0:
+        raise ValueError(f"oracle call failed with code {rc}")
+    return rc
+
+
+def philox4x64_10(counter, key):
+    """Philox4x64-10 block for a 4-word counter and 2-word key (ints)."""
+    c = np.array(counter, dtype=np.uint64)
+    k = np.array(key, dtype=np.uint64)
+    out = np.zeros(4, np.uint64)
+    _load().orc_philox4x64_10(_p(c, _u64p), _p(k, _u64p), _p(out, _u64p))
+    return [int(x) for x in out]
+
+
+def draw_source(seed: int, qid: int, i: int, n: int) -> int:
+    return int(_load().orc_draw_source(seed, qid, i, n))
+
+
+def draw_pair(seed: int, qid: int, i: int, n: int):
+    u, t = _i32(), _i32()
+    _load().orc_draw_pair(seed, qid, i, n, ctypes.byref(u), ctypes.byref(t))
+    return int(u.value), int(t.value)
+
+
+def exact_sum(values) -> float:
+    """Exact sum of non-negative doubles, rounded once to nearest-even."""
+    x = np.ascontiguousarray(values, dtype=np.float64)
+    if x.size == 0:
+        return 0.0
+    return float(_load().orc_exact_sum(_p(x, _f64p), x.size))
+
+
+def bfs(g, s: int):
+    """(dist int32[n] with -1 = unreachable, sigma uint64[n], order, overflow flag)."""
+    n, rp, col = _csr(g)
+    dist = np.empty(n, np.int32)
+    sigma = np.empty(n, np.uint64)
+    order = np.empty(n, np.int32)
+    nr = _i32()
+    rc = _check(_load().orc_bfs(n, _p(rp, _i32p), _p(col, _i32p), s, _p(dist, _i32p),
+                                _p(sigma, _u64p), _p(order, _i32p), ctypes.byref(nr)))
+    return dist, sigma, order[:nr.value], rc == SIGMA_OVERFLOW
+
+
+def dependencies(g, s: int):
+    """(delta float64[n], dist, sigma, overflow) for source s (Theorem 1)."""
+    n, rp, col = _csr(g)
+    delta = np.empty(n, np.float64)
+    dist = np.empty(n, np.int32)
+    sigma = np.empty(n, np.uint64)
+    rc = _check(_load().orc_source_dependencies(n, _p(rp, _i32p), _p(col, _i32p), s,
+                                                _p(delta, _f64p), _p(dist, _i32p),
+                                                _p(sigma, _u64p)))
+    return delta, dist, sigma, rc == SIGMA_OVERFLOW
+
+
+def exact_bc(g) -> np.ndarray:
+    """Exact BC over ordered pairs (Eq. 4) for every vertex."""
+    n, rp, col = _csr(g)
+    bc = np.empty(n, np.float64)
+    _check(_load().orc_exact_bc(n, _p(rp, _i32p), _p(col, _i32p), _p(bc, _f64p)))
+    return bc
+
+
+def uniform_sources(g, k: int, seed: int, qid: int) -> np.ndarray:
+    n, rp, col = _csr(g)
+    est = np.empty(n, np.float64)
+    _check(_load().orc_uniform_sources(n, _p(rp, _i32p), _p(col, _i32p), k, seed, qid,
+                                       _p(est, _f64p)))
+    return est
+
+
+def adaptive_sources(g, targets, c: float, cap: int, seed: int, qid: int):
+    """Bader's adaptive source sampling. Returns dict(est, k, S, status)."""
+    n, rp, col = _csr(g)
+    tg = np.ascontiguousarray(targets, dtype=np.int32)
+    T = tg.size
+    est = np.empty(T, np.float64)
+    k = np.empty(T, np.int64)
+    S = np.empty(T, np.float64)
+    st = np.empty(T, np.int32)
+    tgp = tg if T else np.zeros(1, np.int32)
+    _check(_load().orc_adaptive_sources(n, _p(rp, _i32p), _p(col, _i32p), T, _p(tgp, _i32p),
+                                        c, cap, seed, qid, _p(est, _f64p), _p(k, _i64p),
+                                        _p(S, _f64p), _p(st, _i32p)))
+    return dict(est=est, k=k, S=S, status=st)
+
+
+def adaptive_pairs(g, targets, c: float, cap: int, seed: int, qid: int,
+                   threshold_scale: float = 1.0):
+    """Algorithm 1 (adaptive pair sampling). Returns dict(est, k, S, status)."""
+    n, rp, col = _csr(g)
+    tg = np.ascontiguousarray(targets, dtype=np.int32)
+    T = tg.size
+    est = np.empty(T, np.float64)
+    k = np.empty(T, np.int64)
+    S = np.empty(T, np.float64)
+    st = np.empty(T, np.int32)
+    tgp = tg if T else np.zeros(1, np.int32)
+    _check(_load().orc_adaptive_pairs(n, _p(rp, _i32p), _p(col, _i32p), T, _p(tgp, _i32p),
+                                      c, cap, seed, qid, threshold_scale, _p(est, _f64p),
+                                      _p(k, _i64p), _p(S, _f64p), _p(st, _i32p)))
+    return dict(est=est, k=k, S=S, status=st)
+
+
+def pair_value(v: int, s: int, t: int, dist_v, sigma_v, d_st: int, sigma_st: int) -> float:
+    """sigma_st(v)/sigma_st from a BFS at v (dist_v, sigma_v) and d(s,t), sigma_st."""
+    dv = np.ascontiguousarray(dist_v, dtype=np.int32)
+    sv = np.ascontiguousarray(sigma_v, dtype=np.uint64)
+    return float(_load().orc_pair_value(v, s, t, _p(dv, _i32p), _p(sv, _u64p), d_st, sigma_st))
+
+
+def pair_sequence(g, v: int, seed: int, qid: int, i0: int, count: int):
+    """Per-draw pair dependencies y_i(v) for draws i0..i0+count-1; returns (y, s, t)."""
+    n, rp, col = _csr(g)
+    y = np.empty(count, np.float64)
+    s = np.empty(count, np.int32)
+    t = np.empty(count, np.int32)
+    _check(_load().orc_pair_sequence(n, _p(rp, _i32p), _p(col, _i32p), v, seed, qid, i0, count,
+                                     _p(y, _f64p), _p(s, _i32p), _p(t, _i32p)))
+    return y, s, t

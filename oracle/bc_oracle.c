@@ -1,0 +1,468 @@
+/*
+ * bc_oracle.c -- plain, slow, single-threaded CPU oracle for sampled
+ * betweenness centrality (Ji & Yan, "Refining Approximating Betweenness
+ * Centrality Based on Samplings").
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this file. It shares no code, header or constant
+ * table with the CUDA library; it consumes the same CSR inputs.
+ *
+ * Every function follows the paper's definitions in the paper's order:
+ *   - BFS distances and shortest-path counts sigma (Sec. 3, step 1 of Brandes'
+ *     algorithm; predecessor sets of Def. 3).
+ *   - Dependencies by the recursion of Theorem 1, visiting vertices in
+ *     non-increasing distance (Sec. 3, step 2).
+ *   - Exact BC as the sum of dependencies over all sources (Eq. 4).
+ *   - Bader's adaptive source sampling (Sec. 4, steps 1-3).
+ *   - Adaptive pair sampling (Algorithm 1, Sec. 6.1).
+ *   - Uniform k-source all-vertex estimate (n/k times the summed dependencies).
+ *
+ * Readings where the paper is silent (the same list appears in the design notes):
+ *   R1 pairs are ordered; BC(v) ranges over [0, n^2] (Def. 1).
+ *   R2 s, t, v pairwise distinct; delta_s(s) = 0.
+ *   R3 sigma_st = 0 (t unreachable) contributes 0.
+ *   R4 sources uniform over all n vertices, with replacement.
+ *   R5 stop at the first k with S > c*n (strict); k counts every draw.
+ *   R6 pairs: ordered, uniform over the n(n-1) distinct pairs.
+ *   R7 a cap on draws is mandatory; reaching it reports CAPPED.
+ *   R10 floating point: every operation is one IEEE double rounding
+ *       (round to nearest even), no contraction. The successor sum of
+ *       Theorem 1 and the sums over sources are EXACT sums rounded once, so
+ *       their value does not depend on summation order. sigma is converted to
+ *       double by round-to-nearest.
+ *   R11 sigma is exact uint64; an overflow is reported, never wrapped.
+ *
+ * Random draws: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC'11) with key = (seed, qid) and counter =
+ * (i, 0, 0, 0) for the i-th draw (0-based). A source is floor(x0*n/2^64); an
+ * ordered distinct pair is u = floor(x0*n/2^64), w = floor(x1*(n-1)/2^64),
+ * t = w + (w >= u).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_E_NOMEM -2
+#define ORC_E_INVALID -1
+#define ORC_SIGMA_OVERFLOW 1
+
+#define ORC_STOPPED 0
+#define ORC_CAPPED 1
+
+/* ------------------------------------------------------------- Philox -- */
+
+static void orc_mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo) {
+  unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+  *hi = (uint64_t)(p >> 64);
+  *lo = (uint64_t)p;
+}
+
+/* Philox4x64 with 10 rounds: each round multiplies counter words 0 and 2 by
+ * the two round multipliers, permutes/xors with the key, and the key is bumped
+ * by the two Weyl increments between rounds. */
+void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+  const uint64_t MUL0 = 0xD2E7470EE14C6C93ULL, MUL1 = 0xCA5A826395121157ULL;
+  const uint64_t WEYL0 = 0x9E3779B97F4A7C15ULL, WEYL1 = 0xBB67AE8584CAA73BULL;
+  uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint64_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { k0 += WEYL0; k1 += WEYL1; }
+    uint64_t hi0, lo0, hi1, lo1;
+    orc_mulhilo64(MUL0, c0, &hi0, &lo0);
+    orc_mulhilo64(MUL1, c2, &hi1, &lo1);
+    uint64_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static uint64_t orc_scale(uint64_t x, uint64_t m) {
+  return (uint64_t)(((unsigned __int128)x * m) >> 64);
+}
+
+/* Source of draw i: uniform over all n vertices (Sec. 4 step 2, reading R4). */
+int32_t orc_draw_source(uint64_t seed, uint64_t qid, uint64_t i, int32_t n) {
+  uint64_t ctr[4] = {i, 0, 0, 0}, key[2] = {seed, qid}, x[4];
+  orc_philox4x64_10(ctr, key, x);
+  return (int32_t)orc_scale(x[0], (uint64_t)n);
+}
+
+/* Ordered pair of different vertices of draw i (Algorithm 1, reading R6). */
+void orc_draw_pair(uint64_t seed, uint64_t qid, uint64_t i, int32_t n, int32_t *u,
+                   int32_t *t) {
+  uint64_t ctr[4] = {i, 0, 0, 0}, key[2] = {seed, qid}, x[4];
+  orc_philox4x64_10(ctr, key, x);
+  uint64_t a = orc_scale(x[0], (uint64_t)n);
+  uint64_t w = orc_scale(x[1], (uint64_t)n - 1);
+  *u = (int32_t)a;
+  *t = (int32_t)(w + (w >= a));
+}
+
+/* ------------------------------------------------------------ exact sum -- */
+/*
+ * An exact accumulator for non-negative finite doubles: a 2304-bit unsigned
+ * integer holding the sum in units of 2^-1074 (the smallest subnormal), so
+ * every double is an integer multiple of the unit and every addition is exact.
+ * orc_acc_round() returns the sum rounded once to the nearest double (ties to
+ * even).
+ */
+#define ORC_ACC_WORDS 36
+typedef struct { uint64_t w[ORC_ACC_WORDS]; } orc_acc;
+
+static void orc_acc_clear(orc_acc *a) {
+  memset(a->w, 0, sizeof a->w);
+}
+
+static void orc_acc_add_bits(orc_acc *a, uint64_t mant, int pos) {
+  /* adds mant * 2^pos (pos counted from the accumulator's bit 0) */
+  int word = pos >> 6, sh = pos & 63;
+  uint64_t lo = mant << sh;
+  uint64_t hi = sh ? (mant >> (64 - sh)) : 0;
+  int i = word;
+  uint64_t old = a->w[i];
+  a->w[i] = old + lo;
+  uint64_t carry = (a->w[i] < old);
+  ++i;
+  uint64_t add = hi;
+  while (add || carry) {
+    old = a->w[i];
+    uint64_t s = old + add;
+    uint64_t c1 = (s < old);
+    uint64_t s2 = s + carry;
+    uint64_t c2 = (s2 < s);
+    a->w[i] = s2;
+    carry = c1 | c2;
+    add = 0;
+    ++i;
+  }
+}
+
+static void orc_acc_add(orc_acc *a, double x) {
+  if (x == 0.0) return;
+  uint64_t bits;
+  memcpy(&bits, &x, 8);
+  int e = (int)((bits >> 52) & 0x7ff);
+  uint64_t m = bits & ((1ULL << 52) - 1);
+  if (e == 0) orc_acc_add_bits(a, m, 0);               /* subnormal: m * 2^-1074 */
+  else orc_acc_add_bits(a, m | (1ULL << 52), e - 1);   /* (2^52+m) * 2^(e-1075) */
+}
+
+static double orc_acc_round(const orc_acc *a) {
+  int top = -1;
+  for (int i = ORC_ACC_WORDS - 1; i >= 0; --i)
+    if (a->w[i]) { top = i * 64 + 63 - __builtin_clzll(a->w[i]); break; }
+  if (top < 0) return 0.0;
+  if (top <= 52) { /* below 2^-1021: exactly representable */
+    uint64_t k = a->w[0];
+    return ldexp((double)k, -1074);
+  }
+  /* keep bits [top-52, top]; round bit top-53; sticky below */
+  int lsb = top - 52;
+  uint64_t mant = 0;
+  for (int b = 0; b < 53; ++b) {
+    int p = lsb + b;
+    mant |= ((a->w[p >> 6] >> (p & 63)) & 1ULL) << b;
+  }
+  int rpos = lsb - 1;
+  int round = (int)((a->w[rpos >> 6] >> (rpos & 63)) & 1ULL);
+  int sticky = 0; /* any set bit strictly below rpos */
+  for (int i = 0; i < (rpos >> 6); ++i)
+    if (a->w[i]) sticky = 1;
+  if ((rpos & 63) && (a->w[rpos >> 6] & ((1ULL << (rpos & 63)) - 1))) sticky = 1;
+  if (round && (sticky || (mant & 1ULL))) {
+    mant += 1;
+    if (mant == (1ULL << 53)) { mant >>= 1; lsb += 1; }
+  }
+  return ldexp((double)mant, lsb - 1074);
+}
+
+/* Exact sum of non-negative doubles, rounded once (exposed for pinning). */
+double orc_exact_sum(const double *x, int64_t count) {
+  orc_acc *a = (orc_acc *)malloc(sizeof(orc_acc));
+  if (!a) return NAN;
+  orc_acc_clear(a);
+  for (int64_t i = 0; i < count; ++i) orc_acc_add(a, x[i]);
+  double r = orc_acc_round(a);
+  free(a);
+  return r;
+}
+
+/* ------------------------------------------------------------------ BFS -- */
+/*
+ * Single-source shortest paths on an unweighted graph (Sec. 3 step 1: Dijkstra
+ * reduces to BFS when every edge has length 1). FIFO queue, neighbours in CSR
+ * order. dist[v] = d(s,v) or -1 when unreachable; sigma[v] = sigma_sv, the sum
+ * of sigma over the predecessor set P_s(v) of Def. 3, sigma_ss = 1;
+ * order[0..*nreached) lists reached vertices by non-decreasing distance.
+ * Returns ORC_SIGMA_OVERFLOW if some sigma does not fit in 64 bits.
+ */
+int orc_bfs(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
+            int32_t *dist, uint64_t *sigma, int32_t *order, int32_t *nreached) {
+  int overflow = 0;
+  for (int32_t v = 0; v < n; ++v) { dist[v] = -1; sigma[v] = 0; }
+  int32_t head = 0, tail = 0;
+  dist[s] = 0;
+  sigma[s] = 1;
+  order[tail++] = s;
+  while (head < tail) {
+    int32_t v = order[head++];
+    for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) {
+      int32_t w = col[j];
+      if (dist[w] < 0) { dist[w] = dist[v] + 1; order[tail++] = w; }
+      if (dist[w] == dist[v] + 1) { /* v is in P_s(w) */
+        uint64_t before = sigma[w];
+        sigma[w] = before + sigma[v];
+        if (sigma[w] < before) overflow = 1;
+      }
+    }
+  }
+  *nreached = tail;
+  return overflow ? ORC_SIGMA_OVERFLOW : ORC_OK;
+}
+
+/*
+ * Dependencies delta_s(v) by Theorem 1:
+ *   delta_s(v) = sum over w with v in P_s(w) of sigma_sv/sigma_sw * (1 + delta_s(w)),
+ * evaluated in the factored form delta_s(v) = sigma_sv * SUM_w coef_w with
+ * coef_w = (1 + delta_s(w)) / sigma_sw, visiting vertices in non-increasing
+ * distance (Sec. 3 step 2). The successor sum is exact, rounded once (R10).
+ * delta_s(s) = 0 (R2); unreachable vertices get 0 (R3).
+ */
+int orc_dependencies(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
+                     const int32_t *dist, const uint64_t *sigma, const int32_t *order,
+                     int32_t nreached, double *delta) {
+  double *coef = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  orc_acc *acc = (orc_acc *)malloc(sizeof(orc_acc));
+  if (!coef || !acc) { free(coef); free(acc); return ORC_E_NOMEM; }
+  orc_acc_clear(acc);
+  for (int32_t v = 0; v < n; ++v) delta[v] = 0.0;
+  for (int32_t idx = nreached - 1; idx >= 0; --idx) {
+    int32_t v = order[idx];
+    for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) {
+      int32_t w = col[j];
+      if (dist[w] == dist[v] + 1) orc_acc_add(acc, coef[w]); /* v in P_s(w) */
+    }
+    double sum = orc_acc_round(acc);
+    orc_acc_clear(acc);
+    double sv = (double)sigma[v];
+    double d = sv * sum;
+    if (v == s) d = 0.0;
+    delta[v] = d;
+    coef[v] = (1.0 + d) / sv;
+  }
+  free(coef);
+  free(acc);
+  return ORC_OK;
+}
+
+/* BFS + dependencies for one source. dist/sigma may be NULL. */
+int orc_source_dependencies(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                            int32_t s, double *delta, int32_t *dist_out,
+                            uint64_t *sigma_out) {
+  int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+  uint64_t *sigma = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n ? n : 1));
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+  if (!dist || !sigma || !order) { free(dist); free(sigma); free(order); return ORC_E_NOMEM; }
+  int32_t nr = 0;
+  int rc = orc_bfs(n, row_ptr, col, s, dist, sigma, order, &nr);
+  int rc2 = orc_dependencies(n, row_ptr, col, s, dist, sigma, order, nr, delta);
+  if (dist_out) memcpy(dist_out, dist, sizeof(int32_t) * (size_t)n);
+  if (sigma_out) memcpy(sigma_out, sigma, sizeof(uint64_t) * (size_t)n);
+  free(dist); free(sigma); free(order);
+  return rc2 != ORC_OK ? rc2 : rc;
+}
+
+/* --------------------------------------------------------------- exact BC -- */
+/* BC(x) = sum over sources s != x of delta_s(x) (Eq. 4, Brandes' algorithm of
+ * Sec. 3), the sum over s exact and rounded once. */
+int orc_exact_bc(int32_t n, const int32_t *row_ptr, const int32_t *col, double *bc) {
+  double *delta = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  orc_acc *acc = (orc_acc *)malloc(sizeof(orc_acc) * (size_t)(n ? n : 1));
+  if (!delta || !acc) { free(delta); free(acc); return ORC_E_NOMEM; }
+  for (int32_t v = 0; v < n; ++v) orc_acc_clear(&acc[v]);
+  int status = ORC_OK;
+  for (int32_t s = 0; s < n; ++s) {
+    int rc = orc_source_dependencies(n, row_ptr, col, s, delta, NULL, NULL);
+    if (rc < 0) { free(delta); free(acc); return rc; }
+    if (rc == ORC_SIGMA_OVERFLOW) status = ORC_SIGMA_OVERFLOW;
+    for (int32_t v = 0; v < n; ++v) orc_acc_add(&acc[v], delta[v]);
+  }
+  for (int32_t v = 0; v < n; ++v) bc[v] = orc_acc_round(&acc[v]);
+  free(delta);
+  free(acc);
+  return status;
+}
+
+/* ----------------------------------------------------- uniform estimate -- */
+/* est(x) = n/k * sum_{i<k} delta_{s_i}(x), s_i the first k source draws of
+ * (seed, qid); the sum over i exact and rounded once, then (n*S)/k. */
+int orc_uniform_sources(int32_t n, const int32_t *row_ptr, const int32_t *col, int64_t k,
+                        uint64_t seed, uint64_t qid, double *est) {
+  if (k < 1 || n < 1) return ORC_E_INVALID;
+  double *delta = (double *)malloc(sizeof(double) * (size_t)n);
+  orc_acc *acc = (orc_acc *)malloc(sizeof(orc_acc) * (size_t)n);
+  if (!delta || !acc) { free(delta); free(acc); return ORC_E_NOMEM; }
+  for (int32_t v = 0; v < n; ++v) orc_acc_clear(&acc[v]);
+  int status = ORC_OK;
+  for (int64_t i = 0; i < k; ++i) {
+    int32_t s = orc_draw_source(seed, qid, (uint64_t)i, n);
+    int rc = orc_source_dependencies(n, row_ptr, col, s, delta, NULL, NULL);
+    if (rc < 0) { free(delta); free(acc); return rc; }
+    if (rc == ORC_SIGMA_OVERFLOW) status = ORC_SIGMA_OVERFLOW;
+    for (int32_t v = 0; v < n; ++v) orc_acc_add(&acc[v], delta[v]);
+  }
+  for (int32_t v = 0; v < n; ++v) {
+    double S = orc_acc_round(&acc[v]);
+    est[v] = ((double)n * S) / (double)k;
+  }
+  free(delta);
+  free(acc);
+  return status;
+}
+
+/* ---------------------------------------------------- Bader (Sec. 4) ----- */
+/*
+ * For each target v: S <- 0; draw s_i, S <- S + delta_{s_i}(v), k <- k+1;
+ * repeat while S <= c*n; output n*S/k (Sec. 4 steps 1-3). All targets read the
+ * same draw stream. The loop for a target also ends at k = cap (status CAPPED).
+ * S is the running double sum in draw order.
+ */
+int orc_adaptive_sources(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                         int32_t T, const int32_t *targets, double c, int64_t cap,
+                         uint64_t seed, uint64_t qid, double *est, int64_t *k_out,
+                         double *S_out, int32_t *stop_status) {
+  if (n < 1 || T < 0 || cap < 1 || !(c >= 1.0)) return ORC_E_INVALID;
+  for (int32_t j = 0; j < T; ++j)
+    if (targets[j] < 0 || targets[j] >= n) return ORC_E_INVALID;
+  double *delta = (double *)malloc(sizeof(double) * (size_t)n);
+  int32_t *done = (int32_t *)calloc((size_t)(T ? T : 1), sizeof(int32_t));
+  if (!delta || !done) { free(delta); free(done); return ORC_E_NOMEM; }
+  const double cn = c * (double)n;
+  for (int32_t j = 0; j < T; ++j) { S_out[j] = 0.0; k_out[j] = 0; stop_status[j] = ORC_CAPPED; }
+  int32_t remaining = T;
+  int status = ORC_OK;
+  for (int64_t i = 0; i < cap && remaining > 0; ++i) {
+    int32_t s = orc_draw_source(seed, qid, (uint64_t)i, n);
+    int rc = orc_source_dependencies(n, row_ptr, col, s, delta, NULL, NULL);
+    if (rc < 0) { free(delta); free(done); return rc; }
+    if (rc == ORC_SIGMA_OVERFLOW) status = ORC_SIGMA_OVERFLOW;
+    for (int32_t j = 0; j < T; ++j) {
+      if (done[j]) continue;
+      S_out[j] = S_out[j] + delta[targets[j]];
+      k_out[j] = i + 1;
+      if (S_out[j] > cn) { done[j] = 1; stop_status[j] = ORC_STOPPED; --remaining; }
+    }
+  }
+  for (int32_t j = 0; j < T; ++j)
+    est[j] = ((double)n * S_out[j]) / (double)k_out[j];
+  free(delta);
+  free(done);
+  return status;
+}
+
+/* ------------------------------------------------ pairs (Algorithm 1) ---- */
+/*
+ * Pair dependency of v for the ordered pair (s, t) (Eq. 2):
+ *   sigma_st(v)/sigma_st = sigma_sv*sigma_vt/sigma_st if d(s,v)+d(v,t) = d(s,t),
+ * else 0; also 0 when v is s or t (R2) or t is unreachable from s (R3).
+ * d(v,.), sigma_v. come from a BFS at v (undirected: d(s,v) = d(v,s),
+ * sigma_sv = sigma_vs); d(s,t), sigma_st from a BFS at s.
+ * Evaluated as ((double)sigma_sv * (double)sigma_vt) / (double)sigma_st.
+ */
+double orc_pair_value(int32_t v, int32_t s, int32_t t, const int32_t *dist_v,
+                      const uint64_t *sigma_v, int32_t d_st, uint64_t sigma_st) {
+  if (v == s || v == t || sigma_st == 0 || d_st < 0) return 0.0;
+  if (dist_v[s] < 0 || dist_v[t] < 0) return 0.0;
+  if (dist_v[s] + dist_v[t] != d_st) return 0.0;
+  return ((double)sigma_v[s] * (double)sigma_v[t]) / (double)sigma_st;
+}
+
+/*
+ * Algorithm 1 for each target v: S <- 0, k <- 0; while S <= c*n: draw an
+ * ordered pair (s,t) of different vertices, S <- S + sigma_st(v)/sigma_st,
+ * k <- k+1; return n(n-1)S/k. All targets share the pair stream; a target also
+ * stops at k = cap (CAPPED). threshold_scale multiplies S in the stop test
+ * (1 = the paper's test S <= c*n).
+ */
+int orc_adaptive_pairs(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t T,
+                       const int32_t *targets, double c, int64_t cap, uint64_t seed,
+                       uint64_t qid, double threshold_scale, double *est, int64_t *k_out,
+                       double *S_out, int32_t *stop_status) {
+  if (n < 2 || T < 0 || cap < 1 || !(c >= 1.0) || !(threshold_scale > 0.0))
+    return ORC_E_INVALID;
+  for (int32_t j = 0; j < T; ++j)
+    if (targets[j] < 0 || targets[j] >= n) return ORC_E_INVALID;
+  size_t nn = (size_t)n;
+  int32_t *dist_t = (int32_t *)malloc(sizeof(int32_t) * nn * (size_t)(T ? T : 1));
+  uint64_t *sig_t = (uint64_t *)malloc(sizeof(uint64_t) * nn * (size_t)(T ? T : 1));
+  int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * nn);
+  uint64_t *sigma = (uint64_t *)malloc(sizeof(uint64_t) * nn);
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *done = (int32_t *)calloc((size_t)(T ? T : 1), sizeof(int32_t));
+  if (!dist_t || !sig_t || !dist || !sigma || !order || !done) {
+    free(dist_t); free(sig_t); free(dist); free(sigma); free(order); free(done);
+    return ORC_E_NOMEM;
+  }
+  int status = ORC_OK;
+  int32_t nr;
+  for (int32_t j = 0; j < T; ++j) {
+    if (orc_bfs(n, row_ptr, col, targets[j], dist_t + (size_t)j * nn, sig_t + (size_t)j * nn,
+                order, &nr) == ORC_SIGMA_OVERFLOW)
+      status = ORC_SIGMA_OVERFLOW;
+  }
+  const double cn = c * (double)n;
+  for (int32_t j = 0; j < T; ++j) { S_out[j] = 0.0; k_out[j] = 0; stop_status[j] = ORC_CAPPED; }
+  int32_t remaining = T;
+  for (int64_t i = 0; i < cap && remaining > 0; ++i) {
+    int32_t s, t;
+    orc_draw_pair(seed, qid, (uint64_t)i, n, &s, &t);
+    if (orc_bfs(n, row_ptr, col, s, dist, sigma, order, &nr) == ORC_SIGMA_OVERFLOW)
+      status = ORC_SIGMA_OVERFLOW;
+    for (int32_t j = 0; j < T; ++j) {
+      if (done[j]) continue;
+      double y = orc_pair_value(targets[j], s, t, dist_t + (size_t)j * nn,
+                                sig_t + (size_t)j * nn, dist[t], sigma[t]);
+      S_out[j] = S_out[j] + y;
+      k_out[j] = i + 1;
+      if (S_out[j] * threshold_scale > cn) {
+        done[j] = 1; stop_status[j] = ORC_STOPPED; --remaining;
+      }
+    }
+  }
+  const double nn1 = (double)n * (double)(n - 1);
+  for (int32_t j = 0; j < T; ++j) est[j] = (nn1 * S_out[j]) / (double)k_out[j];
+  free(dist_t); free(sig_t); free(dist); free(sigma); free(order); free(done);
+  return status;
+}
+
+/* Pair values y_i(v) for explicit draws i in [i0, i0+count) of (seed, qid), for
+ * one target v: the per-draw sequence Algorithm 1 accumulates (test helper). */
+int orc_pair_sequence(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t v,
+                      uint64_t seed, uint64_t qid, int64_t i0, int64_t count, double *y,
+                      int32_t *s_out, int32_t *t_out) {
+  size_t nn = (size_t)n;
+  int32_t *dist_v = (int32_t *)malloc(sizeof(int32_t) * nn);
+  uint64_t *sig_v = (uint64_t *)malloc(sizeof(uint64_t) * nn);
+  int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * nn);
+  uint64_t *sigma = (uint64_t *)malloc(sizeof(uint64_t) * nn);
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * nn);
+  if (!dist_v || !sig_v || !dist || !sigma || !order) {
+    free(dist_v); free(sig_v); free(dist); free(sigma); free(order);
+    return ORC_E_NOMEM;
+  }
+  int32_t nr;
+  int status = orc_bfs(n, row_ptr, col, v, dist_v, sig_v, order, &nr);
+  for (int64_t q = 0; q < count; ++q) {
+    int32_t s, t;
+    orc_draw_pair(seed, qid, (uint64_t)(i0 + q), n, &s, &t);
+    if (orc_bfs(n, row_ptr, col, s, dist, sigma, order, &nr) == ORC_SIGMA_OVERFLOW)
+      status = ORC_SIGMA_OVERFLOW;
+    y[q] = orc_pair_value(v, s, t, dist_v, sig_v, dist[t], sigma[t]);
+    if (s_out) s_out[q] = s;
+    if (t_out) t_out[q] = t;
+  }
+  free(dist_v); free(sig_v); free(dist); free(sigma); free(order);
+  return status;
+}
