@@ -1,0 +1,362 @@
+"""Benchmark: Brandes samples/s and GTEPS on undirected R-MAT scale 20.
+
+Workload (one step): on the resident R-MAT scale-20 graph (edge factor 16,
+a=0.57 b=0.19 c=0.19, seed 2; int32 CSR, symmetrised and deduplicated):
+  * Bader's adaptive source sampling, c = 5, 512 uniform targets, cap n/20
+    draws (Sec. 4), and
+  * a uniform 4096-source all-vertex estimate,
+each with its own draw stream (a fresh qid per step, so nothing is reused).
+A sample is one per-source Brandes step (forward BFS with sigma + backward
+dependency accumulation). samples = (largest k over the Bader targets) + 4096;
+draws computed past the last target's stop inside the final batch are not
+counted. GTEPS counts, per sample, the undirected edges of the source's
+connected component.
+
+Timing: CUDA events on the stream the library launches on, after W warm-up
+steps, K timed steps bracketed by (barrier +) synchronize; max over ranks.
+Inputs exceed L2 (CSR 134 MB, per-batch lane state 0.6 GB), so no L2 flush.
+`e2e` repeats the step through the C ABI with host buffers: the CSR upload,
+both queries and their result downloads are inside the timed region.
+
+--impl reference times the CPU oracle (single-threaded C) on a bounded
+sample of the same workload (the first Bader draws), same metric and unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SCALE, EF, A, B, C, SEED = 20, 16, 0.57, 0.19, 0.19, 2
+T_TARGETS, C_BADER, K_UNIFORM = 512, 5.0, 4096
+WORKLOAD = "rmat_s20_ef16_bader_c5_T512_capn20_plus_uniform_k4096"
+METRIC = "Brandes samples/s (R-MAT s20, batched 64-wide)"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_graph():
+    import graphgen as gg
+    return gg.rmat(SCALE, EF, A, B, C, SEED)
+
+
+def component_edges(g):
+    """Undirected edges of each vertex's connected component (for TEPS)."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    adj = sp.csr_matrix((np.ones(g.nnz, np.int8), g.col, g.row_ptr), shape=(g.n, g.n))
+    ncomp, labels = connected_components(adj, directed=False)
+    comp_nnz = np.bincount(labels, weights=g.degrees(), minlength=ncomp)
+    return (comp_nnz / 2.0)[labels]
+
+
+def run_reference(args):
+    """CPU oracle on a bounded sample of the same workload."""
+    import graphgen as gg
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    g = build_graph()
+    targets = gg.uniform_targets(g.n, T_TARGETS, SEED)
+    per_step = 4  # oracle per-sample Brandes steps per bench step
+    ce = component_edges(g)
+    n = g.n
+    for w in range(args.warmup):
+        oracle.adaptive_sources(g, targets, C_BADER, 1, SEED, 1000 + w)
+    t0 = time.perf_counter()
+    edges = 0.0
+    for st in range(args.steps):
+        qid = 2000 + st
+        oracle.adaptive_sources(g, targets, C_BADER, per_step, SEED, qid)
+        for i in range(per_step):
+            edges += ce[oracle.draw_source(SEED, qid, i, n)]
+    dt = time.perf_counter() - t0
+    samples = per_step * args.steps
+    value = samples / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph": f"rmat s{SCALE} ef{EF} seed {SEED}",
+                   "reference": "CPU oracle (oracle/bc_oracle.c), single thread",
+                   "sample": f"{per_step} Bader draws per step (full per-sample Brandes step each)"},
+        "gteps": edges / dt / 1e9,
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {per_step} draws of the Bader stream per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline(g, targets, budget_s=12.0):
+    """The oracle timed on a bounded sample: Bader draws until ~budget_s."""
+    import oracle
+    n = g.n
+    oracle.dependencies(g, 0)  # warm the library
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < budget_s and k < 64:
+        oracle.dependencies(g, oracle.draw_source(SEED, 999, k, n))
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} per-sample Brandes steps (Bader draws of R-MAT s20), single-threaded C"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+
+    import graphgen as gg
+    import paper_1608_04472_gb300 as pkg
+
+    g = build_graph()
+    n = g.n
+    cap = n // 20
+    targets = gg.uniform_targets(n, T_TARGETS, SEED)
+    ce = component_edges(g)
+
+    stream = torch.cuda.current_stream()
+    ctx = pkg.Context(local, batch_width=64, stream=stream.cuda_stream)
+    h = ctx.load_graph(g.row_ptr, g.col)
+
+    def step(qid_base):
+        rb = ctx.adaptive_sources(h, targets, C_BADER, cap, SEED, qid_base)
+        est = ctx.uniform_sources(h, K_UNIFORM, SEED, qid_base + 1)
+        return rb, est
+
+    qid = 1_000_000 * (rank + 1)
+    for _ in range(args.warmup):
+        step(qid)
+        qid += 2
+    ctx.reset_stats()
+    ctx.set_profiling(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    kmax, qids = [], []
+    for _ in range(args.steps):
+        rb, _ = step(qid)
+        kmax.append(int(rb["k"].max()))
+        qids.append(qid)
+        qid += 2
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    stats = ctx.stats()
+    ctx.set_profiling(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    samples_local = sum(kmax) + K_UNIFORM * args.steps
+    edges_local = 0.0
+    for q, km in zip(qids, kmax):
+        edges_local += float(ce[ctx.draw_sources(SEED, q, 0, km, n)].sum())
+        edges_local += float(ce[ctx.draw_sources(SEED, q + 1, 0, K_UNIFORM, n)].sum())
+    if dist:
+        t = torch.tensor([samples_local, edges_local], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t)
+        samples_total, edges_total = float(t[0]), float(t[1])
+    else:
+        samples_total, edges_total = float(samples_local), edges_local
+    value = samples_total / (ms / 1e3)
+
+    # roofline of the dominant kernel family (measured live over the timed region)
+    peaks, peak_kind = load_peaks()
+    kern = stats["kernels"]
+    dom = max(("fwd", "bwd"), key=lambda k: kern[k]["ms"])
+    lanes_processed = stats["samples"]
+    bytes_fwd = 8.0 * stats["dag_edges"] + 8.0 * stats["reached"]
+    bytes_bwd = 8.0 * stats["dag_edges"] + 16.0 * stats["reached"]
+    alg_bytes = bytes_bwd if dom == "bwd" else bytes_fwd
+    dom_ms = kern[dom]["ms"]
+    achieved = alg_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": f"{dom} (k_{dom}_light + heavy segments)", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": None, "peak_kind": peak_kind,
+                "launches": kern[dom]["launches"], "avg_launch_ms": dom_ms / max(kern[dom]["launches"], 1),
+                "alg_bytes_per_launch": alg_bytes / max(kern[dom]["launches"], 1),
+                "dag_edges_per_sample": stats["dag_edges"] / max(lanes_processed, 1),
+                "reached_per_sample": stats["reached"] / max(lanes_processed, 1)}
+    gpu_launches = int(stats["launches"])
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph": f"R-MAT s{SCALE} ef{EF} a{A} b{B} c{C} seed {SEED}",
+                   "n": n, "nnz": g.nnz, "targets": T_TARGETS, "c": C_BADER, "cap": cap,
+                   "uniform_k": K_UNIFORM, "batch_width": 64, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (CSR 134 MB + 0.6 GB lane state); no flush"},
+        "gteps": edges_total / (ms / 1e3) / 1e9,
+        "samples_per_step": samples_total / args.steps,
+        "lane_samples_computed": lanes_processed,
+        "kernel_ms": {k: round(v["ms"], 3) for k, v in kern.items() if v["launches"]},
+        "roofline": roofline,
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+    }
+
+    if rank == 0 and not args.no_plain:
+        # plain (one source per launch sequence) vs batched on the same uniform query
+        kq = 256
+        ctx.set_batch_width(1)
+        ctx.uniform_sources(h, 8, SEED, 7)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        est_plain = ctx.uniform_sources(h, kq, SEED, 77)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_plain = e0.elapsed_time(e1)
+        ctx.set_batch_width(64)
+        e0.record(stream)
+        est_b = ctx.uniform_sources(h, kq, SEED, 77)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_b = e0.elapsed_time(e1)
+        out["plain"] = {"workload": f"uniform k={kq} on the same graph",
+                        "plain_samples_per_s": kq / (ms_plain / 1e3),
+                        "batched_samples_per_s": kq / (ms_b / 1e3),
+                        "speedup": ms_plain / ms_b,
+                        "identical_estimates": bool(np.array_equal(est_plain, est_b))}
+
+    if not args.no_e2e:
+        e2e_steps = max(1, min(2, args.steps))
+        h2d = g.row_ptr.nbytes + g.col.nbytes + targets.nbytes
+        d2h = T_TARGETS * (8 + 8 + 8 + 4) + n * 8
+        ctx.free_graph(h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        samp = 0
+        for _ in range(e2e_steps):
+            h2 = ctx.load_graph(g.row_ptr, g.col)
+            rb = ctx.adaptive_sources(h2, targets, C_BADER, cap, SEED, qid)
+            ctx.uniform_sources(h2, K_UNIFORM, SEED, qid + 1)
+            samp += int(rb["k"].max()) + K_UNIFORM
+            ctx.free_graph(h2)
+            qid += 2
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e_val = samp / dt
+        if dist:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_val = samp * world / float(t.item())
+        out["e2e"] = {"value": e2e_val, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
+    else:
+        ctx.free_graph(h)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(g, targets)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

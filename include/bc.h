@@ -1,0 +1,193 @@
+/*
+ * bc.h -- C ABI of the GB300 sampled-betweenness library (libbcgb300.so).
+ *
+ * Implements the per-sample Brandes step and the estimators built on it from
+ * Ji & Yan, "Refining Approximating Betweenness Centrality Based on
+ * Samplings":
+ *   - betweenness over ordered pairs, BC(v) = sum_{s!=t!=v} sigma_st(v)/sigma_st
+ *     (Def. 1, Eq. 1-2);
+ *   - the dependency recursion of Theorem 1 evaluated in decreasing distance
+ *     after an unweighted single-source shortest-path pass (Sec. 3, Brandes'
+ *     algorithm steps 1-2);
+ *   - Bader's adaptive source sampling with the relaxed bound c >= 1 (Sec. 4);
+ *   - adaptive sampling on pairs of vertices (Algorithm 1, Sec. 6.1).
+ *
+ * Conventions for every entry point:
+ *   - All pointers are HOST pointers unless the name says "device". Arrays are
+ *     caller-owned; synchronous calls copy their inputs and have finished with
+ *     them on return.
+ *   - Vertices are int32 in [0, n). Graphs are undirected and unweighted, in
+ *     CSR form: row_ptr[n+1] (row_ptr[0] = 0, non-decreasing), col[nnz]; every
+ *     undirected edge appears in both rows.
+ *   - Errors are returned as negative bc_status codes; bc_last_error() gives a
+ *     message. No C++ exception crosses this boundary. A context serialises the
+ *     calls made on it (calls on one context from several threads are safe).
+ *   - Random draws come from Philox4x64-10 (Salmon et al., SC'11) keyed by
+ *     (seed, qid), counter (i, 0, 0, 0) for draw i = 0, 1, ...: a source is
+ *     floor(x0*n/2^64); an ordered pair of different vertices is
+ *     u = floor(x0*n/2^64), w = floor(x1*(n-1)/2^64), t = w + (w >= u).
+ *   - Arithmetic: sigma is an exact uint64 count (overflow is reported as
+ *     BC_E_SIGMA_OVERFLOW, never wrapped). Dependencies are IEEE doubles: the
+ *     successor sum of Theorem 1 and every sum of dependencies over sources are
+ *     exact sums rounded once to nearest-even, so results do not depend on the
+ *     order or batching of the work; all other double operations round once
+ *     (no fused multiply-add).
+ */
+#ifndef BC_GB300_H
+#define BC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t bc_status;
+
+#define BC_OK 0
+#define BC_PENDING 1               /* bc_poll: query still running */
+#define BC_E_INVALID (-1)          /* bad argument (NULL pointer, range, c < 1, ...) */
+#define BC_E_NOMEM (-2)            /* device or host allocation failed */
+#define BC_E_TOO_LARGE (-3)        /* n or nnz beyond int32 limits */
+#define BC_E_BAD_GRAPH (-4)        /* CSR failed validation (asymmetric, loop, duplicate, unsorted, out of range) */
+#define BC_E_DEVICE (-5)           /* CUDA error; the message names the call */
+#define BC_E_DEVICE_TIMEOUT (-6)   /* a bounded device-side wait ran out */
+#define BC_E_CANCELLED (-7)        /* query cancelled before it finished */
+#define BC_E_UNKNOWN_HANDLE (-8)   /* graph handle or ticket not known to this context */
+#define BC_E_SIGMA_OVERFLOW (-9)   /* a shortest-path count exceeded 2^64-1 */
+#define BC_E_RANGE (-10)           /* a dependency left the exact accumulator's range */
+
+/* per-target stop status of the adaptive estimators */
+#define BC_STOPPED 0               /* S exceeded c*n after k draws */
+#define BC_CAPPED 1                /* k reached cap before S exceeded c*n */
+
+/* graph load flags */
+#define BC_UNDIRECTED 1u           /* required: the CSR is an undirected adjacency */
+#define BC_VALIDATE 2u             /* check symmetry, sorted rows, no loops or duplicates */
+
+typedef struct bc_ctx bc_ctx;
+typedef int64_t bc_graph;          /* graph handle, valid in the context that made it */
+
+typedef struct bc_options {
+  int32_t batch_width;             /* sources per batched launch: 0 = auto, 1 = plain
+                                      single-source kernels, 32 or 64 = lane-batched */
+  int32_t reserved0;
+  void *stream;                    /* cudaStream_t to launch on; NULL = the context's own */
+} bc_options;
+
+/* ---------------------------------------------------------------- context -- */
+
+/* Creates a context on CUDA device `device`. opt may be NULL (defaults).
+ * On success *out owns device memory until bc_destroy. */
+bc_status bc_create(bc_ctx **out, int device, const bc_options *opt);
+
+/* Frees every graph, buffer and stream the context owns. NULL is ignored. */
+void bc_destroy(bc_ctx *ctx);
+
+/* Message of the last failed call on this context (library-owned string,
+ * valid until the next call). Never NULL. */
+const char *bc_last_error(bc_ctx *ctx);
+
+/* Changes the batch width (0 = auto, 1 = plain, 32, 64) for later calls. */
+bc_status bc_set_batch_width(bc_ctx *ctx, int32_t width);
+
+/* ------------------------------------------------------------------ graphs -- */
+
+/* Copies a CSR graph to the device and returns a handle. flags must contain
+ * BC_UNDIRECTED; with BC_VALIDATE the CSR is checked first (BC_E_BAD_GRAPH on
+ * failure). nnz = row_ptr[n] must be < 2^31 (BC_E_TOO_LARGE). n >= 1.
+ * The caller keeps ownership of row_ptr and col. */
+bc_status bc_graph_load_csr(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col,
+                            int64_t nnz, uint32_t flags, bc_graph *out);
+
+/* Releases a graph's device memory. */
+bc_status bc_graph_free(bc_ctx *ctx, bc_graph g);
+
+/* Reports n and nnz of a loaded graph (either pointer may be NULL). */
+bc_status bc_graph_info(bc_ctx *ctx, bc_graph g, int32_t *n, int64_t *nnz);
+
+/* ------------------------------------------------------- per-source step -- */
+
+/* The per-sample Brandes step for explicit sources (Sec. 3 steps 1-2; Def. 3
+ * predecessor sets; Theorem 1): for each sources[i] fills
+ *   delta_out[i*n + v] = delta_{s_i}(v)        (delta_s(s) = 0, unreachable 0)
+ *   dist_out[i*n + v]  = d(s_i, v) or -1       (may be NULL)
+ *   sigma_out[i*n + v] = sigma_{s_i v}         (may be NULL)
+ * count >= 0; every source in [0, n). */
+bc_status bc_source_dependencies(bc_ctx *ctx, bc_graph g, const int32_t *sources, int32_t count,
+                                 double *delta_out, int32_t *dist_out, uint64_t *sigma_out);
+
+/* ----------------------------------------------------------- estimators -- */
+
+/* Exact BC of every vertex (Eq. 4 summed over all n sources; Brandes' algorithm,
+ * Sec. 3). bc_out[n], ordered pairs (range [0, n^2]). */
+bc_status bc_exact(bc_ctx *ctx, bc_graph g, double *bc_out);
+
+/* Uniform k-source estimate of every vertex: est[v] = (n * S_v) / k with
+ * S_v = sum_{i<k} delta_{s_i}(v) over the first k source draws of (seed, qid)
+ * (the same per-sample step and source distribution as Sec. 4, without the
+ * adaptive stop). k >= 1; est_out[n]. */
+bc_status bc_uniform_sources(bc_ctx *ctx, bc_graph g, int64_t k, uint64_t seed, uint64_t qid,
+                             double *est_out);
+
+/* Bader's adaptive source sampling (Sec. 4 steps 1-3) for T distinct targets
+ * sharing one draw stream: per target, S <- S + delta_{s_i}(v) in draw order
+ * until S > c*n (BC_STOPPED) or k = cap (BC_CAPPED); est = (n*S)/k.
+ * c >= 1 (Sec. 4 footnote), cap >= 1, targets distinct and in [0, n).
+ * Outputs est[T], k[T], S[T], stop_status[T] (S and stop_status may be NULL). */
+bc_status bc_adaptive_sources(bc_ctx *ctx, bc_graph g, const int32_t *targets, int32_t T,
+                              double c, int64_t cap, uint64_t seed, uint64_t qid, double *est,
+                              int64_t *k, double *S, int32_t *stop_status);
+
+/* Adaptive pair sampling (Algorithm 1) for T distinct targets sharing one pair
+ * stream: per target, S <- S + sigma_st(v)/sigma_st for ordered pairs (s, t) of
+ * different vertices until S*threshold_scale > c*n (BC_STOPPED) or k = cap
+ * (BC_CAPPED); est = (n(n-1)*S)/k. sigma_st(v)/sigma_st is
+ * sigma_sv*sigma_vt/sigma_st when d(s,v)+d(v,t) = d(s,t) and v not in {s,t},
+ * else 0. threshold_scale = 1 is the paper's test; other values (> 0) rescale
+ * S only in the stop test. n >= 2, c >= 1, cap >= 1. */
+bc_status bc_adaptive_pairs(bc_ctx *ctx, bc_graph g, const int32_t *targets, int32_t T,
+                            double c, int64_t cap, uint64_t seed, uint64_t qid,
+                            double threshold_scale, double *est, int64_t *k, double *S,
+                            int32_t *stop_status);
+
+/* ------------------------------------------------------------ utilities -- */
+
+/* Source draws i0..i0+count-1 of (seed, qid) for n vertices, computed on the
+ * device (the same generator the estimators use). out[count]. */
+bc_status bc_draw_sources(bc_ctx *ctx, uint64_t seed, uint64_t qid, uint64_t i0, int64_t count,
+                          int32_t n, int32_t *out);
+
+/* Pair draws i0..i0+count-1 of (seed, qid): s_out[count], t_out[count]. */
+bc_status bc_draw_pairs(bc_ctx *ctx, uint64_t seed, uint64_t qid, uint64_t i0, int64_t count,
+                        int32_t n, int32_t *s_out, int32_t *t_out);
+
+/* Exact sum of count non-negative finite doubles on the device, rounded once to
+ * nearest-even (the summation the dependency step uses). Values must lie in
+ * [2^-76, 2^63) or be 0 (else BC_E_RANGE). */
+bc_status bc_exact_sum(bc_ctx *ctx, const double *x, int64_t count, double *out);
+
+/* Run statistics accumulated since the last reset. When profiling is on, each
+ * kernel family's launches are bracketed by CUDA events on the launch stream. */
+typedef struct bc_stats {
+  int64_t launches;                /* kernels launched by the library */
+  int64_t samples;                 /* per-source (or per-pair) BFS lanes processed */
+  int64_t batches;                 /* forward/backward launch sequences (batches) */
+  int64_t dag_edges;               /* (vertex, successor, lane) triples of the shortest-path DAGs */
+  int64_t reached;                 /* (vertex, lane) pairs reached at distance >= 1 */
+  int32_t n_kernels;               /* entries used in the arrays below */
+  int32_t reserved0;
+  char kernel_name[16][32];
+  int64_t kernel_launches[16];
+  double kernel_ms[16];            /* summed event time per kernel family (profiling on) */
+} bc_stats;
+
+bc_status bc_set_profiling(bc_ctx *ctx, int32_t on);
+bc_status bc_get_stats(bc_ctx *ctx, bc_stats *out);
+bc_status bc_reset_stats(bc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BC_GB300_H */

@@ -1,0 +1,315 @@
+"""ctypes binding of include/bc.h: argument marshalling and status checks only.
+
+Every function named ``bc_*`` here wraps the C entry point of the same name.
+Arrays are numpy; outputs are allocated here and returned. A negative status
+raises :class:`BCError` carrying the code and ``bc_last_error``'s message.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from types import SimpleNamespace
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libbcgb300.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_1608_04472_gb300.build` "
+        "(nvcc, sm_103a). There is no CPU fallback.")
+_lib = ctypes.CDLL(LIB_PATH)
+
+BC_OK = 0
+BC_STOPPED = 0
+BC_CAPPED = 1
+BC_UNDIRECTED = 1
+BC_VALIDATE = 2
+STATUS_NAMES = {
+    -1: "BC_E_INVALID", -2: "BC_E_NOMEM", -3: "BC_E_TOO_LARGE", -4: "BC_E_BAD_GRAPH",
+    -5: "BC_E_DEVICE", -6: "BC_E_DEVICE_TIMEOUT", -7: "BC_E_CANCELLED",
+    -8: "BC_E_UNKNOWN_HANDLE", -9: "BC_E_SIGMA_OVERFLOW", -10: "BC_E_RANGE",
+}
+
+_vp = ctypes.c_void_p
+_i32, _i64, _u32, _u64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+_i32p = ctypes.POINTER(_i32)
+_i64p = ctypes.POINTER(_i64)
+_u64p = ctypes.POINTER(_u64)
+_f64p = ctypes.POINTER(_f64)
+
+
+class bc_options(ctypes.Structure):
+    _fields_ = [("batch_width", _i32), ("reserved0", _i32), ("stream", _vp)]
+
+
+class bc_stats(ctypes.Structure):
+    _fields_ = [("launches", _i64), ("samples", _i64), ("batches", _i64), ("dag_edges", _i64),
+                ("reached", _i64),
+                ("n_kernels", _i32), ("reserved0", _i32), ("kernel_name", (ctypes.c_char * 32) * 16),
+                ("kernel_launches", _i64 * 16), ("kernel_ms", _f64 * 16)]
+
+
+_SIGS = {
+    "bc_create": (_i32, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(bc_options)]),
+    "bc_destroy": (None, [_vp]),
+    "bc_last_error": (ctypes.c_char_p, [_vp]),
+    "bc_set_batch_width": (_i32, [_vp, _i32]),
+    "bc_graph_load_csr": (_i32, [_vp, _i32, _i32p, _i32p, _i64, _u32, _i64p]),
+    "bc_graph_free": (_i32, [_vp, _i64]),
+    "bc_graph_info": (_i32, [_vp, _i64, _i32p, _i64p]),
+    "bc_source_dependencies": (_i32, [_vp, _i64, _i32p, _i32, _f64p, _i32p, _u64p]),
+    "bc_exact": (_i32, [_vp, _i64, _f64p]),
+    "bc_uniform_sources": (_i32, [_vp, _i64, _i64, _u64, _u64, _f64p]),
+    "bc_adaptive_sources": (_i32, [_vp, _i64, _i32p, _i32, _f64, _i64, _u64, _u64, _f64p, _i64p,
+                                   _f64p, _i32p]),
+    "bc_adaptive_pairs": (_i32, [_vp, _i64, _i32p, _i32, _f64, _i64, _u64, _u64, _f64, _f64p, _i64p,
+                                 _f64p, _i32p]),
+    "bc_draw_sources": (_i32, [_vp, _u64, _u64, _u64, _i64, _i32, _i32p]),
+    "bc_draw_pairs": (_i32, [_vp, _u64, _u64, _u64, _i64, _i32, _i32p, _i32p]),
+    "bc_exact_sum": (_i32, [_vp, _f64p, _i64, _f64p]),
+    "bc_set_profiling": (_i32, [_vp, _i32]),
+    "bc_get_stats": (_i32, [_vp, ctypes.POINTER(bc_stats)]),
+    "bc_reset_stats": (_i32, [_vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+class BCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ck(ctx, rc):
+    if rc < 0:
+        msg = _lib.bc_last_error(ctx)
+        raise BCError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _i32arr(x):
+    return np.ascontiguousarray(x, dtype=np.int32)
+
+
+# ------------------------------------------------------- same-name functions --
+
+def bc_create(device: int = 0, batch_width: int = 0, stream: int | None = None):
+    opt = bc_options(batch_width, 0, stream or None)
+    out = _vp()
+    rc = _lib.bc_create(ctypes.byref(out), device, ctypes.byref(opt))
+    if rc < 0:
+        raise BCError(rc, "bc_create failed (no CUDA device or bad option)")
+    return out
+
+
+def bc_destroy(ctx):
+    _lib.bc_destroy(ctx)
+
+
+def bc_last_error(ctx) -> str:
+    return _lib.bc_last_error(ctx).decode()
+
+
+def bc_set_batch_width(ctx, width: int):
+    _ck(ctx, _lib.bc_set_batch_width(ctx, width))
+
+
+def bc_graph_load_csr(ctx, row_ptr, col, flags: int = BC_UNDIRECTED) -> int:
+    rp = _i32arr(row_ptr)
+    cl = _i32arr(col)
+    n = rp.shape[0] - 1
+    cl_ = cl if cl.size else np.zeros(1, np.int32)
+    h = _i64()
+    _ck(ctx, _lib.bc_graph_load_csr(ctx, n, _p(rp, _i32p), _p(cl_, _i32p), int(cl.size), flags,
+                                    ctypes.byref(h)))
+    return int(h.value)
+
+
+def bc_graph_free(ctx, g: int):
+    _ck(ctx, _lib.bc_graph_free(ctx, g))
+
+
+def bc_graph_info(ctx, g: int):
+    n, nnz = _i32(), _i64()
+    _ck(ctx, _lib.bc_graph_info(ctx, g, ctypes.byref(n), ctypes.byref(nnz)))
+    return int(n.value), int(nnz.value)
+
+
+def bc_source_dependencies(ctx, g: int, sources, want_dist: bool = False, want_sigma: bool = False):
+    n, _ = bc_graph_info(ctx, g)
+    src = _i32arr(sources)
+    cnt = src.size
+    delta = np.zeros((cnt, n), np.float64)
+    dist = np.zeros((cnt, n), np.int32) if want_dist else None
+    sigma = np.zeros((cnt, n), np.uint64) if want_sigma else None
+    srcp = src if cnt else np.zeros(1, np.int32)
+    _ck(ctx, _lib.bc_source_dependencies(
+        ctx, g, _p(srcp, _i32p), cnt, _p(delta, _f64p) if cnt else None,
+        _p(dist, _i32p) if dist is not None and cnt else None,
+        _p(sigma, _u64p) if sigma is not None and cnt else None))
+    return delta, dist, sigma
+
+
+def bc_exact(ctx, g: int) -> np.ndarray:
+    n, _ = bc_graph_info(ctx, g)
+    out = np.empty(n, np.float64)
+    _ck(ctx, _lib.bc_exact(ctx, g, _p(out, _f64p)))
+    return out
+
+
+def bc_uniform_sources(ctx, g: int, k: int, seed: int, qid: int) -> np.ndarray:
+    n, _ = bc_graph_info(ctx, g)
+    out = np.empty(n, np.float64)
+    _ck(ctx, _lib.bc_uniform_sources(ctx, g, k, seed, qid, _p(out, _f64p)))
+    return out
+
+
+def _target_outputs(T):
+    return (np.zeros(max(T, 1), np.float64), np.zeros(max(T, 1), np.int64),
+            np.zeros(max(T, 1), np.float64), np.zeros(max(T, 1), np.int32))
+
+
+def bc_adaptive_sources(ctx, g: int, targets, c: float, cap: int, seed: int, qid: int):
+    tg = _i32arr(targets)
+    T = tg.size
+    est, k, S, st = _target_outputs(T)
+    tgp = tg if T else np.zeros(1, np.int32)
+    _ck(ctx, _lib.bc_adaptive_sources(ctx, g, _p(tgp, _i32p), T, c, cap, seed, qid, _p(est, _f64p),
+                                      _p(k, _i64p), _p(S, _f64p), _p(st, _i32p)))
+    return dict(est=est[:T], k=k[:T], S=S[:T], status=st[:T])
+
+
+def bc_adaptive_pairs(ctx, g: int, targets, c: float, cap: int, seed: int, qid: int,
+                      threshold_scale: float = 1.0):
+    tg = _i32arr(targets)
+    T = tg.size
+    est, k, S, st = _target_outputs(T)
+    tgp = tg if T else np.zeros(1, np.int32)
+    _ck(ctx, _lib.bc_adaptive_pairs(ctx, g, _p(tgp, _i32p), T, c, cap, seed, qid, threshold_scale,
+                                    _p(est, _f64p), _p(k, _i64p), _p(S, _f64p), _p(st, _i32p)))
+    return dict(est=est[:T], k=k[:T], S=S[:T], status=st[:T])
+
+
+def bc_draw_sources(ctx, seed: int, qid: int, i0: int, count: int, n: int) -> np.ndarray:
+    out = np.zeros(max(count, 1), np.int32)
+    _ck(ctx, _lib.bc_draw_sources(ctx, seed, qid, i0, count, n, _p(out, _i32p)))
+    return out[:count]
+
+
+def bc_draw_pairs(ctx, seed: int, qid: int, i0: int, count: int, n: int):
+    s = np.zeros(max(count, 1), np.int32)
+    t = np.zeros(max(count, 1), np.int32)
+    _ck(ctx, _lib.bc_draw_pairs(ctx, seed, qid, i0, count, n, _p(s, _i32p), _p(t, _i32p)))
+    return s[:count], t[:count]
+
+
+def bc_exact_sum(ctx, x) -> float:
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    out = _f64()
+    ap = a if a.size else np.zeros(1, np.float64)
+    _ck(ctx, _lib.bc_exact_sum(ctx, _p(ap, _f64p), a.size, ctypes.byref(out)))
+    return float(out.value)
+
+
+def bc_set_profiling(ctx, on: bool):
+    _ck(ctx, _lib.bc_set_profiling(ctx, 1 if on else 0))
+
+
+def bc_get_stats(ctx) -> dict:
+    s = bc_stats()
+    _ck(ctx, _lib.bc_get_stats(ctx, ctypes.byref(s)))
+    kern = {}
+    for i in range(s.n_kernels):
+        name = bytes(s.kernel_name[i]).split(b"\0", 1)[0].decode()
+        kern[name] = dict(launches=int(s.kernel_launches[i]), ms=float(s.kernel_ms[i]))
+    return dict(launches=int(s.launches), samples=int(s.samples), batches=int(s.batches),
+                dag_edges=int(s.dag_edges), reached=int(s.reached), kernels=kern)
+
+
+def bc_reset_stats(ctx):
+    _ck(ctx, _lib.bc_reset_stats(ctx))
+
+
+capi = SimpleNamespace(**{name: globals()[name] for name in _SIGS})
+
+
+# ------------------------------------------------------------ object wrapper --
+
+class Context:
+    """Owns one bc_ctx (one CUDA device) and the graphs loaded into it."""
+
+    def __init__(self, device: int = 0, batch_width: int = 0, stream: int | None = None):
+        self.ptr = bc_create(device, batch_width, stream)
+        self.graphs: set[int] = set()
+
+    def close(self):
+        if self.ptr:
+            bc_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_graph(self, row_ptr, col, validate: bool = False) -> int:
+        flags = BC_UNDIRECTED | (BC_VALIDATE if validate else 0)
+        h = bc_graph_load_csr(self.ptr, row_ptr, col, flags)
+        self.graphs.add(h)
+        return h
+
+    def free_graph(self, g: int):
+        bc_graph_free(self.ptr, g)
+        self.graphs.discard(g)
+
+    def set_batch_width(self, w: int):
+        bc_set_batch_width(self.ptr, w)
+
+    def source_dependencies(self, g, sources, want_dist=False, want_sigma=False):
+        return bc_source_dependencies(self.ptr, g, sources, want_dist, want_sigma)
+
+    def exact(self, g):
+        return bc_exact(self.ptr, g)
+
+    def uniform_sources(self, g, k, seed, qid):
+        return bc_uniform_sources(self.ptr, g, k, seed, qid)
+
+    def adaptive_sources(self, g, targets, c, cap, seed, qid):
+        return bc_adaptive_sources(self.ptr, g, targets, c, cap, seed, qid)
+
+    def adaptive_pairs(self, g, targets, c, cap, seed, qid, threshold_scale=1.0):
+        return bc_adaptive_pairs(self.ptr, g, targets, c, cap, seed, qid, threshold_scale)
+
+    def draw_sources(self, seed, qid, i0, count, n):
+        return bc_draw_sources(self.ptr, seed, qid, i0, count, n)
+
+    def draw_pairs(self, seed, qid, i0, count, n):
+        return bc_draw_pairs(self.ptr, seed, qid, i0, count, n)
+
+    def exact_sum(self, x):
+        return bc_exact_sum(self.ptr, x)
+
+    def set_profiling(self, on: bool):
+        bc_set_profiling(self.ptr, on)
+
+    def stats(self):
+        return bc_get_stats(self.ptr)
+
+    def reset_stats(self):
+        bc_reset_stats(self.ptr)

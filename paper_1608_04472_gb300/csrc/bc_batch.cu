@@ -1,0 +1,621 @@
+// bc_batch.cu -- lane-batched Brandes step: 64 sampled sources share one
+// level-synchronous traversal of the CSR.
+//
+// Layout (n vertices, 64 lanes, lane t = one sampled source):
+//   lm[l][v]    u64  bit t set iff d(s_t, v) = l            (level masks)
+//   visited[v]  u64  OR of lm[0..l][v]
+//   sigma[v][t] u64  sigma_{s_t v}; in the backward pass the slot of (v, t)
+//                    is overwritten by coef = (1+delta)/sigma (double bits)
+//                    once v's level in lane t is done. Lane-minor rows of 512 B,
+//                    so one warp reads a neighbour's 32 lanes with one request.
+//
+// Forward level l (Sec. 3 step 1, predecessor sets of Def. 3): every vertex v
+// with lanes still unvisited pulls from its CSR neighbours w:
+//   new(v)       = OR_w lm[l-1][w] & ~visited[v]
+//   sigma[v][t]  = sum over w with t in lm[l-1][w] of sigma[w][t]   (t in new)
+// Backward level l (Sec. 3 step 2, Theorem 1): every vertex v with lanes at
+// level l pulls coefficients from its successors (neighbours one level deeper
+// in the same lane), summing them exactly:
+//   delta[v][t] = RN(sigma[v][t] * RN(sum_w coef[w][t]))
+//   coef[v][t]  = RN(RN(1 + delta[v][t]) / sigma[v][t]).
+// Vertices of degree > HEAVY are split into SEG-long neighbour segments, each
+// handled by one warp; partial results are combined exactly afterwards.
+#include <algorithm>
+
+#include "bc_internal.h"
+
+namespace bcg {
+
+constexpr int HEAVY = 2048;
+constexpr int SEG = 2048;
+constexpr int FWD_THREADS = 256;
+
+__device__ __forceinline__ uint64_t warp_or64(uint64_t x) {
+  const unsigned lo = __reduce_or_sync(FULL, (unsigned)x);
+  const unsigned hi = __reduce_or_sync(FULL, (unsigned)(x >> 32));
+  return ((uint64_t)hi << 32) | lo;
+}
+
+__device__ __forceinline__ void block_or_to(uint64_t x, uint64_t *dst) {
+  __shared__ unsigned long long s_or;
+  if (threadIdx.x == 0) s_or = 0ull;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0 && x) atomicOr(&s_or, (unsigned long long)x);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_or) atomicOr((unsigned long long *)dst, s_or);
+}
+
+// ------------------------------------------------------------------ init --
+__global__ void k_batch_init(int count, const int32_t *__restrict__ sources,
+                             uint64_t *__restrict__ lm0, uint64_t *__restrict__ visited,
+                             uint64_t *__restrict__ sigma, uint64_t *__restrict__ active0,
+                             uint64_t *__restrict__ enable, int32_t *__restrict__ pair_d,
+                             uint64_t *__restrict__ pair_sig) {
+  const int t = threadIdx.x;
+  if (t < 64) {
+    pair_d[t] = -1;
+    pair_sig[t] = 0ull;
+  }
+  if (t == 0) *enable = (count >= 64) ? ~0ull : ((1ull << count) - 1ull);
+  __syncthreads();
+  if (t < count) {
+    const int32_t s = sources[t];
+    const uint64_t bit = 1ull << t;
+    atomicOr((unsigned long long *)&lm0[s], (unsigned long long)bit);
+    atomicOr((unsigned long long *)&visited[s], (unsigned long long)bit);
+    sigma[(size_t)s * 64 + t] = 1ull;
+    atomicOr((unsigned long long *)active0, (unsigned long long)bit);
+  }
+}
+
+// Zero sigma rows of heavy vertices (their lanes are filled with atomics).
+__global__ void k_zero_heavy_rows(int nh, const int32_t *__restrict__ heavy, uint64_t *__restrict__ sigma) {
+  const int h = blockIdx.x;
+  if (h < nh && threadIdx.x < 64) sigma[(size_t)heavy[h] * 64 + threadIdx.x] = 0ull;
+}
+
+// --------------------------------------------------------------- forward --
+// One warp per vertex (grid-stride); heavy vertices only get lm_cur[v] = 0 here.
+__global__ void __launch_bounds__(FWD_THREADS)
+k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+            const uint64_t *__restrict__ lm_prev, uint64_t *__restrict__ lm_cur,
+            uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
+            const uint64_t *__restrict__ active_prev, const uint64_t *__restrict__ enable,
+            uint64_t *__restrict__ active_cur, unsigned *__restrict__ err,
+            unsigned long long *__restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint64_t act = *active_prev & *enable;
+  uint64_t any_new = 0ull;
+  unsigned long long tri = 0ull, rch = 0ull;
+  unsigned e = 0u;
+  for (int v = warp; v < n; v += nwarps) {
+    const int beg = rp[v], end = rp[v + 1];
+    const uint64_t vis = visited[v];
+    const uint64_t pend = ~vis & act;
+    uint64_t newm = 0ull;
+    if (pend && end - beg <= HEAVY) {
+      uint64_t s0 = 0ull, s1 = 0ull;
+      for (int base = beg; base < end; base += 32) {
+        const int j = base + lane;
+        int32_t w = 0;
+        uint64_t m = 0ull;
+        if (j < end) {
+          w = col[j];
+          m = lm_prev[w] & pend;
+        }
+        newm |= m;
+        unsigned bal = __ballot_sync(FULL, m != 0ull);
+        while (bal) {
+          const int src = __ffs(bal) - 1;
+          bal &= bal - 1u;
+          const uint64_t mj = __shfl_sync(FULL, m, src);
+          const int32_t wj = __shfl_sync(FULL, w, src);
+          tri += (unsigned long long)__popcll((long long)mj);
+          const uint64_t *row = sigma + (size_t)wj * 64;
+          if ((mj >> lane) & 1ull) {
+            const uint64_t x = row[lane];
+            const uint64_t t = s0 + x;
+            if (t < s0) e |= ERR_SIGMA_OVERFLOW;
+            s0 = t;
+          }
+          if ((mj >> (lane + 32)) & 1ull) {
+            const uint64_t x = row[lane + 32];
+            const uint64_t t = s1 + x;
+            if (t < s1) e |= ERR_SIGMA_OVERFLOW;
+            s1 = t;
+          }
+        }
+      }
+      newm = warp_or64(newm);
+      if ((newm >> lane) & 1ull) sigma[(size_t)v * 64 + lane] = s0;
+      if ((newm >> (lane + 32)) & 1ull) sigma[(size_t)v * 64 + 32 + lane] = s1;
+    }
+    if (lane == 0) {
+      lm_cur[v] = newm;
+      if (newm) visited[v] = vis | newm;
+    }
+    rch += (unsigned long long)__popcll((long long)newm);
+    any_new |= newm;
+  }
+  if (e) atomicOr(err, e);
+  if (lane == 0 && (tri | rch)) {
+    atomicAdd(cnt, tri);
+    atomicAdd(cnt + 1, rch);
+  }
+  block_or_to(any_new, active_cur);
+}
+
+// One warp per segment of a heavy vertex: partial sigma sums via atomics.
+__global__ void __launch_bounds__(FWD_THREADS)
+k_fwd_heavy(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restrict__ seg_b,
+            const int32_t *__restrict__ seg_e, const int32_t *__restrict__ col,
+            const uint64_t *__restrict__ lm_prev, uint64_t *__restrict__ lm_cur,
+            const uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
+            const uint64_t *__restrict__ active_prev, const uint64_t *__restrict__ enable,
+            unsigned *__restrict__ err, unsigned long long *__restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint64_t act = *active_prev & *enable;
+  unsigned long long tri = 0ull;
+  unsigned e = 0u;
+  for (int s = warp; s < nseg; s += nwarps) {
+    const int32_t v = seg_v[s];
+    const int beg = seg_b[s], end = seg_e[s];
+    const uint64_t pend = ~visited[v] & act;
+    if (!pend) continue;
+    uint64_t newm = 0ull, s0 = 0ull, s1 = 0ull;
+    for (int base = beg; base < end; base += 32) {
+      const int j = base + lane;
+      int32_t w = 0;
+      uint64_t m = 0ull;
+      if (j < end) {
+        w = col[j];
+        m = lm_prev[w] & pend;
+      }
+      newm |= m;
+      unsigned bal = __ballot_sync(FULL, m != 0ull);
+      while (bal) {
+        const int src = __ffs(bal) - 1;
+        bal &= bal - 1u;
+        const uint64_t mj = __shfl_sync(FULL, m, src);
+        const int32_t wj = __shfl_sync(FULL, w, src);
+        tri += (unsigned long long)__popcll((long long)mj);
+        const uint64_t *row = sigma + (size_t)wj * 64;
+        if ((mj >> lane) & 1ull) {
+          const uint64_t t = s0 + row[lane];
+          if (t < s0) e |= ERR_SIGMA_OVERFLOW;
+          s0 = t;
+        }
+        if ((mj >> (lane + 32)) & 1ull) {
+          const uint64_t t = s1 + row[lane + 32];
+          if (t < s1) e |= ERR_SIGMA_OVERFLOW;
+          s1 = t;
+        }
+      }
+    }
+    newm = warp_or64(newm);
+    if (!newm) continue;
+    unsigned long long *dst = (unsigned long long *)(sigma + (size_t)v * 64);
+    if ((newm >> lane) & 1ull) {
+      const unsigned long long old = atomicAdd(dst + lane, (unsigned long long)s0);
+      if (old + s0 < old) e |= ERR_SIGMA_OVERFLOW;
+    }
+    if ((newm >> (lane + 32)) & 1ull) {
+      const unsigned long long old = atomicAdd(dst + 32 + lane, (unsigned long long)s1);
+      if (old + s1 < old) e |= ERR_SIGMA_OVERFLOW;
+    }
+    if (lane == 0) atomicOr((unsigned long long *)&lm_cur[v], (unsigned long long)newm);
+  }
+  if (e) atomicOr(err, e);
+  if (lane == 0 && tri) atomicAdd(cnt, tri);
+}
+
+__global__ void k_fwd_heavy_fin(int nh, const int32_t *__restrict__ heavy,
+                                const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ visited,
+                                uint64_t *__restrict__ active_cur, unsigned long long *__restrict__ cnt) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t newm = 0ull;
+  if (h < nh) {
+    const int32_t v = heavy[h];
+    newm = lm_cur[v];
+    if (newm) {
+      visited[v] |= newm;
+      atomicAdd(cnt + 1, (unsigned long long)__popcll((long long)newm));
+    }
+  }
+  newm = warp_or64(newm);
+  if ((threadIdx.x & 31) == 0 && newm) atomicOr((unsigned long long *)active_cur, (unsigned long long)newm);
+}
+
+// Pair lanes: lane i is finished once its destination appears at this level.
+__global__ void k_pair_check(int count, int level, const int32_t *__restrict__ dest,
+                             const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ sigma,
+                             uint64_t *__restrict__ enable, int32_t *__restrict__ pair_d,
+                             uint64_t *__restrict__ pair_sig, const uint64_t *__restrict__ active_cur,
+                             uint64_t *__restrict__ cont) {
+  const int i = threadIdx.x;
+  const uint64_t en = *enable;
+  bool done = false;
+  if (i < count && ((en >> i) & 1ull)) {
+    const int32_t t = dest[i];
+    if ((lm_cur[t] >> i) & 1ull) {
+      pair_d[i] = level;
+      pair_sig[i] = sigma[(size_t)t * 64 + i];
+      done = true;
+    }
+  }
+  const unsigned b0 = __ballot_sync(FULL, done);  // block = 2 full warps
+  __shared__ unsigned long long s_done;
+  if (i == 0) s_done = 0ull;
+  __syncthreads();
+  if ((i & 31) == 0) atomicOr(&s_done, ((unsigned long long)b0) << (i & 32));
+  __syncthreads();
+  if (i == 0) {
+    const uint64_t en2 = en & ~(uint64_t)s_done;
+    *enable = en2;
+    *cont = *active_cur & en2;
+  }
+}
+
+// -------------------------------------------------------------- backward --
+// Finalises lanes of v at this level from per-lane exact sums, writes coef over
+// sigma and the requested outputs. Called by a full warp; lane handles t, t+32.
+__device__ __forceinline__ void bwd_finalize(int32_t v, uint64_t lanes, const Acc &a0, const Acc &a1,
+                                             uint64_t *__restrict__ sigma, const Sink &sink, unsigned &e) {
+  const int lane = threadIdx.x & 31;
+  double d0 = 0.0, d1 = 0.0;
+  uint64_t *row = sigma + (size_t)v * 64;
+  if ((lanes >> lane) & 1ull) {
+    const uint64_t sg = row[lane];
+    d0 = __dmul_rn(sigma_to_double(sg), acc_round(a0));
+    row[lane] = (uint64_t)__double_as_longlong(coef_of(d0, sg));
+  }
+  if ((lanes >> (lane + 32)) & 1ull) {
+    const uint64_t sg = row[lane + 32];
+    d1 = __dmul_rn(sigma_to_double(sg), acc_round(a1));
+    row[lane + 32] = (uint64_t)__double_as_longlong(coef_of(d1, sg));
+  }
+  if (sink.delta_lm) {
+    if ((lanes >> lane) & 1ull) sink.delta_lm[(size_t)v * 64 + lane] = d0;
+    if ((lanes >> (lane + 32)) & 1ull) sink.delta_lm[(size_t)v * 64 + 32 + lane] = d1;
+  }
+  if (sink.tslot) {
+    const int32_t slot = sink.tslot[v];
+    if (slot >= 0) {
+      if ((lanes >> lane) & 1ull) sink.tdelta[(size_t)slot * 64 + lane] = d0;
+      if ((lanes >> (lane + 32)) & 1ull) sink.tdelta[(size_t)slot * 64 + 32 + lane] = d1;
+    }
+  }
+  if (sink.acc) {
+    Acc t = acc_zero();
+    acc_add(t, d0, e);
+    acc_add(t, d1, e);
+    t = acc_warp_sum(t);
+    if (lane == 0) {
+      Acc cur = sink.acc[v];
+      acc_add_acc(cur, t);
+      sink.acc[v] = cur;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(FWD_THREADS)
+k_bwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+            const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
+            uint64_t *__restrict__ sigma, Sink sink, unsigned *__restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned e = 0u;
+  for (int v = warp; v < n; v += nwarps) {
+    const uint64_t lanes = lm_cur[v];
+    if (!lanes) continue;
+    const int beg = rp[v], end = rp[v + 1];
+    if (end - beg > HEAVY) continue;
+    Acc a0 = acc_zero(), a1 = acc_zero();
+    for (int base = beg; base < end; base += 32) {
+      const int j = base + lane;
+      int32_t w = 0;
+      uint64_t m = 0ull;
+      if (j < end) {
+        w = col[j];
+        m = lm_next[w] & lanes;
+      }
+      unsigned bal = __ballot_sync(FULL, m != 0ull);
+      while (bal) {
+        const int src = __ffs(bal) - 1;
+        bal &= bal - 1u;
+        const uint64_t mj = __shfl_sync(FULL, m, src);
+        const int32_t wj = __shfl_sync(FULL, w, src);
+        const uint64_t *row = sigma + (size_t)wj * 64;
+        if ((mj >> lane) & 1ull) acc_add(a0, __longlong_as_double((long long)row[lane]), e);
+        if ((mj >> (lane + 32)) & 1ull) acc_add(a1, __longlong_as_double((long long)row[lane + 32]), e);
+      }
+    }
+    bwd_finalize(v, lanes, a0, a1, sigma, sink, e);
+  }
+  if (e) atomicOr(err, e);
+}
+
+// Heavy vertices: one warp per segment writes 64 partial sums to part[s][64].
+__global__ void __launch_bounds__(FWD_THREADS)
+k_bwd_heavy_seg(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restrict__ seg_b,
+                const int32_t *__restrict__ seg_e, const int32_t *__restrict__ col,
+                const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
+                const uint64_t *__restrict__ sigma, Acc *__restrict__ part, unsigned *__restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned e = 0u;
+  for (int s = warp; s < nseg; s += nwarps) {
+    const int32_t v = seg_v[s];
+    const uint64_t lanes = lm_cur[v];
+    if (!lanes) continue;
+    const int beg = seg_b[s], end = seg_e[s];
+    Acc a0 = acc_zero(), a1 = acc_zero();
+    for (int base = beg; base < end; base += 32) {
+      const int j = base + lane;
+      int32_t w = 0;
+      uint64_t m = 0ull;
+      if (j < end) {
+        w = col[j];
+        m = lm_next[w] & lanes;
+      }
+      unsigned bal = __ballot_sync(FULL, m != 0ull);
+      while (bal) {
+        const int src = __ffs(bal) - 1;
+        bal &= bal - 1u;
+        const uint64_t mj = __shfl_sync(FULL, m, src);
+        const int32_t wj = __shfl_sync(FULL, w, src);
+        const uint64_t *row = sigma + (size_t)wj * 64;
+        if ((mj >> lane) & 1ull) acc_add(a0, __longlong_as_double((long long)row[lane]), e);
+        if ((mj >> (lane + 32)) & 1ull) acc_add(a1, __longlong_as_double((long long)row[lane + 32]), e);
+      }
+    }
+    part[(size_t)s * 64 + lane] = a0;
+    part[(size_t)s * 64 + 32 + lane] = a1;
+  }
+  if (e) atomicOr(err, e);
+}
+
+__global__ void __launch_bounds__(FWD_THREADS)
+k_bwd_heavy_fin(int nh, const int32_t *__restrict__ heavy, const int32_t *__restrict__ hseg0,
+                const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ sigma,
+                const Acc *__restrict__ part, Sink sink, unsigned *__restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  unsigned e = 0u;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int h = warp; h < nh; h += nwarps) {
+    const int32_t v = heavy[h];
+    const uint64_t lanes = lm_cur[v];
+    if (!lanes) continue;
+    Acc a0 = acc_zero(), a1 = acc_zero();
+    for (int s = hseg0[h]; s < hseg0[h + 1]; ++s) {
+      acc_add_acc(a0, part[(size_t)s * 64 + lane]);
+      acc_add_acc(a1, part[(size_t)s * 64 + 32 + lane]);
+    }
+    bwd_finalize(v, lanes, a0, a1, sigma, sink, e);
+  }
+  if (e) atomicOr(err, e);
+}
+
+// Per-lane distance / sigma extraction after a forward pass.
+__global__ void k_extract(int32_t n, int count, int maxlevel, const uint64_t *__restrict__ lm,
+                          const uint64_t *__restrict__ sigma, int32_t *__restrict__ dist,
+                          uint64_t *__restrict__ sig_out, int64_t row_stride, int64_t lane_stride) {
+  const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  uint64_t seen = 0ull;
+  for (int l = 0; l <= maxlevel; ++l) {
+    uint64_t m = lm[(size_t)l * n + v];
+    seen |= m;
+    while (m) {
+      const int t = __ffsll((long long)m) - 1;
+      m &= m - 1ull;
+      if (t < count) {
+        if (dist) dist[(int64_t)t * lane_stride + (int64_t)v * row_stride] = l;
+        if (sig_out) sig_out[(int64_t)t * lane_stride + (int64_t)v * row_stride] = sigma[(size_t)v * 64 + t];
+      }
+    }
+  }
+  for (int t = 0; t < count; ++t) {
+    if (!((seen >> t) & 1ull)) {
+      if (dist) dist[(int64_t)t * lane_stride + (int64_t)v * row_stride] = -1;
+      if (sig_out) sig_out[(int64_t)t * lane_stride + (int64_t)v * row_stride] = 0ull;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host --
+struct HeavyMeta {
+  int nh = 0, nseg = 0;
+  DevBuf heavy, hseg0, seg_v, seg_b, seg_e, part;
+};
+static std::map<const int32_t *, HeavyMeta> g_heavy;  // keyed by the graph's device col pointer
+static std::mutex g_heavy_mu;
+
+static HeavyMeta &heavy_meta(bc_ctx *ctx, const Graph &g) {
+  std::lock_guard<std::mutex> lk(g_heavy_mu);
+  auto it = g_heavy.find(g.rp);
+  if (it != g_heavy.end()) return it->second;
+  HeavyMeta &hm = g_heavy[g.rp];
+  std::vector<int32_t> rp(g.n + 1);
+  BCG_CUDA(cudaMemcpy(rp.data(), g.rp, sizeof(int32_t) * (g.n + 1), cudaMemcpyDeviceToHost));
+  std::vector<int32_t> heavy, hseg0, sv, sb, se;
+  for (int32_t v = 0; v < g.n; ++v) {
+    const int d = rp[v + 1] - rp[v];
+    if (d <= HEAVY) continue;
+    hseg0.push_back((int32_t)sv.size());
+    heavy.push_back(v);
+    for (int b = rp[v]; b < rp[v + 1]; b += SEG) {
+      sv.push_back(v);
+      sb.push_back(b);
+      se.push_back(std::min(b + SEG, rp[v + 1]));
+    }
+  }
+  hseg0.push_back((int32_t)sv.size());
+  hm.nh = (int)heavy.size();
+  hm.nseg = (int)sv.size();
+  auto up = [&](DevBuf &b, const std::vector<int32_t> &x) {
+    b.ensure(std::max<size_t>(x.size(), 1) * sizeof(int32_t));
+    if (!x.empty()) BCG_CUDA(cudaMemcpy(b.p, x.data(), x.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  };
+  up(hm.heavy, heavy);
+  up(hm.hseg0, hseg0);
+  up(hm.seg_v, sv);
+  up(hm.seg_b, sb);
+  up(hm.seg_e, se);
+  hm.part.ensure(std::max<size_t>(hm.nseg, 1) * 64 * sizeof(Acc));
+  (void)ctx;
+  return hm;
+}
+
+void forget_heavy_meta(const int32_t *rp) {
+  std::lock_guard<std::mutex> lk(g_heavy_mu);
+  auto it = g_heavy.find(rp);
+  if (it == g_heavy.end()) return;
+  HeavyMeta &hm = it->second;
+  hm.heavy.release(); hm.hseg0.release(); hm.seg_v.release(); hm.seg_b.release();
+  hm.seg_e.release(); hm.part.release();
+  g_heavy.erase(it);
+}
+
+static int g_num_sms = 0;
+static int grid_blocks() {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 148;
+  }
+  return g_num_sms * 8;
+}
+
+void batch_ensure(bc_ctx *ctx, const Graph &g) {
+  Workspace &ws = ctx->ws;
+  const size_t n = (size_t)g.n;
+  if (ws.lcap < 16 || ws.lm.bytes < (size_t)ws.lcap * n * 8) {
+    ws.lcap = std::max(ws.lcap, 16);
+    ws.lm.ensure((size_t)ws.lcap * n * 8);
+  }
+  ws.visited.ensure(n * 8);
+  ws.sigma.ensure(n * 64 * 8);
+  ws.active.ensure((size_t)(ws.lcap + 2) * 8);
+  heavy_meta(ctx, g);
+}
+
+static uint64_t read_u64(bc_ctx *ctx, const uint64_t *dptr) {
+  uint64_t *h = static_cast<uint64_t *>(ctx->ws.pinned);
+  BCG_CUDA(cudaMemcpyAsync(h, dptr, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  BCG_CUDA(cudaStreamSynchronize(ctx->stream));
+  return *h;
+}
+
+int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs) {
+  Workspace &ws = ctx->ws;
+  batch_ensure(ctx, g);
+  HeavyMeta &hm = heavy_meta(ctx, g);
+  const size_t n = (size_t)g.n;
+  cudaStream_t st = ctx->stream;
+  BCG_CUDA(cudaMemsetAsync(ws.lm.p, 0, n * 8, st));
+  BCG_CUDA(cudaMemsetAsync(ws.visited.p, 0, n * 8, st));
+  BCG_CUDA(cudaMemsetAsync(ws.active.p, 0, (size_t)(ws.lcap + 2) * 8, st));
+  {
+    LaunchScope ls(ctx, F_INIT);
+    if (hm.nh) k_zero_heavy_rows<<<hm.nh, 64, 0, st>>>(hm.nh, hm.heavy.as<int32_t>(), ws.sigma.as<uint64_t>());
+  }
+  {
+    LaunchScope ls(ctx, F_INIT);
+    k_batch_init<<<1, 64, 0, st>>>(count, ws.sources.as<int32_t>(), ws.lm.as<uint64_t>(),
+                                   ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
+                                   ws.active.as<uint64_t>(), ws.enable.as<uint64_t>(),
+                                   ws.pair_d.as<int32_t>(), ws.pair_sig.as<uint64_t>());
+  }
+  ctx->samples += count;
+  ctx->batches += 1;
+  const int blocks = grid_blocks();
+  int l = 0;
+  for (;;) {
+    if (l + 2 >= ws.lcap) {
+      const int ncap = ws.lcap * 2;
+      ws.lm.grow_keep((size_t)ncap * n * 8, st);
+      ws.active.grow_keep((size_t)(ncap + 2) * 8, st);
+      BCG_CUDA(cudaMemsetAsync(ws.active.as<uint64_t>() + ws.lcap + 2, 0, (size_t)(ncap - ws.lcap) * 8, st));
+      ws.lcap = ncap;
+    }
+    uint64_t *lm = ws.lm.as<uint64_t>();
+    uint64_t *act = ws.active.as<uint64_t>();
+    {
+      LaunchScope ls(ctx, F_FWD);
+      k_fwd_light<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
+                                                 ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(), act + l,
+                                                 ws.enable.as<uint64_t>(), act + l + 1, ws.err.as<unsigned>(),
+                                                 ws.cnt.as<unsigned long long>());
+    }
+    if (hm.nseg) {
+      LaunchScope ls(ctx, F_FWD);
+      k_fwd_heavy<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
+          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
+          lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
+          act + l, ws.enable.as<uint64_t>(), ws.err.as<unsigned>(), ws.cnt.as<unsigned long long>());
+    }
+    if (hm.nseg) {
+      LaunchScope ls(ctx, F_FWD);
+      k_fwd_heavy_fin<<<(hm.nh + 255) / 256, 256, 0, st>>>(hm.nh, hm.heavy.as<int32_t>(), lm + (size_t)(l + 1) * n,
+                                                          ws.visited.as<uint64_t>(), act + l + 1,
+                                                          ws.cnt.as<unsigned long long>());
+    }
+    uint64_t cont;
+    if (pairs) {
+      LaunchScope ls(ctx, F_PAIR);
+      k_pair_check<<<1, 64, 0, st>>>(count, l + 1, ws.targets.as<int32_t>(), lm + (size_t)(l + 1) * n,
+                                     ws.sigma.as<uint64_t>(), ws.enable.as<uint64_t>(), ws.pair_d.as<int32_t>(),
+                                     ws.pair_sig.as<uint64_t>(), act + l + 1, ws.enable.as<uint64_t>() + 1);
+      cont = read_u64(ctx, ws.enable.as<uint64_t>() + 1);
+    } else {
+      cont = read_u64(ctx, act + l + 1);
+    }
+    if (!cont) return l;
+    ++l;
+  }
+}
+
+void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink) {
+  Workspace &ws = ctx->ws;
+  HeavyMeta &hm = heavy_meta(ctx, g);
+  const size_t n = (size_t)g.n;
+  cudaStream_t st = ctx->stream;
+  const int blocks = grid_blocks();
+  uint64_t *lm = ws.lm.as<uint64_t>();
+  for (int l = maxlevel; l >= 1; --l) {
+    {
+      LaunchScope ls(ctx, F_BWD);
+      k_bwd_light<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
+                                                 ws.sigma.as<uint64_t>(), sink, ws.err.as<unsigned>());
+    }
+    if (hm.nseg) {
+      LaunchScope ls(ctx, F_BWD);
+      k_bwd_heavy_seg<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
+          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
+          lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), hm.part.as<Acc>(),
+          ws.err.as<unsigned>());
+      k_bwd_heavy_fin<<<std::min(blocks, (hm.nh + 7) / 8), FWD_THREADS, 0, st>>>(
+          hm.nh, hm.heavy.as<int32_t>(), hm.hseg0.as<int32_t>(), lm + (size_t)l * n, ws.sigma.as<uint64_t>(),
+          hm.part.as<Acc>(), sink, ws.err.as<unsigned>());
+    }
+  }
+}
+
+void batch_extract(bc_ctx *ctx, const Graph &g, int count, int maxlevel, int32_t *dist, uint64_t *sigma,
+                   int64_t row_stride, int64_t lane_stride) {
+  LaunchScope ls(ctx, F_MISC);
+  k_extract<<<(g.n + 255) / 256, 256, 0, ctx->stream>>>(g.n, count, maxlevel, ctx->ws.lm.as<uint64_t>(),
+                                                        ctx->ws.sigma.as<uint64_t>(), dist, sigma, row_stride,
+                                                        lane_stride);
+}
+
+}  // namespace bcg

@@ -1,0 +1,902 @@
+// bc_capi.cu -- the C ABI (include/bc.h): contexts, resident graphs, the
+// estimator drivers and their small kernels (draws, stop scans, finalisers).
+//
+// Drivers:
+//   bc_exact             all n sources in lane batches, exact per-vertex sums (Eq. 4)
+//   bc_uniform_sources   first k draws, exact per-vertex sums, est = n*S/k
+//   bc_adaptive_sources  Bader's loop (Sec. 4): per batch, the dependencies of the
+//                        targets go through a sequential per-target stop scan
+//   bc_adaptive_pairs    Algorithm 1: one BFS per target, then batched pair BFS
+//                        truncated at the destination's level, pair values, scan
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "bc_internal.h"
+
+namespace bcg {
+
+void forget_heavy_meta(const int32_t *rp);
+void plain_pair(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dest);
+
+const char *kFamilyName[F_NFAM] = {"draw", "init", "fwd", "bwd", "scan", "pair", "misc", "plain_fwd", "plain_bwd"};
+
+void fail(bc_status code, const std::string &msg) { throw Error{code, msg}; }
+
+void cuda_check(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    fail(BC_E_NOMEM, std::string("out of device memory in ") + what);
+  }
+  fail(BC_E_DEVICE, std::string(cudaGetErrorString(e)) + " in " + what);
+}
+
+void DevBuf::ensure(size_t b) {
+  if (b <= bytes) return;
+  release();
+  size_t nb = std::max<size_t>(b, 256);
+  cuda_check(cudaMalloc(&p, nb), "cudaMalloc(workspace)");
+  bytes = nb;
+}
+
+void DevBuf::grow_keep(size_t b, cudaStream_t st) {
+  if (b <= bytes) return;
+  void *np = nullptr;
+  cuda_check(cudaMalloc(&np, b), "cudaMalloc(workspace growth)");
+  if (p) {
+    cuda_check(cudaMemcpyAsync(np, p, bytes, cudaMemcpyDeviceToDevice, st), "cudaMemcpyAsync(growth)");
+    cuda_check(cudaStreamSynchronize(st), "cudaStreamSynchronize(growth)");
+    cudaFree(p);
+  }
+  p = np;
+  bytes = b;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+LaunchScope::LaunchScope(bc_ctx *c, int f) : ctx(c), fam(f) {
+  if (ctx->profiling) {
+    for (cudaEvent_t *e : {&e0, &e1}) {
+      if (!ctx->event_pool.empty()) {
+        *e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+      } else {
+        cudaEventCreate(e);
+      }
+    }
+    cudaEventRecord(e0, ctx->stream);
+  }
+}
+
+LaunchScope::~LaunchScope() {
+  ctx->launches += 1;
+  ctx->fam_launches[fam] += 1;
+  if (e0) {
+    cudaEventRecord(e1, ctx->stream);
+    ctx->pending_events.push_back({fam, {e0, e1}});
+  }
+}
+
+void resolve_events(bc_ctx *ctx) {
+  for (auto &pe : ctx->pending_events) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) ctx->fam_ms[pe.first] += ms;
+    ctx->event_pool.push_back(pe.second.first);
+    ctx->event_pool.push_back(pe.second.second);
+  }
+  ctx->pending_events.clear();
+}
+
+const Graph &get_graph(bc_ctx *ctx, bc_graph g) {
+  auto it = ctx->graphs.find(g);
+  if (it == ctx->graphs.end()) fail(BC_E_UNKNOWN_HANDLE, "unknown graph handle");
+  return it->second;
+}
+
+void sync(bc_ctx *ctx) {
+  BCG_CUDA(cudaGetLastError());
+  BCG_CUDA(cudaStreamSynchronize(ctx->stream));
+  resolve_events(ctx);
+}
+
+unsigned read_and_clear_err(bc_ctx *ctx) {
+  unsigned *h = static_cast<unsigned *>(ctx->ws.pinned);
+  BCG_CUDA(cudaMemcpyAsync(h, ctx->ws.err.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  BCG_CUDA(cudaMemsetAsync(ctx->ws.err.p, 0, 4, ctx->stream));
+  sync(ctx);
+  return *h;
+}
+
+static void check_err_bits(bc_ctx *ctx) {
+  const unsigned e = read_and_clear_err(ctx);
+  if (e & ERR_SIGMA_OVERFLOW) fail(BC_E_SIGMA_OVERFLOW, "a shortest-path count exceeded 2^64-1");
+  if (e & ERR_RANGE) fail(BC_E_RANGE, "a dependency left the exact accumulator range");
+  if (e & ERR_TIMEOUT) fail(BC_E_DEVICE_TIMEOUT, "a bounded device wait ran out");
+}
+
+// ------------------------------------------------------------------ kernels --
+
+__global__ void k_draw_sources(uint64_t seed, uint64_t qid, uint64_t i0, int count, int32_t n,
+                               int32_t *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = draw_source(seed, qid, i0 + (uint64_t)i, n);
+}
+
+__global__ void k_draw_pairs(uint64_t seed, uint64_t qid, uint64_t i0, int count, int32_t n,
+                             int32_t *__restrict__ s_out, int32_t *__restrict__ t_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) {
+    int32_t u, t;
+    draw_pair(seed, qid, i0 + (uint64_t)i, n, u, t);
+    s_out[i] = u;
+    t_out[i] = t;
+  }
+}
+
+__global__ void k_iota(int count, int32_t first, int32_t *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = first + i;
+}
+
+__global__ void k_fill_i32(int64_t count, int32_t v, int32_t *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = v;
+}
+
+__global__ void k_set_slots(int T, const int32_t *__restrict__ targets, int32_t *__restrict__ tslot) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < T) tslot[targets[j]] = j;
+}
+
+struct ScanState {
+  double *S;
+  int64_t *k;
+  int32_t *done;
+  int32_t *remaining;
+};
+
+// Sequential stop test per target, in draw order (Sec. 4 step 3; Algorithm 1's
+// while-condition): S <- S + x_i, k <- k + 1, stop at the first S*scale > cn.
+__global__ void k_stop_scan(int T, int count, const double *__restrict__ vals, ScanState st, int64_t k0,
+                            double cn, double scale) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= T || st.done[j]) return;
+  double S = st.S[j];
+  int64_t k = k0;
+  bool stop = false;
+  for (int t = 0; t < count; ++t) {
+    S = __dadd_rn(S, vals[(size_t)j * 64 + t]);
+    k = k0 + t + 1;
+    if (__dmul_rn(S, scale) > cn) {
+      stop = true;
+      break;
+    }
+  }
+  st.S[j] = S;
+  st.k[j] = k;
+  if (stop) {
+    st.done[j] = 1;
+    atomicSub(st.remaining, 1);
+  }
+}
+
+__global__ void k_finalize_targets(int T, ScanState st, double scale_n, double *__restrict__ est,
+                                   int32_t *__restrict__ status) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= T) return;
+  est[j] = __ddiv_rn(__dmul_rn(scale_n, st.S[j]), (double)st.k[j]);
+  status[j] = st.done[j] ? BC_STOPPED : BC_CAPPED;
+}
+
+__global__ void k_finalize_vertices(int32_t n, const Acc *__restrict__ acc, double scale_n, double denom,
+                                    bool scaled, double *__restrict__ out) {
+  const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const double S = acc_round(acc[v]);
+  out[v] = scaled ? __ddiv_rn(__dmul_rn(scale_n, S), denom) : S;
+}
+
+// y = sigma_sv*sigma_vt/sigma_st if d(s,v)+d(v,t) = d(s,t) and v not in {s,t}
+// (Algorithm 1 with the pair-dependency of Eq. 2), else 0.
+__global__ void k_pair_values(int T, int count, const int32_t *__restrict__ targets,
+                              const int32_t *__restrict__ ps, const int32_t *__restrict__ pt,
+                              const int32_t *__restrict__ pd, const uint64_t *__restrict__ psig,
+                              const int32_t *__restrict__ tdist, const uint64_t *__restrict__ tsig, int tstride,
+                              double *__restrict__ vals) {
+  const int i = threadIdx.x;           // pair lane
+  const int j = blockIdx.x;            // target
+  if (j >= T || i >= 64) return;
+  double y = 0.0;
+  if (i < count) {
+    const int32_t v = targets[j], s = ps[i], t = pt[i];
+    const int32_t dst = pd[i];
+    const uint64_t sst = psig[i];
+    if (v != s && v != t && sst != 0ull && dst >= 0) {
+      const int32_t ds = tdist[(size_t)s * tstride + j], dt = tdist[(size_t)t * tstride + j];
+      if (ds >= 0 && dt >= 0 && ds + dt == dst) {
+        const double a = sigma_to_double(tsig[(size_t)s * tstride + j]);
+        const double b = sigma_to_double(tsig[(size_t)t * tstride + j]);
+        y = __ddiv_rn(__dmul_rn(a, b), sigma_to_double(sst));
+      }
+    }
+  }
+  vals[(size_t)j * 64 + i] = y;
+}
+
+__global__ void k_transpose_delta(int32_t n, int count, const double *__restrict__ delta_lm,
+                                  double *__restrict__ out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * count) return;
+  const int t = (int)(idx / n);
+  const int32_t v = (int32_t)(idx % n);
+  out[idx] = delta_lm[(size_t)v * 64 + t];
+}
+
+__global__ void k_exact_sum(int64_t count, const double *__restrict__ x, double *__restrict__ out,
+                            unsigned *__restrict__ err) {
+  unsigned e = 0u;
+  Acc a = acc_zero();
+  for (int64_t i = threadIdx.x; i < count; i += 32) acc_add(a, x[i], e);
+  a = acc_warp_sum(a);
+  if (threadIdx.x == 0) *out = acc_round(a);
+  if (e) atomicOr(err, e);
+}
+
+// Graph validation: symmetric, sorted, no loops, no duplicates, in range.
+__global__ void k_validate(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                           int64_t nnz, unsigned *__restrict__ bad) {
+  const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const int b = rp[v], e = rp[v + 1];
+  if (b < 0 || e < b || (int64_t)e > nnz) {
+    atomicOr(bad, 1u);
+    return;
+  }
+  for (int j = b; j < e; ++j) {
+    const int32_t w = col[j];
+    if (w < 0 || w >= n || w == v) { atomicOr(bad, 2u); return; }
+    if (j > b && col[j - 1] >= w) { atomicOr(bad, 4u); return; }
+    // symmetric: binary search v in row w
+    int lo = rp[w], hi = rp[w + 1] - 1;
+    bool found = false;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const int32_t x = col[mid];
+      if (x == v) { found = true; break; }
+      if (x < v) lo = mid + 1; else hi = mid - 1;
+    }
+    if (!found) { atomicOr(bad, 8u); return; }
+  }
+}
+
+// --------------------------------------------------------------- helpers ----
+
+static int batch_width(bc_ctx *ctx) {
+  const int w = ctx->batch_width;
+  return (w == 1) ? 1 : 64;
+}
+
+template <class T>
+static T *dev_upload(bc_ctx *ctx, DevBuf &buf, const T *host, size_t count) {
+  buf.ensure(std::max<size_t>(count, 1) * sizeof(T));
+  if (count) BCG_CUDA(cudaMemcpyAsync(buf.p, host, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  return buf.as<T>();
+}
+
+static void launch_draw_sources(bc_ctx *ctx, uint64_t seed, uint64_t qid, uint64_t i0, int count, int32_t n,
+                                int32_t *out) {
+  LaunchScope ls(ctx, F_DRAW);
+  k_draw_sources<<<(count + 63) / 64, 64, 0, ctx->stream>>>(seed, qid, i0, count, n, out);
+}
+
+// One batch of the per-sample step for the sources in ws.sources[0..count).
+static void run_batch(bc_ctx *ctx, const Graph &g, int count, const Sink &sink) {
+  if (batch_width(ctx) == 1) {
+    plain_source(ctx, g, ctx->ws.sources.as<int32_t>(), sink, nullptr, nullptr);
+  } else {
+    const int maxl = batch_forward(ctx, g, count, false);
+    batch_backward(ctx, g, maxl, sink);
+  }
+}
+
+static void validate_targets(const Graph &g, const int32_t *targets, int32_t T) {
+  if (T < 0) fail(BC_E_INVALID, "T must be >= 0");
+  if (T > 0 && !targets) fail(BC_E_INVALID, "targets is NULL");
+  std::vector<int32_t> s(targets, targets + T);
+  for (int32_t v : s)
+    if (v < 0 || v >= g.n) fail(BC_E_INVALID, "target out of range");
+  std::sort(s.begin(), s.end());
+  for (size_t i = 1; i < s.size(); ++i)
+    if (s[i] == s[i - 1]) fail(BC_E_INVALID, "targets must be distinct");
+}
+
+struct ScanBuffers {
+  ScanState st;
+};
+
+static ScanState make_scan(bc_ctx *ctx, int32_t T) {
+  Workspace &ws = ctx->ws;
+  const size_t Tp = (size_t)std::max(T, 1);
+  const size_t off_rem = (Tp * 20 + 15) / 16 * 16;  // S[Tp] f64, k[Tp] i64, done[Tp] i32, remaining
+  ws.scan.ensure(off_rem + 16);
+  char *base = ws.scan.as<char>();
+  ScanState st;
+  st.S = reinterpret_cast<double *>(base);
+  st.k = reinterpret_cast<int64_t *>(base + Tp * 8);
+  st.done = reinterpret_cast<int32_t *>(base + Tp * 16);
+  st.remaining = reinterpret_cast<int32_t *>(base + off_rem);
+  BCG_CUDA(cudaMemsetAsync(base, 0, ws.scan.bytes, ctx->stream));
+  BCG_CUDA(cudaMemcpyAsync(st.remaining, &T, 4, cudaMemcpyHostToDevice, ctx->stream));
+  return st;
+}
+
+static int32_t read_remaining(bc_ctx *ctx, const ScanState &st) {
+  int32_t *h = static_cast<int32_t *>(ctx->ws.pinned);
+  BCG_CUDA(cudaMemcpyAsync(h, st.remaining, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  sync(ctx);
+  return *h;
+}
+
+static void copy_scan_out(bc_ctx *ctx, int32_t T, const ScanState &st, double scale_n, double *est, int64_t *k,
+                          double *S, int32_t *status) {
+  Workspace &ws = ctx->ws;
+  ws.misc2.ensure((size_t)std::max(T, 1) * 12 + 64);
+  double *d_est = ws.misc2.as<double>();
+  int32_t *d_status = reinterpret_cast<int32_t *>(d_est + std::max(T, 1));
+  if (T > 0) {
+    LaunchScope ls(ctx, F_SCAN);
+    k_finalize_targets<<<(T + 127) / 128, 128, 0, ctx->stream>>>(T, st, scale_n, d_est, d_status);
+  }
+  sync(ctx);
+  if (T > 0) {
+    BCG_CUDA(cudaMemcpy(est, d_est, (size_t)T * 8, cudaMemcpyDeviceToHost));
+    BCG_CUDA(cudaMemcpy(k, st.k, (size_t)T * 8, cudaMemcpyDeviceToHost));
+    if (S) BCG_CUDA(cudaMemcpy(S, st.S, (size_t)T * 8, cudaMemcpyDeviceToHost));
+    if (status) BCG_CUDA(cudaMemcpy(status, d_status, (size_t)T * 4, cudaMemcpyDeviceToHost));
+  }
+}
+
+// ---------------------------------------------------------------- drivers ---
+
+static void do_exact_or_uniform(bc_ctx *ctx, const Graph &g, bool exact, int64_t k, uint64_t seed, uint64_t qid,
+                                double *out) {
+  Workspace &ws = ctx->ws;
+  const size_t n = (size_t)g.n;
+  ws.acc.ensure(n * sizeof(Acc));
+  BCG_CUDA(cudaMemsetAsync(ws.acc.p, 0, n * sizeof(Acc), ctx->stream));
+  Sink sink;
+  sink.acc = ws.acc.as<Acc>();
+  const int width = batch_width(ctx);
+  const int64_t total = exact ? (int64_t)g.n : k;
+  for (int64_t i0 = 0; i0 < total; i0 += width) {
+    const int count = (int)std::min<int64_t>(width, total - i0);
+    if (exact) {
+      LaunchScope ls(ctx, F_DRAW);
+      k_iota<<<1, 64, 0, ctx->stream>>>(count, (int32_t)i0, ws.sources.as<int32_t>());
+    } else {
+      launch_draw_sources(ctx, seed, qid, (uint64_t)i0, count, g.n, ws.sources.as<int32_t>());
+    }
+    run_batch(ctx, g, count, sink);
+  }
+  ws.misc2.ensure(n * 8);
+  {
+    LaunchScope ls(ctx, F_MISC);
+    k_finalize_vertices<<<(g.n + 255) / 256, 256, 0, ctx->stream>>>(g.n, ws.acc.as<Acc>(), (double)g.n,
+                                                                    (double)k, !exact, ws.misc2.as<double>());
+  }
+  check_err_bits(ctx);
+  BCG_CUDA(cudaMemcpy(out, ws.misc2.p, n * 8, cudaMemcpyDeviceToHost));
+}
+
+static void do_adaptive_sources(bc_ctx *ctx, const Graph &g, const int32_t *targets, int32_t T, double c,
+                                int64_t cap, uint64_t seed, uint64_t qid, double *est, int64_t *k, double *S,
+                                int32_t *status) {
+  Workspace &ws = ctx->ws;
+  const size_t n = (size_t)g.n;
+  cudaStream_t st = ctx->stream;
+  ws.tslot.ensure(n * 4);
+  ws.tdelta.ensure((size_t)std::max(T, 1) * 64 * 8);
+  {
+    LaunchScope ls(ctx, F_MISC);
+    k_fill_i32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((int64_t)n, -1, ws.tslot.as<int32_t>());
+  }
+  ws.misc.ensure((size_t)std::max(T, 1) * 4 + 64);
+  int32_t *d_targets = dev_upload(ctx, ws.misc, targets, (size_t)T);
+  if (T > 0) {
+    LaunchScope ls(ctx, F_MISC);
+    k_set_slots<<<(T + 127) / 128, 128, 0, st>>>(T, d_targets, ws.tslot.as<int32_t>());
+  }
+  ScanState ss = make_scan(ctx, T);
+  Sink sink;
+  sink.tslot = ws.tslot.as<int32_t>();
+  sink.tdelta = ws.tdelta.as<double>();
+  const double cn = c * (double)g.n;
+  const int width = batch_width(ctx);
+  int32_t remaining = T;
+  for (int64_t i0 = 0; i0 < cap && remaining > 0; i0 += width) {
+    const int count = (int)std::min<int64_t>(width, cap - i0);
+    launch_draw_sources(ctx, seed, qid, (uint64_t)i0, count, g.n, ws.sources.as<int32_t>());
+    BCG_CUDA(cudaMemsetAsync(ws.tdelta.p, 0, (size_t)T * 64 * 8, st));
+    run_batch(ctx, g, count, sink);
+    {
+      LaunchScope ls(ctx, F_SCAN);
+      k_stop_scan<<<(T + 127) / 128, 128, 0, st>>>(T, count, ws.tdelta.as<double>(), ss, i0, cn, 1.0);
+    }
+    remaining = read_remaining(ctx, ss);
+  }
+  check_err_bits(ctx);
+  copy_scan_out(ctx, T, ss, (double)g.n, est, k, S, status);
+}
+
+static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *targets, int32_t T, double c,
+                              int64_t cap, uint64_t seed, uint64_t qid, double scale, double *est, int64_t *k,
+                              double *S, int32_t *status) {
+  Workspace &ws = ctx->ws;
+  const size_t n = (size_t)g.n;
+  cudaStream_t st = ctx->stream;
+  const int Tp = std::max(T, 1);
+  // Per-target BFS (distance and sigma from every target), layout [n][Tp].
+  DevBuf tdist, tsig;
+  tdist.ensure(n * Tp * 4);
+  tsig.ensure(n * Tp * 8);
+  ws.misc.ensure((size_t)Tp * 4 + 64);
+  int32_t *d_targets = dev_upload(ctx, ws.misc, targets, (size_t)T);
+  try {
+    for (int j0 = 0; j0 < T; j0 += 64) {
+      const int count = std::min(64, T - j0);
+      BCG_CUDA(cudaMemcpyAsync(ws.sources.p, d_targets + j0, (size_t)count * 4, cudaMemcpyDeviceToDevice, st));
+      batch_ensure(ctx, g);
+      const int maxl = batch_forward(ctx, g, count, false);
+      batch_extract(ctx, g, count, maxl, tdist.as<int32_t>() + j0, tsig.as<uint64_t>() + j0, Tp, 1);
+    }
+    ws.tdelta.ensure((size_t)Tp * 64 * 8);
+    ScanState ss = make_scan(ctx, T);
+    const double cn = c * (double)g.n;
+    const int width = batch_width(ctx);
+    int32_t remaining = T;
+    for (int64_t i0 = 0; i0 < cap && remaining > 0; i0 += width) {
+      const int count = (int)std::min<int64_t>(width, cap - i0);
+      {
+        LaunchScope ls(ctx, F_DRAW);
+        k_draw_pairs<<<1, 64, 0, st>>>(seed, qid, (uint64_t)i0, count, g.n, ws.sources.as<int32_t>(),
+                                       ws.targets.as<int32_t>());
+      }
+      if (width == 1) {
+        plain_pair(ctx, g, ws.sources.as<int32_t>(), ws.targets.as<int32_t>());
+      } else {
+        batch_forward(ctx, g, count, true);
+      }
+      if (T > 0) {
+        LaunchScope ls(ctx, F_PAIR);
+        k_pair_values<<<T, 64, 0, st>>>(T, count, d_targets, ws.sources.as<int32_t>(), ws.targets.as<int32_t>(),
+                                        ws.pair_d.as<int32_t>(), ws.pair_sig.as<uint64_t>(), tdist.as<int32_t>(),
+                                        tsig.as<uint64_t>(), Tp, ws.tdelta.as<double>());
+      }
+      {
+        LaunchScope ls(ctx, F_SCAN);
+        k_stop_scan<<<(T + 127) / 128, 128, 0, st>>>(T, count, ws.tdelta.as<double>(), ss, i0, cn, scale);
+      }
+      remaining = read_remaining(ctx, ss);
+    }
+    check_err_bits(ctx);
+    copy_scan_out(ctx, T, ss, (double)g.n * (double)(g.n - 1), est, k, S, status);
+  } catch (...) {
+    cudaStreamSynchronize(st);
+    tdist.release();
+    tsig.release();
+    throw;
+  }
+  sync(ctx);
+  tdist.release();
+  tsig.release();
+}
+
+static void do_source_dependencies(bc_ctx *ctx, const Graph &g, const int32_t *sources, int32_t count,
+                                   double *delta_out, int32_t *dist_out, uint64_t *sigma_out) {
+  Workspace &ws = ctx->ws;
+  const size_t n = (size_t)g.n;
+  cudaStream_t st = ctx->stream;
+  for (int32_t i = 0; i < count; ++i)
+    if (sources[i] < 0 || sources[i] >= g.n) fail(BC_E_INVALID, "source out of range");
+  ws.delta_lm.ensure(n * 64 * 8);
+  DevBuf dd, ddist, dsig;
+  const int width = batch_width(ctx);
+  const int chunk = std::min<int>(64, std::max(1, count));
+  dd.ensure(n * chunk * 8);
+  if (dist_out) ddist.ensure(n * chunk * 4);
+  if (sigma_out) dsig.ensure(n * chunk * 8);
+  Sink sink;
+  sink.delta_lm = ws.delta_lm.as<double>();
+  try {
+    for (int32_t i0 = 0; i0 < count; i0 += (width == 1 ? 1 : 64)) {
+      const int cnt = std::min<int>(width == 1 ? 1 : 64, count - i0);
+      BCG_CUDA(cudaMemcpyAsync(ws.sources.p, sources + i0, (size_t)cnt * 4, cudaMemcpyHostToDevice, st));
+      BCG_CUDA(cudaMemsetAsync(ws.delta_lm.p, 0, n * 64 * 8, st));
+      if (width == 1) {
+        plain_source(ctx, g, ws.sources.as<int32_t>(), sink, dist_out ? ddist.as<int32_t>() : nullptr,
+                     sigma_out ? dsig.as<uint64_t>() : nullptr);
+      } else {
+        const int maxl = batch_forward(ctx, g, cnt, false);
+        if (dist_out || sigma_out)
+          batch_extract(ctx, g, cnt, maxl, dist_out ? ddist.as<int32_t>() : nullptr,
+                        sigma_out ? dsig.as<uint64_t>() : nullptr, 1, (int64_t)n);
+        batch_backward(ctx, g, maxl, sink);
+      }
+      {
+        LaunchScope ls(ctx, F_MISC);
+        const int64_t tot = (int64_t)n * cnt;
+        k_transpose_delta<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(g.n, cnt, ws.delta_lm.as<double>(),
+                                                                          dd.as<double>());
+      }
+      sync(ctx);
+      BCG_CUDA(cudaMemcpy(delta_out + (size_t)i0 * n, dd.p, n * cnt * 8, cudaMemcpyDeviceToHost));
+      if (dist_out) BCG_CUDA(cudaMemcpy(dist_out + (size_t)i0 * n, ddist.p, n * cnt * 4, cudaMemcpyDeviceToHost));
+      if (sigma_out)
+        BCG_CUDA(cudaMemcpy(sigma_out + (size_t)i0 * n, dsig.p, n * cnt * 8, cudaMemcpyDeviceToHost));
+    }
+    check_err_bits(ctx);
+  } catch (...) {
+    cudaStreamSynchronize(st);
+    dd.release(); ddist.release(); dsig.release();
+    throw;
+  }
+  dd.release(); ddist.release(); dsig.release();
+}
+
+}  // namespace bcg
+
+using namespace bcg;
+
+// ----------------------------------------------------------------- the ABI ---
+
+#define BC_GUARD_BEGIN                               \
+  if (!ctx) return BC_E_INVALID;                     \
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu); \
+  try {
+#define BC_GUARD_END                                                   \
+  ctx->err = "no error";                                               \
+  return BC_OK;                                                        \
+  }                                                                    \
+  catch (const Error &e) {                                             \
+    ctx->err = e.msg;                                                  \
+    return e.code;                                                     \
+  }                                                                    \
+  catch (const std::exception &e) {                                    \
+    ctx->err = std::string("internal error: ") + e.what();             \
+    return BC_E_DEVICE;                                                \
+  }                                                                    \
+  catch (...) {                                                        \
+    ctx->err = "internal error";                                       \
+    return BC_E_DEVICE;                                                \
+  }
+
+extern "C" {
+
+bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
+  if (!out) return BC_E_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return BC_E_DEVICE;
+  }
+  if (device < 0 || device >= ndev) return BC_E_INVALID;
+  if (opt && !(opt->batch_width == 0 || opt->batch_width == 1 || opt->batch_width == 32 || opt->batch_width == 64))
+    return BC_E_INVALID;
+  bc_ctx *ctx = new (std::nothrow) bc_ctx();
+  if (!ctx) return BC_E_NOMEM;
+  try {
+    ctx->device = device;
+    BCG_CUDA(cudaSetDevice(device));
+    if (opt && opt->stream) {
+      ctx->stream = static_cast<cudaStream_t>(opt->stream);
+    } else {
+      BCG_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+      ctx->own_stream = true;
+    }
+    if (opt) ctx->batch_width = opt->batch_width;
+    BCG_CUDA(cudaMallocHost(&ctx->ws.pinned, 4096));
+    ctx->ws.enable.ensure(64);   // [0] lane enable mask, [1] pair continuation word
+    ctx->ws.sources.ensure(64 * 4);
+    ctx->ws.targets.ensure(64 * 4);
+    ctx->ws.pair_d.ensure(64 * 4);
+    ctx->ws.pair_sig.ensure(64 * 8);
+    ctx->ws.err.ensure(16);
+    BCG_CUDA(cudaMemset(ctx->ws.err.p, 0, 16));
+    ctx->ws.cnt.ensure(16);
+    BCG_CUDA(cudaMemset(ctx->ws.cnt.p, 0, 16));
+  } catch (const Error &e) {
+    bc_destroy(ctx);
+    return e.code;
+  }
+  *out = ctx;
+  return BC_OK;
+}
+
+void bc_destroy(bc_ctx *ctx) {
+  if (!ctx) return;
+  {
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    resolve_events(ctx);
+    for (auto &kv : ctx->graphs) {
+      forget_heavy_meta(kv.second.rp);
+      cudaFree(kv.second.rp);
+      cudaFree(kv.second.col);
+    }
+    ctx->graphs.clear();
+    Workspace &ws = ctx->ws;
+    for (DevBuf *b : {&ws.lm, &ws.visited, &ws.sigma, &ws.active, &ws.enable, &ws.sources, &ws.targets, &ws.pair_d,
+                      &ws.pair_sig, &ws.err, &ws.cnt, &ws.acc, &ws.tslot, &ws.tdelta, &ws.scan, &ws.misc, &ws.misc2,
+                      &ws.delta_lm, &ws.p_dist, &ws.p_sigma, &ws.p_coef, &ws.p_queue, &ws.p_ctr})
+      b->release();
+    if (ws.pinned) cudaFreeHost(ws.pinned);
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  }
+  delete ctx;
+}
+
+const char *bc_last_error(bc_ctx *ctx) {
+  if (!ctx) return "NULL context";
+  return ctx->err.c_str();
+}
+
+bc_status bc_set_batch_width(bc_ctx *ctx, int32_t width) {
+  BC_GUARD_BEGIN
+  if (!(width == 0 || width == 1 || width == 32 || width == 64)) fail(BC_E_INVALID, "batch width must be 0, 1, 32 or 64");
+  ctx->batch_width = width;
+  BC_GUARD_END
+}
+
+bc_status bc_graph_load_csr(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col, int64_t nnz,
+                            uint32_t flags, bc_graph *out) {
+  BC_GUARD_BEGIN
+  if (!out || !row_ptr) fail(BC_E_INVALID, "NULL argument");
+  if (!(flags & BC_UNDIRECTED)) fail(BC_E_INVALID, "only undirected graphs (BC_UNDIRECTED) are supported");
+  if (n < 1) fail(BC_E_INVALID, "n must be >= 1");
+  if (n > (1 << 30)) fail(BC_E_TOO_LARGE, "n too large");
+  if (nnz < 0 || nnz >= ((int64_t)1 << 31)) fail(BC_E_TOO_LARGE, "nnz must be < 2^31");
+  if (row_ptr[0] != 0 || (int64_t)row_ptr[n] != nnz) fail(BC_E_BAD_GRAPH, "row_ptr[0] must be 0 and row_ptr[n] == nnz");
+  if (nnz > 0 && !col) fail(BC_E_INVALID, "col is NULL");
+  int32_t maxdeg = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    const int32_t d = row_ptr[v + 1] - row_ptr[v];
+    if (d < 0) fail(BC_E_BAD_GRAPH, "row_ptr must be non-decreasing");
+    maxdeg = std::max(maxdeg, d);
+  }
+  Graph g;
+  g.n = n;
+  g.nnz = nnz;
+  g.max_deg = maxdeg;
+  BCG_CUDA(cudaMalloc(&g.rp, sizeof(int32_t) * ((size_t)n + 1)));
+  if (cudaMalloc(&g.col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(g.rp);
+    fail(BC_E_NOMEM, "out of device memory for col");
+  }
+  try {
+    BCG_CUDA(cudaMemcpyAsync(g.rp, row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, ctx->stream));
+    if (nnz > 0)
+      BCG_CUDA(cudaMemcpyAsync(g.col, col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, ctx->stream));
+    if (flags & BC_VALIDATE) {
+      unsigned *d_bad = ctx->ws.err.as<unsigned>() + 1;
+      BCG_CUDA(cudaMemsetAsync(d_bad, 0, 4, ctx->stream));
+      {
+        LaunchScope ls(ctx, F_MISC);
+        k_validate<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, g.rp, g.col, nnz, d_bad);
+      }
+      unsigned *h = static_cast<unsigned *>(ctx->ws.pinned);
+      BCG_CUDA(cudaMemcpyAsync(h, d_bad, 4, cudaMemcpyDeviceToHost, ctx->stream));
+      sync(ctx);
+      if (*h) {
+        const unsigned b = *h;
+        fail(BC_E_BAD_GRAPH, (b & 1u) ? "bad row_ptr" : (b & 2u) ? "column out of range or self loop"
+                                          : (b & 4u) ? "row not sorted or duplicate edge" : "adjacency not symmetric");
+      }
+    }
+    sync(ctx);
+  } catch (...) {
+    cudaFree(g.rp);
+    cudaFree(g.col);
+    throw;
+  }
+  const bc_graph h = ctx->next_handle++;
+  ctx->graphs[h] = g;
+  *out = h;
+  BC_GUARD_END
+}
+
+bc_status bc_graph_free(bc_ctx *ctx, bc_graph g) {
+  BC_GUARD_BEGIN
+  auto it = ctx->graphs.find(g);
+  if (it == ctx->graphs.end()) fail(BC_E_UNKNOWN_HANDLE, "unknown graph handle");
+  sync(ctx);
+  forget_heavy_meta(it->second.rp);
+  cudaFree(it->second.rp);
+  cudaFree(it->second.col);
+  ctx->graphs.erase(it);
+  BC_GUARD_END
+}
+
+bc_status bc_graph_info(bc_ctx *ctx, bc_graph g, int32_t *n, int64_t *nnz) {
+  BC_GUARD_BEGIN
+  const Graph &gr = get_graph(ctx, g);
+  if (n) *n = gr.n;
+  if (nnz) *nnz = gr.nnz;
+  BC_GUARD_END
+}
+
+bc_status bc_source_dependencies(bc_ctx *ctx, bc_graph g, const int32_t *sources, int32_t count, double *delta_out,
+                                 int32_t *dist_out, uint64_t *sigma_out) {
+  BC_GUARD_BEGIN
+  const Graph &gr = get_graph(ctx, g);
+  if (count < 0) fail(BC_E_INVALID, "count must be >= 0");
+  if (count > 0 && (!sources || !delta_out)) fail(BC_E_INVALID, "NULL argument");
+  BCG_CUDA(cudaSetDevice(ctx->device));
+  if (count > 0) do_source_dependencies(ctx, gr, sources, count, delta_out, dist_out, sigma_out);
+  BC_GUARD_END
+}
+
+bc_status bc_exact(bc_ctx *ctx, bc_graph g, double *bc_out) {
+  BC_GUARD_BEGIN
+  const Graph &gr = get_graph(ctx, g);
+  if (!bc_out) fail(BC_E_INVALID, "bc_out is NULL");
+  BCG_CUDA(cudaSetDevice(ctx->device));
+  do_exact_or_uniform(ctx, gr, true, gr.n, 0, 0, bc_out);
+  BC_GUARD_END
+}
+
+bc_status bc_uniform_sources(bc_ctx *ctx, bc_graph g, int64_t k, uint64_t seed, uint64_t qid, double *est_out) {
+  BC_GUARD_BEGIN
+  const Graph &gr = get_graph(ctx, g);
+  if (!est_out) fail(BC_E_INVALID, "est_out is NULL");
+  if (k < 1 || k > ((int64_t)1 << 32)) fail(BC_E_INVALID, "k must be in [1, 2^32]");
+  BCG_CUDA(cudaSetDevice(ctx->device));
+  do_exact_or_uniform(ctx, gr, false, k, seed, qid, est_out);
+  BC_GUARD_END
+}
+
+bc_status bc_adaptive_sources(bc_ctx *ctx, bc_graph g, const int32_t *targets, int32_t T, double c, int64_t cap,
+                              uint64_t seed, uint64_t qid, double *est, int64_t *k, double *S,
+                              int32_t *stop_status) {
+  BC_GUARD_BEGIN
+  const Graph &gr = get_graph(ctx, g);
+  if (!(c >= 1.0) || !(c < 1e300)) fail(BC_E_INVALID, "c must be >= 1 and finite");
+  if (cap < 1 || cap > ((int64_t)1 << 32)) fail(BC_E_INVALID, "cap must be in [1, 2^32]");
+  if (T > 0 && (!est || !k)) fail(BC_E_INVALID, "NULL output");
+  validate_targets(gr, targets, T);
+  BCG_CUDA(cudaSetDevice(ctx->device));
+  if (T > 0) do_adaptive_sources(ctx, gr, targets, T, c, cap, seed, qid, est, k, S, stop_status);
+  BC_GUARD_END
+}
+
+bc_status bc_adaptive_pairs(bc_ctx *ctx, bc_graph g, const int32_t *targets, int32_t T, double c, int64_t cap,
+                            uint64_t seed, uint64_t qid, double threshold_scale, double *est, int64_t *k,
+                            double *S, int32_t *stop_status) {
+  BC_GUARD_BEGIN
+  const Graph &gr = get_graph(ctx, g);
+  if (gr.n < 2) fail(BC_E_INVALID, "pair sampling needs n >= 2");
+  if (!(c >= 1.0) || !(c < 1e300)) fail(BC_E_INVALID, "c must be >= 1 and finite");
+  if (!(threshold_scale > 0.0) || !(threshold_scale < 1e300)) fail(BC_E_INVALID, "threshold_scale must be > 0");
+  if (cap < 1 || cap > ((int64_t)1 << 32)) fail(BC_E_INVALID, "cap must be in [1, 2^32]");
+  if (T > 0 && (!est || !k)) fail(BC_E_INVALID, "NULL output");
+  validate_targets(gr, targets, T);
+  BCG_CUDA(cudaSetDevice(ctx->device));
+  if (T > 0) do_adaptive_pairs(ctx, gr, targets, T, c, cap, seed, qid, threshold_scale, est, k, S, stop_status);
+  BC_GUARD_END
+}
+
+bc_status bc_draw_sources(bc_ctx *ctx, uint64_t seed, uint64_t qid, uint64_t i0, int64_t count, int32_t n,
+                          int32_t *out) {
+  BC_GUARD_BEGIN
+  if (n < 1 || count < 0 || count > (1 << 28) || (count > 0 && !out)) fail(BC_E_INVALID, "bad argument");
+  if (count == 0) { ctx->err = "no error"; return BC_OK; }
+  DevBuf b;
+  b.ensure((size_t)count * 4);
+  try {
+    launch_draw_sources(ctx, seed, qid, i0, (int)count, n, b.as<int32_t>());
+    sync(ctx);
+    BCG_CUDA(cudaMemcpy(out, b.p, (size_t)count * 4, cudaMemcpyDeviceToHost));
+  } catch (...) {
+    b.release();
+    throw;
+  }
+  b.release();
+  BC_GUARD_END
+}
+
+bc_status bc_draw_pairs(bc_ctx *ctx, uint64_t seed, uint64_t qid, uint64_t i0, int64_t count, int32_t n,
+                        int32_t *s_out, int32_t *t_out) {
+  BC_GUARD_BEGIN
+  if (n < 2 || count < 0 || count > (1 << 28) || (count > 0 && (!s_out || !t_out))) fail(BC_E_INVALID, "bad argument");
+  if (count == 0) { ctx->err = "no error"; return BC_OK; }
+  DevBuf b;
+  b.ensure((size_t)count * 8);
+  try {
+    {
+      LaunchScope ls(ctx, F_DRAW);
+      k_draw_pairs<<<(unsigned)((count + 63) / 64), 64, 0, ctx->stream>>>(seed, qid, i0, (int)count, n, b.as<int32_t>(),
+                                                                        b.as<int32_t>() + count);
+    }
+    sync(ctx);
+    BCG_CUDA(cudaMemcpy(s_out, b.p, (size_t)count * 4, cudaMemcpyDeviceToHost));
+    BCG_CUDA(cudaMemcpy(t_out, b.as<int32_t>() + count, (size_t)count * 4, cudaMemcpyDeviceToHost));
+  } catch (...) {
+    b.release();
+    throw;
+  }
+  b.release();
+  BC_GUARD_END
+}
+
+bc_status bc_exact_sum(bc_ctx *ctx, const double *x, int64_t count, double *out) {
+  BC_GUARD_BEGIN
+  if (count < 0 || !out || (count > 0 && !x)) fail(BC_E_INVALID, "bad argument");
+  DevBuf b;
+  b.ensure((size_t)std::max<int64_t>(count, 1) * 8 + 16);
+  try {
+    if (count) BCG_CUDA(cudaMemcpyAsync(b.p, x, (size_t)count * 8, cudaMemcpyHostToDevice, ctx->stream));
+    double *d_out = reinterpret_cast<double *>(b.as<char>() + (size_t)std::max<int64_t>(count, 1) * 8);
+    {
+      LaunchScope ls(ctx, F_MISC);
+      k_exact_sum<<<1, 32, 0, ctx->stream>>>(count, b.as<double>(), d_out, ctx->ws.err.as<unsigned>());
+    }
+    check_err_bits(ctx);
+    BCG_CUDA(cudaMemcpy(out, d_out, 8, cudaMemcpyDeviceToHost));
+  } catch (...) {
+    b.release();
+    throw;
+  }
+  b.release();
+  BC_GUARD_END
+}
+
+bc_status bc_set_profiling(bc_ctx *ctx, int32_t on) {
+  BC_GUARD_BEGIN
+  ctx->profiling = (on != 0);
+  BC_GUARD_END
+}
+
+bc_status bc_get_stats(bc_ctx *ctx, bc_stats *out) {
+  BC_GUARD_BEGIN
+  if (!out) fail(BC_E_INVALID, "NULL argument");
+  sync(ctx);
+  std::memset(out, 0, sizeof(*out));
+  out->launches = ctx->launches;
+  out->samples = ctx->samples;
+  out->batches = ctx->batches;
+  {
+    uint64_t c2[2];
+    BCG_CUDA(cudaMemcpy(c2, ctx->ws.cnt.p, 16, cudaMemcpyDeviceToHost));
+    out->dag_edges = (int64_t)c2[0];
+    out->reached = (int64_t)c2[1];
+  }
+  out->n_kernels = F_NFAM;
+  for (int f = 0; f < F_NFAM; ++f) {
+    std::strncpy(out->kernel_name[f], kFamilyName[f], 31);
+    out->kernel_launches[f] = ctx->fam_launches[f];
+    out->kernel_ms[f] = ctx->fam_ms[f];
+  }
+  BC_GUARD_END
+}
+
+bc_status bc_reset_stats(bc_ctx *ctx) {
+  BC_GUARD_BEGIN
+  sync(ctx);
+  ctx->launches = ctx->samples = ctx->batches = 0;
+  BCG_CUDA(cudaMemset(ctx->ws.cnt.p, 0, 16));
+  for (int f = 0; f < F_NFAM; ++f) {
+    ctx->fam_launches[f] = 0;
+    ctx->fam_ms[f] = 0.0;
+  }
+  BC_GUARD_END
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// bc_internal.h -- host-side structures shared by the library's translation
+// units: the context, resident graphs, the growable device workspace, launch
+// accounting and the per-batch output "sink".
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bc.h"
+#include "bc_common.cuh"
+
+namespace bcg {
+
+// Thrown inside the library only; converted to a bc_status at the ABI.
+struct Error {
+  bc_status code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(bc_status code, const std::string &msg);
+void cuda_check(cudaError_t e, const char *what);
+#define BCG_CUDA(call) ::bcg::cuda_check((call), #call)
+
+// A device allocation that only grows (contents are not preserved on growth
+// unless grow_keep is used).
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  void ensure(size_t b);
+  void grow_keep(size_t b, cudaStream_t st);
+  void release();
+  template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+struct Graph {
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int32_t max_deg = 0;
+  int32_t *rp = nullptr;   // device row_ptr[n+1]
+  int32_t *col = nullptr;  // device col[nnz]
+};
+
+// Kernel families timed separately when profiling is on.
+enum Family {
+  F_DRAW = 0,
+  F_INIT,
+  F_FWD,
+  F_BWD,
+  F_SCAN,
+  F_PAIR,
+  F_MISC,
+  F_PFWD,
+  F_PBWD,
+  F_NFAM
+};
+extern const char *kFamilyName[F_NFAM];
+
+// Where the backward pass of a batch writes its results.
+struct Sink {
+  const int32_t *tslot = nullptr;  // [n] target slot of a vertex or -1 (may be null)
+  double *tdelta = nullptr;        // [T][64] delta of slot j for lane t (lane-minor rows)
+  Acc *acc = nullptr;              // [n] exact all-vertex sum of delta over lanes (may be null)
+  double *delta_lm = nullptr;      // [n][64] full per-lane delta (may be null)
+};
+
+struct Workspace {
+  DevBuf lm;       // [lcap][n] u64 level masks
+  int32_t lcap = 0;
+  DevBuf visited;  // [n] u64
+  DevBuf sigma;    // [n][64] u64 sigma, overwritten by coef (double) in the backward
+  DevBuf active;   // [lcap+2] u64 OR of level masks; [0..] per level
+  DevBuf enable;   // u64 lane enable mask
+  DevBuf sources;  // [64] i32
+  DevBuf targets;  // [64] i32 pair destinations
+  DevBuf pair_d;   // [64] i32 d(s,t) of pair lanes
+  DevBuf pair_sig; // [64] u64 sigma_st of pair lanes
+  DevBuf err;      // u32 error bits
+  DevBuf cnt;      // u64[2]: shortest-path DAG triples, reached (vertex, lane) pairs
+  DevBuf acc;      // [n] Acc
+  DevBuf tslot;    // [n] i32
+  DevBuf tdelta;   // [T][64] f64
+  DevBuf scan;     // stop-scan state
+  DevBuf misc;     // scratch
+  DevBuf misc2;
+  DevBuf delta_lm; // [n][64] f64
+  // plain single-source engine
+  DevBuf p_dist, p_sigma, p_coef, p_queue, p_ctr;
+  void *pinned = nullptr;  // 4 KiB pinned host staging
+};
+
+}  // namespace bcg
+
+struct bc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int32_t batch_width = 0;
+  std::recursive_mutex mu;
+  std::string err = "no error";
+  std::map<bc_graph, bcg::Graph> graphs;
+  bc_graph next_handle = 1;
+  bcg::Workspace ws;
+  // accounting
+  int64_t launches = 0, samples = 0, batches = 0;
+  bool profiling = false;
+  int64_t fam_launches[bcg::F_NFAM] = {};
+  double fam_ms[bcg::F_NFAM] = {};
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending_events;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace bcg {
+
+// Launch accounting: call before and after each kernel launch.
+struct LaunchScope {
+  bc_ctx *ctx;
+  int fam;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LaunchScope(bc_ctx *c, int f);
+  ~LaunchScope();
+};
+void resolve_events(bc_ctx *ctx);  // after a stream sync
+
+const Graph &get_graph(bc_ctx *ctx, bc_graph g);
+void sync(bc_ctx *ctx);
+unsigned read_and_clear_err(bc_ctx *ctx);
+void raise_err_bits(unsigned bits);
+
+// ---- lane-batched engine (64 lanes) ----
+// Runs the forward BFS for `count` (<= 64) sources already on the device in
+// ws.sources. Returns the deepest level reached. With `pairs`, lane i stops
+// once ws.targets[i] is discovered and its d/sigma are recorded.
+int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs);
+// Runs the backward accumulation for levels maxlevel..1 into the sink.
+void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink);
+// Copies per-lane dist/sigma of the last forward into [count][n] device arrays.
+void batch_extract(bc_ctx *ctx, const Graph &g, int count, int maxlevel, int32_t *dist,
+                   uint64_t *sigma, int64_t row_stride, int64_t lane_stride);
+void batch_ensure(bc_ctx *ctx, const Graph &g);
+
+// ---- plain single-source engine ----
+// Forward + backward for one source; outputs to a sink laid out as for lane 0.
+void plain_source(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const Sink &sink, int32_t *dist_out,
+                  uint64_t *sigma_out);
+void plain_ensure(bc_ctx *ctx, const Graph &g);
+
+}  // namespace bcg

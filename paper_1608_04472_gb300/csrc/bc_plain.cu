@@ -1,0 +1,295 @@
+// bc_plain.cu -- the plain form of the per-sample Brandes step: one source per
+// launch sequence, per-vertex state (dist int32, sigma u64, coef double).
+//
+// Forward (Sec. 3 step 1; Def. 3): level-synchronous BFS from the source with a
+// frontier queue. Small frontiers expand top-down (each frontier vertex pushes
+// sigma to undiscovered or same-level neighbours with integer atomics, which
+// are order-independent); large frontiers switch to bottom-up (every
+// undiscovered vertex sums sigma over neighbours on the frontier), following
+// Beamer's direction-optimising rule m_f > m_u / ALPHA.
+// Backward (Sec. 3 step 2; Theorem 1): levels in decreasing distance, one warp
+// per vertex summing the successors' coefficients exactly.
+#include <algorithm>
+
+#include "bc_internal.h"
+
+namespace bcg {
+
+constexpr int PTHREADS = 256;
+constexpr int64_t ALPHA = 4;
+
+struct PlainCtr {
+  int32_t qtail;
+  int32_t pad;
+  unsigned long long next_edges;
+};
+
+__global__ void k_pinit(const int32_t *__restrict__ src, const int32_t *__restrict__ rp,
+                        int32_t *__restrict__ dist, uint64_t *__restrict__ sigma,
+                        int32_t *__restrict__ queue, PlainCtr *__restrict__ ctr) {
+  const int32_t s = *src;
+  dist[s] = 0;
+  sigma[s] = 1ull;
+  queue[0] = s;
+  ctr->qtail = 1;
+  ctr->next_edges = (unsigned long long)(rp[s + 1] - rp[s]);
+}
+
+__global__ void __launch_bounds__(PTHREADS)
+k_ptd(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, const int32_t *__restrict__ queue_in,
+      int32_t qb, int32_t qe, int32_t level, int32_t *__restrict__ dist, uint64_t *__restrict__ sigma,
+      int32_t *__restrict__ queue_out, PlainCtr *__restrict__ ctr, unsigned *__restrict__ err,
+      unsigned long long *__restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned e = 0u;
+  unsigned long long edges = 0ull, tri = 0ull, rch = 0ull;
+  for (int i = qb + warp; i < qe; i += nwarps) {
+    const int32_t w = queue_in[i];
+    const uint64_t sw = sigma[w];
+    const int beg = rp[w], end = rp[w + 1];
+    for (int base = beg; base < end; base += 32) {
+      const int j = base + lane;
+      bool won = false;
+      int32_t v = 0;
+      if (j < end) {
+        v = col[j];
+        const int32_t old = atomicCAS(&dist[v], -1, level + 1);
+        won = (old == -1);
+        if (won || old == level + 1) {
+          const unsigned long long o = atomicAdd((unsigned long long *)&sigma[v], (unsigned long long)sw);
+          if (o + sw < o) e |= ERR_SIGMA_OVERFLOW;
+          ++tri;
+        }
+      }
+      const unsigned bal = __ballot_sync(FULL, won);
+      if (bal) {
+        int base_pos = 0;
+        if (lane == 0) base_pos = atomicAdd(&ctr->qtail, __popc(bal));
+        base_pos = __shfl_sync(FULL, base_pos, 0);
+        if (won) {
+          queue_out[base_pos + __popc(bal & ((1u << lane) - 1u))] = v;
+          edges += (unsigned long long)(rp[v + 1] - rp[v]);
+          ++rch;
+        }
+      }
+    }
+  }
+  edges = __reduce_add_sync(FULL, (unsigned)edges);  // per-warp edge totals stay < 2^32
+  if (lane == 0 && edges) atomicAdd(&ctr->next_edges, edges);
+  if (tri) atomicAdd(cnt, tri);
+  if (rch) atomicAdd(cnt + 1, rch);
+  if (e) atomicOr(err, e);
+}
+
+__global__ void __launch_bounds__(PTHREADS)
+k_pbu(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t level,
+      int32_t *__restrict__ dist, uint64_t *__restrict__ sigma, int32_t *__restrict__ queue_out,
+      PlainCtr *__restrict__ ctr, unsigned *__restrict__ err, unsigned long long *__restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned e = 0u;
+  unsigned long long edges = 0ull, tri = 0ull, rch = 0ull;
+  for (int32_t v = warp; v < n; v += nwarps) {
+    if (dist[v] != -1) continue;
+    const int beg = rp[v], end = rp[v + 1];
+    uint64_t s = 0ull;
+    for (int j = beg + lane; j < end; j += 32) {
+      const int32_t w = col[j];
+      if (dist[w] == level) {
+        const uint64_t x = sigma[w];
+        const uint64_t t = s + x;
+        if (t < s) e |= ERR_SIGMA_OVERFLOW;
+        s = t;
+        ++tri;
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const uint64_t o = __shfl_xor_sync(FULL, s, off);
+      const uint64_t t = s + o;
+      if (t < s) e |= ERR_SIGMA_OVERFLOW;
+      s = t;
+    }
+    if (s != 0ull && lane == 0) {
+      dist[v] = level + 1;
+      sigma[v] = s;
+      const int pos = atomicAdd(&ctr->qtail, 1);
+      queue_out[pos] = v;
+      edges += (unsigned long long)(end - beg);
+      ++rch;
+    }
+  }
+  if (lane == 0 && edges) atomicAdd(&ctr->next_edges, edges);
+  if (tri) atomicAdd(cnt, tri);
+  if (lane == 0 && rch) atomicAdd(cnt + 1, rch);
+  if (e) atomicOr(err, e);
+}
+
+__global__ void __launch_bounds__(PTHREADS)
+k_pbwd(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, const int32_t *__restrict__ queue,
+       int32_t qb, int32_t qe, int32_t level, const int32_t *__restrict__ dist,
+       const uint64_t *__restrict__ sigma, double *__restrict__ coef, Sink sink,
+       unsigned *__restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned e = 0u;
+  for (int i = qb + warp; i < qe; i += nwarps) {
+    const int32_t v = queue[i];
+    const int beg = rp[v], end = rp[v + 1];
+    Acc a = acc_zero();
+    for (int j = beg + lane; j < end; j += 32) {
+      const int32_t w = col[j];
+      if (dist[w] == level + 1) acc_add(a, coef[w], e);  // v in P_s(w)
+    }
+    a = acc_warp_sum(a);
+    if (lane == 0) {
+      const uint64_t sg = sigma[v];
+      const double d = __dmul_rn(sigma_to_double(sg), acc_round(a));
+      coef[v] = coef_of(d, sg);
+      if (sink.delta_lm) sink.delta_lm[(size_t)v * 64] = d;
+      if (sink.tslot) {
+        const int32_t slot = sink.tslot[v];
+        if (slot >= 0) sink.tdelta[(size_t)slot * 64] = d;
+      }
+      if (sink.acc) {
+        Acc cur = sink.acc[v];
+        acc_add(cur, d, e);
+        sink.acc[v] = cur;
+      }
+    }
+  }
+  if (e) atomicOr(err, e);
+}
+
+// Pair lane of the plain path: records d(s,t), sigma_st once t is discovered.
+__global__ void k_pplain_pair(const int32_t *__restrict__ dest, const int32_t *__restrict__ dist,
+                              const uint64_t *__restrict__ sigma, int32_t *__restrict__ pair_d,
+                              uint64_t *__restrict__ pair_sig) {
+  const int32_t t = *dest;
+  pair_d[0] = dist[t];
+  pair_sig[0] = dist[t] >= 0 ? sigma[t] : 0ull;
+}
+
+static int plain_blocks() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  return sms * 8;
+}
+
+void plain_ensure(bc_ctx *ctx, const Graph &g) {
+  Workspace &ws = ctx->ws;
+  const size_t n = (size_t)g.n;
+  ws.p_dist.ensure(n * 4);
+  ws.p_sigma.ensure(n * 8);
+  ws.p_coef.ensure(n * 8);
+  ws.p_queue.ensure(n * 4);
+  ws.p_ctr.ensure(sizeof(PlainCtr));
+}
+
+// Forward pass; returns the deepest non-empty level and fills level offsets.
+// With dest != null the traversal stops after the level that discovers *dest.
+static int plain_forward(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dest,
+                         std::vector<int32_t> &offs) {
+  Workspace &ws = ctx->ws;
+  plain_ensure(ctx, g);
+  cudaStream_t st = ctx->stream;
+  const size_t n = (size_t)g.n;
+  int32_t *dist = ws.p_dist.as<int32_t>();
+  uint64_t *sigma = ws.p_sigma.as<uint64_t>();
+  int32_t *queue = ws.p_queue.as<int32_t>();
+  PlainCtr *ctr = ws.p_ctr.as<PlainCtr>();
+  BCG_CUDA(cudaMemsetAsync(dist, 0xFF, n * 4, st));
+  BCG_CUDA(cudaMemsetAsync(sigma, 0, n * 8, st));
+  {
+    LaunchScope ls(ctx, F_INIT);
+    k_pinit<<<1, 1, 0, st>>>(d_src, g.rp, dist, sigma, queue, ctr);
+  }
+  ctx->samples += 1;
+  ctx->batches += 1;
+  offs.assign(1, 0);
+  int32_t qb = 0, qe = 1;
+  int64_t explored_edges = 0;
+  PlainCtr *h = static_cast<PlainCtr *>(ctx->ws.pinned);
+  BCG_CUDA(cudaMemcpyAsync(h, ctr, sizeof(PlainCtr), cudaMemcpyDeviceToHost, st));
+  BCG_CUDA(cudaGetLastError());
+  BCG_CUDA(cudaStreamSynchronize(st));
+  int64_t frontier_edges = (int64_t)h->next_edges;
+  const int blocks = plain_blocks();
+  int level = 0;
+  for (;;) {
+    offs.push_back(qe);
+    explored_edges += frontier_edges;
+    const int64_t unexplored = g.nnz - explored_edges;
+    BCG_CUDA(cudaMemsetAsync(&ctr->next_edges, 0, sizeof(unsigned long long), st));
+    if (frontier_edges * ALPHA > unexplored) {
+      LaunchScope ls(ctx, F_PFWD);
+      k_pbu<<<blocks, PTHREADS, 0, st>>>(g.n, g.rp, g.col, level, dist, sigma, queue, ctr, ws.err.as<unsigned>(),
+                                         ws.cnt.as<unsigned long long>());
+    } else {
+      LaunchScope ls(ctx, F_PFWD);
+      const int nb = std::max(1, std::min(blocks, (qe - qb + 7) / 8));
+      k_ptd<<<nb, PTHREADS, 0, st>>>(g.rp, g.col, queue, qb, qe, level, dist, sigma, queue, ctr,
+                                     ws.err.as<unsigned>(), ws.cnt.as<unsigned long long>());
+    }
+    if (d_dest) {
+      LaunchScope ls(ctx, F_PAIR);
+      k_pplain_pair<<<1, 1, 0, st>>>(d_dest, dist, sigma, ws.pair_d.as<int32_t>(), ws.pair_sig.as<uint64_t>());
+      BCG_CUDA(cudaMemcpyAsync(h + 1, ws.pair_d.p, 4, cudaMemcpyDeviceToHost, st));
+    }
+    BCG_CUDA(cudaMemcpyAsync(h, ctr, sizeof(PlainCtr), cudaMemcpyDeviceToHost, st));
+    BCG_CUDA(cudaGetLastError());
+    BCG_CUDA(cudaStreamSynchronize(st));
+    const int32_t ntail = h->qtail;
+    frontier_edges = (int64_t)h->next_edges;
+    if (d_dest && reinterpret_cast<int32_t *>(h + 1)[0] >= 0) {
+      offs.push_back(ntail);
+      return level + 1;
+    }
+    if (ntail == qe) return level;  // no new vertices: deepest level is `level`
+    qb = qe;
+    qe = ntail;
+    ++level;
+  }
+}
+
+void plain_source(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const Sink &sink, int32_t *dist_out,
+                  uint64_t *sigma_out) {
+  std::vector<int32_t> offs;
+  const int maxlevel = plain_forward(ctx, g, d_src, nullptr, offs);
+  Workspace &ws = ctx->ws;
+  cudaStream_t st = ctx->stream;
+  const size_t n = (size_t)g.n;
+  if (dist_out) BCG_CUDA(cudaMemcpyAsync(dist_out, ws.p_dist.p, n * 4, cudaMemcpyDeviceToDevice, st));
+  if (sigma_out) BCG_CUDA(cudaMemcpyAsync(sigma_out, ws.p_sigma.p, n * 8, cudaMemcpyDeviceToDevice, st));
+  const int blocks = plain_blocks();
+  for (int l = maxlevel; l >= 1; --l) {
+    const int32_t qb = offs[l], qe = offs[l + 1];
+    if (qe <= qb) continue;
+    LaunchScope ls(ctx, F_PBWD);
+    const int nb = std::max(1, std::min(blocks, (qe - qb + 7) / 8));
+    k_pbwd<<<nb, PTHREADS, 0, st>>>(g.rp, g.col, ws.p_queue.as<int32_t>(), qb, qe, l, ws.p_dist.as<int32_t>(),
+                                    ws.p_sigma.as<uint64_t>(), ws.p_coef.as<double>(), sink,
+                                    ws.err.as<unsigned>());
+  }
+}
+
+// Plain pair lane: BFS from *d_src truncated at the level that reaches *d_dest;
+// leaves d(s,t) and sigma_st in ws.pair_d[0], ws.pair_sig[0].
+void plain_pair(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dest) {
+  std::vector<int32_t> offs;
+  plain_forward(ctx, g, d_src, d_dest, offs);
+  LaunchScope ls(ctx, F_PAIR);
+  k_pplain_pair<<<1, 1, 0, ctx->stream>>>(d_dest, ctx->ws.p_dist.as<int32_t>(), ctx->ws.p_sigma.as<uint64_t>(),
+                                          ctx->ws.pair_d.as<int32_t>(), ctx->ws.pair_sig.as<uint64_t>());
+}
+
+}  // namespace bcg
