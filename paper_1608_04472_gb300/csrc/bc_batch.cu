@@ -26,8 +26,10 @@
 
 namespace bcg {
 
-constexpr int HEAVY = 2048;
-constexpr int SEG = 2048;
+constexpr int HEAVY = 256;   // vertices above this degree are split into segments
+constexpr int SEG = 256;     // neighbours per heavy segment
+constexpr int GRAB = 16;     // vertices taken per work-queue grab
+constexpr int UNR = 4;       // neighbours gathered per unrolled step
 constexpr int FWD_THREADS = 256;
 
 __device__ __forceinline__ uint64_t warp_or64(uint64_t x) {
@@ -43,6 +45,28 @@ __device__ __forceinline__ void block_or_to(uint64_t x, uint64_t *dst) {
   if ((threadIdx.x & 31) == 0 && x) atomicOr(&s_or, (unsigned long long)x);
   __syncthreads();
   if (threadIdx.x == 0 && s_or) atomicOr((unsigned long long *)dst, s_or);
+}
+
+
+// Dynamic work distribution: a warp takes GRAB consecutive items per atomic.
+__device__ __forceinline__ int grab(unsigned *wq) {
+  int base = 0;
+  if ((threadIdx.x & 31) == 0) base = (int)atomicAdd(wq, (unsigned)GRAB);
+  return __shfl_sync(FULL, base, 0);
+}
+
+// Takes up to UNR neighbours with a non-empty lane mask from the warp ballot
+// `bal` (lowest CSR positions first); every lane receives (mask, vertex).
+__device__ __forceinline__ void take(unsigned &bal, uint64_t m, int32_t w, uint64_t (&mk)[UNR],
+                                     int32_t (&wk)[UNR]) {
+#pragma unroll
+  for (int k = 0; k < UNR; ++k) {
+    const int src = bal ? (__ffs(bal) - 1) : 0;
+    const uint64_t mm = __shfl_sync(FULL, m, src);
+    wk[k] = __shfl_sync(FULL, w, src);
+    mk[k] = bal ? mm : 0ull;
+    bal &= bal - 1u;
+  }
 }
 
 // ------------------------------------------------------------------ init --
@@ -82,7 +106,7 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
             uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
             const uint64_t *__restrict__ active_prev, const uint64_t *__restrict__ enable,
             uint64_t *__restrict__ active_cur, unsigned *__restrict__ err,
-            unsigned long long *__restrict__ cnt) {
+            unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -90,7 +114,8 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
   uint64_t any_new = 0ull;
   unsigned long long tri = 0ull, rch = 0ull;
   unsigned e = 0u;
-  for (int v = warp; v < n; v += nwarps) {
+  for (int base = grab(wq); base < n; base = grab(wq))
+  for (int v = base; v < min(base + GRAB, n); ++v) {
     const int beg = rp[v], end = rp[v + 1];
     const uint64_t vis = visited[v];
     const uint64_t pend = ~vis & act;
@@ -108,23 +133,25 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
         newm |= m;
         unsigned bal = __ballot_sync(FULL, m != 0ull);
         while (bal) {
-          const int src = __ffs(bal) - 1;
-          bal &= bal - 1u;
-          const uint64_t mj = __shfl_sync(FULL, m, src);
-          const int32_t wj = __shfl_sync(FULL, w, src);
-          tri += (unsigned long long)__popcll((long long)mj);
-          const uint64_t *row = sigma + (size_t)wj * 64;
-          if ((mj >> lane) & 1ull) {
-            const uint64_t x = row[lane];
-            const uint64_t t = s0 + x;
-            if (t < s0) e |= ERR_SIGMA_OVERFLOW;
-            s0 = t;
+          uint64_t mk[UNR];
+          int32_t wk[UNR];
+          take(bal, m, w, mk, wk);
+          uint64_t x0[UNR], x1[UNR];
+#pragma unroll
+          for (int k = 0; k < UNR; ++k) {
+            const uint64_t *row = sigma + (size_t)wk[k] * 64;
+            x0[k] = ((mk[k] >> lane) & 1ull) ? row[lane] : 0ull;
+            x1[k] = ((mk[k] >> (lane + 32)) & 1ull) ? row[lane + 32] : 0ull;
+            tri += (unsigned long long)__popcll((long long)mk[k]);
           }
-          if ((mj >> (lane + 32)) & 1ull) {
-            const uint64_t x = row[lane + 32];
-            const uint64_t t = s1 + x;
-            if (t < s1) e |= ERR_SIGMA_OVERFLOW;
-            s1 = t;
+#pragma unroll
+          for (int k = 0; k < UNR; ++k) {
+            const uint64_t t0 = s0 + x0[k];
+            if (t0 < s0) e |= ERR_SIGMA_OVERFLOW;
+            s0 = t0;
+            const uint64_t t1 = s1 + x1[k];
+            if (t1 < s1) e |= ERR_SIGMA_OVERFLOW;
+            s1 = t1;
           }
         }
       }
@@ -178,21 +205,25 @@ k_fwd_heavy(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restri
       newm |= m;
       unsigned bal = __ballot_sync(FULL, m != 0ull);
       while (bal) {
-        const int src = __ffs(bal) - 1;
-        bal &= bal - 1u;
-        const uint64_t mj = __shfl_sync(FULL, m, src);
-        const int32_t wj = __shfl_sync(FULL, w, src);
-        tri += (unsigned long long)__popcll((long long)mj);
-        const uint64_t *row = sigma + (size_t)wj * 64;
-        if ((mj >> lane) & 1ull) {
-          const uint64_t t = s0 + row[lane];
-          if (t < s0) e |= ERR_SIGMA_OVERFLOW;
-          s0 = t;
+        uint64_t mk[UNR];
+        int32_t wk[UNR];
+        take(bal, m, w, mk, wk);
+        uint64_t x0[UNR], x1[UNR];
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+          const uint64_t *row = sigma + (size_t)wk[k] * 64;
+          x0[k] = ((mk[k] >> lane) & 1ull) ? row[lane] : 0ull;
+          x1[k] = ((mk[k] >> (lane + 32)) & 1ull) ? row[lane + 32] : 0ull;
+          tri += (unsigned long long)__popcll((long long)mk[k]);
         }
-        if ((mj >> (lane + 32)) & 1ull) {
-          const uint64_t t = s1 + row[lane + 32];
-          if (t < s1) e |= ERR_SIGMA_OVERFLOW;
-          s1 = t;
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+          const uint64_t t0 = s0 + x0[k];
+          if (t0 < s0) e |= ERR_SIGMA_OVERFLOW;
+          s0 = t0;
+          const uint64_t t1 = s1 + x1[k];
+          if (t1 < s1) e |= ERR_SIGMA_OVERFLOW;
+          s1 = t1;
         }
       }
     }
@@ -305,12 +336,13 @@ __device__ __forceinline__ void bwd_finalize(int32_t v, uint64_t lanes, const Ac
 __global__ void __launch_bounds__(FWD_THREADS)
 k_bwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
             const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
-            uint64_t *__restrict__ sigma, Sink sink, unsigned *__restrict__ err) {
+            uint64_t *__restrict__ sigma, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   unsigned e = 0u;
-  for (int v = warp; v < n; v += nwarps) {
+  for (int base = grab(wq); base < n; base = grab(wq))
+  for (int v = base; v < min(base + GRAB, n); ++v) {
     const uint64_t lanes = lm_cur[v];
     if (!lanes) continue;
     const int beg = rp[v], end = rp[v + 1];
@@ -326,13 +358,21 @@ k_bwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
       }
       unsigned bal = __ballot_sync(FULL, m != 0ull);
       while (bal) {
-        const int src = __ffs(bal) - 1;
-        bal &= bal - 1u;
-        const uint64_t mj = __shfl_sync(FULL, m, src);
-        const int32_t wj = __shfl_sync(FULL, w, src);
-        const uint64_t *row = sigma + (size_t)wj * 64;
-        if ((mj >> lane) & 1ull) acc_add(a0, __longlong_as_double((long long)row[lane]), e);
-        if ((mj >> (lane + 32)) & 1ull) acc_add(a1, __longlong_as_double((long long)row[lane + 32]), e);
+        uint64_t mk[UNR];
+        int32_t wk[UNR];
+        take(bal, m, w, mk, wk);
+        uint64_t x0[UNR], x1[UNR];
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+          const uint64_t *row = sigma + (size_t)wk[k] * 64;
+          x0[k] = ((mk[k] >> lane) & 1ull) ? row[lane] : 0ull;
+          x1[k] = ((mk[k] >> (lane + 32)) & 1ull) ? row[lane + 32] : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+          acc_add(a0, __longlong_as_double((long long)x0[k]), e);
+          acc_add(a1, __longlong_as_double((long long)x1[k]), e);
+        }
       }
     }
     bwd_finalize(v, lanes, a0, a1, sigma, sink, e);
@@ -366,13 +406,21 @@ k_bwd_heavy_seg(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__re
       }
       unsigned bal = __ballot_sync(FULL, m != 0ull);
       while (bal) {
-        const int src = __ffs(bal) - 1;
-        bal &= bal - 1u;
-        const uint64_t mj = __shfl_sync(FULL, m, src);
-        const int32_t wj = __shfl_sync(FULL, w, src);
-        const uint64_t *row = sigma + (size_t)wj * 64;
-        if ((mj >> lane) & 1ull) acc_add(a0, __longlong_as_double((long long)row[lane]), e);
-        if ((mj >> (lane + 32)) & 1ull) acc_add(a1, __longlong_as_double((long long)row[lane + 32]), e);
+        uint64_t mk[UNR];
+        int32_t wk[UNR];
+        take(bal, m, w, mk, wk);
+        uint64_t x0[UNR], x1[UNR];
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+          const uint64_t *row = sigma + (size_t)wk[k] * 64;
+          x0[k] = ((mk[k] >> lane) & 1ull) ? row[lane] : 0ull;
+          x1[k] = ((mk[k] >> (lane + 32)) & 1ull) ? row[lane + 32] : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+          acc_add(a0, __longlong_as_double((long long)x0[k]), e);
+          acc_add(a1, __longlong_as_double((long long)x1[k]), e);
+        }
       }
     }
     part[(size_t)s * 64 + lane] = a0;
@@ -505,6 +553,7 @@ void batch_ensure(bc_ctx *ctx, const Graph &g) {
   ws.visited.ensure(n * 8);
   ws.sigma.ensure(n * 64 * 8);
   ws.active.ensure((size_t)(ws.lcap + 2) * 8);
+  ws.wq.ensure((size_t)(ws.lcap + 2) * 2 * 4);
   heavy_meta(ctx, g);
 }
 
@@ -524,6 +573,7 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs) {
   BCG_CUDA(cudaMemsetAsync(ws.lm.p, 0, n * 8, st));
   BCG_CUDA(cudaMemsetAsync(ws.visited.p, 0, n * 8, st));
   BCG_CUDA(cudaMemsetAsync(ws.active.p, 0, (size_t)(ws.lcap + 2) * 8, st));
+  BCG_CUDA(cudaMemsetAsync(ws.wq.p, 0, ws.wq.bytes, st));
   {
     LaunchScope ls(ctx, F_INIT);
     if (hm.nh) k_zero_heavy_rows<<<hm.nh, 64, 0, st>>>(hm.nh, hm.heavy.as<int32_t>(), ws.sigma.as<uint64_t>());
@@ -544,6 +594,8 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs) {
       const int ncap = ws.lcap * 2;
       ws.lm.grow_keep((size_t)ncap * n * 8, st);
       ws.active.grow_keep((size_t)(ncap + 2) * 8, st);
+      ws.wq.grow_keep((size_t)(ncap + 2) * 2 * 4, st);
+      BCG_CUDA(cudaMemsetAsync(ws.wq.as<unsigned>() + 2 * (ws.lcap + 2), 0, (size_t)(ncap - ws.lcap) * 2 * 4, st));
       BCG_CUDA(cudaMemsetAsync(ws.active.as<uint64_t>() + ws.lcap + 2, 0, (size_t)(ncap - ws.lcap) * 8, st));
       ws.lcap = ncap;
     }
@@ -554,7 +606,7 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs) {
       k_fwd_light<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
                                                  ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(), act + l,
                                                  ws.enable.as<uint64_t>(), act + l + 1, ws.err.as<unsigned>(),
-                                                 ws.cnt.as<unsigned long long>());
+                                                 ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 2 * l);
     }
     if (hm.nseg) {
       LaunchScope ls(ctx, F_FWD);
@@ -595,7 +647,8 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink)
     {
       LaunchScope ls(ctx, F_BWD);
       k_bwd_light<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
-                                                 ws.sigma.as<uint64_t>(), sink, ws.err.as<unsigned>());
+                                                 ws.sigma.as<uint64_t>(), sink, ws.err.as<unsigned>(),
+                                                 ws.wq.as<unsigned>() + 2 * l + 1);
     }
     if (hm.nseg) {
       LaunchScope ls(ctx, F_BWD);

@@ -632,7 +632,7 @@ void bc_destroy(bc_ctx *ctx) {
     }
     ctx->graphs.clear();
     Workspace &ws = ctx->ws;
-    for (DevBuf *b : {&ws.lm, &ws.visited, &ws.sigma, &ws.active, &ws.enable, &ws.sources, &ws.targets, &ws.pair_d,
+    for (DevBuf *b : {&ws.lm, &ws.visited, &ws.sigma, &ws.active, &ws.wq, &ws.enable, &ws.sources, &ws.targets, &ws.pair_d,
                       &ws.pair_sig, &ws.err, &ws.cnt, &ws.acc, &ws.tslot, &ws.tdelta, &ws.scan, &ws.misc, &ws.misc2,
                       &ws.delta_lm, &ws.p_dist, &ws.p_sigma, &ws.p_coef, &ws.p_queue, &ws.p_ctr})
       b->release();

@@ -74,6 +74,7 @@ struct Workspace {
   DevBuf visited;  // [n] u64
   DevBuf sigma;    // [n][64] u64 sigma, overwritten by coef (double) in the backward
   DevBuf active;   // [lcap+2] u64 OR of level masks; [0..] per level
+  DevBuf wq;       // [2*(lcap+2)] u32 work-queue counters (forward / backward per level)
   DevBuf enable;   // u64 lane enable mask
   DevBuf sources;  // [64] i32
   DevBuf targets;  // [64] i32 pair destinations
