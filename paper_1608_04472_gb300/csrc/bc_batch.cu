@@ -38,6 +38,15 @@ __device__ __forceinline__ uint64_t warp_or64(uint64_t x) {
   return ((uint64_t)hi << 32) | lo;
 }
 
+__device__ __forceinline__ uint64_t warp_max64(uint64_t x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const uint64_t o = __shfl_xor_sync(FULL, x, off);
+    x = o > x ? o : x;
+  }
+  return x;
+}
+
 __device__ __forceinline__ void block_or_to(uint64_t x, uint64_t *dst) {
   __shared__ unsigned long long s_or;
   if (threadIdx.x == 0) s_or = 0ull;
@@ -80,7 +89,10 @@ __global__ void k_batch_init(int count, const int32_t *__restrict__ sources,
     pair_d[t] = -1;
     pair_sig[t] = 0ull;
   }
-  if (t == 0) *enable = (count >= 64) ? ~0ull : ((1ull << count) - 1ull);
+  if (t == 0) {
+    enable[0] = (count >= 64) ? ~0ull : ((1ull << count) - 1ull);
+    enable[2] = 1ull;  // largest sigma of the batch (sources have sigma 1)
+  }
   __syncthreads();
   if (t < count) {
     const int32_t s = sources[t];
@@ -104,14 +116,14 @@ __global__ void __launch_bounds__(FWD_THREADS)
 k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
             const uint64_t *__restrict__ lm_prev, uint64_t *__restrict__ lm_cur,
             uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
-            const uint64_t *__restrict__ active_prev, const uint64_t *__restrict__ enable,
+            const uint64_t *__restrict__ active_prev, uint64_t *__restrict__ enable,
             uint64_t *__restrict__ active_cur, unsigned *__restrict__ err,
             unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint64_t act = *active_prev & *enable;
-  uint64_t any_new = 0ull;
+  uint64_t any_new = 0ull, smax = 0ull;
   unsigned long long tri = 0ull, rch = 0ull;
   unsigned e = 0u;
   for (int base = grab(wq); base < n; base = grab(wq))
@@ -156,8 +168,14 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
         }
       }
       newm = warp_or64(newm);
-      if ((newm >> lane) & 1ull) sigma[(size_t)v * 64 + lane] = s0;
-      if ((newm >> (lane + 32)) & 1ull) sigma[(size_t)v * 64 + 32 + lane] = s1;
+      if ((newm >> lane) & 1ull) {
+        sigma[(size_t)v * 64 + lane] = s0;
+        smax = s0 > smax ? s0 : smax;
+      }
+      if ((newm >> (lane + 32)) & 1ull) {
+        sigma[(size_t)v * 64 + 32 + lane] = s1;
+        smax = s1 > smax ? s1 : smax;
+      }
     }
     if (lane == 0) {
       lm_cur[v] = newm;
@@ -171,6 +189,8 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
     atomicAdd(cnt, tri);
     atomicAdd(cnt + 1, rch);
   }
+  smax = warp_max64(smax);
+  if (lane == 0 && smax > 1ull) atomicMax((unsigned long long *)(enable + 2), (unsigned long long)smax);
   block_or_to(any_new, active_cur);
 }
 
@@ -246,7 +266,8 @@ k_fwd_heavy(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restri
 
 __global__ void k_fwd_heavy_fin(int nh, const int32_t *__restrict__ heavy,
                                 const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ visited,
-                                uint64_t *__restrict__ active_cur, unsigned long long *__restrict__ cnt) {
+                                uint64_t *__restrict__ active_cur, unsigned long long *__restrict__ cnt,
+                                const uint64_t *__restrict__ sigma, uint64_t *__restrict__ enable) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   uint64_t newm = 0ull;
   if (h < nh) {
@@ -255,6 +276,14 @@ __global__ void k_fwd_heavy_fin(int nh, const int32_t *__restrict__ heavy,
     if (newm) {
       visited[v] |= newm;
       atomicAdd(cnt + 1, (unsigned long long)__popcll((long long)newm));
+      uint64_t mx = 0ull, m = newm;
+      while (m) {
+        const int t = __ffsll((long long)m) - 1;
+        m &= m - 1ull;
+        const uint64_t x = sigma[(size_t)v * 64 + t];
+        mx = x > mx ? x : mx;
+      }
+      atomicMax((unsigned long long *)(enable + 2), (unsigned long long)mx);
     }
   }
   newm = warp_or64(newm);
@@ -292,95 +321,184 @@ __global__ void k_pair_check(int count, int level, const int32_t *__restrict__ d
 }
 
 // -------------------------------------------------------------- backward --
-// Finalises lanes of v at this level from per-lane exact sums, writes coef over
-// sigma and the requested outputs. Called by a full warp; lane handles t, t+32.
-__device__ __forceinline__ void bwd_finalize(int32_t v, uint64_t lanes, const Acc &a0, const Acc &a1,
-                                             uint64_t *__restrict__ sigma, const Sink &sink, unsigned &e) {
+// Accumulator policies for the successor sums: the 128-bit window (used when
+// the batch's largest sigma is <= 2^44) and the general 192-bit one.
+struct NarrowAcc {
+  using A = Acc2;
+  static __device__ __forceinline__ A zero() { return acc2_zero(); }
+  static __device__ __forceinline__ void add(A &a, double x, unsigned &e) { acc2_add(a, x, e); }
+  static __device__ __forceinline__ Acc widen(const A &a) { return acc2_widen(a); }
+};
+struct WideAcc {
+  using A = Acc;
+  static __device__ __forceinline__ A zero() { return acc_zero(); }
+  static __device__ __forceinline__ void add(A &a, double x, unsigned &e) { acc_add(a, x, e); }
+  static __device__ __forceinline__ Acc widen(const A &a) { return a; }
+};
+
+// Finished (vertex, lane) pairs wait in a per-warp ring in shared memory until
+// 32 of them fill one warp-wide round of double arithmetic. The FP64 pipe is
+// charged per warp instruction whatever the number of active lanes, so the
+// rounds keep it busy with useful lanes only.
+constexpr int RING = 128;
+struct Ring {
+  int32_t v[RING];
+  int32_t t[RING];
+  double sum[RING];
+  uint64_t sig[RING];
+};
+
+// delta = RN(RN(sigma) * sum); a power-of-two sigma scales exactly (integer
+// exponent add), everything else is one multiply.
+__device__ __forceinline__ double delta_of(double sum, uint64_t sg) {
+  if ((sg & (sg - 1ull)) == 0ull) {
+    const uint64_t b = (uint64_t)__double_as_longlong(sum);
+    if (b == 0ull) return 0.0;
+    const int k = 63 - __clzll((long long)sg);
+    return __longlong_as_double((long long)(b + ((uint64_t)k << 52)));
+  }
+  return __dmul_rn(sigma_to_double(sg), sum);
+}
+
+// coef = RN(RN(1 + delta) / RN(sigma)); power-of-two sigma: exact exponent shift.
+__device__ __forceinline__ double coef_round(double delta, uint64_t sg) {
+  const double x = __dadd_rn(1.0, delta);
+  if ((sg & (sg - 1ull)) == 0ull) {
+    const int k = 63 - __clzll((long long)sg);
+    return __longlong_as_double((long long)((uint64_t)__double_as_longlong(x) - ((uint64_t)k << 52)));
+  }
+  return __ddiv_rn(x, sigma_to_double(sg));
+}
+
+__device__ __forceinline__ void ring_append(Ring &R, unsigned &tail, int32_t v, uint64_t lanes, const Acc &a0,
+                                            const Acc &a1, const uint64_t *__restrict__ row) {
   const int lane = threadIdx.x & 31;
-  double d0 = 0.0, d1 = 0.0;
-  uint64_t *row = sigma + (size_t)v * 64;
-  if ((lanes >> lane) & 1ull) {
-    const uint64_t sg = row[lane];
-    d0 = __dmul_rn(sigma_to_double(sg), acc_round(a0));
-    row[lane] = (uint64_t)__double_as_longlong(coef_of(d0, sg));
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned lo = (unsigned)lanes, hi = (unsigned)(lanes >> 32);
+  if ((lo >> lane) & 1u) {
+    const unsigned pos = (tail + __popc(lo & lt)) & (RING - 1);
+    R.v[pos] = v;
+    R.t[pos] = lane;
+    R.sum[pos] = acc_round(a0);
+    R.sig[pos] = row[lane];
   }
-  if ((lanes >> (lane + 32)) & 1ull) {
-    const uint64_t sg = row[lane + 32];
-    d1 = __dmul_rn(sigma_to_double(sg), acc_round(a1));
-    row[lane + 32] = (uint64_t)__double_as_longlong(coef_of(d1, sg));
+  tail += __popc(lo);
+  if ((hi >> lane) & 1u) {
+    const unsigned pos = (tail + __popc(hi & lt)) & (RING - 1);
+    R.v[pos] = v;
+    R.t[pos] = lane + 32;
+    R.sum[pos] = acc_round(a1);
+    R.sig[pos] = row[lane + 32];
   }
-  if (sink.delta_lm) {
-    if ((lanes >> lane) & 1ull) sink.delta_lm[(size_t)v * 64 + lane] = d0;
-    if ((lanes >> (lane + 32)) & 1ull) sink.delta_lm[(size_t)v * 64 + 32 + lane] = d1;
-  }
-  if (sink.tslot) {
-    const int32_t slot = sink.tslot[v];
-    if (slot >= 0) {
-      if ((lanes >> lane) & 1ull) sink.tdelta[(size_t)slot * 64 + lane] = d0;
-      if ((lanes >> (lane + 32)) & 1ull) sink.tdelta[(size_t)slot * 64 + 32 + lane] = d1;
+  tail += __popc(hi);
+}
+
+// One warp-wide round over ring records head..head+count-1 (count <= 32).
+__device__ __forceinline__ void ring_round(Ring &R, unsigned head, int count, uint64_t *__restrict__ sigma,
+                                           const Sink &sink, unsigned &e) {
+  const int lane = threadIdx.x & 31;
+  int32_t v = -1;
+  double d = 0.0;
+  if (lane < count) {
+    const unsigned pos = (head + lane) & (RING - 1);
+    v = R.v[pos];
+    const int32_t t = R.t[pos];
+    const uint64_t sg = R.sig[pos];
+    d = delta_of(R.sum[pos], sg);
+    sigma[(size_t)v * 64 + t] = (uint64_t)__double_as_longlong(coef_round(d, sg));
+    if (sink.delta_lm) sink.delta_lm[(size_t)v * 64 + t] = d;
+    if (sink.tslot) {
+      const int32_t slot = sink.tslot[v];
+      if (slot >= 0) sink.tdelta[(size_t)slot * 64 + t] = d;
     }
   }
   if (sink.acc) {
-    Acc t = acc_zero();
-    acc_add(t, d0, e);
-    acc_add(t, d1, e);
-    t = acc_warp_sum(t);
-    if (lane == 0) {
+    // records of one vertex are consecutive: segmented exact inclusive scan
+    Acc a = acc_zero();
+    acc_add(a, d, e);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      Acc o;
+      o.w0 = __shfl_up_sync(FULL, a.w0, off);
+      o.w1 = __shfl_up_sync(FULL, a.w1, off);
+      o.w2 = __shfl_up_sync(FULL, a.w2, off);
+      const int32_t vo = __shfl_up_sync(FULL, v, off);
+      if (lane >= off && vo == v) acc_add_acc(a, o);
+    }
+    const int32_t vn = __shfl_down_sync(FULL, v, 1);
+    if (v >= 0 && (lane == 31 || vn != v)) {
       Acc cur = sink.acc[v];
-      acc_add_acc(cur, t);
+      acc_add_acc(cur, a);
       sink.acc[v] = cur;
     }
   }
 }
 
+template <class P>
+__device__ __forceinline__ void gather_successors(int beg, int end, uint64_t lanes, const uint64_t *__restrict__ col_lm,
+                                                  const int32_t *__restrict__ col, const uint64_t *__restrict__ sigma,
+                                                  typename P::A &a0, typename P::A &a1, unsigned &e) {
+  const int lane = threadIdx.x & 31;
+  for (int base = beg; base < end; base += 32) {
+    const int j = base + lane;
+    int32_t w = 0;
+    uint64_t m = 0ull;
+    if (j < end) {
+      w = col[j];
+      m = col_lm[w] & lanes;
+    }
+    unsigned bal = __ballot_sync(FULL, m != 0ull);
+    while (bal) {
+      uint64_t mk[UNR];
+      int32_t wk[UNR];
+      take(bal, m, w, mk, wk);
+      uint64_t x0[UNR], x1[UNR];
+#pragma unroll
+      for (int k = 0; k < UNR; ++k) {
+        const uint64_t *row = sigma + (size_t)wk[k] * 64;
+        x0[k] = ((mk[k] >> lane) & 1ull) ? row[lane] : 0ull;
+        x1[k] = ((mk[k] >> (lane + 32)) & 1ull) ? row[lane + 32] : 0ull;
+      }
+#pragma unroll
+      for (int k = 0; k < UNR; ++k) {
+        P::add(a0, __longlong_as_double((long long)x0[k]), e);
+        P::add(a1, __longlong_as_double((long long)x1[k]), e);
+      }
+    }
+  }
+}
+
+template <class P>
 __global__ void __launch_bounds__(FWD_THREADS)
 k_bwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
             const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
             uint64_t *__restrict__ sigma, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  __shared__ Ring rings[FWD_THREADS / 32];
+  Ring &R = rings[threadIdx.x >> 5];
+  unsigned head = 0u, tail = 0u;
   unsigned e = 0u;
   for (int base = grab(wq); base < n; base = grab(wq))
-  for (int v = base; v < min(base + GRAB, n); ++v) {
-    const uint64_t lanes = lm_cur[v];
-    if (!lanes) continue;
-    const int beg = rp[v], end = rp[v + 1];
-    if (end - beg > HEAVY) continue;
-    Acc a0 = acc_zero(), a1 = acc_zero();
-    for (int base = beg; base < end; base += 32) {
-      const int j = base + lane;
-      int32_t w = 0;
-      uint64_t m = 0ull;
-      if (j < end) {
-        w = col[j];
-        m = lm_next[w] & lanes;
-      }
-      unsigned bal = __ballot_sync(FULL, m != 0ull);
-      while (bal) {
-        uint64_t mk[UNR];
-        int32_t wk[UNR];
-        take(bal, m, w, mk, wk);
-        uint64_t x0[UNR], x1[UNR];
-#pragma unroll
-        for (int k = 0; k < UNR; ++k) {
-          const uint64_t *row = sigma + (size_t)wk[k] * 64;
-          x0[k] = ((mk[k] >> lane) & 1ull) ? row[lane] : 0ull;
-          x1[k] = ((mk[k] >> (lane + 32)) & 1ull) ? row[lane + 32] : 0ull;
-        }
-#pragma unroll
-        for (int k = 0; k < UNR; ++k) {
-          acc_add(a0, __longlong_as_double((long long)x0[k]), e);
-          acc_add(a1, __longlong_as_double((long long)x1[k]), e);
-        }
+    for (int v = base; v < min(base + GRAB, n); ++v) {
+      const uint64_t lanes = lm_cur[v];
+      if (!lanes) continue;
+      const int beg = rp[v], end = rp[v + 1];
+      if (end - beg > HEAVY) continue;
+      typename P::A a0 = P::zero(), a1 = P::zero();
+      gather_successors<P>(beg, end, lanes, lm_next, col, sigma, a0, a1, e);
+      ring_append(R, tail, v, lanes, P::widen(a0), P::widen(a1), sigma + (size_t)v * 64);
+      __syncwarp();
+      while (tail - head >= 32u) {
+        ring_round(R, head, 32, sigma, sink, e);
+        head += 32u;
+        __syncwarp();
       }
     }
-    bwd_finalize(v, lanes, a0, a1, sigma, sink, e);
-  }
+  if (tail != head) ring_round(R, head, (int)(tail - head), sigma, sink, e);
   if (e) atomicOr(err, e);
 }
 
 // Heavy vertices: one warp per segment writes 64 partial sums to part[s][64].
+template <class P>
 __global__ void __launch_bounds__(FWD_THREADS)
 k_bwd_heavy_seg(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restrict__ seg_b,
                 const int32_t *__restrict__ seg_e, const int32_t *__restrict__ col,
@@ -394,37 +512,10 @@ k_bwd_heavy_seg(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__re
     const int32_t v = seg_v[s];
     const uint64_t lanes = lm_cur[v];
     if (!lanes) continue;
-    const int beg = seg_b[s], end = seg_e[s];
-    Acc a0 = acc_zero(), a1 = acc_zero();
-    for (int base = beg; base < end; base += 32) {
-      const int j = base + lane;
-      int32_t w = 0;
-      uint64_t m = 0ull;
-      if (j < end) {
-        w = col[j];
-        m = lm_next[w] & lanes;
-      }
-      unsigned bal = __ballot_sync(FULL, m != 0ull);
-      while (bal) {
-        uint64_t mk[UNR];
-        int32_t wk[UNR];
-        take(bal, m, w, mk, wk);
-        uint64_t x0[UNR], x1[UNR];
-#pragma unroll
-        for (int k = 0; k < UNR; ++k) {
-          const uint64_t *row = sigma + (size_t)wk[k] * 64;
-          x0[k] = ((mk[k] >> lane) & 1ull) ? row[lane] : 0ull;
-          x1[k] = ((mk[k] >> (lane + 32)) & 1ull) ? row[lane + 32] : 0ull;
-        }
-#pragma unroll
-        for (int k = 0; k < UNR; ++k) {
-          acc_add(a0, __longlong_as_double((long long)x0[k]), e);
-          acc_add(a1, __longlong_as_double((long long)x1[k]), e);
-        }
-      }
-    }
-    part[(size_t)s * 64 + lane] = a0;
-    part[(size_t)s * 64 + 32 + lane] = a1;
+    typename P::A a0 = P::zero(), a1 = P::zero();
+    gather_successors<P>(seg_b[s], seg_e[s], lanes, lm_next, col, sigma, a0, a1, e);
+    part[(size_t)s * 64 + lane] = P::widen(a0);
+    part[(size_t)s * 64 + 32 + lane] = P::widen(a1);
   }
   if (e) atomicOr(err, e);
 }
@@ -433,6 +524,9 @@ __global__ void __launch_bounds__(FWD_THREADS)
 k_bwd_heavy_fin(int nh, const int32_t *__restrict__ heavy, const int32_t *__restrict__ hseg0,
                 const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ sigma,
                 const Acc *__restrict__ part, Sink sink, unsigned *__restrict__ err) {
+  __shared__ Ring rings[FWD_THREADS / 32];
+  Ring &R = rings[threadIdx.x >> 5];
+  unsigned head = 0u, tail = 0u;
   const int lane = threadIdx.x & 31;
   unsigned e = 0u;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -446,8 +540,15 @@ k_bwd_heavy_fin(int nh, const int32_t *__restrict__ heavy, const int32_t *__rest
       acc_add_acc(a0, part[(size_t)s * 64 + lane]);
       acc_add_acc(a1, part[(size_t)s * 64 + 32 + lane]);
     }
-    bwd_finalize(v, lanes, a0, a1, sigma, sink, e);
+    ring_append(R, tail, v, lanes, a0, a1, sigma + (size_t)v * 64);
+    __syncwarp();
+    while (tail - head >= 32u) {
+      ring_round(R, head, 32, sigma, sink, e);
+      head += 32u;
+      __syncwarp();
+    }
   }
+  if (tail != head) ring_round(R, head, (int)(tail - head), sigma, sink, e);
   if (e) atomicOr(err, e);
 }
 
@@ -619,7 +720,8 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs) {
       LaunchScope ls(ctx, F_FWD);
       k_fwd_heavy_fin<<<(hm.nh + 255) / 256, 256, 0, st>>>(hm.nh, hm.heavy.as<int32_t>(), lm + (size_t)(l + 1) * n,
                                                           ws.visited.as<uint64_t>(), act + l + 1,
-                                                          ws.cnt.as<unsigned long long>());
+                                                          ws.cnt.as<unsigned long long>(), ws.sigma.as<uint64_t>(),
+                                                          ws.enable.as<uint64_t>());
     }
     uint64_t cont;
     if (pairs) {
@@ -631,7 +733,10 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs) {
     } else {
       cont = read_u64(ctx, act + l + 1);
     }
-    if (!cont) return l;
+    if (!cont) {
+      ws.last_sigmax = read_u64(ctx, ws.enable.as<uint64_t>() + 2);
+      return l;
+    }
     ++l;
   }
 }
@@ -643,16 +748,23 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink)
   cudaStream_t st = ctx->stream;
   const int blocks = grid_blocks();
   uint64_t *lm = ws.lm.as<uint64_t>();
+  const bool narrow = ws.last_sigmax <= (1ull << 44);
   for (int l = maxlevel; l >= 1; --l) {
     {
       LaunchScope ls(ctx, F_BWD);
-      k_bwd_light<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
-                                                 ws.sigma.as<uint64_t>(), sink, ws.err.as<unsigned>(),
-                                                 ws.wq.as<unsigned>() + 2 * l + 1);
+      if (narrow)
+        k_bwd_light<NarrowAcc><<<blocks, FWD_THREADS, 0, st>>>(
+            g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), sink,
+            ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 2 * l + 1);
+      else
+        k_bwd_light<WideAcc><<<blocks, FWD_THREADS, 0, st>>>(
+            g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), sink,
+            ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 2 * l + 1);
     }
     if (hm.nseg) {
       LaunchScope ls(ctx, F_BWD);
-      k_bwd_heavy_seg<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
+      auto kseg = narrow ? k_bwd_heavy_seg<NarrowAcc> : k_bwd_heavy_seg<WideAcc>;
+      kseg<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
           hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
           lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), hm.part.as<Acc>(),
           ws.err.as<unsigned>());

@@ -154,6 +154,49 @@ __device__ __forceinline__ Acc acc_warp_sum(Acc a) {
   return a;
 }
 
+// A narrower exact accumulator for successor sums: 128 bits in 32-bit limbs,
+// value = (l3:l2:l1:l0) * 2^-96, holding every double in [2^-44, 2^32). When
+// sigma <= 2^44 every coefficient RN((1+delta)/sigma) is >= 2^-44, and a
+// successor sum equals delta_v/sigma_v <= n < 2^31 up to rounding, so the
+// window is never left; out-of-window values set ERR_RANGE.
+struct Acc2 {
+  uint32_t l0, l1, l2, l3;
+};
+
+__device__ __forceinline__ Acc2 acc2_zero() { return Acc2{0u, 0u, 0u, 0u}; }
+
+__device__ __forceinline__ void acc2_add4(Acc2 &a, uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3) {
+  asm("add.cc.u32 %0, %0, %4;\n\t"
+      "addc.cc.u32 %1, %1, %5;\n\t"
+      "addc.cc.u32 %2, %2, %6;\n\t"
+      "addc.u32 %3, %3, %7;"
+      : "+r"(a.l0), "+r"(a.l1), "+r"(a.l2), "+r"(a.l3)
+      : "r"(t0), "r"(t1), "r"(t2), "r"(t3));
+}
+
+__device__ __forceinline__ void acc2_add(Acc2 &a, double x, unsigned &err) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(x);
+  if (bits == 0ull) return;
+  const uint32_t hi = (uint32_t)(bits >> 32), lo = (uint32_t)bits;
+  const int p = (int)(hi >> 20) - 979;  // lowest mantissa bit, in units of 2^-96
+  if ((unsigned)p > 75u) { err |= ERR_RANGE; return; }
+  const uint32_t mh = (hi & 0x000FFFFFu) | 0x00100000u;
+  const int r = p & 31, q = p >> 5;
+  const uint32_t c0 = lo << r;
+  const uint32_t c1 = __funnelshift_l(lo, mh, r);
+  const uint32_t c2 = __funnelshift_l(mh, 0u, r);
+  const uint32_t t0 = (q == 0) ? c0 : 0u;
+  const uint32_t t1 = (q == 0) ? c1 : ((q == 1) ? c0 : 0u);
+  const uint32_t t2 = (q == 0) ? c2 : ((q == 1) ? c1 : c0);
+  const uint32_t t3 = (q == 1) ? c2 : ((q == 2) ? c1 : 0u);
+  acc2_add4(a, t0, t1, t2, t3);
+}
+
+// The same value in the 192-bit format (unit 2^-128).
+__device__ __forceinline__ Acc acc2_widen(const Acc2 &a) {
+  return Acc{(uint64_t)a.l0 << 32, (uint64_t)a.l1 | ((uint64_t)a.l2 << 32), (uint64_t)a.l3};
+}
+
 // ------------------------------------------------------ Brandes arithmetic --
 // The per-vertex step of Theorem 1 in factored form, every operation rounded
 // once: delta = RN(RN(sigma) * sum), coef = RN(RN(1 + delta) / RN(sigma)).

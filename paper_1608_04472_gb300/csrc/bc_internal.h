@@ -92,6 +92,7 @@ struct Workspace {
   // plain single-source engine
   DevBuf p_dist, p_sigma, p_coef, p_queue, p_ctr;
   void *pinned = nullptr;  // 4 KiB pinned host staging
+  uint64_t last_sigmax = ~0ull;  // largest sigma of the last batched forward pass
 };
 
 }  // namespace bcg
