@@ -42,6 +42,28 @@ WORKLOAD = "rmat_s20_ef16_bader_c5_T512_capn20_plus_uniform_k4096"
 METRIC = "Brandes samples/s (R-MAT s20, batched 64-wide)"
 
 
+def rank_qids(rank: int, steps: int, warmup: int):
+    """Query ids of one rank: (warm-up qids, timed qids). Each step uses two
+    streams (Bader, uniform); ranks never share a stream, so N ranks do N times
+    the work of one (weak scaling) with no data exchanged between them."""
+    base = 1_000_000 * (rank + 1)
+    warm = [base + 2 * i for i in range(warmup)]
+    timed = [base + 2 * (warmup + i) for i in range(steps)]
+    return warm, timed
+
+
+def reduce_over_ranks(dist, device, ms: float, samples: float, edges: float):
+    """Max of the timed region over ranks; sums of samples and edges."""
+    if dist is None:
+        return ms, samples, edges
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([samples, edges], dtype=torch.float64, device=device)
+    dist.all_reduce(u)
+    return float(t[0]), float(u[0]), float(u[1])
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -183,6 +205,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--cap", type=int, default=0,
+                    help="override the Bader cap (default n/20); for short profiling runs only")
+    ap.add_argument("--uniform-k", type=int, default=K_UNIFORM,
+                    help="override the uniform sample count; for short profiling runs only")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -202,7 +228,8 @@ def main():
 
     g = build_graph()
     n = g.n
-    cap = n // 20
+    cap = args.cap if args.cap > 0 else n // 20
+    kuni = args.uniform_k
     targets = gg.uniform_targets(n, T_TARGETS, SEED)
     ce = component_edges(g)
 
@@ -212,13 +239,12 @@ def main():
 
     def step(qid_base):
         rb = ctx.adaptive_sources(h, targets, C_BADER, cap, SEED, qid_base)
-        est = ctx.uniform_sources(h, K_UNIFORM, SEED, qid_base + 1)
+        est = ctx.uniform_sources(h, kuni, SEED, qid_base + 1)
         return rb, est
 
-    qid = 1_000_000 * (rank + 1)
-    for _ in range(args.warmup):
-        step(qid)
-        qid += 2
+    warm_qids, timed_qids = rank_qids(rank, args.steps, args.warmup)
+    for q in warm_qids:
+        step(q)
     ctx.reset_stats()
     ctx.set_profiling(True)
     if dist:
@@ -230,33 +256,23 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     kmax, qids = [], []
-    for _ in range(args.steps):
-        rb, _ = step(qid)
+    for q in timed_qids:
+        rb, _ = step(q)
         kmax.append(int(rb["k"].max()))
-        qids.append(qid)
-        qid += 2
+        qids.append(q)
+    qid = timed_qids[-1] + 2 if timed_qids else 0
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     stats = ctx.stats()
     ctx.set_profiling(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-
-    samples_local = sum(kmax) + K_UNIFORM * args.steps
+    samples_local = sum(kmax) + kuni * args.steps
     edges_local = 0.0
     for q, km in zip(qids, kmax):
         edges_local += float(ce[ctx.draw_sources(SEED, q, 0, km, n)].sum())
-        edges_local += float(ce[ctx.draw_sources(SEED, q + 1, 0, K_UNIFORM, n)].sum())
-    if dist:
-        t = torch.tensor([samples_local, edges_local], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t)
-        samples_total, edges_total = float(t[0]), float(t[1])
-    else:
-        samples_total, edges_total = float(samples_local), edges_local
+        edges_local += float(ce[ctx.draw_sources(SEED, q + 1, 0, kuni, n)].sum())
+    ms, samples_total, edges_total = reduce_over_ranks(dist, "cuda", ms, float(samples_local), edges_local)
     value = samples_total / (ms / 1e3)
 
     # roofline of the dominant kernel family (measured live over the timed region)
@@ -284,7 +300,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "graph": f"R-MAT s{SCALE} ef{EF} a{A} b{B} c{C} seed {SEED}",
                    "n": n, "nnz": g.nnz, "targets": T_TARGETS, "c": C_BADER, "cap": cap,
-                   "uniform_k": K_UNIFORM, "batch_width": 64, "parallelism": f"replicas x{world}",
+                   "uniform_k": kuni, "batch_width": 64, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (CSR 134 MB + 0.6 GB lane state); no flush"},
         "gteps": edges_total / (ms / 1e3) / 1e9,
         "samples_per_step": samples_total / args.steps,
@@ -331,8 +347,8 @@ def main():
         for _ in range(e2e_steps):
             h2 = ctx.load_graph(g.row_ptr, g.col)
             rb = ctx.adaptive_sources(h2, targets, C_BADER, cap, SEED, qid)
-            ctx.uniform_sources(h2, K_UNIFORM, SEED, qid + 1)
-            samp += int(rb["k"].max()) + K_UNIFORM
+            ctx.uniform_sources(h2, kuni, SEED, qid + 1)
+            samp += int(rb["k"].max()) + kuni
             ctx.free_graph(h2)
             qid += 2
         torch.cuda.synchronize()

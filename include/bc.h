@@ -151,6 +151,64 @@ bc_status bc_adaptive_pairs(bc_ctx *ctx, bc_graph g, const int32_t *targets, int
                             double threshold_scale, double *est, int64_t *k, double *S,
                             int32_t *stop_status);
 
+/* --------------------------------------------------------------- serving -- */
+/*
+ * Asynchronous queries with continuous batching: a context owns one worker
+ * thread that admits queries (FIFO) while the device-memory budget and the
+ * active-slot limit allow, and fills every 64-lane batch with the next draws of
+ * several active queries on the same graph (each query's lanes contiguous and in
+ * its own draw order). Every query's result is bit-identical to the same query
+ * run alone (per-query draw streams, exact sums, per-query sequential stop scans).
+ * Estimators: Bader's adaptive sampling (Sec. 4), Algorithm 1, uniform k-source.
+ */
+typedef int64_t bc_ticket;
+
+#define BC_QUERY_SOURCES 1         /* Bader's adaptive source sampling (Sec. 4) */
+#define BC_QUERY_PAIRS 2           /* adaptive pair sampling (Algorithm 1) */
+#define BC_QUERY_UNIFORM 3         /* uniform k-source all-vertex estimate */
+
+typedef struct bc_query_stats {
+  double queue_ms;                 /* submit -> admission */
+  double run_ms;                   /* admission -> result written */
+  int64_t samples;                 /* draws processed for this query (batch lanes) */
+  int64_t batches;                 /* batches the query took part in */
+} bc_query_stats;
+
+typedef struct bc_query {
+  int32_t kind;                    /* BC_QUERY_* */
+  int32_t T;                       /* number of targets (SOURCES, PAIRS); distinct, in [0, n) */
+  bc_graph graph;                  /* a loaded graph; it must stay loaded until the query ends */
+  const int32_t *targets;          /* [T], copied by bc_submit */
+  double c;                        /* >= 1 (SOURCES, PAIRS) */
+  int64_t cap;                     /* >= 1 (SOURCES, PAIRS) */
+  int64_t k;                       /* >= 1 (UNIFORM) */
+  uint64_t seed, qid;              /* draw stream */
+  double threshold_scale;          /* PAIRS stop-test scale (0 means 1) */
+  double *est;                     /* [T] (SOURCES, PAIRS) or [n] (UNIFORM); caller-owned */
+  int64_t *k_out;                  /* [T] or NULL */
+  double *S_out;                   /* [T] or NULL */
+  int32_t *stop_status;            /* [T] or NULL */
+  bc_query_stats *stats;           /* or NULL; filled when the query ends */
+} bc_query;
+
+/* Queues a query and returns its ticket. The query's output buffers must stay
+ * valid until bc_poll returns something other than BC_PENDING for it. */
+bc_status bc_submit(bc_ctx *ctx, const bc_query *q, bc_ticket *out);
+
+/* Waits up to timeout_us microseconds (0 = do not wait, < 0 = wait until done).
+ * Returns BC_PENDING while the query runs; BC_OK once its outputs are written;
+ * or the query's error (BC_E_CANCELLED, BC_E_SIGMA_OVERFLOW, ...). After a
+ * non-BC_PENDING return the ticket is released. */
+bc_status bc_poll(bc_ctx *ctx, bc_ticket t, int64_t timeout_us);
+
+/* Cancels a queued or running query; a later bc_poll returns BC_E_CANCELLED. */
+bc_status bc_cancel(bc_ctx *ctx, bc_ticket t);
+
+/* Admission limits: queries active at once (default 64) and device bytes that
+ * admitted queries may hold (default 1/4 of the device's memory). <= 0 keeps
+ * the current value. */
+bc_status bc_server_limits(bc_ctx *ctx, int32_t max_active, int64_t mem_budget_bytes);
+
 /* ------------------------------------------------------------ utilities -- */
 
 /* Source draws i0..i0+count-1 of (seed, qid) for n vertices, computed on the

@@ -24,6 +24,10 @@ BC_STOPPED = 0
 BC_CAPPED = 1
 BC_UNDIRECTED = 1
 BC_VALIDATE = 2
+BC_PENDING = 1
+BC_QUERY_SOURCES = 1
+BC_QUERY_PAIRS = 2
+BC_QUERY_UNIFORM = 3
 STATUS_NAMES = {
     -1: "BC_E_INVALID", -2: "BC_E_NOMEM", -3: "BC_E_TOO_LARGE", -4: "BC_E_BAD_GRAPH",
     -5: "BC_E_DEVICE", -6: "BC_E_DEVICE_TIMEOUT", -7: "BC_E_CANCELLED",
@@ -40,6 +44,17 @@ _f64p = ctypes.POINTER(_f64)
 
 class bc_options(ctypes.Structure):
     _fields_ = [("batch_width", _i32), ("reserved0", _i32), ("stream", _vp)]
+
+
+class bc_query_stats(ctypes.Structure):
+    _fields_ = [("queue_ms", _f64), ("run_ms", _f64), ("samples", _i64), ("batches", _i64)]
+
+
+class bc_query(ctypes.Structure):
+    _fields_ = [("kind", _i32), ("T", _i32), ("graph", _i64), ("targets", _i32p), ("c", _f64),
+                ("cap", _i64), ("k", _i64), ("seed", _u64), ("qid", _u64), ("threshold_scale", _f64),
+                ("est", _f64p), ("k_out", _i64p), ("S_out", _f64p), ("stop_status", _i32p),
+                ("stats", ctypes.POINTER(bc_query_stats))]
 
 
 class bc_stats(ctypes.Structure):
@@ -64,6 +79,10 @@ _SIGS = {
                                    _f64p, _i32p]),
     "bc_adaptive_pairs": (_i32, [_vp, _i64, _i32p, _i32, _f64, _i64, _u64, _u64, _f64, _f64p, _i64p,
                                  _f64p, _i32p]),
+    "bc_submit": (_i32, [_vp, ctypes.POINTER(bc_query), _i64p]),
+    "bc_poll": (_i32, [_vp, _i64, _i64]),
+    "bc_cancel": (_i32, [_vp, _i64]),
+    "bc_server_limits": (_i32, [_vp, _i32, _i64]),
     "bc_draw_sources": (_i32, [_vp, _u64, _u64, _u64, _i64, _i32, _i32p]),
     "bc_draw_pairs": (_i32, [_vp, _u64, _u64, _u64, _i64, _i32, _i32p, _i32p]),
     "bc_exact_sum": (_i32, [_vp, _f64p, _i64, _f64p]),
@@ -199,6 +218,67 @@ def bc_adaptive_pairs(ctx, g: int, targets, c: float, cap: int, seed: int, qid: 
     return dict(est=est[:T], k=k[:T], S=S[:T], status=st[:T])
 
 
+class Ticket:
+    """A submitted query: owns its input copy and output buffers until polled."""
+
+    def __init__(self, kind, T, n):
+        self.kind = kind
+        m = n if kind == BC_QUERY_UNIFORM else max(T, 1)
+        self.est = np.zeros(m, np.float64)
+        self.k = np.zeros(max(T, 1), np.int64)
+        self.S = np.zeros(max(T, 1), np.float64)
+        self.status = np.zeros(max(T, 1), np.int32)
+        self.stats = bc_query_stats()
+        self.T = T
+        self.id = None
+        self.targets = None
+        self.result = None
+
+    def outputs(self):
+        if self.kind == BC_QUERY_UNIFORM:
+            return dict(est=self.est)
+        T = self.T
+        return dict(est=self.est[:T], k=self.k[:T], S=self.S[:T], status=self.status[:T])
+
+    def stats_dict(self):
+        s = self.stats
+        return dict(queue_ms=s.queue_ms, run_ms=s.run_ms, samples=int(s.samples), batches=int(s.batches))
+
+
+def bc_submit(ctx, g: int, kind: int, targets=None, c: float = 1.0, cap: int = 1, k: int = 0,
+              seed: int = 0, qid: int = 0, threshold_scale: float = 1.0) -> Ticket:
+    n, _ = bc_graph_info(ctx, g)
+    tg = _i32arr(targets if targets is not None else [])
+    T = int(tg.size)
+    tk = Ticket(kind, T, n)
+    tk.targets = tg if T else np.zeros(1, np.int32)
+    q = bc_query(kind, T, g, _p(tk.targets, _i32p), c, cap, k, seed, qid, threshold_scale,
+                 _p(tk.est, _f64p), _p(tk.k, _i64p), _p(tk.S, _f64p), _p(tk.status, _i32p),
+                 ctypes.pointer(tk.stats))
+    t = _i64()
+    _ck(ctx, _lib.bc_submit(ctx, ctypes.byref(q), ctypes.byref(t)))
+    tk.id = int(t.value)
+    return tk
+
+
+def bc_poll(ctx, ticket: Ticket, timeout_us: int = -1) -> int:
+    """Returns BC_OK (outputs ready) or BC_PENDING; raises BCError on a failed query."""
+    rc = _lib.bc_poll(ctx, ticket.id, timeout_us)
+    if rc == BC_PENDING:
+        return rc
+    ticket.result = rc
+    _ck(ctx, rc)
+    return rc
+
+
+def bc_cancel(ctx, ticket: Ticket):
+    _ck(ctx, _lib.bc_cancel(ctx, ticket.id))
+
+
+def bc_server_limits(ctx, max_active: int = 0, mem_budget_bytes: int = 0):
+    _ck(ctx, _lib.bc_server_limits(ctx, max_active, mem_budget_bytes))
+
+
 def bc_draw_sources(ctx, seed: int, qid: int, i0: int, count: int, n: int) -> np.ndarray:
     out = np.zeros(max(count, 1), np.int32)
     _ck(ctx, _lib.bc_draw_sources(ctx, seed, qid, i0, count, n, _p(out, _i32p)))
@@ -304,6 +384,18 @@ class Context:
 
     def exact_sum(self, x):
         return bc_exact_sum(self.ptr, x)
+
+    def submit(self, g, kind, targets=None, c=1.0, cap=1, k=0, seed=0, qid=0, threshold_scale=1.0):
+        return bc_submit(self.ptr, g, kind, targets, c, cap, k, seed, qid, threshold_scale)
+
+    def poll(self, ticket, timeout_us=-1):
+        return bc_poll(self.ptr, ticket, timeout_us)
+
+    def cancel(self, ticket):
+        bc_cancel(self.ptr, ticket)
+
+    def server_limits(self, max_active=0, mem_budget_bytes=0):
+        bc_server_limits(self.ptr, max_active, mem_budget_bytes)
 
     def set_profiling(self, on: bool):
         bc_set_profiling(self.ptr, on)

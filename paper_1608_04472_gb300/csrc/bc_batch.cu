@@ -26,8 +26,8 @@
 
 namespace bcg {
 
-constexpr int HEAVY = 256;   // vertices above this degree are split into segments
-constexpr int SEG = 256;     // neighbours per heavy segment
+constexpr int HEAVY_DEFAULT = 256;   // vertices above this degree are split into segments
+constexpr int SEG_DEFAULT = 256;     // neighbours per heavy segment
 constexpr int GRAB = 16;     // vertices taken per work-queue grab
 constexpr int UNR = 4;       // neighbours gathered per unrolled step
 constexpr int FWD_THREADS = 256;
@@ -57,10 +57,11 @@ __device__ __forceinline__ void block_or_to(uint64_t x, uint64_t *dst) {
 }
 
 
-// Dynamic work distribution: a warp takes GRAB consecutive items per atomic.
-__device__ __forceinline__ int grab(unsigned *wq) {
+// Dynamic work distribution: a warp takes `step` consecutive items per atomic
+// (GRAB light vertices; one heavy segment or heavy vertex, whose work is large).
+__device__ __forceinline__ int grab(unsigned *wq, int step = GRAB) {
   int base = 0;
-  if ((threadIdx.x & 31) == 0) base = (int)atomicAdd(wq, (unsigned)GRAB);
+  if ((threadIdx.x & 31) == 0) base = (int)atomicAdd(wq, (unsigned)step);
   return __shfl_sync(FULL, base, 0);
 }
 
@@ -110,6 +111,30 @@ __global__ void k_zero_heavy_rows(int nh, const int32_t *__restrict__ heavy, uin
   if (h < nh && threadIdx.x < 64) sigma[(size_t)heavy[h] * 64 + threadIdx.x] = 0ull;
 }
 
+// Level 1 directly: the vertices at distance 1 from s_t are its neighbours, each
+// with exactly one shortest path (sigma = 1). One block per lane.
+__global__ void k_fwd_level1(int count, const int32_t *__restrict__ sources, const int32_t *__restrict__ rp,
+                             const int32_t *__restrict__ col, uint64_t *__restrict__ lm1,
+                             uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
+                             uint64_t *__restrict__ active1, unsigned long long *__restrict__ cnt) {
+  const int t = blockIdx.x;
+  if (t >= count) return;
+  const int32_t s = sources[t];
+  const uint64_t bit = 1ull << t;
+  const int beg = rp[s], end = rp[s + 1];
+  for (int j = beg + threadIdx.x; j < end; j += blockDim.x) {
+    const int32_t v = col[j];
+    sigma[(size_t)v * 64 + t] = 1ull;
+    atomicOr((unsigned long long *)&lm1[v], (unsigned long long)bit);
+    atomicOr((unsigned long long *)&visited[v], (unsigned long long)bit);
+  }
+  if (threadIdx.x == 0 && end > beg) {
+    atomicOr((unsigned long long *)active1, (unsigned long long)bit);
+    atomicAdd(cnt, (unsigned long long)(end - beg));      // DAG edges s -> v
+    atomicAdd(cnt + 1, (unsigned long long)(end - beg));  // reached at distance 1
+  }
+}
+
 // --------------------------------------------------------------- forward --
 // One warp per vertex (grid-stride); heavy vertices only get lm_cur[v] = 0 here.
 __global__ void __launch_bounds__(FWD_THREADS)
@@ -118,7 +143,7 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
             uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
             const uint64_t *__restrict__ active_prev, uint64_t *__restrict__ enable,
             uint64_t *__restrict__ active_cur, unsigned *__restrict__ err,
-            unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq) {
+            unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq, int heavy_deg) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -132,7 +157,7 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
     const uint64_t vis = visited[v];
     const uint64_t pend = ~vis & act;
     uint64_t newm = 0ull;
-    if (pend && end - beg <= HEAVY) {
+    if (pend && end - beg <= heavy_deg) {
       uint64_t s0 = 0ull, s1 = 0ull;
       for (int base = beg; base < end; base += 32) {
         const int j = base + lane;
@@ -201,14 +226,12 @@ k_fwd_heavy(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restri
             const uint64_t *__restrict__ lm_prev, uint64_t *__restrict__ lm_cur,
             const uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
             const uint64_t *__restrict__ active_prev, const uint64_t *__restrict__ enable,
-            unsigned *__restrict__ err, unsigned long long *__restrict__ cnt) {
+            unsigned *__restrict__ err, unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq) {
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint64_t act = *active_prev & *enable;
   unsigned long long tri = 0ull;
   unsigned e = 0u;
-  for (int s = warp; s < nseg; s += nwarps) {
+  for (int s = grab(wq, 1); s < nseg; s = grab(wq, 1)) {
     const int32_t v = seg_v[s];
     const int beg = seg_b[s], end = seg_e[s];
     const uint64_t pend = ~visited[v] & act;
@@ -394,8 +417,11 @@ __device__ __forceinline__ void ring_append(Ring &R, unsigned &tail, int32_t v, 
 }
 
 // One warp-wide round over ring records head..head+count-1 (count <= 32).
+// With `coefx` set (128-bit window), the coefficient is stored as its exact
+// fixed-point limbs (unit 2^-96) in coefx[v][t] and sigma stays in place;
+// otherwise the coefficient's double bits overwrite sigma[v][t].
 __device__ __forceinline__ void ring_round(Ring &R, unsigned head, int count, uint64_t *__restrict__ sigma,
-                                           const Sink &sink, unsigned &e) {
+                                           const Sink &sink, unsigned &e, uint4 *__restrict__ coefx = nullptr) {
   const int lane = threadIdx.x & 31;
   int32_t v = -1;
   double d = 0.0;
@@ -405,12 +431,16 @@ __device__ __forceinline__ void ring_round(Ring &R, unsigned head, int count, ui
     const int32_t t = R.t[pos];
     const uint64_t sg = R.sig[pos];
     d = delta_of(R.sum[pos], sg);
-    sigma[(size_t)v * 64 + t] = (uint64_t)__double_as_longlong(coef_round(d, sg));
-    if (sink.delta_lm) sink.delta_lm[(size_t)v * 64 + t] = d;
-    if (sink.tslot) {
-      const int32_t slot = sink.tslot[v];
-      if (slot >= 0) sink.tdelta[(size_t)slot * 64 + t] = d;
+    const double cf = coef_round(d, sg);
+    if (coefx) {
+      Acc2 z = acc2_zero();
+      acc2_add(z, cf, e);
+      coefx[(size_t)v * 64 + t] = make_uint4(z.l0, z.l1, z.l2, z.l3);
+    } else {
+      sigma[(size_t)v * 64 + t] = (uint64_t)__double_as_longlong(cf);
     }
+    if (sink.delta_lm) sink.delta_lm[(size_t)v * 64 + t] = d;
+    if (sink.tslot) sink_targets(sink, v, t, d);
   }
   if (sink.acc) {
     // records of one vertex are consecutive: segmented exact inclusive scan
@@ -434,11 +464,31 @@ __device__ __forceinline__ void ring_round(Ring &R, unsigned head, int count, ui
   }
 }
 
+// Lane compaction: thread i of the warp takes the i-th set lane of `lanes`
+// (and the (i+32)-th when more than 32 lanes are set); -1 when absent.
+__device__ __forceinline__ void compact_lanes(uint64_t lanes, int &p0, int &p1) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lo = (unsigned)lanes, hi = (unsigned)(lanes >> 32);
+  const int nlo = __popc(lo), ntot = nlo + __popc(hi);
+  auto nth = [&](int i) -> int {
+    if (i >= ntot) return -1;
+    if (i < nlo) return (int)__fns(lo, 0u, i + 1);
+    return 32 + (int)__fns(hi, 0u, i - nlo + 1);
+  };
+  p0 = nth(lane);
+  p1 = nth(lane + 32);
+}
+
+// Exact sums over the successors of v (neighbours one level deeper in the same
+// lane) for the compacted lanes p0 (and p1 when `two`).
 template <class P>
 __device__ __forceinline__ void gather_successors(int beg, int end, uint64_t lanes, const uint64_t *__restrict__ col_lm,
                                                   const int32_t *__restrict__ col, const uint64_t *__restrict__ sigma,
-                                                  typename P::A &a0, typename P::A &a1, unsigned &e) {
+                                                  int p0, int p1, bool two, typename P::A &a0, typename P::A &a1,
+                                                  unsigned &e) {
   const int lane = threadIdx.x & 31;
+  const int q0 = p0 < 0 ? 0 : p0, q1 = p1 < 0 ? 0 : p1;
+  const uint64_t b0 = p0 < 0 ? 0ull : (1ull << q0), b1 = p1 < 0 ? 0ull : (1ull << q1);
   for (int base = beg; base < end; base += 32) {
     const int j = base + lane;
     int32_t w = 0;
@@ -452,27 +502,50 @@ __device__ __forceinline__ void gather_successors(int beg, int end, uint64_t lan
       uint64_t mk[UNR];
       int32_t wk[UNR];
       take(bal, m, w, mk, wk);
-      uint64_t x0[UNR], x1[UNR];
+      uint64_t x0[UNR];
 #pragma unroll
-      for (int k = 0; k < UNR; ++k) {
-        const uint64_t *row = sigma + (size_t)wk[k] * 64;
-        x0[k] = ((mk[k] >> lane) & 1ull) ? row[lane] : 0ull;
-        x1[k] = ((mk[k] >> (lane + 32)) & 1ull) ? row[lane + 32] : 0ull;
-      }
+      for (int k = 0; k < UNR; ++k) x0[k] = (mk[k] & b0) ? sigma[(size_t)wk[k] * 64 + q0] : 0ull;
 #pragma unroll
-      for (int k = 0; k < UNR; ++k) {
-        P::add(a0, __longlong_as_double((long long)x0[k]), e);
-        P::add(a1, __longlong_as_double((long long)x1[k]), e);
+      for (int k = 0; k < UNR; ++k) P::add(a0, __longlong_as_double((long long)x0[k]), e);
+      if (two) {
+        uint64_t x1[UNR];
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) x1[k] = (mk[k] & b1) ? sigma[(size_t)wk[k] * 64 + q1] : 0ull;
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) P::add(a1, __longlong_as_double((long long)x1[k]), e);
       }
     }
   }
+}
+
+// Appends the finished lanes of v (compacted positions p0, p1) to the ring.
+__device__ __forceinline__ void ring_append_c(Ring &R, unsigned &tail, int32_t v, uint64_t lanes, int p0, int p1,
+                                              const Acc &a0, const Acc &a1, const uint64_t *__restrict__ row) {
+  const int lane = threadIdx.x & 31;
+  const int ntot = __popcll((long long)lanes);
+  if (p0 >= 0) {
+    const unsigned pos = (tail + lane) & (RING - 1);
+    R.v[pos] = v;
+    R.t[pos] = p0;
+    R.sum[pos] = acc_round(a0);
+    R.sig[pos] = row[p0];
+  }
+  if (p1 >= 0) {
+    const unsigned pos = (tail + 32 + lane) & (RING - 1);
+    R.v[pos] = v;
+    R.t[pos] = p1;
+    R.sum[pos] = acc_round(a1);
+    R.sig[pos] = row[p1];
+  }
+  tail += (unsigned)ntot;
 }
 
 template <class P>
 __global__ void __launch_bounds__(FWD_THREADS)
 k_bwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
             const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
-            uint64_t *__restrict__ sigma, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq) {
+            uint64_t *__restrict__ sigma, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq,
+            int heavy_deg) {
   __shared__ Ring rings[FWD_THREADS / 32];
   Ring &R = rings[threadIdx.x >> 5];
   unsigned head = 0u, tail = 0u;
@@ -482,9 +555,13 @@ k_bwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
       const uint64_t lanes = lm_cur[v];
       if (!lanes) continue;
       const int beg = rp[v], end = rp[v + 1];
-      if (end - beg > HEAVY) continue;
+      if (end - beg > heavy_deg) continue;
+      // thread t owns lanes t and t + 32 (no compaction: cheapest per vertex)
+      const int lane = threadIdx.x & 31;
+      const int p0 = ((lanes >> lane) & 1ull) ? lane : -1;
+      const int p1 = ((lanes >> (lane + 32)) & 1ull) ? lane + 32 : -1;
       typename P::A a0 = P::zero(), a1 = P::zero();
-      gather_successors<P>(beg, end, lanes, lm_next, col, sigma, a0, a1, e);
+      gather_successors<P>(beg, end, lanes, lm_next, col, sigma, p0, p1, (lanes >> 32) != 0ull, a0, a1, e);
       ring_append(R, tail, v, lanes, P::widen(a0), P::widen(a1), sigma + (size_t)v * 64);
       __syncwarp();
       while (tail - head >= 32u) {
@@ -497,50 +574,51 @@ k_bwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
   if (e) atomicOr(err, e);
 }
 
-// Heavy vertices: one warp per segment writes 64 partial sums to part[s][64].
+// Heavy vertices: one warp per segment (taken dynamically) writes the partial
+// sums of the vertex's active lanes to part[s][lane].
 template <class P>
 __global__ void __launch_bounds__(FWD_THREADS)
 k_bwd_heavy_seg(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restrict__ seg_b,
                 const int32_t *__restrict__ seg_e, const int32_t *__restrict__ col,
                 const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
-                const uint64_t *__restrict__ sigma, Acc *__restrict__ part, unsigned *__restrict__ err) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+                const uint64_t *__restrict__ sigma, Acc *__restrict__ part, unsigned *__restrict__ err,
+                unsigned *__restrict__ wq) {
   unsigned e = 0u;
-  for (int s = warp; s < nseg; s += nwarps) {
-    const int32_t v = seg_v[s];
-    const uint64_t lanes = lm_cur[v];
-    if (!lanes) continue;
-    typename P::A a0 = P::zero(), a1 = P::zero();
-    gather_successors<P>(seg_b[s], seg_e[s], lanes, lm_next, col, sigma, a0, a1, e);
-    part[(size_t)s * 64 + lane] = P::widen(a0);
-    part[(size_t)s * 64 + 32 + lane] = P::widen(a1);
-  }
+  for (int s = grab(wq, 1); s < nseg; s = grab(wq, 1)) {
+      const int32_t v = seg_v[s];
+      const uint64_t lanes = lm_cur[v];
+      if (!lanes) continue;
+      int p0, p1;
+      compact_lanes(lanes, p0, p1);
+      const bool two = __popcll((long long)lanes) > 32;
+      typename P::A a0 = P::zero(), a1 = P::zero();
+      gather_successors<P>(seg_b[s], seg_e[s], lanes, lm_next, col, sigma, p0, p1, two, a0, a1, e);
+      if (p0 >= 0) part[(size_t)s * 64 + p0] = P::widen(a0);
+      if (p1 >= 0) part[(size_t)s * 64 + p1] = P::widen(a1);
+    }
   if (e) atomicOr(err, e);
 }
 
 __global__ void __launch_bounds__(FWD_THREADS)
 k_bwd_heavy_fin(int nh, const int32_t *__restrict__ heavy, const int32_t *__restrict__ hseg0,
                 const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ sigma,
-                const Acc *__restrict__ part, Sink sink, unsigned *__restrict__ err) {
+                const Acc *__restrict__ part, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq) {
   __shared__ Ring rings[FWD_THREADS / 32];
   Ring &R = rings[threadIdx.x >> 5];
   unsigned head = 0u, tail = 0u;
-  const int lane = threadIdx.x & 31;
   unsigned e = 0u;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int h = warp; h < nh; h += nwarps) {
+  for (int h = grab(wq, 1); h < nh; h = grab(wq, 1)) {
     const int32_t v = heavy[h];
     const uint64_t lanes = lm_cur[v];
     if (!lanes) continue;
+    int p0, p1;
+    compact_lanes(lanes, p0, p1);
     Acc a0 = acc_zero(), a1 = acc_zero();
     for (int s = hseg0[h]; s < hseg0[h + 1]; ++s) {
-      acc_add_acc(a0, part[(size_t)s * 64 + lane]);
-      acc_add_acc(a1, part[(size_t)s * 64 + 32 + lane]);
+      if (p0 >= 0) acc_add_acc(a0, part[(size_t)s * 64 + p0]);
+      if (p1 >= 0) acc_add_acc(a1, part[(size_t)s * 64 + p1]);
     }
-    ring_append(R, tail, v, lanes, a0, a1, sigma + (size_t)v * 64);
+    ring_append_c(R, tail, v, lanes, p0, p1, a0, a1, sigma + (size_t)v * 64);
     __syncwarp();
     while (tail - head >= 32u) {
       ring_round(R, head, 32, sigma, sink, e);
@@ -548,6 +626,208 @@ k_bwd_heavy_fin(int nh, const int32_t *__restrict__ heavy, const int32_t *__rest
       __syncwarp();
     }
   }
+  if (tail != head) ring_round(R, head, (int)(tail - head), sigma, sink, e);
+  if (e) atomicOr(err, e);
+}
+
+// ------------------------------------------- packed fixed-point backward --
+// Used when the batch's largest sigma is <= 2^44: coefficients are stored as
+// exact 128-bit fixed-point limbs, so a successor add is a 4-limb carry chain.
+// A vertex at a level usually has few lanes L; the warp is split into 32/G
+// groups of G >= |L| threads and each group takes a different listed
+// successor per step (thread (g, s) owns the s-th active lane).
+
+struct Packed {
+  int glog;  // log2 of the group width G
+  int p0;    // lane owned by this thread (-1: none)
+  int p1;    // second lane when |L| > 32 (G = 32), else -1
+  bool two;
+};
+
+// Active lane positions in increasing order: each set lane writes its position
+// at its rank in a per-warp table, then thread i reads entry i.
+__device__ __forceinline__ Packed pack_lanes(uint64_t lanes, int8_t *tab) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lo = (unsigned)lanes, hi = (unsigned)(lanes >> 32);
+  const unsigned lt = (1u << lane) - 1u;
+  const int nlo = __popc(lo), L = nlo + __popc(hi);
+  if ((lo >> lane) & 1u) tab[__popc(lo & lt)] = (int8_t)lane;
+  if ((hi >> lane) & 1u) tab[nlo + __popc(hi & lt)] = (int8_t)(lane + 32);
+  __syncwarp();
+  Packed pk;
+  pk.glog = L > 16 ? 5 : (L > 8 ? 4 : (L > 4 ? 3 : 2));
+  const int slot = lane & ((1 << pk.glog) - 1);
+  pk.p0 = slot < L ? (int)tab[slot] : -1;
+  pk.p1 = (pk.glog == 5 && lane + 32 < L) ? (int)tab[lane + 32] : -1;
+  pk.two = L > 32;
+  __syncwarp();
+  return pk;
+}
+
+__device__ __forceinline__ void acc2_add_u4(Acc2 &a, const uint4 &x) { acc2_add4(a, x.x, x.y, x.z, x.w); }
+
+__device__ __forceinline__ void acc2_shfl_xor_add(Acc2 &a, int off) {
+  const uint32_t o0 = __shfl_xor_sync(FULL, a.l0, off), o1 = __shfl_xor_sync(FULL, a.l1, off);
+  const uint32_t o2 = __shfl_xor_sync(FULL, a.l2, off), o3 = __shfl_xor_sync(FULL, a.l3, off);
+  acc2_add4(a, o0, o1, o2, o3);
+}
+
+// Packed successor sums over double coefficients held in the sigma slots
+// (coefficient of (w, t) at sigma[w][t] once w's level is done).
+__device__ __forceinline__ void gather_packed(int beg, int end, uint64_t lanes, const uint64_t *__restrict__ lm_next,
+                                              const int32_t *__restrict__ col, const uint64_t *__restrict__ coef,
+                                              const Packed &pk, int32_t *list, Acc2 &a0, Acc2 &a1, unsigned &e) {
+  const int lane = threadIdx.x & 31;
+  const int NG = 32 >> pk.glog, g = lane >> pk.glog;
+  const uint64_t b0 = pk.p0 >= 0 ? (1ull << pk.p0) : 0ull, b1 = pk.p1 >= 0 ? (1ull << pk.p1) : 0ull;
+  const int q0 = pk.p0 < 0 ? 0 : pk.p0, q1 = pk.p1 < 0 ? 0 : pk.p1;
+  for (int base = beg; base < end; base += 32) {
+    const int j = base + lane;
+    int32_t w = 0;
+    uint64_t m = 0ull;
+    if (j < end) {
+      w = col[j];
+      m = lm_next[w] & lanes;
+    }
+    const unsigned bal = __ballot_sync(FULL, m != 0ull);
+    const int cnt = __popc(bal);
+    if (m != 0ull) list[__popc(bal & ((1u << lane) - 1u))] = lane;
+    __syncwarp();
+    for (int r = 0; r < cnt; r += 2 * NG) {
+      const int i0 = r + g, i1 = r + NG + g;
+      const bool h0 = i0 < cnt, h1 = i1 < cnt;
+      const int s0 = h0 ? list[i0] : 0, s1 = h1 ? list[i1] : 0;
+      const uint64_t m0 = __shfl_sync(FULL, m, s0), m1 = __shfl_sync(FULL, m, s1);
+      const int32_t w0 = __shfl_sync(FULL, w, s0), w1 = __shfl_sync(FULL, w, s1);
+      const uint64_t x0 = (h0 && (m0 & b0)) ? coef[(size_t)w0 * 64 + q0] : 0ull;
+      const uint64_t x1 = (h1 && (m1 & b0)) ? coef[(size_t)w1 * 64 + q0] : 0ull;
+      if (pk.two) {
+        const uint64_t y0 = (h0 && (m0 & b1)) ? coef[(size_t)w0 * 64 + q1] : 0ull;
+        const uint64_t y1 = (h1 && (m1 & b1)) ? coef[(size_t)w1 * 64 + q1] : 0ull;
+        acc2_add(a1, __longlong_as_double((long long)y0), e);
+        acc2_add(a1, __longlong_as_double((long long)y1), e);
+      }
+      acc2_add(a0, __longlong_as_double((long long)x0), e);
+      acc2_add(a0, __longlong_as_double((long long)x1), e);
+    }
+    __syncwarp();
+  }
+  for (int off = 1 << pk.glog; off < 32; off <<= 1) acc2_shfl_xor_add(a0, off);
+}
+
+// Finished lanes of v (threads of group 0 own them) into the ring.
+__device__ __forceinline__ void ring_append_fx(Ring &R, unsigned &tail, int32_t v, uint64_t lanes, const Packed &pk,
+                                               const Acc2 &a0, const Acc2 &a1, const uint64_t *__restrict__ row) {
+  const int lane = threadIdx.x & 31;
+  if ((lane >> pk.glog) == 0 && pk.p0 >= 0) {
+    const unsigned pos = (tail + lane) & (RING - 1);
+    R.v[pos] = v;
+    R.t[pos] = pk.p0;
+    R.sum[pos] = acc_round(acc2_widen(a0));
+    R.sig[pos] = row[pk.p0];
+  }
+  if (pk.p1 >= 0) {
+    const unsigned pos = (tail + 32 + lane) & (RING - 1);
+    R.v[pos] = v;
+    R.t[pos] = pk.p1;
+    R.sum[pos] = acc_round(acc2_widen(a1));
+    R.sig[pos] = row[pk.p1];
+  }
+  tail += (unsigned)__popcll((long long)lanes);
+}
+
+__global__ void __launch_bounds__(FWD_THREADS)
+k_bwd_light_fx(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+               const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
+               uint64_t *__restrict__ sigma, uint4 *__restrict__ coefx, Sink sink, unsigned *__restrict__ err,
+               unsigned *__restrict__ wq, int heavy_deg) {
+  __shared__ Ring rings[FWD_THREADS / 32];
+  __shared__ int32_t lists[FWD_THREADS / 32][32];
+  __shared__ int8_t tabs[FWD_THREADS / 32][64];
+  Ring &R = rings[threadIdx.x >> 5];
+  int32_t *list = lists[threadIdx.x >> 5];
+  int8_t *tab = tabs[threadIdx.x >> 5];
+  unsigned head = 0u, tail = 0u;
+  unsigned e = 0u;
+  (void)coefx;
+  for (int base = grab(wq); base < n; base = grab(wq))
+    for (int v = base; v < min(base + GRAB, n); ++v) {
+      const uint64_t lanes = lm_cur[v];
+      if (!lanes) continue;
+      const int beg = rp[v], end = rp[v + 1];
+      if (end - beg > heavy_deg) continue;
+      const Packed pk = pack_lanes(lanes, tab);
+      Acc2 a0 = acc2_zero(), a1 = acc2_zero();
+      gather_packed(beg, end, lanes, lm_next, col, sigma, pk, list, a0, a1, e);
+      ring_append_fx(R, tail, v, lanes, pk, a0, a1, sigma + (size_t)v * 64);
+      __syncwarp();
+      while (tail - head >= 32u) {
+        ring_round(R, head, 32, sigma, sink, e);
+        head += 32u;
+        __syncwarp();
+      }
+    }
+  if (tail != head) ring_round(R, head, (int)(tail - head), sigma, sink, e);
+  if (e) atomicOr(err, e);
+}
+
+__global__ void __launch_bounds__(FWD_THREADS)
+k_bwd_heavy_seg_fx(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restrict__ seg_b,
+                   const int32_t *__restrict__ seg_e, const int32_t *__restrict__ col,
+                   const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
+                   const uint64_t *__restrict__ coef, uint4 *__restrict__ part, unsigned *__restrict__ wq,
+                   unsigned *__restrict__ err) {
+  __shared__ int32_t lists[FWD_THREADS / 32][32];
+  __shared__ int8_t tabs[FWD_THREADS / 32][64];
+  int32_t *list = lists[threadIdx.x >> 5];
+  int8_t *tab = tabs[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  unsigned e = 0u;
+  for (int s = grab(wq, 1); s < nseg; s = grab(wq, 1)) {
+      const int32_t v = seg_v[s];
+      const uint64_t lanes = lm_cur[v];
+      if (!lanes) continue;
+      const Packed pk = pack_lanes(lanes, tab);
+      Acc2 a0 = acc2_zero(), a1 = acc2_zero();
+      gather_packed(seg_b[s], seg_e[s], lanes, lm_next, col, coef, pk, list, a0, a1, e);
+      if ((lane >> pk.glog) == 0 && pk.p0 >= 0) part[(size_t)s * 64 + pk.p0] = make_uint4(a0.l0, a0.l1, a0.l2, a0.l3);
+      if (pk.p1 >= 0) part[(size_t)s * 64 + pk.p1] = make_uint4(a1.l0, a1.l1, a1.l2, a1.l3);
+    }
+  if (e) atomicOr(err, e);
+}
+
+__global__ void __launch_bounds__(FWD_THREADS)
+k_bwd_heavy_fin_fx(int nh, const int32_t *__restrict__ heavy, const int32_t *__restrict__ hseg0,
+                   const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ sigma, uint4 *__restrict__ coefx,
+                   const uint4 *__restrict__ part, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq) {
+  __shared__ Ring rings[FWD_THREADS / 32];
+  Ring &R = rings[threadIdx.x >> 5];
+  unsigned head = 0u, tail = 0u;
+  unsigned e = 0u;
+  for (int h = grab(wq, 1); h < nh; h = grab(wq, 1)) {
+      const int32_t v = heavy[h];
+      const uint64_t lanes = lm_cur[v];
+      if (!lanes) continue;
+      int p0, p1;
+      compact_lanes(lanes, p0, p1);
+      Acc2 a0 = acc2_zero(), a1 = acc2_zero();
+      for (int s = hseg0[h]; s < hseg0[h + 1]; ++s) {
+        if (p0 >= 0) acc2_add_u4(a0, part[(size_t)s * 64 + p0]);
+        if (p1 >= 0) acc2_add_u4(a1, part[(size_t)s * 64 + p1]);
+      }
+      Packed pk;
+      pk.glog = 5;
+      pk.p0 = p0;
+      pk.p1 = p1;
+      pk.two = p1 >= 0;
+      ring_append_fx(R, tail, v, lanes, pk, a0, a1, sigma + (size_t)v * 64);
+      __syncwarp();
+      while (tail - head >= 32u) {
+        ring_round(R, head, 32, sigma, sink, e);
+        head += 32u;
+        __syncwarp();
+      }
+    }
   if (tail != head) ring_round(R, head, (int)(tail - head), sigma, sink, e);
   if (e) atomicOr(err, e);
 }
@@ -581,8 +861,8 @@ __global__ void k_extract(int32_t n, int count, int maxlevel, const uint64_t *__
 
 // ------------------------------------------------------------------ host --
 struct HeavyMeta {
-  int nh = 0, nseg = 0;
-  DevBuf heavy, hseg0, seg_v, seg_b, seg_e, part;
+  int nh = 0, nseg = 0, heavy_deg = 0;
+  DevBuf heavy, hseg0, seg_v, seg_b, seg_e, part, part2;
 };
 static std::map<const int32_t *, HeavyMeta> g_heavy;  // keyed by the graph's device col pointer
 static std::mutex g_heavy_mu;
@@ -595,15 +875,17 @@ static HeavyMeta &heavy_meta(bc_ctx *ctx, const Graph &g) {
   std::vector<int32_t> rp(g.n + 1);
   BCG_CUDA(cudaMemcpy(rp.data(), g.rp, sizeof(int32_t) * (g.n + 1), cudaMemcpyDeviceToHost));
   std::vector<int32_t> heavy, hseg0, sv, sb, se;
+  hm.heavy_deg = ctx->heavy_deg > 0 ? ctx->heavy_deg : HEAVY_DEFAULT;
+  const int seg = ctx->seg_len > 0 ? ctx->seg_len : SEG_DEFAULT;
   for (int32_t v = 0; v < g.n; ++v) {
     const int d = rp[v + 1] - rp[v];
-    if (d <= HEAVY) continue;
+    if (d <= hm.heavy_deg) continue;
     hseg0.push_back((int32_t)sv.size());
     heavy.push_back(v);
-    for (int b = rp[v]; b < rp[v + 1]; b += SEG) {
+    for (int b = rp[v]; b < rp[v + 1]; b += seg) {
       sv.push_back(v);
       sb.push_back(b);
-      se.push_back(std::min(b + SEG, rp[v + 1]));
+      se.push_back(std::min(b + seg, rp[v + 1]));
     }
   }
   hseg0.push_back((int32_t)sv.size());
@@ -629,7 +911,7 @@ void forget_heavy_meta(const int32_t *rp) {
   if (it == g_heavy.end()) return;
   HeavyMeta &hm = it->second;
   hm.heavy.release(); hm.hseg0.release(); hm.seg_v.release(); hm.seg_b.release();
-  hm.seg_e.release(); hm.part.release();
+  hm.seg_e.release(); hm.part.release(); hm.part2.release();
   g_heavy.erase(it);
 }
 
@@ -654,7 +936,7 @@ void batch_ensure(bc_ctx *ctx, const Graph &g) {
   ws.visited.ensure(n * 8);
   ws.sigma.ensure(n * 64 * 8);
   ws.active.ensure((size_t)(ws.lcap + 2) * 8);
-  ws.wq.ensure((size_t)(ws.lcap + 2) * 2 * 4);
+  ws.wq.ensure((size_t)(ws.lcap + 2) * 8 * 4);
   heavy_meta(ctx, g);
 }
 
@@ -671,7 +953,7 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs) {
   HeavyMeta &hm = heavy_meta(ctx, g);
   const size_t n = (size_t)g.n;
   cudaStream_t st = ctx->stream;
-  BCG_CUDA(cudaMemsetAsync(ws.lm.p, 0, n * 8, st));
+  BCG_CUDA(cudaMemsetAsync(ws.lm.p, 0, 2 * n * 8, st));  // levels 0 and 1
   BCG_CUDA(cudaMemsetAsync(ws.visited.p, 0, n * 8, st));
   BCG_CUDA(cudaMemsetAsync(ws.active.p, 0, (size_t)(ws.lcap + 2) * 8, st));
   BCG_CUDA(cudaMemsetAsync(ws.wq.p, 0, ws.wq.bytes, st));
@@ -690,13 +972,40 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs) {
   ctx->batches += 1;
   const int blocks = grid_blocks();
   int l = 0;
+  {
+    // level 1 straight from the sources' adjacency; heavy sigma rows were zeroed
+    // above and only receive stores here, so the atomics-based heavy path is not needed
+    {
+      LaunchScope ls(ctx, F_FWD);
+      k_fwd_level1<<<count, 128, 0, st>>>(count, ws.sources.as<int32_t>(), g.rp, g.col,
+                                           ws.lm.as<uint64_t>() + n, ws.visited.as<uint64_t>(),
+                                           ws.sigma.as<uint64_t>(), ws.active.as<uint64_t>() + 1,
+                                           ws.cnt.as<unsigned long long>());
+    }
+    uint64_t cont1;
+    if (pairs) {
+      LaunchScope ls(ctx, F_PAIR);
+      k_pair_check<<<1, 64, 0, st>>>(count, 1, ws.targets.as<int32_t>(), ws.lm.as<uint64_t>() + n,
+                                     ws.sigma.as<uint64_t>(), ws.enable.as<uint64_t>(), ws.pair_d.as<int32_t>(),
+                                     ws.pair_sig.as<uint64_t>(), ws.active.as<uint64_t>() + 1,
+                                     ws.enable.as<uint64_t>() + 1);
+      cont1 = read_u64(ctx, ws.enable.as<uint64_t>() + 1);
+    } else {
+      cont1 = read_u64(ctx, ws.active.as<uint64_t>() + 1);
+    }
+    if (!cont1) {  // no vertex at distance 1 (or, for pairs, every destination found)
+      ws.last_sigmax = 1ull;
+      return pairs ? 1 : 0;
+    }
+    l = 1;
+  }
   for (;;) {
     if (l + 2 >= ws.lcap) {
       const int ncap = ws.lcap * 2;
       ws.lm.grow_keep((size_t)ncap * n * 8, st);
       ws.active.grow_keep((size_t)(ncap + 2) * 8, st);
-      ws.wq.grow_keep((size_t)(ncap + 2) * 2 * 4, st);
-      BCG_CUDA(cudaMemsetAsync(ws.wq.as<unsigned>() + 2 * (ws.lcap + 2), 0, (size_t)(ncap - ws.lcap) * 2 * 4, st));
+      ws.wq.grow_keep((size_t)(ncap + 2) * 8 * 4, st);
+      BCG_CUDA(cudaMemsetAsync(ws.wq.as<unsigned>() + 8 * (ws.lcap + 2), 0, (size_t)(ncap - ws.lcap) * 8 * 4, st));
       BCG_CUDA(cudaMemsetAsync(ws.active.as<uint64_t>() + ws.lcap + 2, 0, (size_t)(ncap - ws.lcap) * 8, st));
       ws.lcap = ncap;
     }
@@ -707,14 +1016,16 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs) {
       k_fwd_light<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
                                                  ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(), act + l,
                                                  ws.enable.as<uint64_t>(), act + l + 1, ws.err.as<unsigned>(),
-                                                 ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 2 * l);
+                                                 ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 0,
+                                                 hm.heavy_deg);
     }
     if (hm.nseg) {
       LaunchScope ls(ctx, F_FWD);
       k_fwd_heavy<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
           hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
           lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
-          act + l, ws.enable.as<uint64_t>(), ws.err.as<unsigned>(), ws.cnt.as<unsigned long long>());
+          act + l, ws.enable.as<uint64_t>(), ws.err.as<unsigned>(), ws.cnt.as<unsigned long long>(),
+          ws.wq.as<unsigned>() + 8 * l + 1);
     }
     if (hm.nseg) {
       LaunchScope ls(ctx, F_FWD);
@@ -749,17 +1060,43 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink)
   const int blocks = grid_blocks();
   uint64_t *lm = ws.lm.as<uint64_t>();
   const bool narrow = ws.last_sigmax <= (1ull << 44);
+  if (narrow && ctx->bwd_variant == 1) {
+    hm.part2.ensure(std::max<size_t>(hm.nseg, 1) * 64 * sizeof(uint4));
+    uint4 *coefx = nullptr;
+    for (int l = maxlevel; l >= 1; --l) {
+      {
+        LaunchScope ls(ctx, F_BWD);
+        k_bwd_light_fx<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
+                                                      ws.sigma.as<uint64_t>(), coefx, sink, ws.err.as<unsigned>(),
+                                                      ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg);
+      }
+      if (hm.nseg) {
+        {
+          LaunchScope ls(ctx, F_BWD);
+          k_bwd_heavy_seg_fx<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
+              hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
+              lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), hm.part2.as<uint4>(),
+              ws.wq.as<unsigned>() + 8 * l + 3, ws.err.as<unsigned>());
+        }
+        LaunchScope ls(ctx, F_BWD);
+        k_bwd_heavy_fin_fx<<<std::min(blocks, (hm.nh + 7) / 8), FWD_THREADS, 0, st>>>(
+            hm.nh, hm.heavy.as<int32_t>(), hm.hseg0.as<int32_t>(), lm + (size_t)l * n, ws.sigma.as<uint64_t>(),
+            coefx, hm.part2.as<uint4>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 4);
+      }
+    }
+    return;
+  }
   for (int l = maxlevel; l >= 1; --l) {
     {
       LaunchScope ls(ctx, F_BWD);
       if (narrow)
         k_bwd_light<NarrowAcc><<<blocks, FWD_THREADS, 0, st>>>(
             g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), sink,
-            ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 2 * l + 1);
+            ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg);
       else
         k_bwd_light<WideAcc><<<blocks, FWD_THREADS, 0, st>>>(
             g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), sink,
-            ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 2 * l + 1);
+            ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg);
     }
     if (hm.nseg) {
       LaunchScope ls(ctx, F_BWD);
@@ -767,10 +1104,10 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink)
       kseg<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
           hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
           lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), hm.part.as<Acc>(),
-          ws.err.as<unsigned>());
+          ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 3);
       k_bwd_heavy_fin<<<std::min(blocks, (hm.nh + 7) / 8), FWD_THREADS, 0, st>>>(
           hm.nh, hm.heavy.as<int32_t>(), hm.hseg0.as<int32_t>(), lm + (size_t)l * n, ws.sigma.as<uint64_t>(),
-          hm.part.as<Acc>(), sink, ws.err.as<unsigned>());
+          hm.part.as<Acc>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 4);
     }
   }
 }

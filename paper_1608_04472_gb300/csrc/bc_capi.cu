@@ -9,6 +9,7 @@
 //   bc_adaptive_pairs    Algorithm 1: one BFS per target, then batched pair BFS
 //                        truncated at the destination's level, pair values, scan
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -294,8 +295,7 @@ static void launch_draw_sources(bc_ctx *ctx, uint64_t seed, uint64_t qid, uint64
   k_draw_sources<<<(count + 63) / 64, 64, 0, ctx->stream>>>(seed, qid, i0, count, n, out);
 }
 
-// One batch of the per-sample step for the sources in ws.sources[0..count).
-static void run_batch(bc_ctx *ctx, const Graph &g, int count, const Sink &sink) {
+void run_source_batch(bc_ctx *ctx, const Graph &g, int count, const Sink &sink) {
   if (batch_width(ctx) == 1) {
     plain_source(ctx, g, ctx->ws.sources.as<int32_t>(), sink, nullptr, nullptr);
   } else {
@@ -381,7 +381,7 @@ static void do_exact_or_uniform(bc_ctx *ctx, const Graph &g, bool exact, int64_t
     } else {
       launch_draw_sources(ctx, seed, qid, (uint64_t)i0, count, g.n, ws.sources.as<int32_t>());
     }
-    run_batch(ctx, g, count, sink);
+    run_source_batch(ctx, g, count, sink);
   }
   ws.misc2.ensure(n * 8);
   {
@@ -422,7 +422,7 @@ static void do_adaptive_sources(bc_ctx *ctx, const Graph &g, const int32_t *targ
     const int count = (int)std::min<int64_t>(width, cap - i0);
     launch_draw_sources(ctx, seed, qid, (uint64_t)i0, count, g.n, ws.sources.as<int32_t>());
     BCG_CUDA(cudaMemsetAsync(ws.tdelta.p, 0, (size_t)T * 64 * 8, st));
-    run_batch(ctx, g, count, sink);
+    run_source_batch(ctx, g, count, sink);
     {
       LaunchScope ls(ctx, F_SCAN);
       k_stop_scan<<<(T + 127) / 128, 128, 0, st>>>(T, count, ws.tdelta.as<double>(), ss, i0, cn, 1.0);
@@ -600,6 +600,9 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
       ctx->own_stream = true;
     }
     if (opt) ctx->batch_width = opt->batch_width;
+    if (const char *hd = std::getenv("BCG_HEAVY_DEGREE")) ctx->heavy_deg = std::atoi(hd);
+    if (const char *sl = std::getenv("BCG_SEGMENT")) ctx->seg_len = std::atoi(sl);
+    if (const char *bv = std::getenv("BCG_BWD_VARIANT")) ctx->bwd_variant = std::atoi(bv);
     BCG_CUDA(cudaMallocHost(&ctx->ws.pinned, 4096));
     ctx->ws.enable.ensure(64);   // [0] lane enable mask, [1] pair continuation word
     ctx->ws.sources.ensure(64 * 4);
@@ -620,6 +623,7 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
 
 void bc_destroy(bc_ctx *ctx) {
   if (!ctx) return;
+  server_shutdown(ctx);
   {
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     cudaSetDevice(ctx->device);
@@ -634,7 +638,7 @@ void bc_destroy(bc_ctx *ctx) {
     Workspace &ws = ctx->ws;
     for (DevBuf *b : {&ws.lm, &ws.visited, &ws.sigma, &ws.active, &ws.wq, &ws.enable, &ws.sources, &ws.targets, &ws.pair_d,
                       &ws.pair_sig, &ws.err, &ws.cnt, &ws.acc, &ws.tslot, &ws.tdelta, &ws.scan, &ws.misc, &ws.misc2,
-                      &ws.delta_lm, &ws.p_dist, &ws.p_sigma, &ws.p_coef, &ws.p_queue, &ws.p_ctr})
+                      &ws.delta_lm, &ws.coefx, &ws.p_dist, &ws.p_sigma, &ws.p_coef, &ws.p_queue, &ws.p_ctr})
       b->release();
     if (ws.pinned) cudaFreeHost(ws.pinned);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
@@ -717,6 +721,7 @@ bc_status bc_graph_free(bc_ctx *ctx, bc_graph g) {
   BC_GUARD_BEGIN
   auto it = ctx->graphs.find(g);
   if (it == ctx->graphs.end()) fail(BC_E_UNKNOWN_HANDLE, "unknown graph handle");
+  if (server_uses_graph(ctx, g)) fail(BC_E_INVALID, "graph is used by a queued or running query");
   sync(ctx);
   forget_heavy_meta(it->second.rp);
   cudaFree(it->second.rp);

@@ -16,6 +16,8 @@
 
 namespace bcg {
 
+struct Server;  // the query server behind bc_submit / bc_poll (bc_serve.cu)
+
 // Thrown inside the library only; converted to a bc_status at the ABI.
 struct Error {
   bc_status code;
@@ -61,12 +63,23 @@ enum Family {
 extern const char *kFamilyName[F_NFAM];
 
 // Where the backward pass of a batch writes its results.
+// Target entries: tslot[v] is the first entry e of vertex v (or -1); with
+// several concurrent queries, tnext[e] chains further entries of the same vertex
+// and an entry only takes lanes whose owner lane_q[t] equals its query eq[e].
 struct Sink {
-  const int32_t *tslot = nullptr;  // [n] target slot of a vertex or -1 (may be null)
-  double *tdelta = nullptr;        // [T][64] delta of slot j for lane t (lane-minor rows)
+  const int32_t *tslot = nullptr;  // [n] first target entry of a vertex or -1 (may be null)
+  const int32_t *tnext = nullptr;  // [E] next entry of the same vertex or -1 (null: one entry per vertex)
+  const int32_t *eq = nullptr;     // [E] query of the entry (null: every lane belongs to it)
+  const int32_t *lane_q = nullptr; // [64] query owning each lane
+  double *tdelta = nullptr;        // [E][64] delta of entry e for lane t (lane-minor rows)
   Acc *acc = nullptr;              // [n] exact all-vertex sum of delta over lanes (may be null)
   double *delta_lm = nullptr;      // [n][64] full per-lane delta (may be null)
 };
+
+__device__ __forceinline__ void sink_targets(const Sink &sink, int32_t v, int t, double d) {
+  for (int32_t e = sink.tslot[v]; e >= 0; e = sink.tnext ? sink.tnext[e] : -1)
+    if (!sink.eq || sink.lane_q[t] == sink.eq[e]) sink.tdelta[(size_t)e * 64 + t] = d;
+}
 
 struct Workspace {
   DevBuf lm;       // [lcap][n] u64 level masks
@@ -89,6 +102,7 @@ struct Workspace {
   DevBuf misc;     // scratch
   DevBuf misc2;
   DevBuf delta_lm; // [n][64] f64
+  DevBuf coefx;    // [n][64] uint4: coefficients as 128-bit fixed point (unit 2^-96)
   // plain single-source engine
   DevBuf p_dist, p_sigma, p_coef, p_queue, p_ctr;
   void *pinned = nullptr;  // 4 KiB pinned host staging
@@ -114,6 +128,13 @@ struct bc_ctx {
   double fam_ms[bcg::F_NFAM] = {};
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending_events;
   std::vector<cudaEvent_t> event_pool;
+  bcg::Server *server = nullptr;
+  // batched-engine tuning: degree above which a vertex is split into segments,
+  // and the segment length (0 = library defaults)
+  int32_t heavy_deg = 0, seg_len = 0;
+  // backward kernel form (128-bit window only): 1 = packed lane groups (default),
+  // 0 = two lane halves per thread
+  int32_t bwd_variant = 1;
 };
 
 namespace bcg {
@@ -150,5 +171,14 @@ void batch_ensure(bc_ctx *ctx, const Graph &g);
 void plain_source(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const Sink &sink, int32_t *dist_out,
                   uint64_t *sigma_out);
 void plain_ensure(bc_ctx *ctx, const Graph &g);
+
+// One batch of the per-sample step (plain or lane-batched, per the context's
+// width) for the sources already in ws.sources[0..count).
+void run_source_batch(bc_ctx *ctx, const Graph &g, int count, const Sink &sink);
+inline bool batch_width_is_plain(bc_ctx *ctx) { return ctx->batch_width == 1; }
+
+// query server lifetime (bc_serve.cu)
+void server_shutdown(bc_ctx *ctx);
+bool server_uses_graph(bc_ctx *ctx, bc_graph g);
 
 }  // namespace bcg

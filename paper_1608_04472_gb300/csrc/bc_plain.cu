@@ -151,10 +151,7 @@ k_pbwd(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, const in
       const double d = __dmul_rn(sigma_to_double(sg), acc_round(a));
       coef[v] = coef_of(d, sg);
       if (sink.delta_lm) sink.delta_lm[(size_t)v * 64] = d;
-      if (sink.tslot) {
-        const int32_t slot = sink.tslot[v];
-        if (slot >= 0) sink.tdelta[(size_t)slot * 64] = d;
-      }
+      if (sink.tslot) sink_targets(sink, v, 0, d);
       if (sink.acc) {
         Acc cur = sink.acc[v];
         acc_add(cur, d, e);
