@@ -64,6 +64,21 @@ def reduce_over_ranks(dist, device, ms: float, samples: float, edges: float):
     return float(t[0]), float(u[0]), float(u[1])
 
 
+def recorded_traffic():
+    """DRAM bytes per backward launch from the committed ncu summary, or None when
+    the kernel source has changed since the counters were taken."""
+    import hashlib
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "bwd_traffic_rmat_s20.md")).read()
+        val = float(txt.split("traffic_bytes_per_launch:")[1].split()[0])
+        sha = txt.split("sha256/16 = ")[1].split()[0]
+        cur = hashlib.sha256(open(os.path.join(ROOT, "paper_1608_04472_gb300", "csrc", "bc_batch.cu"),
+                                  "rb").read()).hexdigest()[:16]
+        return val if cur == sha else None
+    except Exception:
+        return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -285,9 +300,11 @@ def main():
     alg_bytes = bytes_bwd if dom == "bwd" else bytes_fwd
     dom_ms = kern[dom]["ms"]
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": f"{dom} (k_{dom}_light + heavy segments)", "achieved": achieved,
+    kern_names = {"bwd": "backward pass: k_bwd_light_fx + k_bwd_heavy_seg_fx + k_bwd_heavy_fin_fx per level",
+                  "fwd": "forward pass: k_fwd_light + k_fwd_heavy + k_fwd_heavy_fin per level"}
+    roofline = {"bound": "hbm", "kernel": kern_names[dom], "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": None, "peak_kind": peak_kind,
+                "traffic": recorded_traffic() if dom == "bwd" else None, "peak_kind": peak_kind,
                 "launches": kern[dom]["launches"], "avg_launch_ms": dom_ms / max(kern[dom]["launches"], 1),
                 "alg_bytes_per_launch": alg_bytes / max(kern[dom]["launches"], 1),
                 "dag_edges_per_sample": stats["dag_edges"] / max(lanes_processed, 1),
