@@ -211,6 +211,75 @@ def cpu_baseline(g, targets, budget_s=12.0):
             "sample": f"{k} per-sample Brandes steps (Bader draws of R-MAT s20), single-threaded C"}
 
 
+def measure_pairs(pkg, torch, local, stream, cap=2048, T=256):
+    """Algorithm 1 on BA n=2,000,000 (4 edges per new vertex, seed 3) with 256
+    degree-proportional targets and the paper's threshold c*n (c=1): every
+    target runs to the cap, so the run is `cap` pair draws plus one BFS per
+    target. Returns pair draws per second."""
+    import graphgen as gg
+    g = gg.barabasi_albert(2_000_000, 4, 3)
+    targets = gg.degree_targets(g, T, 3)
+    ctx = pkg.Context(local, batch_width=64, stream=stream.cuda_stream)
+    h = ctx.load_graph(g.row_ptr, g.col)
+    ctx.adaptive_pairs(h, targets[:8], 1.0, 64, 3, 1)  # warm-up
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = ctx.adaptive_pairs(h, targets, 1.0, cap, 3, 2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    return {"workload": f"BA n=2e6 m=4 seed 3, {T} degree-proportional targets, c=1 (threshold c*n), cap {cap}",
+            "pair_draws_per_s": cap / (ms / 1e3), "ms": ms, "targets_capped": int((res["status"] == 1).sum()),
+            "note": "includes one BFS per target (256) before the pair draws"}
+
+
+def measure_serving(pkg, g, h_ctx, rng_seed=7, nq=48, cap=1024):
+    """Continuous batching on the resident R-MAT s20 graph: a mix of Bader
+    queries (75 %) and pair queries (25 %), 1-64 uniform targets each, c in
+    {2, 5, 10}, cap draws each. Saturation rate from submitting all at once, then
+    Poisson arrivals at 0.5 and 0.8 of it; latency = submit -> result written."""
+    import graphgen as gg
+    ctx, h = h_ctx
+    rng = np.random.default_rng(rng_seed)
+    specs = []
+    for i in range(nq):
+        T = int(rng.integers(1, 65))
+        specs.append(dict(kind=pkg.BC_QUERY_PAIRS if rng.random() < 0.25 else pkg.BC_QUERY_SOURCES,
+                          targets=gg.uniform_targets(g.n, T, 1000 + i), c=float(rng.choice([2.0, 5.0, 10.0])),
+                          cap=cap, seed=SEED, qid=5_000_000 + i))
+
+    def run(rate):
+        tks = []
+        t0 = time.perf_counter()
+        for i, sp in enumerate(specs):
+            if rate:
+                time.sleep(float(rng.exponential(1.0 / rate)))
+            kw = dict(sp)
+            kw["qid"] = sp["qid"] + int(rate * 1000)
+            tks.append(ctx.submit(h, kw.pop("kind"), **kw))
+        for tk in tks:
+            ctx.poll(tk, -1)
+        wall = time.perf_counter() - t0
+        lat = np.array([tk.stats.queue_ms + tk.stats.run_ms for tk in tks])
+        samples = sum(int(tk.stats.samples) for tk in tks)
+        return wall, lat, samples
+
+    run(0)  # warm-up (per-query state allocation paths)
+    wall, lat, samples = run(0)
+    lam = nq / wall
+    out = {"workload": f"R-MAT s20 resident; {nq} queries, 75% Bader / 25% pairs, 1-64 targets, "
+                       f"c in {{2,5,10}}, cap {cap}",
+           "saturation_queries_per_s": lam, "saturation_samples_per_s": samples / wall,
+           "saturation_p50_ms": float(np.percentile(lat, 50)), "saturation_p99_ms": float(np.percentile(lat, 99))}
+    for frac in (0.5, 0.8):
+        wall, lat, samples = run(frac * lam)
+        out[f"load_{frac}"] = {"offered_queries_per_s": frac * lam, "p50_ms": float(np.percentile(lat, 50)),
+                               "p99_ms": float(np.percentile(lat, 99)), "samples_per_s": samples / wall}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -220,6 +289,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the pair-sampling (BA 2M) and serving-latency measurements")
     ap.add_argument("--cap", type=int, default=0,
                     help="override the Bader cap (default n/20); for short profiling runs only")
     ap.add_argument("--uniform-k", type=int, default=K_UNIFORM,
@@ -352,6 +423,10 @@ def main():
                         "batched_samples_per_s": kq / (ms_b / 1e3),
                         "speedup": ms_plain / ms_b,
                         "identical_estimates": bool(np.array_equal(est_plain, est_b))}
+
+    if rank == 0 and world == 1 and not args.no_extra:
+        out["serving"] = measure_serving(pkg, g, (ctx, h))
+        out["pairs"] = measure_pairs(pkg, torch, local, stream)
 
     if not args.no_e2e:
         e2e_steps = max(1, min(2, args.steps))

@@ -347,3 +347,44 @@ def test_rmat20_bader_first_draws(ctx, rmat20):
     ref = oracle.adaptive_sources(rmat20, targets, 5.0, 66, 2, 1)
     for key in ["k", "status", "S", "est"]:
         _assert_same(res[key], ref[key], key)
+
+
+# ------------------------------------------- pairs at the BA workload's size --
+
+@pytest.fixture(scope="module")
+def ba2m():
+    """Barabasi-Albert n=2,000,000, 4 edges per new vertex, seed 3."""
+    return gg.barabasi_albert(2_000_000, 4, 3)
+
+
+def test_ba2m_pairs_sampled(ctx, ba2m):
+    """Algorithm 1 on the full-size BA graph with degree-proportional targets and
+    the 64-wide pair batches: 4 targets and the top hub, cap 70 draws (a full batch + a ragged
+    one), literal threshold c*n; k, S, status and est bit-exact."""
+    targets = np.concatenate([gg.degree_targets(ba2m, 4, 3),
+                              [int(np.argmax(ba2m.degrees()))]]).astype(np.int32)  # + the top hub
+    targets = np.unique(targets)
+    h = ctx.load_graph(ba2m.row_ptr, ba2m.col)
+    try:
+        res = ctx.adaptive_pairs(h, targets, 1.0, 70, 3, 21)
+    finally:
+        ctx.free_graph(h)
+    ref = oracle.adaptive_pairs(ba2m, targets, 1.0, 70, 3, 21)
+    for key in ["k", "status", "S", "est"]:
+        _assert_same(res[key], ref[key], key)
+
+
+def test_ba20k_pairs_full_run():
+    """A complete Algorithm 1 run (every target stops before its cap under the
+    Bader-scaled test S*(n-1) > c*n) on BA n=20,000 built like the 2M workload."""
+    import paper_1608_04472_gb300 as pkg
+    g = gg.barabasi_albert(20_000, 4, 3)
+    targets = np.argsort(-g.degrees(), kind="stable")[:8].astype(np.int32)  # the hubs: high BC
+    scale = float(g.n - 1)
+    ref = oracle.adaptive_pairs(g, targets, 2.0, 6000, 4, 4, threshold_scale=scale)
+    with pkg.Context(0, batch_width=64) as c:
+        h = c.load_graph(g.row_ptr, g.col)
+        res = c.adaptive_pairs(h, targets, 2.0, 6000, 4, 4, threshold_scale=scale)
+    for key in ["k", "status", "S", "est"]:
+        _assert_same(res[key], ref[key], key)
+    assert np.all(res["status"] == pkg.BC_STOPPED)
