@@ -225,6 +225,39 @@ bc_status bc_draw_pairs(bc_ctx *ctx, uint64_t seed, uint64_t qid, uint64_t i0, i
  * [2^-76, 2^63) or be 0 (else BC_E_RANGE). */
 bc_status bc_exact_sum(bc_ctx *ctx, const double *x, int64_t count, double *out);
 
+/* ------------------------------------------------- allocation-free entry -- */
+/*
+ * Not from the paper (it has no counterpart): a variant of bc_source_dependencies
+ * for callers that cannot allocate device memory -- for example a host
+ * application whose own allocator owns all GPU memory, or code running where
+ * allocation calls are not permitted. It performs no cudaMalloc, cudaFree or
+ * other allocation and needs no bc_ctx. Its scratch (distances, path counts,
+ * coefficients, queue, exact sums; about 12 MB) is one fixed array in the
+ * library's device memory, which every GPU that loads the library keeps until
+ * the process exits.
+ *
+ *   device          CUDA device to run on (the caller's current device is restored)
+ *   d_row_ptr[n+1], d_col[nnz]   DEVICE pointers: a valid undirected CSR as
+ *                   bc_graph_load_csr requires (sorted rows, symmetric, no loops
+ *                   or duplicates, columns in [0, n)); not validated here
+ *   n               1 .. BC_NOALLOC_MAX_VERTICES, else BC_E_TOO_LARGE
+ *   d_sources[count]             DEVICE pointer, every entry in [0, n)
+ *   d_delta_out[count*n]         DEVICE pointer: row i receives delta_{s_i}(v),
+ *                   exactly as bc_source_dependencies computes it
+ *   stream          cudaStream_t to run on (NULL = the legacy default stream);
+ *                   the call returns after its work on that stream is done
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture on
+ * that device. All calls share the one array and each call re-initialises the
+ * parts it reads, so calls whose GPU work overlaps (different streams or host
+ * threads at the same time) race on it and must be serialised by the caller.
+ */
+#define BC_NOALLOC_MAX_VERTICES 262144
+bc_status bc_source_dependencies_noalloc(int device, const int32_t *d_row_ptr, const int32_t *d_col,
+                                         int32_t n, int64_t nnz, const int32_t *d_sources, int32_t count,
+                                         double *d_delta_out, void *stream);
+
 /* Run statistics accumulated since the last reset. When profiling is on, each
  * kernel family's launches are bracketed by CUDA events on the launch stream. */
 typedef struct bc_stats {

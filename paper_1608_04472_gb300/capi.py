@@ -83,6 +83,7 @@ _SIGS = {
     "bc_poll": (_i32, [_vp, _i64, _i64]),
     "bc_cancel": (_i32, [_vp, _i64]),
     "bc_server_limits": (_i32, [_vp, _i32, _i64]),
+    "bc_source_dependencies_noalloc": (_i32, [ctypes.c_int, _vp, _vp, _i32, _i64, _vp, _i32, _vp, _vp]),
     "bc_draw_sources": (_i32, [_vp, _u64, _u64, _u64, _i64, _i32, _i32p]),
     "bc_draw_pairs": (_i32, [_vp, _u64, _u64, _u64, _i64, _i32, _i32p, _i32p]),
     "bc_exact_sum": (_i32, [_vp, _f64p, _i64, _f64p]),
@@ -277,6 +278,19 @@ def bc_cancel(ctx, ticket: Ticket):
 
 def bc_server_limits(ctx, max_active: int = 0, mem_budget_bytes: int = 0):
     _ck(ctx, _lib.bc_server_limits(ctx, max_active, mem_budget_bytes))
+
+
+BC_NOALLOC_MAX_VERTICES = 262144
+
+
+def bc_source_dependencies_noalloc(device: int, d_row_ptr: int, d_col: int, n: int, nnz: int,
+                                   d_sources: int, count: int, d_delta_out: int, stream: int = 0) -> int:
+    """Allocation-free per-source dependencies on caller-owned DEVICE buffers
+    (addresses as ints, e.g. torch tensors' data_ptr()). Returns the status code;
+    there is no context, so there is no error message."""
+    return int(_lib.bc_source_dependencies_noalloc(device, d_row_ptr or None, d_col or None, n, nnz,
+                                                   d_sources or None, count, d_delta_out or None,
+                                                   stream or None))
 
 
 def bc_draw_sources(ctx, seed: int, qid: int, i0: int, count: int, n: int) -> np.ndarray:

@@ -290,3 +290,142 @@ void plain_pair(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t
 }
 
 }  // namespace bcg
+
+// --------------------------------------------------- allocation-free variant --
+// For callers that cannot allocate device memory (their process hands all GPU
+// memory to its own pool or allocator, or allocation calls are not permitted
+// where they run): the plain per-source step on caller-owned device buffers,
+// with every scratch array carved out of one fixed file-scope device array.
+namespace bcg {
+namespace noalloc {
+
+constexpr int64_t MAXN = BC_NOALLOC_MAX_VERTICES;
+// dist i32[n] | sigma u64[n] | coef f64[n] | queue i32[n] | acc Acc[n] | control
+constexpr size_t OFF_DIST = 0;
+constexpr size_t OFF_SIGMA = OFF_DIST + 4 * MAXN;
+constexpr size_t OFF_COEF = OFF_SIGMA + 8 * MAXN;
+constexpr size_t OFF_QUEUE = OFF_COEF + 8 * MAXN;
+constexpr size_t OFF_ACC = OFF_QUEUE + 4 * MAXN;
+constexpr size_t OFF_CTL = OFF_ACC + sizeof(Acc) * MAXN;  // PlainCtr | err u32 | cnt u64[2]
+constexpr size_t BYTES = OFF_CTL + 256;
+
+static __device__ __align__(256) unsigned char g_scratch[BYTES];
+
+static std::mutex g_mu;
+static unsigned char *g_addr[64] = {};  // device address of g_scratch, per device
+
+__global__ void k_acc_to_row(int32_t n, const Acc *__restrict__ acc, double *__restrict__ out) {
+  const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) out[v] = acc_round(acc[v]);  // one term per vertex: the sum is delta itself
+}
+
+static bc_status scratch_of(int device, unsigned char **out) {
+  if (device < 0 || device >= 64) return BC_E_INVALID;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_addr[device]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return BC_E_DEVICE;
+    }
+    g_addr[device] = static_cast<unsigned char *>(p);
+  }
+  *out = g_addr[device];
+  return BC_OK;
+}
+
+static bc_status run(const int32_t *rp, const int32_t *col, int32_t n, int64_t nnz, const int32_t *sources,
+                     int32_t count, double *delta, cudaStream_t st, unsigned char *base) {
+  int32_t *dist = reinterpret_cast<int32_t *>(base + OFF_DIST);
+  uint64_t *sigma = reinterpret_cast<uint64_t *>(base + OFF_SIGMA);
+  double *coef = reinterpret_cast<double *>(base + OFF_COEF);
+  int32_t *queue = reinterpret_cast<int32_t *>(base + OFF_QUEUE);
+  Acc *acc = reinterpret_cast<Acc *>(base + OFF_ACC);
+  PlainCtr *ctr = reinterpret_cast<PlainCtr *>(base + OFF_CTL);
+  unsigned *err = reinterpret_cast<unsigned *>(base + OFF_CTL + 64);
+  unsigned long long *cnt = reinterpret_cast<unsigned long long *>(base + OFF_CTL + 128);
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = (sms > 0 ? sms : 148) * 8;
+  if (cudaMemsetAsync(err, 0, 4, st) != cudaSuccess) return BC_E_DEVICE;
+  Sink sink;
+  sink.acc = acc;
+  for (int32_t i = 0; i < count; ++i) {
+    // every scratch array that is read before written starts from zero / -1
+    if (cudaMemsetAsync(dist, 0xFF, (size_t)n * 4, st) != cudaSuccess ||
+        cudaMemsetAsync(sigma, 0, (size_t)n * 8, st) != cudaSuccess ||
+        cudaMemsetAsync(acc, 0, (size_t)n * sizeof(Acc), st) != cudaSuccess)
+      return BC_E_DEVICE;
+    k_pinit<<<1, 1, 0, st>>>(sources + i, rp, dist, sigma, queue, ctr);
+    PlainCtr h;
+    if (cudaMemcpyAsync(&h, ctr, sizeof(PlainCtr), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return BC_E_DEVICE;
+    std::vector<int32_t> offs(1, 0);
+    int32_t qb = 0, qe = 1;
+    int64_t frontier_edges = (int64_t)h.next_edges, explored = 0;
+    int level = 0;
+    for (;;) {
+      offs.push_back(qe);
+      explored += frontier_edges;
+      if (cudaMemsetAsync(&ctr->next_edges, 0, sizeof(unsigned long long), st) != cudaSuccess) return BC_E_DEVICE;
+      if (frontier_edges * ALPHA > nnz - explored) {
+        k_pbu<<<blocks, PTHREADS, 0, st>>>(n, rp, col, level, dist, sigma, queue, ctr, err, cnt);
+      } else {
+        const int nb = std::max(1, std::min(blocks, (qe - qb + 7) / 8));
+        k_ptd<<<nb, PTHREADS, 0, st>>>(rp, col, queue, qb, qe, level, dist, sigma, queue, ctr, err, cnt);
+      }
+      if (cudaMemcpyAsync(&h, ctr, sizeof(PlainCtr), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return BC_E_DEVICE;
+      frontier_edges = (int64_t)h.next_edges;
+      if (h.qtail == qe) break;
+      qb = qe;
+      qe = h.qtail;
+      ++level;
+    }
+    for (int l = level; l >= 1; --l) {
+      const int32_t b = offs[l], e = offs[l + 1];
+      if (e <= b) continue;
+      const int nb = std::max(1, std::min(blocks, (e - b + 7) / 8));
+      k_pbwd<<<nb, PTHREADS, 0, st>>>(rp, col, queue, b, e, l, dist, sigma, coef, sink, err);
+    }
+    k_acc_to_row<<<(n + 255) / 256, 256, 0, st>>>(n, acc, delta + (size_t)i * n);
+  }
+  unsigned e = 0;
+  if (cudaGetLastError() != cudaSuccess) return BC_E_DEVICE;
+  if (cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+    return BC_E_DEVICE;
+  if (e & ERR_SIGMA_OVERFLOW) return BC_E_SIGMA_OVERFLOW;
+  if (e & ERR_RANGE) return BC_E_RANGE;
+  return BC_OK;
+}
+
+}  // namespace noalloc
+}  // namespace bcg
+
+extern "C" bc_status bc_source_dependencies_noalloc(int device, const int32_t *d_row_ptr, const int32_t *d_col,
+                                                    int32_t n, int64_t nnz, const int32_t *d_sources,
+                                                    int32_t count, double *d_delta_out, void *stream) {
+  using namespace bcg;
+  if (n < 1 || nnz < 0 || count < 0) return BC_E_INVALID;
+  if ((int64_t)n > noalloc::MAXN || nnz >= ((int64_t)1 << 31)) return BC_E_TOO_LARGE;
+  if (!d_row_ptr || (nnz > 0 && !d_col) || (count > 0 && (!d_sources || !d_delta_out))) return BC_E_INVALID;
+  if (count == 0) return BC_OK;
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) {
+    cudaGetLastError();
+    return BC_E_DEVICE;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return BC_E_INVALID;
+  }
+  unsigned char *base = nullptr;
+  bc_status rc = noalloc::scratch_of(device, &base);
+  if (rc == BC_OK)
+    rc = noalloc::run(d_row_ptr, d_col, n, nnz, d_sources, count, d_delta_out, static_cast<cudaStream_t>(stream), base);
+  cudaSetDevice(prev);
+  return rc;
+}
