@@ -151,13 +151,30 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
   uint64_t any_new = 0ull, smax = 0ull;
   unsigned long long tri = 0ull, rch = 0ull;
   unsigned e = 0u;
-  for (int base = grab(wq); base < n; base = grab(wq))
-  for (int v = base; v < min(base + GRAB, n); ++v) {
-    const int beg = rp[v], end = rp[v + 1];
-    const uint64_t vis = visited[v];
+  // a warp takes 32 vertices; each thread loads one vertex's header, and only
+  // vertices with unvisited active lanes and light degree are walked
+  for (int base = grab(wq, 32); base < n; base = grab(wq, 32)) {
+    const int vl = base + lane;
+    int hb = 0, he = 0;
+    uint64_t hv = 0ull;
+    bool work = false;
+    if (vl < n) {
+      hb = rp[vl];
+      he = rp[vl + 1];
+      hv = visited[vl];
+      work = ((~hv & act) != 0ull) && he > hb && he - hb <= heavy_deg;
+      if (!work) lm_cur[vl] = 0ull;  // heavy vertices are then filled by their segments
+    }
+    unsigned todo = __ballot_sync(FULL, work);
+    while (todo) {
+    const int iv = __ffs(todo) - 1;
+    todo &= todo - 1u;
+    const int v = base + iv;
+    const int beg = __shfl_sync(FULL, hb, iv), end = __shfl_sync(FULL, he, iv);
+    const uint64_t vis = __shfl_sync(FULL, hv, iv);
     const uint64_t pend = ~vis & act;
     uint64_t newm = 0ull;
-    if (pend && end - beg <= heavy_deg) {
+    {
       uint64_t s0 = 0ull, s1 = 0ull;
       for (int base = beg; base < end; base += 32) {
         const int j = base + lane;
@@ -208,6 +225,7 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
     }
     rch += (unsigned long long)__popcll((long long)newm);
     any_new |= newm;
+    }
   }
   if (e) atomicOr(err, e);
   if (lane == 0 && (tri | rch)) {
@@ -715,6 +733,119 @@ __device__ __forceinline__ void gather_packed(int beg, int end, uint64_t lanes, 
   for (int off = 1 << pk.glog; off < 32; off <<= 1) acc2_shfl_xor_add(a0, off);
 }
 
+// Forward, packed: predecessor sigma sums for the lanes `newm` that reach v at
+// this level (thread (g, s) of the packed layout owns the s-th lane of newm).
+__device__ __forceinline__ void gather_sigma_packed(int beg, int end, uint64_t newm, const uint64_t *__restrict__ lm_prev,
+                                                    const int32_t *__restrict__ col, const uint64_t *__restrict__ sigma,
+                                                    const Packed &pk, int32_t *list, uint64_t &s0, uint64_t &s1,
+                                                    unsigned &e, unsigned long long &tri) {
+  const int lane = threadIdx.x & 31;
+  const int NG = 32 >> pk.glog, g = lane >> pk.glog;
+  const uint64_t b0 = pk.p0 >= 0 ? (1ull << pk.p0) : 0ull, b1 = pk.p1 >= 0 ? (1ull << pk.p1) : 0ull;
+  const int q0 = pk.p0 < 0 ? 0 : pk.p0, q1 = pk.p1 < 0 ? 0 : pk.p1;
+  for (int base = beg; base < end; base += 32) {
+    const int j = base + lane;
+    int32_t w = 0;
+    uint64_t m = 0ull;
+    if (j < end) {
+      w = col[j];
+      m = lm_prev[w] & newm;
+    }
+    const unsigned bal = __ballot_sync(FULL, m != 0ull);
+    const int cnt = __popc(bal);
+    tri += (unsigned long long)__reduce_add_sync(FULL, (unsigned)__popcll((long long)m));
+    if (m != 0ull) list[__popc(bal & ((1u << lane) - 1u))] = lane;
+    __syncwarp();
+    for (int r = 0; r < cnt; r += 2 * NG) {
+      const int i0 = r + g, i1 = r + NG + g;
+      const bool h0 = i0 < cnt, h1 = i1 < cnt;
+      const int x0s = h0 ? list[i0] : 0, x1s = h1 ? list[i1] : 0;
+      const uint64_t m0 = __shfl_sync(FULL, m, x0s), m1 = __shfl_sync(FULL, m, x1s);
+      const int32_t w0 = __shfl_sync(FULL, w, x0s), w1 = __shfl_sync(FULL, w, x1s);
+      const uint64_t a0 = (h0 && (m0 & b0)) ? sigma[(size_t)w0 * 64 + q0] : 0ull;
+      const uint64_t a1 = (h1 && (m1 & b0)) ? sigma[(size_t)w1 * 64 + q0] : 0ull;
+      if (pk.two) {
+        const uint64_t c0 = (h0 && (m0 & b1)) ? sigma[(size_t)w0 * 64 + q1] : 0ull;
+        const uint64_t c1 = (h1 && (m1 & b1)) ? sigma[(size_t)w1 * 64 + q1] : 0ull;
+        uint64_t t = s1 + c0;
+        if (t < s1) e |= ERR_SIGMA_OVERFLOW;
+        s1 = t + c1;
+        if (s1 < t) e |= ERR_SIGMA_OVERFLOW;
+      }
+      uint64_t t = s0 + a0;
+      if (t < s0) e |= ERR_SIGMA_OVERFLOW;
+      s0 = t + a1;
+      if (s0 < t) e |= ERR_SIGMA_OVERFLOW;
+    }
+    __syncwarp();
+  }
+  for (int off = 1 << pk.glog; off < 32; off <<= 1) {
+    const uint64_t o = __shfl_xor_sync(FULL, s0, off);
+    const uint64_t t = s0 + o;
+    if (t < s0) e |= ERR_SIGMA_OVERFLOW;
+    s0 = t;
+  }
+}
+
+// Forward level, two phases per vertex: an OR-scan of the neighbours' level
+// masks finds the lanes that reach v at this level; only then are the
+// predecessors' sigma values summed, packed over exactly those lanes.
+__global__ void __launch_bounds__(FWD_THREADS)
+k_fwd_light_pk(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+               const uint64_t *__restrict__ lm_prev, uint64_t *__restrict__ lm_cur,
+               uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
+               const uint64_t *__restrict__ active_prev, uint64_t *__restrict__ enable,
+               uint64_t *__restrict__ active_cur, unsigned *__restrict__ err,
+               unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq, int heavy_deg) {
+  __shared__ int32_t lists[FWD_THREADS / 32][32];
+  __shared__ int8_t tabs[FWD_THREADS / 32][64];
+  int32_t *list = lists[threadIdx.x >> 5];
+  int8_t *tab = tabs[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const uint64_t act = *active_prev & *enable;
+  uint64_t any_new = 0ull, smax = 0ull;
+  unsigned long long tri = 0ull, rch = 0ull;
+  unsigned e = 0u;
+  for (int base = grab(wq); base < n; base = grab(wq))
+    for (int v = base; v < min(base + GRAB, n); ++v) {
+      const int beg = rp[v], end = rp[v + 1];
+      const uint64_t vis = visited[v];
+      const uint64_t pend = ~vis & act;
+      uint64_t newm = 0ull;
+      if (pend && end - beg <= heavy_deg) {
+        for (int j = beg + lane; j < end; j += 32) newm |= lm_prev[col[j]] & pend;
+        newm = warp_or64(newm);
+        if (newm) {
+          const Packed pk = pack_lanes(newm, tab);
+          uint64_t s0 = 0ull, s1 = 0ull;
+          gather_sigma_packed(beg, end, newm, lm_prev, col, sigma, pk, list, s0, s1, e, tri);
+          if ((lane >> pk.glog) == 0 && pk.p0 >= 0) {
+            sigma[(size_t)v * 64 + pk.p0] = s0;
+            smax = s0 > smax ? s0 : smax;
+          }
+          if (pk.p1 >= 0) {
+            sigma[(size_t)v * 64 + pk.p1] = s1;
+            smax = s1 > smax ? s1 : smax;
+          }
+        }
+      }
+      if (lane == 0) {
+        lm_cur[v] = newm;
+        if (newm) visited[v] = vis | newm;
+      }
+      rch += (unsigned long long)__popcll((long long)newm);
+      any_new |= newm;
+    }
+  if (e) atomicOr(err, e);
+  if (lane == 0 && (tri | rch)) {
+    atomicAdd(cnt, tri);
+    atomicAdd(cnt + 1, rch);
+  }
+  smax = warp_max64(smax);
+  if (lane == 0 && smax > 1ull) atomicMax((unsigned long long *)(enable + 2), (unsigned long long)smax);
+  block_or_to(any_new, active_cur);
+}
+
 // Finished lanes of v (threads of group 0 own them) into the ring.
 __device__ __forceinline__ void ring_append_fx(Ring &R, unsigned &tail, int32_t v, uint64_t lanes, const Packed &pk,
                                                const Acc2 &a0, const Acc2 &a1, const uint64_t *__restrict__ row) {
@@ -1013,7 +1144,8 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs) {
     uint64_t *act = ws.active.as<uint64_t>();
     {
       LaunchScope ls(ctx, F_FWD);
-      k_fwd_light<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
+      auto kfwd = ctx->fwd_variant == 1 ? k_fwd_light_pk : k_fwd_light;
+      kfwd<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
                                                  ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(), act + l,
                                                  ws.enable.as<uint64_t>(), act + l + 1, ws.err.as<unsigned>(),
                                                  ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 0,

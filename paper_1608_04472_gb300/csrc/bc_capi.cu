@@ -18,6 +18,7 @@
 namespace bcg {
 
 void forget_heavy_meta(const int32_t *rp);
+void forget_key_meta(const int32_t *rp);
 void plain_pair(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dest);
 
 const char *kFamilyName[F_NFAM] = {"draw", "init", "fwd", "bwd", "scan", "pair", "misc", "plain_fwd", "plain_bwd"};
@@ -164,14 +165,14 @@ struct ScanState {
 // Sequential stop test per target, in draw order (Sec. 4 step 3; Algorithm 1's
 // while-condition): S <- S + x_i, k <- k + 1, stop at the first S*scale > cn.
 __global__ void k_stop_scan(int T, int count, const double *__restrict__ vals, ScanState st, int64_t k0,
-                            double cn, double scale) {
+                            double cn, double scale, int stride) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= T || st.done[j]) return;
   double S = st.S[j];
   int64_t k = k0;
   bool stop = false;
   for (int t = 0; t < count; ++t) {
-    S = __dadd_rn(S, vals[(size_t)j * 64 + t]);
+    S = __dadd_rn(S, vals[(size_t)j * stride + t]);
     k = k0 + t + 1;
     if (__dmul_rn(S, scale) > cn) {
       stop = true;
@@ -275,6 +276,48 @@ __global__ void k_validate(int32_t n, const int32_t *__restrict__ rp, const int3
   }
 }
 
+// Key of a vertex for grouping sampled sources: its distance from the graph's
+// highest-degree vertex (capped at 254), 255 when unreachable from it.
+__global__ void k_make_key(int32_t n, const int32_t *__restrict__ dist, uint8_t *__restrict__ key) {
+  const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) {
+    const int32_t d = dist[v];
+    key[v] = d < 0 ? 255 : (uint8_t)(d > 254 ? 254 : d);
+  }
+}
+
+// Counting sort of a window of W <= 1024 drawn sources by key (one block).
+// sorted_src[i] is a source, sorted_pos[i] its draw position in the window.
+__global__ void __launch_bounds__(1024)
+k_sort_window(int W, const int32_t *__restrict__ draws, const uint8_t *__restrict__ key,
+              int32_t *__restrict__ sorted_src, int32_t *__restrict__ sorted_pos) {
+  __shared__ int hist[256];
+  __shared__ int off[256];
+  const int i = threadIdx.x;
+  if (i < 256) hist[i] = 0;
+  __syncthreads();
+  int src = 0, kk = 0, rank = 0;
+  if (i < W) {
+    src = draws[i];
+    kk = key[src];
+    rank = atomicAdd(&hist[kk], 1);
+  }
+  __syncthreads();
+  if (i == 0) {
+    int acc = 0;
+    for (int b = 0; b < 256; ++b) {
+      off[b] = acc;
+      acc += hist[b];
+    }
+  }
+  __syncthreads();
+  if (i < W) {
+    const int pos = off[kk] + rank;
+    sorted_src[pos] = src;
+    sorted_pos[pos] = i;
+  }
+}
+
 // --------------------------------------------------------------- helpers ----
 
 static int batch_width(bc_ctx *ctx) {
@@ -363,6 +406,95 @@ static void copy_scan_out(bc_ctx *ctx, int32_t T, const ScanState &st, double sc
 
 // ---------------------------------------------------------------- drivers ---
 
+// Per-graph source keys (distance from the hub) and, for exact BC, all
+// vertices ordered by key; computed on first use with one BFS from the hub.
+struct KeyMeta {
+  DevBuf key, order;
+};
+static std::map<const int32_t *, KeyMeta> g_keys;
+static std::mutex g_keys_mu;
+
+void forget_key_meta(const int32_t *rp) {
+  std::lock_guard<std::mutex> lk(g_keys_mu);
+  auto it = g_keys.find(rp);
+  if (it == g_keys.end()) return;
+  it->second.key.release();
+  it->second.order.release();
+  g_keys.erase(it);
+}
+
+static KeyMeta &key_meta(bc_ctx *ctx, const Graph &g, bool need_order) {
+  std::lock_guard<std::mutex> lk(g_keys_mu);
+  KeyMeta &km = g_keys[g.rp];
+  Workspace &ws = ctx->ws;
+  const size_t n = (size_t)g.n;
+  if (!km.key.p) {
+    km.key.ensure(n);
+    const int32_t hub = g.hub;
+    BCG_CUDA(cudaMemcpyAsync(ws.sources.p, &hub, 4, cudaMemcpyHostToDevice, ctx->stream));
+    const int64_t s0 = ctx->samples, b0 = ctx->batches;
+    const int maxl = batch_forward(ctx, g, 1, false);
+    ctx->samples = s0;
+    ctx->batches = b0;
+    DevBuf dist;
+    dist.ensure(n * 4);
+    try {
+      batch_extract(ctx, g, 1, maxl, dist.as<int32_t>(), nullptr, 1, (int64_t)n);
+      {
+        LaunchScope ls(ctx, F_MISC);
+        k_make_key<<<(g.n + 255) / 256, 256, 0, ctx->stream>>>(g.n, dist.as<int32_t>(), km.key.as<uint8_t>());
+      }
+      sync(ctx);
+    } catch (...) {
+      dist.release();
+      throw;
+    }
+    dist.release();
+  }
+  if (need_order && !km.order.p) {
+    std::vector<uint8_t> key(n);
+    BCG_CUDA(cudaMemcpy(key.data(), km.key.p, n, cudaMemcpyDeviceToHost));
+    std::vector<int64_t> cnt(257, 0);
+    for (size_t v = 0; v < n; ++v) cnt[key[v] + 1]++;
+    for (int b = 0; b < 256; ++b) cnt[b + 1] += cnt[b];
+    std::vector<int32_t> order(n);
+    for (size_t v = 0; v < n; ++v) order[cnt[key[v]]++] = (int32_t)v;
+    km.order.ensure(n * 4);
+    BCG_CUDA(cudaMemcpy(km.order.p, order.data(), n * 4, cudaMemcpyHostToDevice));
+  }
+  return km;
+}
+
+constexpr int WMAX = 1024;
+
+// Draws [i0, i0+W) of (seed, qid), grouped by source key: afterwards
+// ws.win = draws[W] | sorted sources[W] | sorted draw positions[W].
+static void draw_window(bc_ctx *ctx, const Graph &g, const KeyMeta &km, uint64_t seed, uint64_t qid, int64_t i0,
+                        int W) {
+  Workspace &ws = ctx->ws;
+  ws.win.ensure(3 * WMAX * 4);
+  int32_t *draws = ws.win.as<int32_t>();
+  launch_draw_sources(ctx, seed, qid, (uint64_t)i0, W, g.n, draws);
+  LaunchScope ls(ctx, F_DRAW);
+  k_sort_window<<<1, 1024, 0, ctx->stream>>>(W, draws, km.key.as<uint8_t>(), draws + WMAX, draws + 2 * WMAX);
+}
+
+// Runs the window's sources in batches of the context's width; lane t of the
+// batch starting at position b is the window's sorted entry b + t.
+static void run_window(bc_ctx *ctx, const Graph &g, int W, Sink sink) {
+  Workspace &ws = ctx->ws;
+  const int width = batch_width(ctx);
+  const int32_t *sorted_src = ws.win.as<int32_t>() + WMAX;
+  const int32_t *sorted_pos = ws.win.as<int32_t>() + 2 * WMAX;
+  for (int b = 0; b < W; b += width) {
+    const int count = std::min(width, W - b);
+    BCG_CUDA(cudaMemcpyAsync(ws.sources.p, sorted_src + b, (size_t)count * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    Sink sk = sink;
+    if (sk.tslot) sk.lane_col = sorted_pos + b;
+    run_source_batch(ctx, g, count, sk);
+  }
+}
+
 static void do_exact_or_uniform(bc_ctx *ctx, const Graph &g, bool exact, int64_t k, uint64_t seed, uint64_t qid,
                                 double *out) {
   Workspace &ws = ctx->ws;
@@ -372,16 +504,21 @@ static void do_exact_or_uniform(bc_ctx *ctx, const Graph &g, bool exact, int64_t
   Sink sink;
   sink.acc = ws.acc.as<Acc>();
   const int width = batch_width(ctx);
-  const int64_t total = exact ? (int64_t)g.n : k;
-  for (int64_t i0 = 0; i0 < total; i0 += width) {
-    const int count = (int)std::min<int64_t>(width, total - i0);
-    if (exact) {
-      LaunchScope ls(ctx, F_DRAW);
-      k_iota<<<1, 64, 0, ctx->stream>>>(count, (int32_t)i0, ws.sources.as<int32_t>());
-    } else {
-      launch_draw_sources(ctx, seed, qid, (uint64_t)i0, count, g.n, ws.sources.as<int32_t>());
+  KeyMeta &km = key_meta(ctx, g, exact);
+  if (exact) {
+    // all n sources, grouped by key (the sum over sources is exact, so any order)
+    for (int64_t i0 = 0; i0 < (int64_t)g.n; i0 += width) {
+      const int count = (int)std::min<int64_t>(width, (int64_t)g.n - i0);
+      BCG_CUDA(cudaMemcpyAsync(ws.sources.p, km.order.as<int32_t>() + i0, (size_t)count * 4,
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+      run_source_batch(ctx, g, count, sink);
     }
-    run_source_batch(ctx, g, count, sink);
+  } else {
+    for (int64_t i0 = 0; i0 < k; i0 += WMAX) {
+      const int W = (int)std::min<int64_t>(WMAX, k - i0);
+      draw_window(ctx, g, km, seed, qid, i0, W);
+      run_window(ctx, g, W, sink);
+    }
   }
   ws.misc2.ensure(n * 8);
   {
@@ -393,6 +530,11 @@ static void do_exact_or_uniform(bc_ctx *ctx, const Graph &g, bool exact, int64_t
   BCG_CUDA(cudaMemcpy(out, ws.misc2.p, n * 8, cudaMemcpyDeviceToHost));
 }
 
+// Bader's loop over windows of draws: each window's draws run grouped by source
+// key, their target dependencies land in draw order, and the stop scan walks
+// the window in draw order. The window grows with the number of draws already
+// made (64 .. 1024), so draws past the last stop are at most about half of
+// those made.
 static void do_adaptive_sources(bc_ctx *ctx, const Graph &g, const int32_t *targets, int32_t T, double c,
                                 int64_t cap, uint64_t seed, uint64_t qid, double *est, int64_t *k, double *S,
                                 int32_t *status) {
@@ -400,7 +542,7 @@ static void do_adaptive_sources(bc_ctx *ctx, const Graph &g, const int32_t *targ
   const size_t n = (size_t)g.n;
   cudaStream_t st = ctx->stream;
   ws.tslot.ensure(n * 4);
-  ws.tdelta.ensure((size_t)std::max(T, 1) * 64 * 8);
+  ws.tdelta.ensure((size_t)std::max(T, 1) * WMAX * 8);
   {
     LaunchScope ls(ctx, F_MISC);
     k_fill_i32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((int64_t)n, -1, ws.tslot.as<int32_t>());
@@ -412,22 +554,25 @@ static void do_adaptive_sources(bc_ctx *ctx, const Graph &g, const int32_t *targ
     k_set_slots<<<(T + 127) / 128, 128, 0, st>>>(T, d_targets, ws.tslot.as<int32_t>());
   }
   ScanState ss = make_scan(ctx, T);
-  Sink sink;
-  sink.tslot = ws.tslot.as<int32_t>();
-  sink.tdelta = ws.tdelta.as<double>();
+  KeyMeta &km = key_meta(ctx, g, false);
   const double cn = c * (double)g.n;
-  const int width = batch_width(ctx);
   int32_t remaining = T;
-  for (int64_t i0 = 0; i0 < cap && remaining > 0; i0 += width) {
-    const int count = (int)std::min<int64_t>(width, cap - i0);
-    launch_draw_sources(ctx, seed, qid, (uint64_t)i0, count, g.n, ws.sources.as<int32_t>());
-    BCG_CUDA(cudaMemsetAsync(ws.tdelta.p, 0, (size_t)T * 64 * 8, st));
-    run_source_batch(ctx, g, count, sink);
+  for (int64_t i0 = 0; i0 < cap && remaining > 0;) {
+    const int64_t want = std::max<int64_t>(64, i0 / 2);
+    const int W = (int)std::min<int64_t>(std::min<int64_t>(WMAX, want), cap - i0);
+    draw_window(ctx, g, km, seed, qid, i0, W);
+    BCG_CUDA(cudaMemsetAsync(ws.tdelta.p, 0, (size_t)T * W * 8, st));
+    Sink sink;
+    sink.tslot = ws.tslot.as<int32_t>();
+    sink.tdelta = ws.tdelta.as<double>();
+    sink.tstride = W;
+    run_window(ctx, g, W, sink);
     {
       LaunchScope ls(ctx, F_SCAN);
-      k_stop_scan<<<(T + 127) / 128, 128, 0, st>>>(T, count, ws.tdelta.as<double>(), ss, i0, cn, 1.0);
+      k_stop_scan<<<(T + 127) / 128, 128, 0, st>>>(T, W, ws.tdelta.as<double>(), ss, i0, cn, 1.0, W);
     }
     remaining = read_remaining(ctx, ss);
+    i0 += W;
   }
   check_err_bits(ctx);
   copy_scan_out(ctx, T, ss, (double)g.n, est, k, S, status);
@@ -479,7 +624,7 @@ static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *target
       }
       {
         LaunchScope ls(ctx, F_SCAN);
-        k_stop_scan<<<(T + 127) / 128, 128, 0, st>>>(T, count, ws.tdelta.as<double>(), ss, i0, cn, scale);
+        k_stop_scan<<<(T + 127) / 128, 128, 0, st>>>(T, count, ws.tdelta.as<double>(), ss, i0, cn, scale, 64);
       }
       remaining = read_remaining(ctx, ss);
     }
@@ -603,6 +748,7 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
     if (const char *hd = std::getenv("BCG_HEAVY_DEGREE")) ctx->heavy_deg = std::atoi(hd);
     if (const char *sl = std::getenv("BCG_SEGMENT")) ctx->seg_len = std::atoi(sl);
     if (const char *bv = std::getenv("BCG_BWD_VARIANT")) ctx->bwd_variant = std::atoi(bv);
+    if (const char *fv = std::getenv("BCG_FWD_VARIANT")) ctx->fwd_variant = std::atoi(fv);
     BCG_CUDA(cudaMallocHost(&ctx->ws.pinned, 4096));
     ctx->ws.enable.ensure(64);   // [0] lane enable mask, [1] pair continuation word
     ctx->ws.sources.ensure(64 * 4);
@@ -631,6 +777,7 @@ void bc_destroy(bc_ctx *ctx) {
     resolve_events(ctx);
     for (auto &kv : ctx->graphs) {
       forget_heavy_meta(kv.second.rp);
+      forget_key_meta(kv.second.rp);
       cudaFree(kv.second.rp);
       cudaFree(kv.second.col);
     }
@@ -679,6 +826,11 @@ bc_status bc_graph_load_csr(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, cons
   g.n = n;
   g.nnz = nnz;
   g.max_deg = maxdeg;
+  for (int32_t v = 0; v < n; ++v)
+    if (row_ptr[v + 1] - row_ptr[v] == maxdeg) {
+      g.hub = v;
+      break;
+    }
   BCG_CUDA(cudaMalloc(&g.rp, sizeof(int32_t) * ((size_t)n + 1)));
   if (cudaMalloc(&g.col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)) != cudaSuccess) {
     cudaGetLastError();
@@ -724,6 +876,7 @@ bc_status bc_graph_free(bc_ctx *ctx, bc_graph g) {
   if (server_uses_graph(ctx, g)) fail(BC_E_INVALID, "graph is used by a queued or running query");
   sync(ctx);
   forget_heavy_meta(it->second.rp);
+  forget_key_meta(it->second.rp);
   cudaFree(it->second.rp);
   cudaFree(it->second.col);
   ctx->graphs.erase(it);

@@ -43,6 +43,9 @@ struct Graph {
   int32_t n = 0;
   int64_t nnz = 0;
   int32_t max_deg = 0;
+  int32_t hub = 0;                 // a vertex of maximum degree
+  uint8_t *key = nullptr;          // device [n]: min(d(hub, v), 254), 255 if unreachable (lazy)
+  int32_t *order = nullptr;        // device [n]: all vertices sorted by key (lazy, exact BC)
   int32_t *rp = nullptr;   // device row_ptr[n+1]
   int32_t *col = nullptr;  // device col[nnz]
 };
@@ -71,14 +74,17 @@ struct Sink {
   const int32_t *tnext = nullptr;  // [E] next entry of the same vertex or -1 (null: one entry per vertex)
   const int32_t *eq = nullptr;     // [E] query of the entry (null: every lane belongs to it)
   const int32_t *lane_q = nullptr; // [64] query owning each lane
-  double *tdelta = nullptr;        // [E][64] delta of entry e for lane t (lane-minor rows)
+  double *tdelta = nullptr;        // [E][tstride] delta of entry e for lane t at column lane_col[t]
+  int32_t tstride = 64;            // row length of tdelta
+  const int32_t *lane_col = nullptr;  // [64] column of each lane (null: column = lane)
   Acc *acc = nullptr;              // [n] exact all-vertex sum of delta over lanes (may be null)
   double *delta_lm = nullptr;      // [n][64] full per-lane delta (may be null)
 };
 
 __device__ __forceinline__ void sink_targets(const Sink &sink, int32_t v, int t, double d) {
+  const int32_t c = sink.lane_col ? sink.lane_col[t] : t;
   for (int32_t e = sink.tslot[v]; e >= 0; e = sink.tnext ? sink.tnext[e] : -1)
-    if (!sink.eq || sink.lane_q[t] == sink.eq[e]) sink.tdelta[(size_t)e * 64 + t] = d;
+    if (!sink.eq || sink.lane_q[t] == sink.eq[e]) sink.tdelta[(size_t)e * sink.tstride + c] = d;
 }
 
 struct Workspace {
@@ -103,6 +109,7 @@ struct Workspace {
   DevBuf misc2;
   DevBuf delta_lm; // [n][64] f64
   DevBuf coefx;    // [n][64] uint4: coefficients as 128-bit fixed point (unit 2^-96)
+  DevBuf win;      // draw window: draws[W] | sorted sources[W] | sorted positions[W]
   // plain single-source engine
   DevBuf p_dist, p_sigma, p_coef, p_queue, p_ctr;
   void *pinned = nullptr;  // 4 KiB pinned host staging
@@ -135,6 +142,8 @@ struct bc_ctx {
   // backward kernel form (128-bit window only): 1 = packed lane groups (default),
   // 0 = two lane halves per thread
   int32_t bwd_variant = 1;
+  // forward kernel form: 0 = fused scan and sigma gather, 1 = two-phase packed
+  int32_t fwd_variant = 0;
 };
 
 namespace bcg {
