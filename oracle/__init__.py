@@ -64,6 +64,9 @@ def _load():
         "orc_pair_value": (_f64, [_i32, _i32, _i32, _i32p, _u64p, _i32, _u64]),
         "orc_pair_sequence": (ctypes.c_int, [_i32, _i32p, _i32p, _i32, _u64, _u64, _i64, _i64,
                                              _f64p, _i32p, _i32p]),
+        "orc_source_dependencies_xf": (ctypes.c_int, [_i32, _i32p, _i32p, _i32, _f64p, _i32p,
+                                                      _f64p, _i64p]),
+        "orc_xf_add_pair": (None, [_f64, _i64, _f64, _i64, _f64p, _i64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -131,7 +134,9 @@ def bfs(g, s: int):
 
 
 def dependencies(g, s: int):
-    """(delta float64[n], dist, sigma, overflow) for source s (Theorem 1)."""
+    """(delta float64[n], dist, sigma, overflow) for source s (Theorem 1). When
+    overflow is True some count exceeded 2^64-1: delta comes from the extended
+    form and sigma holds wrapped counts."""
     n, rp, col = _csr(g)
     delta = np.empty(n, np.float64)
     dist = np.empty(n, np.int32)
@@ -140,6 +145,28 @@ def dependencies(g, s: int):
                                                 _p(delta, _f64p), _p(dist, _i32p),
                                                 _p(sigma, _u64p)))
     return delta, dist, sigma, rc == SIGMA_OVERFLOW
+
+
+def dependencies_xf(g, s: int):
+    """The per-source step entirely in the extended form (unbounded exponent):
+    (delta float64[n], dist int32[n], sigma mantissa float64[n] in [1,2) or 0,
+    sigma exponent int64[n]); sigma_sv = mantissa * 2**exponent."""
+    n, rp, col = _csr(g)
+    delta = np.empty(n, np.float64)
+    dist = np.empty(n, np.int32)
+    sm = np.empty(n, np.float64)
+    se = np.empty(n, np.int64)
+    _check(_load().orc_source_dependencies_xf(n, _p(rp, _i32p), _p(col, _i32p), s,
+                                              _p(delta, _f64p), _p(dist, _i32p), _p(sm, _f64p),
+                                              _p(se, _i64p)))
+    return delta, dist, sm, se
+
+
+def xf_add(m1: float, e1: int, m2: float, e2: int):
+    """(m1 2^e1) + (m2 2^e2) rounded once in the extended form -> (m, e)."""
+    m, e = _f64(), _i64()
+    _load().orc_xf_add_pair(m1, e1, m2, e2, ctypes.byref(m), ctypes.byref(e))
+    return float(m.value), int(e.value)
 
 
 def exact_bc(g) -> np.ndarray:

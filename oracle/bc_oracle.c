@@ -30,7 +30,16 @@
  *       Theorem 1 and the sums over sources are EXACT sums rounded once, so
  *       their value does not depend on summation order. sigma is converted to
  *       double by round-to-nearest.
- *   R11 sigma is exact uint64; an overflow is reported, never wrapped.
+ *   R11 sigma is exact uint64 while every count of the sample fits. A sample
+ *       in which some count exceeds 2^64-1 is recomputed in the extended
+ *       form (R17) and the call reports that it happened (return value 1).
+ *   R17 extended form: sigma and coef are doubles with an unbounded exponent
+ *       (value = m * 2^e, m in [1,2)); every operation rounds once to 53 bits
+ *       as IEEE round-to-nearest-even would with no exponent limit. Path
+ *       counts are summed over the predecessors in the CSR order of the
+ *       vertex (pull order) and coefficients over the successors in the CSR
+ *       order of the vertex, one rounding per addition; delta = RN(sigma *
+ *       sum) is then an ordinary double.
  *
  * Random draws: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11) with key = (seed, qid) and counter =
@@ -257,7 +266,13 @@ int orc_dependencies(int32_t n, const int32_t *row_ptr, const int32_t *col, int3
   return ORC_OK;
 }
 
-/* BFS + dependencies for one source. dist/sigma may be NULL. */
+int orc_source_dependencies_xf(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
+                               double *delta, int32_t *dist_out, double *sigma_m,
+                               int64_t *sigma_e);
+
+/* BFS + dependencies for one source. dist/sigma may be NULL. Returns 1 when a
+ * count exceeded 2^64-1: delta then comes from the extended form (R11, R17)
+ * and sigma_out holds counts that wrapped around (not meaningful). */
 int orc_source_dependencies(int32_t n, const int32_t *row_ptr, const int32_t *col,
                             int32_t s, double *delta, int32_t *dist_out,
                             uint64_t *sigma_out) {
@@ -267,11 +282,160 @@ int orc_source_dependencies(int32_t n, const int32_t *row_ptr, const int32_t *co
   if (!dist || !sigma || !order) { free(dist); free(sigma); free(order); return ORC_E_NOMEM; }
   int32_t nr = 0;
   int rc = orc_bfs(n, row_ptr, col, s, dist, sigma, order, &nr);
-  int rc2 = orc_dependencies(n, row_ptr, col, s, dist, sigma, order, nr, delta);
   if (dist_out) memcpy(dist_out, dist, sizeof(int32_t) * (size_t)n);
   if (sigma_out) memcpy(sigma_out, sigma, sizeof(uint64_t) * (size_t)n);
+  if (rc == ORC_SIGMA_OVERFLOW) {
+    /* R11: the sample is recomputed in the extended form */
+    free(dist); free(sigma); free(order);
+    int rc3 = orc_source_dependencies_xf(n, row_ptr, col, s, delta, NULL, NULL, NULL);
+    return rc3 != ORC_OK ? rc3 : ORC_SIGMA_OVERFLOW;
+  }
+  int rc2 = orc_dependencies(n, row_ptr, col, s, dist, sigma, order, nr, delta);
   free(dist); free(sigma); free(order);
   return rc2 != ORC_OK ? rc2 : rc;
+}
+
+/* ------------------------------------------- extended form (R11, R17) -- */
+/*
+ * A double with an unbounded exponent: value = m * 2^e with m in [1,2), or
+ * zero (m = 0, e = 0). Shortest-path counts on long grids exceed the double
+ * range (sigma from a grid corner is a binomial coefficient), so a sample whose
+ * counts overflow 64 bits keeps them in this form.
+ */
+typedef struct {
+  double m;
+  int64_t e;
+} orc_xf;
+
+static orc_xf orc_xf_make(double x, int64_t e) { /* x > 0 finite, or 0 */
+  orc_xf r;
+  if (x == 0.0) { r.m = 0.0; r.e = 0; return r; }
+  int k;
+  double f = frexp(x, &k); /* x = f * 2^k, f in [0.5, 1), exact */
+  r.m = 2.0 * f;
+  r.e = e + (int64_t)k - 1;
+  return r;
+}
+
+/* RN(a + b) for a, b >= 0. When the exponents differ by more than 60 the
+ * smaller term is below a quarter ulp of the larger one, so the sum rounds to
+ * the larger; otherwise both mantissas are exact doubles on a common scale and
+ * one double addition rounds their exact sum. */
+static orc_xf orc_xf_add(orc_xf a, orc_xf b) {
+  if (a.m == 0.0) return b;
+  if (b.m == 0.0) return a;
+  if (a.e < b.e) { orc_xf t = a; a = b; b = t; }
+  int64_t d = a.e - b.e;
+  if (d > 60) return a;
+  return orc_xf_make(a.m + ldexp(b.m, -(int)d), a.e);
+}
+
+/* x * 2^k as a double, rounded once: steps of 2^1000 are exact while the
+ * value stays normal, and only the last multiplication can round. */
+static double orc_scale2(double x, int64_t k) {
+  const double up = ldexp(1.0, 1000), down = ldexp(1.0, -1000);
+  while (k > 1000) { x *= up; k -= 1000; }
+  while (k < -1000) { x *= down; k += 1000; }
+  return x * ldexp(1.0, (int)k);
+}
+
+/* RN(a * b) as an ordinary double (the product of the mantissas rounds once;
+ * the exponent shift is exact while the result is normal). */
+static double orc_xf_mul_to_double(orc_xf a, orc_xf b) {
+  if (a.m == 0.0 || b.m == 0.0) return 0.0;
+  return orc_scale2(a.m * b.m, a.e + b.e);
+}
+
+/* RN(x / b) for a double x > 0 and b > 0. */
+static orc_xf orc_xf_div(double x, orc_xf b) { return orc_xf_make(x / b.m, -b.e); }
+
+/* Test hook: (m1 2^e1) + (m2 2^e2) in the extended form. */
+void orc_xf_add_pair(double m1, int64_t e1, double m2, int64_t e2, double *m, int64_t *e) {
+  orc_xf a = orc_xf_make(m1, e1), b = orc_xf_make(m2, e2);
+  orc_xf r = orc_xf_add(a, b);
+  *m = r.m;
+  *e = r.e;
+}
+
+/*
+ * BFS from s with path counts in the extended form (Sec. 3 step 1, Def. 3):
+ * distances by a FIFO queue as in orc_bfs, then for the reached vertices in
+ * queue order (non-decreasing distance) sigma_sw = sum over CSR neighbours v of
+ * w with d(s,v) = d(s,w) - 1 of sigma_sv, added in CSR order.
+ */
+static void orc_bfs_xf(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
+                       int32_t *dist, orc_xf *sigma, int32_t *order, int32_t *nreached) {
+  for (int32_t v = 0; v < n; ++v) { dist[v] = -1; sigma[v].m = 0.0; sigma[v].e = 0; }
+  int32_t head = 0, tail = 0;
+  dist[s] = 0;
+  order[tail++] = s;
+  while (head < tail) {
+    int32_t v = order[head++];
+    for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) {
+      int32_t w = col[j];
+      if (dist[w] < 0) { dist[w] = dist[v] + 1; order[tail++] = w; }
+    }
+  }
+  sigma[s] = orc_xf_make(1.0, 0);
+  for (int32_t idx = 1; idx < tail; ++idx) {
+    int32_t w = order[idx];
+    orc_xf acc = orc_xf_make(0.0, 0);
+    for (int32_t j = row_ptr[w]; j < row_ptr[w + 1]; ++j) {
+      int32_t v = col[j];
+      if (dist[v] >= 0 && dist[v] == dist[w] - 1) acc = orc_xf_add(acc, sigma[v]); /* v in P_s(w) */
+    }
+    sigma[w] = acc;
+  }
+  *nreached = tail;
+}
+
+/*
+ * Theorem 1 in the extended form: vertices in non-increasing distance;
+ * sum = successor coefficients added in CSR order, delta_v = RN(sigma_v * sum),
+ * coef_v = RN(RN(1 + delta_v) / sigma_v). delta_s(s) = 0 (R2).
+ */
+static void orc_dependencies_xf(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
+                                const int32_t *dist, const orc_xf *sigma, const int32_t *order,
+                                int32_t nreached, orc_xf *coef, double *delta) {
+  for (int32_t v = 0; v < n; ++v) delta[v] = 0.0;
+  for (int32_t idx = nreached - 1; idx >= 0; --idx) {
+    int32_t v = order[idx];
+    orc_xf sum = orc_xf_make(0.0, 0);
+    for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) {
+      int32_t w = col[j];
+      if (dist[w] == dist[v] + 1) sum = orc_xf_add(sum, coef[w]); /* v in P_s(w) */
+    }
+    double d = orc_xf_mul_to_double(sigma[v], sum);
+    if (v == s) d = 0.0;
+    delta[v] = d;
+    coef[v] = orc_xf_div(1.0 + d, sigma[v]);
+  }
+}
+
+/* One source entirely in the extended form (test hook and the recomputation
+ * of R11). sigma_m/sigma_e (may be NULL) receive the counts. */
+int orc_source_dependencies_xf(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
+                               double *delta, int32_t *dist_out, double *sigma_m,
+                               int64_t *sigma_e) {
+  size_t nn = (size_t)(n ? n : 1);
+  int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * nn);
+  orc_xf *sigma = (orc_xf *)malloc(sizeof(orc_xf) * nn);
+  orc_xf *coef = (orc_xf *)malloc(sizeof(orc_xf) * nn);
+  if (!dist || !order || !sigma || !coef) {
+    free(dist); free(order); free(sigma); free(coef);
+    return ORC_E_NOMEM;
+  }
+  int32_t nr = 0;
+  orc_bfs_xf(n, row_ptr, col, s, dist, sigma, order, &nr);
+  for (int32_t v = 0; v < n; ++v) {
+    if (sigma_m) sigma_m[v] = sigma[v].m;
+    if (sigma_e) sigma_e[v] = sigma[v].e;
+  }
+  orc_dependencies_xf(n, row_ptr, col, s, dist, sigma, order, nr, coef, delta);
+  if (dist_out) memcpy(dist_out, dist, sizeof(int32_t) * (size_t)n);
+  free(dist); free(order); free(sigma); free(coef);
+  return ORC_OK;
 }
 
 /* --------------------------------------------------------------- exact BC -- */
