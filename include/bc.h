@@ -26,12 +26,21 @@
  *     (seed, qid), counter (i, 0, 0, 0) for draw i = 0, 1, ...: a source is
  *     floor(x0*n/2^64); an ordered pair of different vertices is
  *     u = floor(x0*n/2^64), w = floor(x1*(n-1)/2^64), t = w + (w >= u).
- *   - Arithmetic: sigma is an exact uint64 count (overflow is reported as
- *     BC_E_SIGMA_OVERFLOW, never wrapped). Dependencies are IEEE doubles: the
- *     successor sum of Theorem 1 and every sum of dependencies over sources are
- *     exact sums rounded once to nearest-even, so results do not depend on the
- *     order or batching of the work; all other double operations round once
- *     (no fused multiply-add).
+ *   - Arithmetic: sigma is an exact uint64 count. Dependencies are IEEE
+ *     doubles: the successor sum of Theorem 1 and every sum of dependencies over
+ *     sources are exact sums rounded once to nearest-even, so results do not
+ *     depend on the order or batching of the work; all other double operations
+ *     round once (no fused multiply-add).
+ *   - A sample in which some path count exceeds 2^64-1 (long grids: from a
+ *     corner, sigma is a binomial coefficient of the distance) is computed in
+ *     the extended form instead: counts and coefficients are doubles with an
+ *     unbounded exponent (m * 2^e, m in [1,2)), each operation rounding once as
+ *     round-to-nearest-even would without an exponent limit; counts are summed
+ *     over the predecessors and coefficients over the successors in the CSR
+ *     order of the vertex; delta = RN(sigma * sum) is an ordinary double. The
+ *     choice is made per sample, so it does not depend on batching either.
+ *     The pair estimator (bc_adaptive_pairs, BC_QUERY_PAIRS) has no extended
+ *     form: a pair or target count beyond 2^64-1 fails with BC_E_SIGMA_OVERFLOW.
  */
 #ifndef BC_GB300_H
 #define BC_GB300_H
@@ -113,9 +122,23 @@ bc_status bc_graph_info(bc_ctx *ctx, bc_graph g, int32_t *n, int64_t *nnz);
  *   delta_out[i*n + v] = delta_{s_i}(v)        (delta_s(s) = 0, unreachable 0)
  *   dist_out[i*n + v]  = d(s_i, v) or -1       (may be NULL)
  *   sigma_out[i*n + v] = sigma_{s_i v}         (may be NULL)
- * count >= 0; every source in [0, n). */
+ * count >= 0; every source in [0, n). For a source whose counts exceed 2^64-1
+ * (computed in the extended form) the sigma row holds UINT64_MAX at every
+ * reached vertex and 0 elsewhere; bc_source_dependencies_ext gives its counts. */
 bc_status bc_source_dependencies(bc_ctx *ctx, bc_graph g, const int32_t *sources, int32_t count,
                                  double *delta_out, int32_t *dist_out, uint64_t *sigma_out);
+
+/* The same step with the path counts of every source in the extended form:
+ *   sigma_mant_out[i*n + v] in [1,2) (0 when unreachable) and
+ *   sigma_exp_out[i*n + v], sigma_{s_i v} = mant * 2^exp. For a source computed
+ *   with exact uint64 counts these are the counts rounded to double (exact
+ *   below 2^53); for a source computed in the extended form they are its
+ *   extended counts. tier_out[i] (may be NULL) is 0 for the uint64 form, 1 for
+ *   the extended form. delta_out and dist_out as in bc_source_dependencies
+ *   (dist_out may be NULL). */
+bc_status bc_source_dependencies_ext(bc_ctx *ctx, bc_graph g, const int32_t *sources, int32_t count,
+                                     double *delta_out, int32_t *dist_out, double *sigma_mant_out,
+                                     int32_t *sigma_exp_out, int32_t *tier_out);
 
 /* ----------------------------------------------------------- estimators -- */
 
@@ -243,7 +266,9 @@ bc_status bc_exact_sum(bc_ctx *ctx, const double *x, int64_t count, double *out)
  *   n               1 .. BC_NOALLOC_MAX_VERTICES, else BC_E_TOO_LARGE
  *   d_sources[count]             DEVICE pointer, every entry in [0, n)
  *   d_delta_out[count*n]         DEVICE pointer: row i receives delta_{s_i}(v),
- *                   exactly as bc_source_dependencies computes it
+ *                   exactly as bc_source_dependencies computes it; a source
+ *                   whose path counts exceed 2^64-1 returns BC_E_SIGMA_OVERFLOW
+ *                   (the extended form needs scratch this entry does not have)
  *   stream          cudaStream_t to run on (NULL = the legacy default stream);
  *                   the call returns after its work on that stream is done
  *

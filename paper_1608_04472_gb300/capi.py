@@ -73,6 +73,7 @@ _SIGS = {
     "bc_graph_free": (_i32, [_vp, _i64]),
     "bc_graph_info": (_i32, [_vp, _i64, _i32p, _i64p]),
     "bc_source_dependencies": (_i32, [_vp, _i64, _i32p, _i32, _f64p, _i32p, _u64p]),
+    "bc_source_dependencies_ext": (_i32, [_vp, _i64, _i32p, _i32, _f64p, _i32p, _f64p, _i32p, _i32p]),
     "bc_exact": (_i32, [_vp, _i64, _f64p]),
     "bc_uniform_sources": (_i32, [_vp, _i64, _i64, _u64, _u64, _f64p]),
     "bc_adaptive_sources": (_i32, [_vp, _i64, _i32p, _i32, _f64, _i64, _u64, _u64, _f64p, _i64p,
@@ -177,6 +178,24 @@ def bc_source_dependencies(ctx, g: int, sources, want_dist: bool = False, want_s
         _p(dist, _i32p) if dist is not None and cnt else None,
         _p(sigma, _u64p) if sigma is not None and cnt else None))
     return delta, dist, sigma
+
+
+def bc_source_dependencies_ext(ctx, g: int, sources):
+    """(delta [count][n], dist [count][n], sigma mantissa [count][n], sigma exponent
+    [count][n], tier [count]); sigma = mantissa * 2**exponent, tier 1 = the
+    source was computed in the extended form."""
+    n, _ = bc_graph_info(ctx, g)
+    src = _i32arr(sources)
+    cnt = src.size
+    delta = np.zeros((cnt, n), np.float64)
+    dist = np.zeros((cnt, n), np.int32)
+    sm = np.zeros((cnt, n), np.float64)
+    se = np.zeros((cnt, n), np.int32)
+    tier = np.zeros(cnt, np.int32)
+    if cnt:
+        _ck(ctx, _lib.bc_source_dependencies_ext(ctx, g, _p(src, _i32p), cnt, _p(delta, _f64p), _p(dist, _i32p),
+                                                 _p(sm, _f64p), _p(se, _i32p), _p(tier, _i32p)))
+    return delta, dist, sm, se, tier
 
 
 def bc_exact(ctx, g: int) -> np.ndarray:
@@ -377,6 +396,9 @@ class Context:
 
     def source_dependencies(self, g, sources, want_dist=False, want_sigma=False):
         return bc_source_dependencies(self.ptr, g, sources, want_dist, want_sigma)
+
+    def source_dependencies_ext(self, g, sources):
+        return bc_source_dependencies_ext(self.ptr, g, sources)
 
     def exact(self, g):
         return bc_exact(self.ptr, g)

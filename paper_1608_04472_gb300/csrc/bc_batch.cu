@@ -93,6 +93,7 @@ __global__ void k_batch_init(int count, const int32_t *__restrict__ sources,
   if (t == 0) {
     enable[0] = (count >= 64) ? ~0ull : ((1ull << count) - 1ull);
     enable[2] = 1ull;  // largest sigma of the batch (sources have sigma 1)
+    enable[3] = 0ull;  // lanes whose path counts exceeded 2^64-1
   }
   __syncthreads();
   if (t < count) {
@@ -150,7 +151,7 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
   const uint64_t act = *active_prev & *enable;
   uint64_t any_new = 0ull, smax = 0ull;
   unsigned long long tri = 0ull, rch = 0ull;
-  unsigned e = 0u;
+  uint64_t ovf = 0ull;  // lanes whose counts exceeded 2^64-1 here
   // a warp takes 32 vertices; each thread loads one vertex's header, and only
   // vertices with unvisited active lanes and light degree are walked
   for (int base = grab(wq, 32); base < n; base = grab(wq, 32)) {
@@ -201,10 +202,10 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
 #pragma unroll
           for (int k = 0; k < UNR; ++k) {
             const uint64_t t0 = s0 + x0[k];
-            if (t0 < s0) e |= ERR_SIGMA_OVERFLOW;
+            if (t0 < s0) ovf |= 1ull << lane;
             s0 = t0;
             const uint64_t t1 = s1 + x1[k];
-            if (t1 < s1) e |= ERR_SIGMA_OVERFLOW;
+            if (t1 < s1) ovf |= 1ull << (lane + 32);
             s1 = t1;
           }
         }
@@ -227,7 +228,9 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
     any_new |= newm;
     }
   }
-  if (e) atomicOr(err, e);
+  ovf = warp_or64(ovf);
+  if (lane == 0 && ovf) atomicOr((unsigned long long *)(enable + 3), (unsigned long long)ovf);
+  (void)err;
   if (lane == 0 && (tri | rch)) {
     atomicAdd(cnt, tri);
     atomicAdd(cnt + 1, rch);
@@ -243,12 +246,12 @@ k_fwd_heavy(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restri
             const int32_t *__restrict__ seg_e, const int32_t *__restrict__ col,
             const uint64_t *__restrict__ lm_prev, uint64_t *__restrict__ lm_cur,
             const uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
-            const uint64_t *__restrict__ active_prev, const uint64_t *__restrict__ enable,
+            const uint64_t *__restrict__ active_prev, uint64_t *__restrict__ enable,
             unsigned *__restrict__ err, unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq) {
   const int lane = threadIdx.x & 31;
   const uint64_t act = *active_prev & *enable;
   unsigned long long tri = 0ull;
-  unsigned e = 0u;
+  uint64_t ovf = 0ull;  // lanes whose counts exceeded 2^64-1 here
   for (int s = grab(wq, 1); s < nseg; s = grab(wq, 1)) {
     const int32_t v = seg_v[s];
     const int beg = seg_b[s], end = seg_e[s];
@@ -280,10 +283,10 @@ k_fwd_heavy(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restri
 #pragma unroll
         for (int k = 0; k < UNR; ++k) {
           const uint64_t t0 = s0 + x0[k];
-          if (t0 < s0) e |= ERR_SIGMA_OVERFLOW;
+          if (t0 < s0) ovf |= 1ull << lane;
           s0 = t0;
           const uint64_t t1 = s1 + x1[k];
-          if (t1 < s1) e |= ERR_SIGMA_OVERFLOW;
+          if (t1 < s1) ovf |= 1ull << (lane + 32);
           s1 = t1;
         }
       }
@@ -293,15 +296,17 @@ k_fwd_heavy(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restri
     unsigned long long *dst = (unsigned long long *)(sigma + (size_t)v * 64);
     if ((newm >> lane) & 1ull) {
       const unsigned long long old = atomicAdd(dst + lane, (unsigned long long)s0);
-      if (old + s0 < old) e |= ERR_SIGMA_OVERFLOW;
+      if (old + s0 < old) ovf |= 1ull << lane;
     }
     if ((newm >> (lane + 32)) & 1ull) {
       const unsigned long long old = atomicAdd(dst + 32 + lane, (unsigned long long)s1);
-      if (old + s1 < old) e |= ERR_SIGMA_OVERFLOW;
+      if (old + s1 < old) ovf |= 1ull << (lane + 32);
     }
     if (lane == 0) atomicOr((unsigned long long *)&lm_cur[v], (unsigned long long)newm);
   }
-  if (e) atomicOr(err, e);
+  ovf = warp_or64(ovf);
+  if (lane == 0 && ovf) atomicOr((unsigned long long *)(enable + 3), (unsigned long long)ovf);
+  (void)err;
   if (lane == 0 && tri) atomicAdd(cnt, tri);
 }
 
@@ -563,14 +568,14 @@ __global__ void __launch_bounds__(FWD_THREADS)
 k_bwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
             const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
             uint64_t *__restrict__ sigma, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq,
-            int heavy_deg) {
+            int heavy_deg, uint64_t keep) {
   __shared__ Ring rings[FWD_THREADS / 32];
   Ring &R = rings[threadIdx.x >> 5];
   unsigned head = 0u, tail = 0u;
   unsigned e = 0u;
   for (int base = grab(wq); base < n; base = grab(wq))
     for (int v = base; v < min(base + GRAB, n); ++v) {
-      const uint64_t lanes = lm_cur[v];
+      const uint64_t lanes = lm_cur[v] & keep;
       if (!lanes) continue;
       const int beg = rp[v], end = rp[v + 1];
       if (end - beg > heavy_deg) continue;
@@ -600,11 +605,11 @@ k_bwd_heavy_seg(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__re
                 const int32_t *__restrict__ seg_e, const int32_t *__restrict__ col,
                 const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
                 const uint64_t *__restrict__ sigma, Acc *__restrict__ part, unsigned *__restrict__ err,
-                unsigned *__restrict__ wq) {
+                unsigned *__restrict__ wq, uint64_t keep) {
   unsigned e = 0u;
   for (int s = grab(wq, 1); s < nseg; s = grab(wq, 1)) {
       const int32_t v = seg_v[s];
-      const uint64_t lanes = lm_cur[v];
+      const uint64_t lanes = lm_cur[v] & keep;
       if (!lanes) continue;
       int p0, p1;
       compact_lanes(lanes, p0, p1);
@@ -620,14 +625,14 @@ k_bwd_heavy_seg(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__re
 __global__ void __launch_bounds__(FWD_THREADS)
 k_bwd_heavy_fin(int nh, const int32_t *__restrict__ heavy, const int32_t *__restrict__ hseg0,
                 const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ sigma,
-                const Acc *__restrict__ part, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq) {
+                const Acc *__restrict__ part, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq, uint64_t keep) {
   __shared__ Ring rings[FWD_THREADS / 32];
   Ring &R = rings[threadIdx.x >> 5];
   unsigned head = 0u, tail = 0u;
   unsigned e = 0u;
   for (int h = grab(wq, 1); h < nh; h = grab(wq, 1)) {
     const int32_t v = heavy[h];
-    const uint64_t lanes = lm_cur[v];
+    const uint64_t lanes = lm_cur[v] & keep;
     if (!lanes) continue;
     int p0, p1;
     compact_lanes(lanes, p0, p1);
@@ -738,7 +743,7 @@ __device__ __forceinline__ void gather_packed(int beg, int end, uint64_t lanes, 
 __device__ __forceinline__ void gather_sigma_packed(int beg, int end, uint64_t newm, const uint64_t *__restrict__ lm_prev,
                                                     const int32_t *__restrict__ col, const uint64_t *__restrict__ sigma,
                                                     const Packed &pk, int32_t *list, uint64_t &s0, uint64_t &s1,
-                                                    unsigned &e, unsigned long long &tri) {
+                                                    uint64_t &ovf, unsigned long long &tri) {
   const int lane = threadIdx.x & 31;
   const int NG = 32 >> pk.glog, g = lane >> pk.glog;
   const uint64_t b0 = pk.p0 >= 0 ? (1ull << pk.p0) : 0ull, b1 = pk.p1 >= 0 ? (1ull << pk.p1) : 0ull;
@@ -768,21 +773,21 @@ __device__ __forceinline__ void gather_sigma_packed(int beg, int end, uint64_t n
         const uint64_t c0 = (h0 && (m0 & b1)) ? sigma[(size_t)w0 * 64 + q1] : 0ull;
         const uint64_t c1 = (h1 && (m1 & b1)) ? sigma[(size_t)w1 * 64 + q1] : 0ull;
         uint64_t t = s1 + c0;
-        if (t < s1) e |= ERR_SIGMA_OVERFLOW;
+        if (t < s1) ovf |= b1;
         s1 = t + c1;
-        if (s1 < t) e |= ERR_SIGMA_OVERFLOW;
+        if (s1 < t) ovf |= b1;
       }
       uint64_t t = s0 + a0;
-      if (t < s0) e |= ERR_SIGMA_OVERFLOW;
+      if (t < s0) ovf |= b0;
       s0 = t + a1;
-      if (s0 < t) e |= ERR_SIGMA_OVERFLOW;
+      if (s0 < t) ovf |= b0;
     }
     __syncwarp();
   }
   for (int off = 1 << pk.glog; off < 32; off <<= 1) {
     const uint64_t o = __shfl_xor_sync(FULL, s0, off);
     const uint64_t t = s0 + o;
-    if (t < s0) e |= ERR_SIGMA_OVERFLOW;
+    if (t < s0 && pk.p0 >= 0) ovf |= 1ull << pk.p0;
     s0 = t;
   }
 }
@@ -803,9 +808,8 @@ k_fwd_light_pk(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restr
   int8_t *tab = tabs[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const uint64_t act = *active_prev & *enable;
-  uint64_t any_new = 0ull, smax = 0ull;
+  uint64_t any_new = 0ull, smax = 0ull, ovf = 0ull;
   unsigned long long tri = 0ull, rch = 0ull;
-  unsigned e = 0u;
   for (int base = grab(wq); base < n; base = grab(wq))
     for (int v = base; v < min(base + GRAB, n); ++v) {
       const int beg = rp[v], end = rp[v + 1];
@@ -818,7 +822,7 @@ k_fwd_light_pk(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restr
         if (newm) {
           const Packed pk = pack_lanes(newm, tab);
           uint64_t s0 = 0ull, s1 = 0ull;
-          gather_sigma_packed(beg, end, newm, lm_prev, col, sigma, pk, list, s0, s1, e, tri);
+          gather_sigma_packed(beg, end, newm, lm_prev, col, sigma, pk, list, s0, s1, ovf, tri);
           if ((lane >> pk.glog) == 0 && pk.p0 >= 0) {
             sigma[(size_t)v * 64 + pk.p0] = s0;
             smax = s0 > smax ? s0 : smax;
@@ -836,7 +840,9 @@ k_fwd_light_pk(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restr
       rch += (unsigned long long)__popcll((long long)newm);
       any_new |= newm;
     }
-  if (e) atomicOr(err, e);
+  ovf = warp_or64(ovf);
+  if (lane == 0 && ovf) atomicOr((unsigned long long *)(enable + 3), (unsigned long long)ovf);
+  (void)err;
   if (lane == 0 && (tri | rch)) {
     atomicAdd(cnt, tri);
     atomicAdd(cnt + 1, rch);
@@ -871,7 +877,7 @@ __global__ void __launch_bounds__(FWD_THREADS)
 k_bwd_light_fx(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
                uint64_t *__restrict__ sigma, uint4 *__restrict__ coefx, Sink sink, unsigned *__restrict__ err,
-               unsigned *__restrict__ wq, int heavy_deg) {
+               unsigned *__restrict__ wq, int heavy_deg, uint64_t keep) {
   __shared__ Ring rings[FWD_THREADS / 32];
   __shared__ int32_t lists[FWD_THREADS / 32][32];
   __shared__ int8_t tabs[FWD_THREADS / 32][64];
@@ -883,7 +889,7 @@ k_bwd_light_fx(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restr
   (void)coefx;
   for (int base = grab(wq); base < n; base = grab(wq))
     for (int v = base; v < min(base + GRAB, n); ++v) {
-      const uint64_t lanes = lm_cur[v];
+      const uint64_t lanes = lm_cur[v] & keep;
       if (!lanes) continue;
       const int beg = rp[v], end = rp[v + 1];
       if (end - beg > heavy_deg) continue;
@@ -907,7 +913,7 @@ k_bwd_heavy_seg_fx(int nseg, const int32_t *__restrict__ seg_v, const int32_t *_
                    const int32_t *__restrict__ seg_e, const int32_t *__restrict__ col,
                    const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
                    const uint64_t *__restrict__ coef, uint4 *__restrict__ part, unsigned *__restrict__ wq,
-                   unsigned *__restrict__ err) {
+                   unsigned *__restrict__ err, uint64_t keep) {
   __shared__ int32_t lists[FWD_THREADS / 32][32];
   __shared__ int8_t tabs[FWD_THREADS / 32][64];
   int32_t *list = lists[threadIdx.x >> 5];
@@ -916,7 +922,7 @@ k_bwd_heavy_seg_fx(int nseg, const int32_t *__restrict__ seg_v, const int32_t *_
   unsigned e = 0u;
   for (int s = grab(wq, 1); s < nseg; s = grab(wq, 1)) {
       const int32_t v = seg_v[s];
-      const uint64_t lanes = lm_cur[v];
+      const uint64_t lanes = lm_cur[v] & keep;
       if (!lanes) continue;
       const Packed pk = pack_lanes(lanes, tab);
       Acc2 a0 = acc2_zero(), a1 = acc2_zero();
@@ -930,14 +936,14 @@ k_bwd_heavy_seg_fx(int nseg, const int32_t *__restrict__ seg_v, const int32_t *_
 __global__ void __launch_bounds__(FWD_THREADS)
 k_bwd_heavy_fin_fx(int nh, const int32_t *__restrict__ heavy, const int32_t *__restrict__ hseg0,
                    const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ sigma, uint4 *__restrict__ coefx,
-                   const uint4 *__restrict__ part, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq) {
+                   const uint4 *__restrict__ part, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq, uint64_t keep) {
   __shared__ Ring rings[FWD_THREADS / 32];
   Ring &R = rings[threadIdx.x >> 5];
   unsigned head = 0u, tail = 0u;
   unsigned e = 0u;
   for (int h = grab(wq, 1); h < nh; h = grab(wq, 1)) {
       const int32_t v = heavy[h];
-      const uint64_t lanes = lm_cur[v];
+      const uint64_t lanes = lm_cur[v] & keep;
       if (!lanes) continue;
       int p0, p1;
       compact_lanes(lanes, p0, p1);
@@ -1078,7 +1084,17 @@ static uint64_t read_u64(bc_ctx *ctx, const uint64_t *dptr) {
   return *h;
 }
 
-int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs) {
+// Two device words to the host with one synchronisation.
+static void read_u64x2(bc_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t &va, uint64_t &vb) {
+  uint64_t *h = static_cast<uint64_t *>(ctx->ws.pinned);
+  BCG_CUDA(cudaMemcpyAsync(h, a, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  BCG_CUDA(cudaMemcpyAsync(h + 1, b, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  BCG_CUDA(cudaStreamSynchronize(ctx->stream));
+  va = h[0];
+  vb = h[1];
+}
+
+int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mode) {
   Workspace &ws = ctx->ws;
   batch_ensure(ctx, g);
   HeavyMeta &hm = heavy_meta(ctx, g);
@@ -1124,6 +1140,7 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs) {
     } else {
       cont1 = read_u64(ctx, ws.active.as<uint64_t>() + 1);
     }
+    ws.last_ovf = 0ull;
     if (!cont1) {  // no vertex at distance 1 (or, for pairs, every destination found)
       ws.last_sigmax = 1ull;
       return pairs ? 1 : 0;
@@ -1166,25 +1183,29 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs) {
                                                           ws.cnt.as<unsigned long long>(), ws.sigma.as<uint64_t>(),
                                                           ws.enable.as<uint64_t>());
     }
-    uint64_t cont;
+    uint64_t cont, ovf;
     if (pairs) {
       LaunchScope ls(ctx, F_PAIR);
       k_pair_check<<<1, 64, 0, st>>>(count, l + 1, ws.targets.as<int32_t>(), lm + (size_t)(l + 1) * n,
                                      ws.sigma.as<uint64_t>(), ws.enable.as<uint64_t>(), ws.pair_d.as<int32_t>(),
                                      ws.pair_sig.as<uint64_t>(), act + l + 1, ws.enable.as<uint64_t>() + 1);
-      cont = read_u64(ctx, ws.enable.as<uint64_t>() + 1);
+      read_u64x2(ctx, ws.enable.as<uint64_t>() + 1, ws.enable.as<uint64_t>() + 3, cont, ovf);
     } else {
-      cont = read_u64(ctx, act + l + 1);
+      read_u64x2(ctx, act + l + 1, ws.enable.as<uint64_t>() + 3, cont, ovf);
     }
-    if (!cont) {
+    ws.last_ovf = ovf;
+    // every lane overflowed: the integer pass has nothing left to give
+    const bool all_ovf = mode == OVF_EXTEND && ovf != 0ull && (ovf & lanes_of(count)) == lanes_of(count);
+    if (!cont || all_ovf) {
       ws.last_sigmax = read_u64(ctx, ws.enable.as<uint64_t>() + 2);
+      if (ovf && mode == OVF_ERROR) raise_err_bits(ctx, ERR_SIGMA_OVERFLOW);
       return l;
     }
     ++l;
   }
 }
 
-void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink) {
+void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink, uint64_t keep) {
   Workspace &ws = ctx->ws;
   HeavyMeta &hm = heavy_meta(ctx, g);
   const size_t n = (size_t)g.n;
@@ -1200,7 +1221,7 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink)
         LaunchScope ls(ctx, F_BWD);
         k_bwd_light_fx<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
                                                       ws.sigma.as<uint64_t>(), coefx, sink, ws.err.as<unsigned>(),
-                                                      ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg);
+                                                      ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg, keep);
       }
       if (hm.nseg) {
         {
@@ -1208,12 +1229,12 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink)
           k_bwd_heavy_seg_fx<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
               hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
               lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), hm.part2.as<uint4>(),
-              ws.wq.as<unsigned>() + 8 * l + 3, ws.err.as<unsigned>());
+              ws.wq.as<unsigned>() + 8 * l + 3, ws.err.as<unsigned>(), keep);
         }
         LaunchScope ls(ctx, F_BWD);
         k_bwd_heavy_fin_fx<<<std::min(blocks, (hm.nh + 7) / 8), FWD_THREADS, 0, st>>>(
             hm.nh, hm.heavy.as<int32_t>(), hm.hseg0.as<int32_t>(), lm + (size_t)l * n, ws.sigma.as<uint64_t>(),
-            coefx, hm.part2.as<uint4>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 4);
+            coefx, hm.part2.as<uint4>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 4, keep);
       }
     }
     return;
@@ -1224,11 +1245,11 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink)
       if (narrow)
         k_bwd_light<NarrowAcc><<<blocks, FWD_THREADS, 0, st>>>(
             g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), sink,
-            ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg);
+            ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg, keep);
       else
         k_bwd_light<WideAcc><<<blocks, FWD_THREADS, 0, st>>>(
             g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), sink,
-            ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg);
+            ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg, keep);
     }
     if (hm.nseg) {
       LaunchScope ls(ctx, F_BWD);
@@ -1236,10 +1257,10 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink)
       kseg<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
           hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
           lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), hm.part.as<Acc>(),
-          ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 3);
+          ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 3, keep);
       k_bwd_heavy_fin<<<std::min(blocks, (hm.nh + 7) / 8), FWD_THREADS, 0, st>>>(
           hm.nh, hm.heavy.as<int32_t>(), hm.hseg0.as<int32_t>(), lm + (size_t)l * n, ws.sigma.as<uint64_t>(),
-          hm.part.as<Acc>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 4);
+          hm.part.as<Acc>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 4, keep);
     }
   }
 }

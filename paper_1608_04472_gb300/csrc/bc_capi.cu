@@ -21,7 +21,8 @@ void forget_heavy_meta(const int32_t *rp);
 void forget_key_meta(const int32_t *rp);
 void plain_pair(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dest);
 
-const char *kFamilyName[F_NFAM] = {"draw", "init", "fwd", "bwd", "scan", "pair", "misc", "plain_fwd", "plain_bwd"};
+const char *kFamilyName[F_NFAM] = {"draw", "init",      "fwd",       "bwd",     "scan",   "pair",
+                                   "misc", "plain_fwd", "plain_bwd", "ext_fwd", "ext_bwd"};
 
 void fail(bc_status code, const std::string &msg) { throw Error{code, msg}; }
 
@@ -112,6 +113,13 @@ unsigned read_and_clear_err(bc_ctx *ctx) {
   BCG_CUDA(cudaMemsetAsync(ctx->ws.err.p, 0, 4, ctx->stream));
   sync(ctx);
   return *h;
+}
+
+__global__ void k_or_bits(unsigned *__restrict__ err, unsigned bits) { atomicOr(err, bits); }
+
+void raise_err_bits(bc_ctx *ctx, unsigned bits) {
+  LaunchScope ls(ctx, F_MISC);
+  k_or_bits<<<1, 1, 0, ctx->stream>>>(ctx->ws.err.as<unsigned>(), bits);
 }
 
 static void check_err_bits(bc_ctx *ctx) {
@@ -338,12 +346,16 @@ static void launch_draw_sources(bc_ctx *ctx, uint64_t seed, uint64_t qid, uint64
   k_draw_sources<<<(count + 63) / 64, 64, 0, ctx->stream>>>(seed, qid, i0, count, n, out);
 }
 
+// Lanes whose path counts exceed 2^64-1 skip the integer backward pass and are
+// recomputed in the extended form (bc_ext.cu); the others are unaffected.
 void run_source_batch(bc_ctx *ctx, const Graph &g, int count, const Sink &sink) {
   if (batch_width(ctx) == 1) {
     plain_source(ctx, g, ctx->ws.sources.as<int32_t>(), sink, nullptr, nullptr);
   } else {
-    const int maxl = batch_forward(ctx, g, count, false);
-    batch_backward(ctx, g, maxl, sink);
+    const int maxl = batch_forward(ctx, g, count, false, OVF_EXTEND);
+    const uint64_t all = lanes_of(count), ovf = ctx->ws.last_ovf & all;
+    if (ovf != all) batch_backward(ctx, g, maxl, sink, all & ~ovf);
+    if (ovf) ext_source_batch(ctx, g, ctx->ws.sources.as<int32_t>(), ovf, sink);
   }
 }
 
@@ -433,13 +445,12 @@ static KeyMeta &key_meta(bc_ctx *ctx, const Graph &g, bool need_order) {
     const int32_t hub = g.hub;
     BCG_CUDA(cudaMemcpyAsync(ws.sources.p, &hub, 4, cudaMemcpyHostToDevice, ctx->stream));
     const int64_t s0 = ctx->samples, b0 = ctx->batches;
-    const int maxl = batch_forward(ctx, g, 1, false);
-    ctx->samples = s0;
-    ctx->batches = b0;
     DevBuf dist;
     dist.ensure(n * 4);
     try {
-      batch_extract(ctx, g, 1, maxl, dist.as<int32_t>(), nullptr, 1, (int64_t)n);
+      plain_distances(ctx, g, ws.sources.as<int32_t>(), dist.as<int32_t>());  // any depth
+      ctx->samples = s0;
+      ctx->batches = b0;
       {
         LaunchScope ls(ctx, F_MISC);
         k_make_key<<<(g.n + 255) / 256, 256, 0, ctx->stream>>>(g.n, dist.as<int32_t>(), km.key.as<uint8_t>());
@@ -641,20 +652,29 @@ static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *target
   tsig.release();
 }
 
+// Per-source outputs. Sources whose counts exceed 2^64-1 are computed in the
+// extended form: their sigma rows hold UINT64_MAX at reached vertices, and the
+// extended outputs (sm_out, se_out; tier_out = 1) carry the counts.
 static void do_source_dependencies(bc_ctx *ctx, const Graph &g, const int32_t *sources, int32_t count,
-                                   double *delta_out, int32_t *dist_out, uint64_t *sigma_out) {
+                                   double *delta_out, int32_t *dist_out, uint64_t *sigma_out, double *sm_out,
+                                   int32_t *se_out, int32_t *tier_out) {
   Workspace &ws = ctx->ws;
   const size_t n = (size_t)g.n;
   cudaStream_t st = ctx->stream;
   for (int32_t i = 0; i < count; ++i)
     if (sources[i] < 0 || sources[i] >= g.n) fail(BC_E_INVALID, "source out of range");
   ws.delta_lm.ensure(n * 64 * 8);
-  DevBuf dd, ddist, dsig;
+  DevBuf dd, ddist, dsig, dsm, dse;
   const int width = batch_width(ctx);
   const int chunk = std::min<int>(64, std::max(1, count));
+  const bool want_xf = sm_out || se_out;
   dd.ensure(n * chunk * 8);
-  if (dist_out) ddist.ensure(n * chunk * 4);
-  if (sigma_out) dsig.ensure(n * chunk * 8);
+  ddist.ensure(n * chunk * 4);  // also used to mark the sigma rows of extended lanes
+  if (sigma_out || want_xf) dsig.ensure(n * chunk * 8);
+  if (want_xf) {
+    dsm.ensure(n * chunk * 8);
+    dse.ensure(n * chunk * 4);
+  }
   Sink sink;
   sink.delta_lm = ws.delta_lm.as<double>();
   try {
@@ -662,16 +682,32 @@ static void do_source_dependencies(bc_ctx *ctx, const Graph &g, const int32_t *s
       const int cnt = std::min<int>(width == 1 ? 1 : 64, count - i0);
       BCG_CUDA(cudaMemcpyAsync(ws.sources.p, sources + i0, (size_t)cnt * 4, cudaMemcpyHostToDevice, st));
       BCG_CUDA(cudaMemsetAsync(ws.delta_lm.p, 0, n * 64 * 8, st));
+      uint64_t ovf = 0ull;
       if (width == 1) {
-        plain_source(ctx, g, ws.sources.as<int32_t>(), sink, dist_out ? ddist.as<int32_t>() : nullptr,
-                     sigma_out ? dsig.as<uint64_t>() : nullptr);
+        ovf = plain_source(ctx, g, ws.sources.as<int32_t>(), sink, ddist.as<int32_t>(),
+                           dsig.p ? dsig.as<uint64_t>() : nullptr, want_xf ? dsm.as<double>() : nullptr,
+                           want_xf ? dse.as<int32_t>() : nullptr)
+                  ? 1ull
+                  : 0ull;
       } else {
-        const int maxl = batch_forward(ctx, g, cnt, false);
-        if (dist_out || sigma_out)
-          batch_extract(ctx, g, cnt, maxl, dist_out ? ddist.as<int32_t>() : nullptr,
-                        sigma_out ? dsig.as<uint64_t>() : nullptr, 1, (int64_t)n);
-        batch_backward(ctx, g, maxl, sink);
+        const int maxl = batch_forward(ctx, g, cnt, false, OVF_EXTEND);
+        const uint64_t all = lanes_of(cnt);
+        ovf = ws.last_ovf & all;
+        batch_extract(ctx, g, cnt, maxl, ddist.as<int32_t>(), dsig.p ? dsig.as<uint64_t>() : nullptr, 1,
+                      (int64_t)n);
+        if (want_xf) sigma_to_xf(ctx, (long long)n * cnt, dsig.as<uint64_t>(), dsm.as<double>(), dse.as<int32_t>());
+        if (ovf != all) batch_backward(ctx, g, maxl, sink, all & ~ovf);
+        if (ovf) {
+          // the integer pass may have stopped early: distances come from the extended pass
+          const int xl = ext_forward(ctx, g, ws.sources.as<int32_t>(), ovf);
+          ext_extract(ctx, g, ovf, ddist.as<int32_t>(), want_xf ? dsm.as<double>() : nullptr,
+                      want_xf ? dse.as<int32_t>() : nullptr);
+          if (dsig.p) ext_mark_sigma(ctx, g, ovf, ddist.as<int32_t>(), dsig.as<uint64_t>());
+          ext_backward(ctx, g, xl, sink);
+        }
       }
+      if (tier_out)
+        for (int t = 0; t < cnt; ++t) tier_out[i0 + t] = (int32_t)((ovf >> t) & 1ull);
       {
         LaunchScope ls(ctx, F_MISC);
         const int64_t tot = (int64_t)n * cnt;
@@ -683,14 +719,16 @@ static void do_source_dependencies(bc_ctx *ctx, const Graph &g, const int32_t *s
       if (dist_out) BCG_CUDA(cudaMemcpy(dist_out + (size_t)i0 * n, ddist.p, n * cnt * 4, cudaMemcpyDeviceToHost));
       if (sigma_out)
         BCG_CUDA(cudaMemcpy(sigma_out + (size_t)i0 * n, dsig.p, n * cnt * 8, cudaMemcpyDeviceToHost));
+      if (sm_out) BCG_CUDA(cudaMemcpy(sm_out + (size_t)i0 * n, dsm.p, n * cnt * 8, cudaMemcpyDeviceToHost));
+      if (se_out) BCG_CUDA(cudaMemcpy(se_out + (size_t)i0 * n, dse.p, n * cnt * 4, cudaMemcpyDeviceToHost));
     }
     check_err_bits(ctx);
   } catch (...) {
     cudaStreamSynchronize(st);
-    dd.release(); ddist.release(); dsig.release();
+    dd.release(); ddist.release(); dsig.release(); dsm.release(); dse.release();
     throw;
   }
-  dd.release(); ddist.release(); dsig.release();
+  dd.release(); ddist.release(); dsig.release(); dsm.release(); dse.release();
 }
 
 }  // namespace bcg
@@ -785,7 +823,9 @@ void bc_destroy(bc_ctx *ctx) {
     Workspace &ws = ctx->ws;
     for (DevBuf *b : {&ws.lm, &ws.visited, &ws.sigma, &ws.active, &ws.wq, &ws.enable, &ws.sources, &ws.targets, &ws.pair_d,
                       &ws.pair_sig, &ws.err, &ws.cnt, &ws.acc, &ws.tslot, &ws.tdelta, &ws.scan, &ws.misc, &ws.misc2,
-                      &ws.delta_lm, &ws.coefx, &ws.p_dist, &ws.p_sigma, &ws.p_coef, &ws.p_queue, &ws.p_ctr})
+                      &ws.delta_lm, &ws.coefx, &ws.p_dist, &ws.p_sigma, &ws.p_coef, &ws.p_queue, &ws.p_ctr,
+                      &ws.x_dist, &ws.x_m, &ws.x_e, &ws.x_vis, &ws.x_nm, &ws.x_list, &ws.x_lmask, &ws.x_ctr,
+                      &ws.x_off})
       b->release();
     if (ws.pinned) cudaFreeHost(ws.pinned);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
@@ -898,7 +938,23 @@ bc_status bc_source_dependencies(bc_ctx *ctx, bc_graph g, const int32_t *sources
   if (count < 0) fail(BC_E_INVALID, "count must be >= 0");
   if (count > 0 && (!sources || !delta_out)) fail(BC_E_INVALID, "NULL argument");
   BCG_CUDA(cudaSetDevice(ctx->device));
-  if (count > 0) do_source_dependencies(ctx, gr, sources, count, delta_out, dist_out, sigma_out);
+  if (count > 0)
+    do_source_dependencies(ctx, gr, sources, count, delta_out, dist_out, sigma_out, nullptr, nullptr, nullptr);
+  BC_GUARD_END
+}
+
+bc_status bc_source_dependencies_ext(bc_ctx *ctx, bc_graph g, const int32_t *sources, int32_t count,
+                                     double *delta_out, int32_t *dist_out, double *sigma_mant_out,
+                                     int32_t *sigma_exp_out, int32_t *tier_out) {
+  BC_GUARD_BEGIN
+  const Graph &gr = get_graph(ctx, g);
+  if (count < 0) fail(BC_E_INVALID, "count must be >= 0");
+  if (count > 0 && (!sources || !delta_out || !sigma_mant_out || !sigma_exp_out))
+    fail(BC_E_INVALID, "NULL argument");
+  BCG_CUDA(cudaSetDevice(ctx->device));
+  if (count > 0)
+    do_source_dependencies(ctx, gr, sources, count, delta_out, dist_out, nullptr, sigma_mant_out, sigma_exp_out,
+                           tier_out);
   BC_GUARD_END
 }
 

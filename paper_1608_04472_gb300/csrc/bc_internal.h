@@ -61,6 +61,8 @@ enum Family {
   F_MISC,
   F_PFWD,
   F_PBWD,
+  F_XFWD,  // extended-form forward (samples whose counts exceed 2^64-1)
+  F_XBWD,  // extended-form backward
   F_NFAM
 };
 extern const char *kFamilyName[F_NFAM];
@@ -110,6 +112,12 @@ struct Workspace {
   DevBuf delta_lm; // [n][64] f64
   DevBuf coefx;    // [n][64] uint4: coefficients as 128-bit fixed point (unit 2^-96)
   DevBuf win;      // draw window: draws[W] | sorted sources[W] | sorted positions[W]
+  uint64_t last_ovf = 0ull;  // lanes of the last batched forward whose counts exceeded 2^64-1
+  // extended-form engine (bc_ext.cu): dist [n][64] i32, sigma/coef as
+  // mantissa [n][64] f64 + exponent [n][64] i32, visited / next masks [n],
+  // level entry lists with lane masks, level offsets (device and host copies)
+  DevBuf x_dist, x_m, x_e, x_vis, x_nm, x_list, x_lmask, x_ctr, x_off;
+  std::vector<unsigned long long> x_hoff;
   // plain single-source engine
   DevBuf p_dist, p_sigma, p_coef, p_queue, p_ctr;
   void *pinned = nullptr;  // 4 KiB pinned host staging
@@ -161,15 +169,35 @@ void resolve_events(bc_ctx *ctx);  // after a stream sync
 const Graph &get_graph(bc_ctx *ctx, bc_graph g);
 void sync(bc_ctx *ctx);
 unsigned read_and_clear_err(bc_ctx *ctx);
-void raise_err_bits(unsigned bits);
+void raise_err_bits(bc_ctx *ctx, unsigned bits);  // ORs bits into ws.err on the stream
 
 // ---- lane-batched engine (64 lanes) ----
+// What a forward pass does with lanes whose path counts exceed 2^64-1 (they are
+// listed in ws.last_ovf afterwards): ignore them (only distances are wanted),
+// raise ERR_SIGMA_OVERFLOW, or leave them to the extended form (the pass stops
+// early once every lane has overflowed).
+enum OvfMode { OVF_IGNORE = 0, OVF_ERROR = 1, OVF_EXTEND = 2 };
+inline uint64_t lanes_of(int count) { return count >= 64 ? ~0ull : ((1ull << count) - 1ull); }
 // Runs the forward BFS for `count` (<= 64) sources already on the device in
 // ws.sources. Returns the deepest level reached. With `pairs`, lane i stops
 // once ws.targets[i] is discovered and its d/sigma are recorded.
-int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs);
-// Runs the backward accumulation for levels maxlevel..1 into the sink.
-void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink);
+int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mode = OVF_ERROR);
+// Runs the backward accumulation for levels maxlevel..1 into the sink, for the
+// lanes in `keep`.
+void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink, uint64_t keep = ~0ull);
+
+// ---- extended-form engine (bc_ext.cu) ----
+// The per-sample step with counts as doubles of unbounded exponent, for the
+// lanes in `mask` (sources d_sources[t]); any depth.
+int ext_forward(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, uint64_t mask);
+void ext_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink);
+void ext_source_batch(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, uint64_t mask, const Sink &sink);
+// After ext_forward: rows [t][v] (stride n) of dist, sigma mantissa, exponent for lanes in mask.
+void ext_extract(bc_ctx *ctx, const Graph &g, uint64_t mask, int32_t *dist_out, double *sm_out, int32_t *se_out);
+// Rows [t][v] (stride n) of lanes in mask: sig = UINT64_MAX where dist >= 0, else 0.
+void ext_mark_sigma(bc_ctx *ctx, const Graph &g, uint64_t mask, const int32_t *dist, uint64_t *sig);
+// u64 counts to (mantissa, exponent), elementwise.
+void sigma_to_xf(bc_ctx *ctx, long long total, const uint64_t *sig, double *sm, int32_t *se);
 // Copies per-lane dist/sigma of the last forward into [count][n] device arrays.
 void batch_extract(bc_ctx *ctx, const Graph &g, int count, int maxlevel, int32_t *dist,
                    uint64_t *sigma, int64_t row_stride, int64_t lane_stride);
@@ -177,9 +205,14 @@ void batch_ensure(bc_ctx *ctx, const Graph &g);
 
 // ---- plain single-source engine ----
 // Forward + backward for one source; outputs to a sink laid out as for lane 0.
-void plain_source(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const Sink &sink, int32_t *dist_out,
-                  uint64_t *sigma_out);
+// A source whose counts exceed 2^64-1 runs in the extended form instead (its
+// sigma_out row then holds UINT64_MAX at every reached vertex); returns true then.
+// With sm_out/se_out (and sigma_out) the counts are also given in the extended form.
+bool plain_source(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const Sink &sink, int32_t *dist_out,
+                  uint64_t *sigma_out, double *sm_out = nullptr, int32_t *se_out = nullptr);
 void plain_ensure(bc_ctx *ctx, const Graph &g);
+// Distances d(*d_src, v) into dist_out[n] (device), -1 when unreachable.
+void plain_distances(bc_ctx *ctx, const Graph &g, const int32_t *d_src, int32_t *dist_out);
 
 // One batch of the per-sample step (plain or lane-batched, per the context's
 // width) for the sources already in ws.sources[0..count).

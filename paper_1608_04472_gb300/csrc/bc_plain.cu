@@ -20,7 +20,7 @@ constexpr int64_t ALPHA = 4;
 
 struct PlainCtr {
   int32_t qtail;
-  int32_t pad;
+  int32_t ovf;  // nonzero once a path count exceeded 2^64-1
   unsigned long long next_edges;
 };
 
@@ -32,6 +32,7 @@ __global__ void k_pinit(const int32_t *__restrict__ src, const int32_t *__restri
   sigma[s] = 1ull;
   queue[0] = s;
   ctr->qtail = 1;
+  ctr->ovf = 0;
   ctr->next_edges = (unsigned long long)(rp[s + 1] - rp[s]);
 }
 
@@ -59,7 +60,7 @@ k_ptd(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, const int
         won = (old == -1);
         if (won || old == level + 1) {
           const unsigned long long o = atomicAdd((unsigned long long *)&sigma[v], (unsigned long long)sw);
-          if (o + sw < o) e |= ERR_SIGMA_OVERFLOW;
+          if (o + sw < o) e = 1u;
           ++tri;
         }
       }
@@ -80,7 +81,8 @@ k_ptd(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, const int
   if (lane == 0 && edges) atomicAdd(&ctr->next_edges, edges);
   if (tri) atomicAdd(cnt, tri);
   if (rch) atomicAdd(cnt + 1, rch);
-  if (e) atomicOr(err, e);
+  if (e) atomicOr(&ctr->ovf, 1);
+  (void)err;
 }
 
 __global__ void __launch_bounds__(PTHREADS)
@@ -101,7 +103,7 @@ k_pbu(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col
       if (dist[w] == level) {
         const uint64_t x = sigma[w];
         const uint64_t t = s + x;
-        if (t < s) e |= ERR_SIGMA_OVERFLOW;
+        if (t < s) e = 1u;
         s = t;
         ++tri;
       }
@@ -110,7 +112,7 @@ k_pbu(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col
     for (int off = 16; off > 0; off >>= 1) {
       const uint64_t o = __shfl_xor_sync(FULL, s, off);
       const uint64_t t = s + o;
-      if (t < s) e |= ERR_SIGMA_OVERFLOW;
+      if (t < s) e = 1u;
       s = t;
     }
     if (s != 0ull && lane == 0) {
@@ -125,7 +127,8 @@ k_pbu(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col
   if (lane == 0 && edges) atomicAdd(&ctr->next_edges, edges);
   if (tri) atomicAdd(cnt, tri);
   if (lane == 0 && rch) atomicAdd(cnt + 1, rch);
-  if (e) atomicOr(err, e);
+  if (e) atomicOr(&ctr->ovf, 1);
+  (void)err;
 }
 
 __global__ void __launch_bounds__(PTHREADS)
@@ -195,7 +198,7 @@ void plain_ensure(bc_ctx *ctx, const Graph &g) {
 // Forward pass; returns the deepest non-empty level and fills level offsets.
 // With dest != null the traversal stops after the level that discovers *dest.
 static int plain_forward(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dest,
-                         std::vector<int32_t> &offs) {
+                         std::vector<int32_t> &offs, bool &overflow) {
   Workspace &ws = ctx->ws;
   plain_ensure(ctx, g);
   cudaStream_t st = ctx->stream;
@@ -246,6 +249,7 @@ static int plain_forward(bc_ctx *ctx, const Graph &g, const int32_t *d_src, cons
     BCG_CUDA(cudaGetLastError());
     BCG_CUDA(cudaStreamSynchronize(st));
     const int32_t ntail = h->qtail;
+    overflow = h->ovf != 0;
     frontier_edges = (int64_t)h->next_edges;
     if (d_dest && reinterpret_cast<int32_t *>(h + 1)[0] >= 0) {
       offs.push_back(ntail);
@@ -258,15 +262,25 @@ static int plain_forward(bc_ctx *ctx, const Graph &g, const int32_t *d_src, cons
   }
 }
 
-void plain_source(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const Sink &sink, int32_t *dist_out,
-                  uint64_t *sigma_out) {
+bool plain_source(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const Sink &sink, int32_t *dist_out,
+                  uint64_t *sigma_out, double *sm_out, int32_t *se_out) {
   std::vector<int32_t> offs;
-  const int maxlevel = plain_forward(ctx, g, d_src, nullptr, offs);
+  bool overflow = false;
+  const int maxlevel = plain_forward(ctx, g, d_src, nullptr, offs, overflow);
   Workspace &ws = ctx->ws;
   cudaStream_t st = ctx->stream;
   const size_t n = (size_t)g.n;
   if (dist_out) BCG_CUDA(cudaMemcpyAsync(dist_out, ws.p_dist.p, n * 4, cudaMemcpyDeviceToDevice, st));
   if (sigma_out) BCG_CUDA(cudaMemcpyAsync(sigma_out, ws.p_sigma.p, n * 8, cudaMemcpyDeviceToDevice, st));
+  if (overflow) {
+    // the sample is recomputed in the extended form
+    const int xl = ext_forward(ctx, g, d_src, 1ull);
+    if (sm_out || se_out) ext_extract(ctx, g, 1ull, nullptr, sm_out, se_out);
+    if (sigma_out) ext_mark_sigma(ctx, g, 1ull, ws.p_dist.as<int32_t>(), sigma_out);
+    ext_backward(ctx, g, xl, sink);
+    return true;
+  }
+  if (sm_out && sigma_out) sigma_to_xf(ctx, (long long)n, sigma_out, sm_out, se_out);
   const int blocks = plain_blocks();
   for (int l = maxlevel; l >= 1; --l) {
     const int32_t qb = offs[l], qe = offs[l + 1];
@@ -277,13 +291,25 @@ void plain_source(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const Sink 
                                     ws.p_sigma.as<uint64_t>(), ws.p_coef.as<double>(), sink,
                                     ws.err.as<unsigned>());
   }
+  return false;
+}
+
+// Distances from one source (-1 = unreachable); counts are not used, so their
+// overflow does not matter. Any depth.
+void plain_distances(bc_ctx *ctx, const Graph &g, const int32_t *d_src, int32_t *dist_out) {
+  std::vector<int32_t> offs;
+  bool overflow = false;
+  plain_forward(ctx, g, d_src, nullptr, offs, overflow);
+  BCG_CUDA(cudaMemcpyAsync(dist_out, ctx->ws.p_dist.p, (size_t)g.n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
 }
 
 // Plain pair lane: BFS from *d_src truncated at the level that reaches *d_dest;
 // leaves d(s,t) and sigma_st in ws.pair_d[0], ws.pair_sig[0].
 void plain_pair(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dest) {
   std::vector<int32_t> offs;
-  plain_forward(ctx, g, d_src, d_dest, offs);
+  bool overflow = false;
+  plain_forward(ctx, g, d_src, d_dest, offs, overflow);
+  if (overflow) raise_err_bits(ctx, ERR_SIGMA_OVERFLOW);
   LaunchScope ls(ctx, F_PAIR);
   k_pplain_pair<<<1, 1, 0, ctx->stream>>>(d_dest, ctx->ws.p_dist.as<int32_t>(), ctx->ws.p_sigma.as<uint64_t>(),
                                           ctx->ws.pair_d.as<int32_t>(), ctx->ws.pair_sig.as<uint64_t>());
@@ -364,6 +390,7 @@ static bc_status run(const int32_t *rp, const int32_t *col, int32_t n, int64_t n
       return BC_E_DEVICE;
     std::vector<int32_t> offs(1, 0);
     int32_t qb = 0, qe = 1;
+    bool overflow = false;
     int64_t frontier_edges = (int64_t)h.next_edges, explored = 0;
     int level = 0;
     for (;;) {
@@ -380,11 +407,13 @@ static bc_status run(const int32_t *rp, const int32_t *col, int32_t n, int64_t n
           cudaStreamSynchronize(st) != cudaSuccess)
         return BC_E_DEVICE;
       frontier_edges = (int64_t)h.next_edges;
+      overflow = overflow || h.ovf != 0;
       if (h.qtail == qe) break;
       qb = qe;
       qe = h.qtail;
       ++level;
     }
+    if (overflow) return BC_E_SIGMA_OVERFLOW;  // no extended form without scratch of its own
     for (int l = level; l >= 1; --l) {
       const int32_t b = offs[l], e = offs[l + 1];
       if (e <= b) continue;

@@ -142,19 +142,22 @@ def test_tiny_graphs(ctx):
             _check_sources(ctx, g, np.arange(n, dtype=np.int32), w)
 
 
-def test_sigma_overflow_reported(ctx, pkg):
-    g = gg.grid(35)  # corner-to-corner sigma C(68,34) > 2^64
+def test_sigma_overflow_boundary(ctx, pkg):
+    g = gg.grid(35)  # corner-to-corner sigma C(68,34) > 2^64: the extended form
     h = ctx.load_graph(g.row_ptr, g.col)
     try:
         for w in WIDTHS:
             ctx.set_batch_width(w)
-            with pytest.raises(pkg.BCError) as e:
-                ctx.source_dependencies(h, [0])
-            assert e.value.code == -9
+            # from (0,0) the far corner has C(68,34) > 2^64 paths; from (0,1) C(67,33) < 2^64
+            d, _, _, _, tier = ctx.source_dependencies_ext(h, [0, 1])
+            assert tier.tolist() == [1, 0]
+            assert np.array_equal(d[0], oracle.dependencies(g, 0)[0])
+            assert np.array_equal(d[1], oracle.dependencies(g, 1)[0])
         g34 = gg.grid(34)
         h2 = ctx.load_graph(g34.row_ptr, g34.col)
         _, _, sig = ctx.source_dependencies(h2, [0], want_sigma=True)
         assert int(sig[0, -1]) == math.comb(66, 33)
+        assert ctx.source_dependencies_ext(h2, [0])[4].tolist() == [0]
         ctx.free_graph(h2)
     finally:
         ctx.set_batch_width(64)

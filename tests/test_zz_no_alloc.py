@@ -63,3 +63,14 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert rc == -3  # BC_E_TOO_LARGE
     assert capi.bc_source_dependencies_noalloc(0, d_rp.data_ptr(), 0, 0, 0, d_src.data_ptr(), 1,
                                                d_out.data_ptr(), 0) == -1  # n < 1
+
+
+def test_noalloc_reports_overflow_without_extended_form():
+    torch = pytest.importorskip("torch")
+    from paper_1608_04472_gb300 import capi
+
+    g = gg.grid(40)  # counts from a corner exceed 2^64-1
+    d_rp, d_col, d_src, d_out = _device_buffers(torch, g, [0])
+    rc = capi.bc_source_dependencies_noalloc(0, d_rp.data_ptr(), d_col.data_ptr(), g.n, g.nnz,
+                                             d_src.data_ptr(), 1, d_out.data_ptr(), 0)
+    assert rc == -9  # BC_E_SIGMA_OVERFLOW
