@@ -1,0 +1,175 @@
+"""Accuracy of the sampled estimators against exact BC over many seeds, set
+beside the bounds the paper states for them.
+
+Workload: the small Erdos-Renyi graph (n = 2000, average degree 8, seed 1) and
+16 uniformly chosen target vertices. Exact BC comes from bc_exact; every
+estimate from the library's adaptive estimators, one query per seed.
+
+Bounds (t = n^2 / BC(v), BC over ordered pairs; "within a factor" read as a
+relative error |est/BC - 1| < d, the way the proofs set d):
+  * Theorem 2 (Bader's, Sec. 4): d = 1/eps, success probability >= 1 - 2 eps;
+  * Theorem 3 (Sec. 5, adaptive source sampling with threshold c*n):
+    d = 1/(eps t^(1/3)), success probability > 1 - (1 + 1/(2c-1)^2) eps, with
+    at least eps t^(2/3) samples;
+  * Theorem 4 (Sec. 6.2, adaptive pair sampling): d = (1/eps) (1/(t(n-1)))^(1/3),
+    the same success probability, at least eps t^(2/3) (n-1)^(1/3) samples.
+Theorems 3 and 4 are only claimed for eps in (0, 1/2); the table uses 0.1, 0.25
+and 0.45. Bounds are reported, not asserted.
+
+It also checks the sampling model of Corollary 1 on this graph: X = delta_s(v)
+for a uniform source s has mean A/n exactly (every source's dependencies are
+computed), and the model's variance (n-1)/(n^2 (n+1)) A^2 is set beside the
+exact variance.
+
+Usage: python accuracy.py [--seeds 100] [--json out.json]
+"""
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+EPS = (0.1, 0.25, 0.45)
+
+
+def _summary(rel):
+    rel = np.asarray(rel, np.float64)
+    return {"median": float(np.median(rel)), "p90": float(np.quantile(rel, 0.9)), "max": float(rel.max())}
+
+
+def _within(rel, d):
+    return float(np.mean(np.asarray(rel) < np.asarray(d)))
+
+
+def run(seeds: int):
+    import paper_1608_04472_gb300 as pkg
+
+    g = gg.erdos_renyi(2000, 8, 1)
+    n = g.n
+    targets = gg.uniform_targets(n, 16, 1)
+    out = {"graph": "ER n=2000 avg degree 8 seed 1", "targets": targets.tolist(), "seeds": seeds}
+    with pkg.Context(0, batch_width=64) as ctx:
+        h = ctx.load_graph(g.row_ptr, g.col)
+        bc = ctx.exact(h)
+        A = bc[targets]
+        keep = A > 0
+        out["bc_targets"] = A.tolist()
+        out["zero_bc_targets"] = int(np.sum(~keep))
+        t = np.where(keep, n * n / np.where(keep, A, 1.0), np.inf)
+
+        # Corollary 1's model against the exact distribution of X = delta_s(v)
+        delta, _, _ = ctx.source_dependencies(h, np.arange(n, dtype=np.int32))
+        X = delta[:, targets]
+        mean_exact = X.mean(axis=0)
+        var_exact = X.var(axis=0)
+        var_model = (n - 1) / (n * n * (n + 1)) * A * A
+        out["model_check"] = {
+            "max_rel_diff_mean_vs_A_over_n": float(np.max(np.abs(mean_exact[keep] * n / A[keep] - 1.0))),
+            "var_exact_over_model_median": float(np.median(var_exact[keep] / var_model[keep])),
+            "var_exact_over_model_range": [float(np.min(var_exact[keep] / var_model[keep])),
+                                           float(np.max(var_exact[keep] / var_model[keep]))],
+        }
+
+        runs = []
+        # adaptive source sampling (Sec. 4 loop), c = 2 and 5, cap 64 n
+        for c in (2.0, 5.0):
+            rel, ks, stopped = [], [], []
+            t0 = time.time()
+            for s in range(seeds):
+                r = ctx.adaptive_sources(h, targets, c, 64 * n, 1000 + s, s)
+                rel.append(np.abs(r["est"][keep] / A[keep] - 1.0))
+                ks.append(r["k"][keep])
+                stopped.append(r["status"][keep] == pkg.BC_STOPPED)
+            rel, ks, stopped = np.concatenate(rel), np.concatenate(ks), np.concatenate(stopped)
+            tt = np.tile(t[keep], seeds)
+            row = {"estimator": "sources", "c": c, "threshold": "S > c n", "runs": int(rel.size),
+                   "seconds": time.time() - t0, "stopped_frac": float(np.mean(stopped)),
+                   "rel_err": _summary(rel), "mean_k": float(ks.mean()), "bounds": []}
+            for eps in EPS:
+                row["bounds"].append({
+                    "eps": eps,
+                    "thm3_d_median": float(np.median(1.0 / (eps * np.cbrt(tt)))),
+                    "thm3_within": _within(rel, 1.0 / (eps * np.cbrt(tt))),
+                    "thm3_promised": 1.0 - (1.0 + 1.0 / (2 * c - 1) ** 2) * eps,
+                    "thm3_min_samples_median": float(np.median(eps * tt ** (2.0 / 3.0))),
+                    "thm2_within": _within(rel, 1.0 / eps),
+                    "thm2_promised": 1.0 - 2 * eps,
+                })
+            runs.append(row)
+        # adaptive pair sampling (Algorithm 1): the paper's threshold c n (every
+        # target reaches the cap here) and the rescaled reading S (n-1) > c n
+        for c, scale, cap in ((1.0, 1.0, 32768), (2.0, float(n - 1), 32768), (5.0, float(n - 1), 32768)):
+            rel, ks, stopped = [], [], []
+            t0 = time.time()
+            for s in range(seeds):
+                r = ctx.adaptive_pairs(h, targets, c, cap, 2000 + s, s, scale)
+                rel.append(np.abs(r["est"][keep] / A[keep] - 1.0))
+                ks.append(r["k"][keep])
+                stopped.append(r["status"][keep] == pkg.BC_STOPPED)
+            rel, ks, stopped = np.concatenate(rel), np.concatenate(ks), np.concatenate(stopped)
+            tt = np.tile(t[keep], seeds)
+            row = {"estimator": "pairs", "c": c, "threshold": "S > c n" if scale == 1.0 else "S (n-1) > c n",
+                   "cap": cap, "runs": int(rel.size), "seconds": time.time() - t0,
+                   "stopped_frac": float(np.mean(stopped)), "rel_err": _summary(rel), "mean_k": float(ks.mean()),
+                   "bounds": []}
+            for eps in EPS:
+                d = (1.0 / eps) * np.cbrt(1.0 / (tt * (n - 1)))
+                row["bounds"].append({
+                    "eps": eps,
+                    "thm4_d_median": float(np.median(d)),
+                    "thm4_within": _within(rel, d),
+                    "thm4_promised": 1.0 - (1.0 + 1.0 / (2 * c - 1) ** 2) * eps,
+                    "thm4_min_samples_median": float(np.median(eps * tt ** (2.0 / 3.0) * (n - 1) ** (1.0 / 3.0))),
+                })
+            runs.append(row)
+        out["runs"] = runs
+    return out
+
+
+def markdown(res):
+    lines = ["| estimator | c | threshold | runs | stopped | mean k | median rel err | p90 | max |",
+             "|---|---|---|---|---|---|---|---|---|"]
+    for r in res["runs"]:
+        e = r["rel_err"]
+        lines.append(f"| {r['estimator']} | {r['c']:g} | {r['threshold']} | {r['runs']} | "
+                     f"{100 * r['stopped_frac']:.0f} % | {r['mean_k']:.0f} | {e['median']:.4f} | {e['p90']:.4f} | "
+                     f"{e['max']:.4f} |")
+    lines += ["", "| estimator | c | eps | bound d (median over targets) | within d | promised | "
+                  "Bader's d = 1/eps: within | promised |",
+              "|---|---|---|---|---|---|---|---|"]
+    for r in res["runs"]:
+        for b in r["bounds"]:
+            if r["estimator"] == "sources":
+                lines.append(f"| sources (Thm 3) | {r['c']:g} | {b['eps']} | {b['thm3_d_median']:.3f} | "
+                             f"{100 * b['thm3_within']:.1f} % | > {100 * b['thm3_promised']:.1f} % | "
+                             f"{100 * b['thm2_within']:.1f} % | >= {100 * b['thm2_promised']:.1f} % |")
+            else:
+                lines.append(f"| pairs (Thm 4), {r['threshold']} | {r['c']:g} | {b['eps']} | "
+                             f"{b['thm4_d_median']:.4f} | {100 * b['thm4_within']:.1f} % | "
+                             f"> {100 * b['thm4_promised']:.1f} % | - | - |")
+    return "\n".join(lines)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--seeds", type=int, default=100)
+    ap.add_argument("--json", default=None)
+    a = ap.parse_args()
+    res = run(a.seeds)
+    if a.json:
+        with open(a.json, "w") as f:
+            json.dump(res, f, indent=1)
+    print(json.dumps({k: v for k, v in res.items() if k != "runs"}))
+    print(markdown(res))
+
+
+if __name__ == "__main__":
+    main()

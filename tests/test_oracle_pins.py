@@ -11,7 +11,7 @@ Nothing here compares the oracle with itself. The pins are:
     has d(s,t)-1 interior vertices);
   * the pair formula of Algorithm 1 against Def. 1 (sum over all pairs = BC);
   * stop rules against a plain re-run of the loop on the logged draws;
-  * unbiasedness E[X_i] = A/n (Corollary 1) and E[Y_i] = A/(n(n-1)) (Corollary 2).
+  * unbiasedness E[X_i] = A/n (Corollary 1) and E[Y_i] = A/(n(n-1)) (Corollary 3).
 """
 import itertools
 import math
@@ -459,7 +459,7 @@ def test_source_sampling_unbiased():
 
 
 def test_pair_sampling_unbiased():
-    """Corollary 2: E[Y_i] = A/(n(n-1)) under uniform ordered distinct pairs."""
+    """Corollary 3: E[Y_i] = A/(n(n-1)) under uniform ordered distinct pairs."""
     g = _random_small(9, 0.3, 5)
     bc_b, _ = brute_bc_and_delta(g)
     v = int(np.argmax([float(x) for x in bc_b]))
