@@ -153,6 +153,20 @@ bc_status bc_exact(bc_ctx *ctx, bc_graph g, double *bc_out);
 bc_status bc_uniform_sources(bc_ctx *ctx, bc_graph g, int64_t k, uint64_t seed, uint64_t qid,
                              double *est_out);
 
+/* Uniform k-source estimates for G graphs at once (the estimate of
+ * bc_uniform_sources, per graph): graph i uses k[i] draws of (seed[i], qid[i])
+ * and its estimates land in est_out[off_i .. off_i + n_i), off_i = n_0 + ... +
+ * n_{i-1}. Results equal G separate bc_uniform_sources calls bit for bit.
+ * Graphs of very different size and depth (a 2D grid is hundreds of levels
+ * deep) share one persistent launch: work items (graph, run of draws) are taken
+ * largest first by CTAs that keep running until the queue is empty, with no
+ * launch or host round trip per BFS level; the launch sequence is a captured
+ * CUDA graph that later calls with the same graphs, k, seeds and qids replay.
+ * Each k[i] in [1, 2^32]. Device memory: about 36 bytes x max n per resident
+ * CTA, plus 24 bytes per vertex per work item. */
+bc_status bc_uniform_sources_multi(bc_ctx *ctx, int32_t G, const bc_graph *graphs, const int64_t *k,
+                                   const uint64_t *seed, const uint64_t *qid, double *est_out);
+
 /* Bader's adaptive source sampling (Sec. 4 steps 1-3) for T distinct targets
  * sharing one draw stream: per target, S <- S + delta_{s_i}(v) in draw order
  * until S > c*n (BC_STOPPED) or k = cap (BC_CAPPED); est = (n*S)/k.

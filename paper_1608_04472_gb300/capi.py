@@ -74,6 +74,7 @@ _SIGS = {
     "bc_graph_info": (_i32, [_vp, _i64, _i32p, _i64p]),
     "bc_source_dependencies": (_i32, [_vp, _i64, _i32p, _i32, _f64p, _i32p, _u64p]),
     "bc_source_dependencies_ext": (_i32, [_vp, _i64, _i32p, _i32, _f64p, _i32p, _f64p, _i32p, _i32p]),
+    "bc_uniform_sources_multi": (_i32, [_vp, _i32, _i64p, _i64p, _u64p, _u64p, _f64p]),
     "bc_exact": (_i32, [_vp, _i64, _f64p]),
     "bc_uniform_sources": (_i32, [_vp, _i64, _i64, _u64, _u64, _f64p]),
     "bc_adaptive_sources": (_i32, [_vp, _i64, _i32p, _i32, _f64, _i64, _u64, _u64, _f64p, _i64p,
@@ -196,6 +197,25 @@ def bc_source_dependencies_ext(ctx, g: int, sources):
         _ck(ctx, _lib.bc_source_dependencies_ext(ctx, g, _p(src, _i32p), cnt, _p(delta, _f64p), _p(dist, _i32p),
                                                  _p(sm, _f64p), _p(se, _i32p), _p(tier, _i32p)))
     return delta, dist, sm, se, tier
+
+
+def bc_uniform_sources_multi(ctx, graphs, k, seeds, qids):
+    """Uniform estimates for several graphs in one persistent launch; returns a
+    list of per-graph arrays (graph i: n_i values)."""
+    hs = np.ascontiguousarray(graphs, dtype=np.int64)
+    G = hs.size
+    kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, dtype=np.int64), (G,)))
+    ss = np.ascontiguousarray(np.broadcast_to(np.asarray(seeds, dtype=np.uint64), (G,)))
+    qq = np.ascontiguousarray(np.broadcast_to(np.asarray(qids, dtype=np.uint64), (G,)))
+    ns = [bc_graph_info(ctx, int(h))[0] for h in hs.tolist()]
+    out = np.empty(max(1, sum(ns)), np.float64)
+    _ck(ctx, _lib.bc_uniform_sources_multi(ctx, G, _p(hs, _i64p), _p(kk, _i64p), _p(ss, _u64p), _p(qq, _u64p),
+                                           _p(out, _f64p)))
+    res, off = [], 0
+    for n in ns:
+        res.append(out[off:off + n].copy())
+        off += n
+    return res
 
 
 def bc_exact(ctx, g: int) -> np.ndarray:
@@ -399,6 +419,9 @@ class Context:
 
     def source_dependencies_ext(self, g, sources):
         return bc_source_dependencies_ext(self.ptr, g, sources)
+
+    def uniform_sources_multi(self, graphs, k, seeds, qids):
+        return bc_uniform_sources_multi(self.ptr, graphs, k, seeds, qids)
 
     def exact(self, g):
         return bc_exact(self.ptr, g)

@@ -1183,22 +1183,32 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
                                                           ws.cnt.as<unsigned long long>(), ws.sigma.as<uint64_t>(),
                                                           ws.enable.as<uint64_t>());
     }
-    uint64_t cont, ovf;
+    // Deep traversals also watch the overflowed lanes every level: once every
+    // lane has overflowed the integer pass has nothing left to give (and its
+    // per-level masks would only grow).
+    const bool watch = mode == OVF_EXTEND && l >= 24;
+    uint64_t cont, ovf = 0ull;
+    const uint64_t *cont_word = act + l + 1;
     if (pairs) {
       LaunchScope ls(ctx, F_PAIR);
       k_pair_check<<<1, 64, 0, st>>>(count, l + 1, ws.targets.as<int32_t>(), lm + (size_t)(l + 1) * n,
                                      ws.sigma.as<uint64_t>(), ws.enable.as<uint64_t>(), ws.pair_d.as<int32_t>(),
                                      ws.pair_sig.as<uint64_t>(), act + l + 1, ws.enable.as<uint64_t>() + 1);
-      read_u64x2(ctx, ws.enable.as<uint64_t>() + 1, ws.enable.as<uint64_t>() + 3, cont, ovf);
-    } else {
-      read_u64x2(ctx, act + l + 1, ws.enable.as<uint64_t>() + 3, cont, ovf);
+      cont_word = ws.enable.as<uint64_t>() + 1;
     }
-    ws.last_ovf = ovf;
-    // every lane overflowed: the integer pass has nothing left to give
-    const bool all_ovf = mode == OVF_EXTEND && ovf != 0ull && (ovf & lanes_of(count)) == lanes_of(count);
+    if (watch)
+      read_u64x2(ctx, cont_word, ws.enable.as<uint64_t>() + 3, cont, ovf);
+    else
+      cont = read_u64(ctx, cont_word);
+    const bool all_ovf = watch && ovf != 0ull && (ovf & lanes_of(count)) == lanes_of(count);
     if (!cont || all_ovf) {
-      ws.last_sigmax = read_u64(ctx, ws.enable.as<uint64_t>() + 2);
-      if (ovf && mode == OVF_ERROR) raise_err_bits(ctx, ERR_SIGMA_OVERFLOW);
+      // largest sigma and overflowed lanes, adjacent words
+      uint64_t *h = static_cast<uint64_t *>(ws.pinned);
+      BCG_CUDA(cudaMemcpyAsync(h, ws.enable.as<uint64_t>() + 2, 16, cudaMemcpyDeviceToHost, st));
+      BCG_CUDA(cudaStreamSynchronize(st));
+      ws.last_sigmax = h[0];
+      ws.last_ovf = h[1];
+      if (ws.last_ovf && mode == OVF_ERROR) raise_err_bits(ctx, ERR_SIGMA_OVERFLOW);
       return l;
     }
     ++l;

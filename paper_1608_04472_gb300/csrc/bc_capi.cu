@@ -812,6 +812,7 @@ void bc_destroy(bc_ctx *ctx) {
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    forget_multi_plan(ctx);
     resolve_events(ctx);
     for (auto &kv : ctx->graphs) {
       forget_heavy_meta(kv.second.rp);
@@ -915,6 +916,7 @@ bc_status bc_graph_free(bc_ctx *ctx, bc_graph g) {
   if (it == ctx->graphs.end()) fail(BC_E_UNKNOWN_HANDLE, "unknown graph handle");
   if (server_uses_graph(ctx, g)) fail(BC_E_INVALID, "graph is used by a queued or running query");
   sync(ctx);
+  if (multi_plan_uses_graph(ctx, g)) forget_multi_plan(ctx);
   forget_heavy_meta(it->second.rp);
   forget_key_meta(it->second.rp);
   cudaFree(it->second.rp);
@@ -974,6 +976,23 @@ bc_status bc_uniform_sources(bc_ctx *ctx, bc_graph g, int64_t k, uint64_t seed, 
   if (k < 1 || k > ((int64_t)1 << 32)) fail(BC_E_INVALID, "k must be in [1, 2^32]");
   BCG_CUDA(cudaSetDevice(ctx->device));
   do_exact_or_uniform(ctx, gr, false, k, seed, qid, est_out);
+  BC_GUARD_END
+}
+
+bc_status bc_uniform_sources_multi(bc_ctx *ctx, int32_t G, const bc_graph *graphs, const int64_t *k,
+                                   const uint64_t *seed, const uint64_t *qid, double *est_out) {
+  BC_GUARD_BEGIN
+  if (G < 1) fail(BC_E_INVALID, "G must be >= 1");
+  if (!graphs || !k || !seed || !qid || !est_out) fail(BC_E_INVALID, "NULL argument");
+  std::vector<bc_graph> hs(graphs, graphs + G);
+  std::vector<const Graph *> gs;
+  for (int32_t i = 0; i < G; ++i) {
+    gs.push_back(&get_graph(ctx, graphs[i]));
+    if (k[i] < 1 || k[i] > ((int64_t)1 << 32)) fail(BC_E_INVALID, "every k must be in [1, 2^32]");
+  }
+  BCG_CUDA(cudaSetDevice(ctx->device));
+  do_uniform_multi(ctx, hs, gs, k, seed, qid, est_out);
+  check_err_bits(ctx);
   BC_GUARD_END
 }
 

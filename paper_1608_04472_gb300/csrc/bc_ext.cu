@@ -23,69 +23,12 @@
 #include <algorithm>
 
 #include "bc_internal.h"
+#include "bc_xf.cuh"
 
 namespace bcg {
 
 constexpr int XTHREADS = 256;
 constexpr int XCHUNK = 16;  // levels launched between two host reads
-
-struct Xf {
-  double m;
-  int e;
-};
-
-// 2^k as a double, k in [-1022, 1023]
-__device__ __forceinline__ double pow2(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
-
-// x * 2^e normalised; x a positive normal double, or 0
-__device__ __forceinline__ Xf xf_make(double x, int e) {
-  if (x == 0.0) return Xf{0.0, 0};
-  const long long b = __double_as_longlong(x);
-  const int k = (int)((b >> 52) & 0x7ff) - 1023;
-  return Xf{__longlong_as_double((b & 0x000fffffffffffffLL) | (1023LL << 52)), e + k};
-}
-
-// RN(a + b), a, b >= 0: a term more than 60 binades below the other is under a
-// quarter ulp of it; otherwise both mantissas are exact on a common scale and
-// one double addition rounds their exact sum.
-__device__ __forceinline__ Xf xf_add(Xf a, Xf b) {
-  if (a.m == 0.0) return b;
-  if (b.m == 0.0) return a;
-  if (a.e < b.e) {
-    const Xf t = a;
-    a = b;
-    b = t;
-  }
-  const long long d = (long long)a.e - (long long)b.e;
-  if (d > 60) return a;
-  return xf_make(__dadd_rn(a.m, __dmul_rn(b.m, pow2(-(int)d))), a.e);
-}
-
-// RN(a * b) as a double: the mantissa product rounds once; steps of 2^1000 are
-// exact while the value stays normal and only the last one can round.
-__device__ __forceinline__ double xf_mul_to_double(Xf a, Xf b) {
-  if (a.m == 0.0 || b.m == 0.0) return 0.0;
-  double p = __dmul_rn(a.m, b.m);
-  long long k = (long long)a.e + (long long)b.e;
-  while (k > 1000) {
-    p = __dmul_rn(p, pow2(1000));
-    k -= 1000;
-  }
-  while (k < -1000) {
-    p = __dmul_rn(p, pow2(-1000));
-    k += 1000;
-  }
-  return __dmul_rn(p, pow2((int)k));
-}
-
-// RN(x / b) for a double x >= 1/2 and b > 0
-__device__ __forceinline__ Xf xf_div(double x, Xf b) { return xf_make(__ddiv_rn(x, b.m), -b.e); }
-
-__device__ __forceinline__ Xf xf_load(const double *xm, const int32_t *xe, size_t i) { return Xf{xm[i], xe[i]}; }
-__device__ __forceinline__ void xf_store(double *xm, int32_t *xe, size_t i, Xf x) {
-  xm[i] = x.m;
-  xe[i] = x.e;
-}
 
 // Level 0: one entry per distinct source vertex of the lanes in `mask`.
 __global__ void k_x_init(uint64_t mask, const int32_t *__restrict__ sources, uint64_t *__restrict__ nm,

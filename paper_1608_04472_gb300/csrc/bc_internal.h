@@ -219,6 +219,12 @@ void plain_distances(bc_ctx *ctx, const Graph &g, const int32_t *d_src, int32_t 
 void run_source_batch(bc_ctx *ctx, const Graph &g, int count, const Sink &sink);
 inline bool batch_width_is_plain(bc_ctx *ctx) { return ctx->batch_width == 1; }
 
+// ---- many graphs in one persistent launch (bc_multi.cu) ----
+void do_uniform_multi(bc_ctx *ctx, const std::vector<bc_graph> &handles, const std::vector<const Graph *> &gs,
+                      const int64_t *k, const uint64_t *seed, const uint64_t *qid, double *est_out);
+void forget_multi_plan(bc_ctx *ctx);
+bool multi_plan_uses_graph(bc_ctx *ctx, bc_graph g);
+
 // query server lifetime (bc_serve.cu)
 void server_shutdown(bc_ctx *ctx);
 bool server_uses_graph(bc_ctx *ctx, bc_graph g);

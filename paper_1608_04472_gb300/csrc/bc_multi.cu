@@ -1,0 +1,474 @@
+// bc_multi.cu -- uniform k-source estimates (n/k times the summed dependencies
+// of k drawn sources, the per-sample step of Sec. 3 without the adaptive stop)
+// for many graphs of uneven size and depth in one persistent launch.
+//
+// Work items are (graph, run of draws). Persistent CTAs take items from one
+// atomic counter, in decreasing order of estimated cost, and run each source of
+// an item on their own: a level-synchronous BFS with a queue (distances by
+// compare-and-swap, then path counts pulled from the previous level), the
+// dependency recursion of Theorem 1 in decreasing distance, and the exact
+// per-vertex sum of the item's dependencies. Levels are separated by CTA
+// barriers, not kernel launches, so graphs hundreds of levels deep (grids) cost
+// no launch or host round trip per level. A second kernel adds the items'
+// exact partial sums per vertex and rounds once; the two launches are replayed
+// from a captured CUDA graph.
+//
+// Arithmetic per source is the library's: exact uint64 counts and exact
+// successor sums (order-free); a source whose counts exceed 2^64-1 has its
+// counts re-pulled and its dependencies computed in the extended form
+// (bc_xf.cuh; sums in CSR order of the vertex). Vertices of degree above 32 are
+// handled by a whole warp.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "bc_internal.h"
+#include "bc_xf.cuh"
+
+namespace bcg {
+
+constexpr int MT = 256;  // threads per CTA
+constexpr int MWARPS = MT / 32;
+constexpr int MHEAVY = 32;  // vertices above this degree are processed by a whole warp
+
+struct MGraph {
+  const int32_t *rp;
+  const int32_t *col;
+  int32_t n;
+  int32_t pad;
+  int64_t k;
+  uint64_t seed, qid;
+};
+
+struct MItem {
+  int32_t g;
+  int32_t pad;
+  int64_t i0, i1;  // draws [i0, i1) of the graph's stream
+  int64_t part;    // first Acc of the item's partial sums
+};
+
+// Per-CTA scratch, each array nmax (+2) long.
+struct MScratch {
+  int32_t *dist, *queue, *lo, *sige, *coefe;
+  uint64_t *sig;  // tier 0 counts; extended-form mantissas (double bits)
+  double *coef;   // tier 0 coefficients; extended-form mantissas
+};
+
+__host__ __device__ inline size_t mscratch_stride(int32_t nmax) {
+  const size_t ints = ((size_t)5 * nmax + 2) * 4;
+  return ((ints + 255) / 256) * 256 + (size_t)nmax * 16;
+}
+
+__device__ inline MScratch mscratch_of(unsigned char *base, int32_t nmax) {
+  MScratch s;
+  s.dist = reinterpret_cast<int32_t *>(base);
+  s.queue = s.dist + nmax;
+  s.lo = s.queue + nmax;
+  s.sige = s.lo + nmax + 2;
+  s.coefe = s.sige + nmax;
+  const size_t ints = ((size_t)5 * nmax + 2) * 4;
+  s.sig = reinterpret_cast<uint64_t *>(base + ((ints + 255) / 256) * 256);
+  s.coef = reinterpret_cast<double *>(s.sig + nmax);
+  return s;
+}
+
+__device__ __forceinline__ Xf xf_at(const MScratch &S, bool coefs, int32_t v) {
+  return coefs ? Xf{S.coef[v], S.coefe[v]} : Xf{__longlong_as_double((long long)S.sig[v]), S.sige[v]};
+}
+
+// Sum over the CSR neighbours u of v with dist[u] == want, in CSR order, of the
+// extended counts (coefs = false) or coefficients (coefs = true). `coop`: the
+// whole warp works on v (every lane returns the sum); otherwise one thread.
+__device__ Xf xf_pull(const MScratch &S, const int32_t *__restrict__ col, int beg, int end, int32_t want,
+                      bool coefs, bool coop) {
+  Xf acc{0.0, 0};
+  if (!coop) {
+    for (int j = beg; j < end; ++j) {
+      const int32_t u = col[j];
+      if (S.dist[u] == want) acc = xf_add(acc, xf_at(S, coefs, u));
+    }
+    return acc;
+  }
+  const int lane = threadIdx.x & 31;
+  for (int base = beg; base < end; base += 32) {
+    const int j = base + lane;
+    bool ok = false;
+    Xf x{0.0, 0};
+    if (j < end) {
+      const int32_t u = col[j];
+      ok = S.dist[u] == want;
+      if (ok) x = xf_at(S, coefs, u);
+    }
+    const unsigned bal = __ballot_sync(FULL, ok);
+    for (unsigned b = bal; b; b &= b - 1u) {  // CSR order: lowest position first
+      const int k = __ffs(b) - 1;
+      acc = xf_add(acc, Xf{__shfl_sync(FULL, x.m, k), __shfl_sync(FULL, x.e, k)});
+    }
+  }
+  return acc;
+}
+
+// Runs fn(v, beg, end, coop) for the queue entries [b, e): light vertices one
+// per thread, heavy ones (degree > MHEAVY) by the whole warp.
+template <class F>
+__device__ __forceinline__ void for_level(const MScratch &S, const int32_t *__restrict__ rp, int b, int e, F fn) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int cb = b + warp * 32; cb < e; cb += MWARPS * 32) {
+    const int idx = cb + lane;
+    int32_t v = -1;
+    int beg = 0, end = 0;
+    if (idx < e) {
+      v = S.queue[idx];
+      beg = rp[v];
+      end = rp[v + 1];
+    }
+    const bool heavy = v >= 0 && end - beg > MHEAVY;
+    if (v >= 0 && !heavy) fn(v, beg, end, false);
+    for (unsigned hb = __ballot_sync(FULL, heavy); hb; hb &= hb - 1u) {
+      const int k = __ffs(hb) - 1;
+      fn(__shfl_sync(FULL, v, k), __shfl_sync(FULL, beg, k), __shfl_sync(FULL, end, k), true);
+    }
+  }
+}
+
+// One source on the whole CTA; its dependencies are added to part[].
+__device__ void multi_source(const MGraph &G, int32_t s, const MScratch &S, Acc *__restrict__ part, unsigned &err,
+                             int *s_tail, int *s_ovf) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int32_t *__restrict__ rp = G.rp;
+  const int32_t *__restrict__ col = G.col;
+  for (int32_t v = tid; v < G.n; v += MT) S.dist[v] = -1;
+  __syncthreads();
+  if (tid == 0) {
+    S.dist[s] = 0;
+    S.sig[s] = 1ull;
+    S.queue[0] = s;
+    S.lo[0] = 0;
+    S.lo[1] = 1;
+    *s_tail = 1;
+    *s_ovf = 0;
+  }
+  __syncthreads();
+  int L = 0;
+  for (;;) {
+    const int b = S.lo[L], e = S.lo[L + 1];
+    // discovery of level L+1
+    for_level(S, rp, b, e, [&](int32_t v, int beg, int end, bool coop) {
+      const int step = coop ? 32 : 1;
+      for (int j = beg + (coop ? lane : 0); j < end; j += step) {
+        const int32_t w = col[j];
+        if (S.dist[w] == -1 && atomicCAS(&S.dist[w], -1, L + 1) == -1) S.queue[atomicAdd(s_tail, 1)] = w;
+      }
+      (void)v;
+    });
+    __syncthreads();
+    const int nt = *s_tail;
+    if (nt == e) break;  // no vertex at distance L+1
+    if (tid == 0) S.lo[L + 2] = nt;
+    // exact counts of level L+1, pulled from level L (order-free integer sums)
+    for_level(S, rp, e, nt, [&](int32_t w, int beg, int end, bool coop) {
+      uint64_t sum = 0ull;
+      bool ov = false;
+      const int step = coop ? 32 : 1;
+      for (int j = beg + (coop ? lane : 0); j < end; j += step) {
+        const int32_t u = col[j];
+        if (S.dist[u] == L) {
+          const uint64_t t = sum + S.sig[u];
+          ov |= t < sum;
+          sum = t;
+        }
+      }
+      if (coop) {
+        for (int off = 16; off > 0; off >>= 1) {
+          const uint64_t o = __shfl_xor_sync(FULL, sum, off);
+          const uint64_t t = sum + o;
+          ov |= t < sum;
+          sum = t;
+        }
+        ov = __any_sync(FULL, ov);
+      }
+      if (!coop || lane == 0) {
+        S.sig[w] = sum;
+        if (ov) *s_ovf = 1;
+      }
+    });
+    __syncthreads();
+    ++L;
+  }
+  const bool ext = *s_ovf != 0;
+  if (ext) {
+    // the counts again, in the extended form (pull order)
+    if (tid == 0) {
+      S.sig[s] = (uint64_t)__double_as_longlong(1.0);
+      S.sige[s] = 0;
+    }
+    __syncthreads();
+    for (int d = 1; d <= L; ++d) {
+      for_level(S, rp, S.lo[d], S.lo[d + 1], [&](int32_t w, int beg, int end, bool coop) {
+        const Xf x = xf_pull(S, col, beg, end, d - 1, false, coop);
+        if (!coop || lane == 0) {
+          S.sig[w] = (uint64_t)__double_as_longlong(x.m);
+          S.sige[w] = x.e;
+        }
+      });
+      __syncthreads();
+    }
+  }
+  // Theorem 1 in decreasing distance
+  for (int d = L; d >= 1; --d) {
+    for_level(S, rp, S.lo[d], S.lo[d + 1], [&](int32_t v, int beg, int end, bool coop) {
+      double delta;
+      if (ext) {
+        const Xf sum = xf_pull(S, col, beg, end, d + 1, true, coop);
+        const Xf sg{__longlong_as_double((long long)S.sig[v]), S.sige[v]};
+        delta = xf_mul_to_double(sg, sum);
+        if (!coop || lane == 0) {
+          const Xf cf = xf_div(__dadd_rn(1.0, delta), sg);
+          S.coef[v] = cf.m;
+          S.coefe[v] = cf.e;
+        }
+      } else {
+        Acc a = acc_zero();
+        const int step = coop ? 32 : 1;
+        for (int j = beg + (coop ? lane : 0); j < end; j += step) {
+          const int32_t w = col[j];
+          if (S.dist[w] == d + 1) acc_add(a, S.coef[w], err);
+        }
+        if (coop) a = acc_warp_sum(a);
+        const uint64_t sg = S.sig[v];
+        delta = __dmul_rn(sigma_to_double(sg), acc_round(a));
+        if (!coop || lane == 0) S.coef[v] = coef_of(delta, sg);
+      }
+      if (!coop || lane == 0) {
+        Acc cur = part[v];
+        acc_add(cur, delta, err);
+        part[v] = cur;
+      }
+    });
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(MT)
+k_multi(const MGraph *__restrict__ graphs, const MItem *__restrict__ items, int nitems, unsigned *__restrict__ next,
+        unsigned char *__restrict__ scratch, size_t stride, int32_t nmax, Acc *__restrict__ partials,
+        unsigned *__restrict__ err) {
+  __shared__ int s_item, s_tail, s_ovf;
+  const MScratch S = mscratch_of(scratch + (size_t)blockIdx.x * stride, nmax);
+  unsigned e = 0u;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(next, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= nitems) break;
+    const MItem item = items[it];
+    const MGraph G = graphs[item.g];
+    Acc *part = partials + item.part;
+    for (int32_t v = threadIdx.x; v < G.n; v += MT) part[v] = acc_zero();
+    for (int64_t i = item.i0; i < item.i1; ++i)
+      multi_source(G, draw_source(G.seed, G.qid, (uint64_t)i, G.n), S, part, e, &s_tail, &s_ovf);
+    __syncthreads();  // s_item is rewritten only after every thread has used it
+  }
+  if (e) atomicOr(err, e);
+}
+
+// est[off_g + v] = (n * RN(sum of the items' exact partial sums)) / k
+__global__ void k_multi_reduce(const MGraph *__restrict__ graphs, const int32_t *__restrict__ gio,
+                               const int32_t *__restrict__ gitems, const MItem *__restrict__ items,
+                               const Acc *__restrict__ partials, const int64_t *__restrict__ est_off,
+                               double *__restrict__ est) {
+  const int g = blockIdx.y;
+  const MGraph G = graphs[g];
+  const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= G.n) return;
+  Acc a = acc_zero();
+  for (int q = gio[g]; q < gio[g + 1]; ++q) acc_add_acc(a, partials[items[gitems[q]].part + v]);
+  est[est_off[g] + v] = __ddiv_rn(__dmul_rn((double)G.n, acc_round(a)), (double)G.k);
+}
+
+// ------------------------------------------------------------------ host --
+
+struct MultiPlan {
+  std::vector<bc_graph> handles;
+  std::vector<int64_t> k;
+  std::vector<uint64_t> seed, qid;
+  int ncta = 0, nitems = 0, G = 0;
+  int32_t nmax = 0;
+  int64_t total_n = 0;
+  DevBuf d_graphs, d_items, d_gio, d_gitems, d_estoff, d_next, partials, scratch, est;
+  cudaGraphExec_t exec = nullptr;
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    nitems = 0;
+    for (DevBuf *b : {&d_graphs, &d_items, &d_gio, &d_gitems, &d_estoff, &d_next, &partials, &scratch, &est})
+      b->release();
+  }
+};
+
+static std::map<bc_ctx *, MultiPlan> g_plans;  // one cached plan per context
+static std::mutex g_plans_mu;
+
+void forget_multi_plan(bc_ctx *ctx) {
+  std::lock_guard<std::mutex> lk(g_plans_mu);
+  auto it = g_plans.find(ctx);
+  if (it == g_plans.end()) return;
+  it->second.release();
+  g_plans.erase(it);
+}
+
+bool multi_plan_uses_graph(bc_ctx *ctx, bc_graph g) {
+  std::lock_guard<std::mutex> lk(g_plans_mu);
+  auto it = g_plans.find(ctx);
+  if (it == g_plans.end()) return false;
+  for (bc_graph h : it->second.handles)
+    if (h == g) return true;
+  return false;
+}
+
+static int multi_ctas() {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_multi, MT, 0) != cudaSuccess || per < 1) {
+    cudaGetLastError();
+    per = 1;
+  }
+  return std::max(1, sms) * per;
+}
+
+static void enqueue_multi(bc_ctx *ctx, MultiPlan &P) {
+  cudaStream_t st = ctx->stream;
+  cudaMemsetAsync(P.d_next.p, 0, 16, st);
+  k_multi<<<P.ncta, MT, 0, st>>>(P.d_graphs.as<MGraph>(), P.d_items.as<MItem>(), P.nitems, P.d_next.as<unsigned>(),
+                                 P.scratch.as<unsigned char>(), mscratch_stride(P.nmax), P.nmax, P.partials.as<Acc>(),
+                                 ctx->ws.err.as<unsigned>());
+  k_multi_reduce<<<dim3((unsigned)((P.nmax + 255) / 256), (unsigned)P.G), 256, 0, st>>>(
+      P.d_graphs.as<MGraph>(), P.d_gio.as<int32_t>(), P.d_gitems.as<int32_t>(), P.d_items.as<MItem>(),
+      P.partials.as<Acc>(), P.d_estoff.as<int64_t>(), P.est.as<double>());
+}
+
+// Items: each graph's draws are cut into runs of about equal cost (cost of a
+// source ~ n + nnz), at least 4 runs per CTA overall; runs are queued largest
+// first so the persistent CTAs finish close together.
+static void build_plan(bc_ctx *ctx, MultiPlan &P, const std::vector<const Graph *> &gs) {
+  const int G = (int)gs.size();
+  P.G = G;
+  P.ncta = multi_ctas();
+  double total = 0.0;
+  P.nmax = 1;
+  P.total_n = 0;
+  for (int g = 0; g < G; ++g) {
+    total += (double)P.k[g] * (double)(gs[g]->n + gs[g]->nnz);
+    P.nmax = std::max(P.nmax, gs[g]->n);
+    P.total_n += gs[g]->n;
+  }
+  const double target = std::max(1.0, total / (4.0 * P.ncta));
+  std::vector<MItem> items;
+  std::vector<double> cost;
+  for (int g = 0; g < G; ++g) {
+    const double c = (double)(gs[g]->n + gs[g]->nnz);
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(P.k[g], (int64_t)(target / c)));
+    for (int64_t i0 = 0; i0 < P.k[g]; i0 += chunk) {
+      MItem it{};
+      it.g = g;
+      it.i0 = i0;
+      it.i1 = std::min(P.k[g], i0 + chunk);
+      items.push_back(it);
+      cost.push_back(c * (double)(it.i1 - it.i0));
+    }
+  }
+  std::vector<int> order(items.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<MItem> sorted(items.size());
+  int64_t part = 0;
+  for (size_t i = 0; i < order.size(); ++i) {
+    sorted[i] = items[order[i]];
+    sorted[i].part = part;
+    part += gs[sorted[i].g]->n;
+  }
+  P.nitems = (int)sorted.size();
+  std::vector<int32_t> gio(G + 1, 0), gitems(sorted.size());
+  for (const MItem &it : sorted) gio[it.g + 1]++;
+  for (int g = 0; g < G; ++g) gio[g + 1] += gio[g];
+  {
+    std::vector<int32_t> fill(gio.begin(), gio.end() - 1);
+    for (size_t i = 0; i < sorted.size(); ++i) gitems[fill[sorted[i].g]++] = (int32_t)i;
+  }
+  std::vector<MGraph> mg(G);
+  std::vector<int64_t> estoff(G);
+  int64_t off = 0;
+  for (int g = 0; g < G; ++g) {
+    mg[g].rp = gs[g]->rp;
+    mg[g].col = gs[g]->col;
+    mg[g].n = gs[g]->n;
+    mg[g].pad = 0;
+    mg[g].k = P.k[g];
+    mg[g].seed = P.seed[g];
+    mg[g].qid = P.qid[g];
+    estoff[g] = off;
+    off += gs[g]->n;
+  }
+  cudaStream_t st = ctx->stream;
+  P.d_graphs.ensure(sizeof(MGraph) * G);
+  P.d_items.ensure(sizeof(MItem) * sorted.size());
+  P.d_gio.ensure(4 * (G + 1));
+  P.d_gitems.ensure(4 * std::max<size_t>(1, sorted.size()));
+  P.d_estoff.ensure(8 * G);
+  P.d_next.ensure(16);
+  P.partials.ensure(sizeof(Acc) * (size_t)std::max<int64_t>(1, part));
+  P.scratch.ensure(mscratch_stride(P.nmax) * (size_t)P.ncta);
+  P.est.ensure(8 * (size_t)P.total_n);
+  BCG_CUDA(cudaMemcpyAsync(P.d_graphs.p, mg.data(), sizeof(MGraph) * G, cudaMemcpyHostToDevice, st));
+  BCG_CUDA(cudaMemcpyAsync(P.d_items.p, sorted.data(), sizeof(MItem) * sorted.size(), cudaMemcpyHostToDevice, st));
+  BCG_CUDA(cudaMemcpyAsync(P.d_gio.p, gio.data(), 4 * (G + 1), cudaMemcpyHostToDevice, st));
+  BCG_CUDA(cudaMemcpyAsync(P.d_gitems.p, gitems.data(), 4 * sorted.size(), cudaMemcpyHostToDevice, st));
+  BCG_CUDA(cudaMemcpyAsync(P.d_estoff.p, estoff.data(), 8 * G, cudaMemcpyHostToDevice, st));
+  BCG_CUDA(cudaStreamSynchronize(st));
+  // the per-call launch sequence, captured once and replayed (a stream that
+  // cannot be captured, such as the legacy default stream, launches directly)
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  enqueue_multi(ctx, P);
+  const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+  if (ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cuda_check(ce, "cudaStreamEndCapture");
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&P.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  cuda_check(ie, "cudaGraphInstantiate");
+}
+
+void do_uniform_multi(bc_ctx *ctx, const std::vector<bc_graph> &handles, const std::vector<const Graph *> &gs,
+                      const int64_t *k, const uint64_t *seed, const uint64_t *qid, double *est_out) {
+  std::lock_guard<std::mutex> lk(g_plans_mu);
+  MultiPlan &P = g_plans[ctx];
+  const int G = (int)gs.size();
+  const bool same = P.nitems > 0 && P.handles == handles && std::equal(k, k + G, P.k.begin()) &&
+                    std::equal(seed, seed + G, P.seed.begin()) && std::equal(qid, qid + G, P.qid.begin());
+  if (!same) {
+    P.release();
+    P.handles = handles;
+    P.k.assign(k, k + G);
+    P.seed.assign(seed, seed + G);
+    P.qid.assign(qid, qid + G);
+    build_plan(ctx, P, gs);
+  }
+  if (P.exec)
+    BCG_CUDA(cudaGraphLaunch(P.exec, ctx->stream));
+  else
+    enqueue_multi(ctx, P);
+  BCG_CUDA(cudaGetLastError());
+  ctx->launches += 2;
+  for (int g = 0; g < G; ++g) ctx->samples += k[g];
+  ctx->batches += P.nitems;
+  BCG_CUDA(cudaMemcpyAsync(est_out, P.est.p, 8 * (size_t)P.total_n, cudaMemcpyDeviceToHost, ctx->stream));
+  BCG_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+}  // namespace bcg
