@@ -235,6 +235,49 @@ def measure_pairs(pkg, torch, local, stream, cap=2048, T=256):
             "note": "includes one BFS per target (256) before the pair draws"}
 
 
+def measure_uneven(pkg, torch, local, stream, k=1024, reps=2):
+    """Uniform 1024-draw estimates for 256 graphs of uneven size and depth
+    (log-uniform 2k-200k vertices; ER, R-MAT ef 8 or 2D grid, from base seed 6)
+    in one bc_uniform_sources_multi call: deep graphs on the persistent kernel,
+    shallow ones beside it on the batched engine. Compared with one
+    bc_uniform_sources call per graph on every 4th graph (the same graphs
+    through both paths)."""
+    import graphgen as gg
+    S = gg.uneven_set()
+    G = len(S)
+    seeds = [6000 + i for i in range(G)]
+    qids = list(range(G))
+    ctx = pkg.Context(local, batch_width=64, stream=stream.cuda_stream)
+    hs = [ctx.load_graph(g.row_ptr, g.col) for _, g in S]
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, r
+
+    ctx.uniform_sources_multi(hs, [k] * G, seeds, qids)  # warm-up: hub distances, plan, captured graph
+    best = min(timed(lambda: ctx.uniform_sources_multi(hs, [k] * G, seeds, qids))[0] for _ in range(reps))
+    sub = list(range(0, G, 4))
+    hsub = [hs[i] for i in sub]
+    ssub = [seeds[i] for i in sub]
+    qsub = [qids[i] for i in sub]
+    ctx.uniform_sources_multi(hsub, [k] * len(sub), ssub, qsub)
+    t_multi, out_m = timed(lambda: ctx.uniform_sources_multi(hsub, [k] * len(sub), ssub, qsub))
+    t_per, out_p = timed(lambda: [ctx.uniform_sources(h, k, s_, q) for h, s_, q in zip(hsub, ssub, qsub)])
+    same = all(np.array_equal(a, b) for a, b in zip(out_m, out_p))
+    fam = {f: sum(1 for x, _ in S if x == f) for f in ("er", "rmat", "grid")}
+    ctx.close()
+    return {"workload": f"{G} graphs (ER {fam['er']}, R-MAT {fam['rmat']}, grid {fam['grid']}), "
+                        f"{sum(g.n for _, g in S)} vertices, {k} draws each",
+            "samples_per_s": G * k / best, "seconds": best,
+            "per_graph_subset": {"graphs": len(sub), "one_call_s": t_multi, "per_graph_calls_s": t_per,
+                                 "speedup": t_per / t_multi, "identical_estimates": bool(same)}}
+
+
 def measure_serving(pkg, g, h_ctx, rng_seed=7, nq=48, cap=1024):
     """Continuous batching on the resident R-MAT s20 graph: a mix of Bader
     queries (75 %) and pair queries (25 %), 1-64 uniform targets each, c in
@@ -290,7 +333,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the pair-sampling (BA 2M) and serving-latency measurements")
+                    help="skip the pair-sampling (BA 2M), serving-latency and uneven multi-graph measurements")
     ap.add_argument("--cap", type=int, default=0,
                     help="override the Bader cap (default n/20); for short profiling runs only")
     ap.add_argument("--uniform-k", type=int, default=K_UNIFORM,
@@ -427,6 +470,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_extra:
         out["serving"] = measure_serving(pkg, g, (ctx, h))
         out["pairs"] = measure_pairs(pkg, torch, local, stream)
+        out["uneven"] = measure_uneven(pkg, torch, local, stream)
 
     if not args.no_e2e:
         e2e_steps = max(1, min(2, args.steps))

@@ -12,6 +12,7 @@ Workload recipes (sizes, seeds) used by the benchmark and the tests live in
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 
@@ -124,17 +125,18 @@ def from_edges(n: int, eu, ev, name: str = "graph") -> Graph:
     return Graph(row_ptr, col, name)
 
 
-def erdos_renyi(n: int, avg_degree: float, seed: int) -> Graph:
+def erdos_renyi(n: int, avg_degree: float, seed: int, pairwise=None) -> Graph:
     """G(n, p) with p = avg_degree/(n-1).
 
-    For n <= 32768 every pair i<j is an exact Bernoulli(p) trial. Above that the
-    pair count is too large to enumerate and the G(n, M) form is used instead:
-    M = round(p*n(n-1)/2) uniform endpoint pairs, then self loops and repeats
-    are dropped.
+    With pairwise (default: n <= 32768) every pair i<j is an exact Bernoulli(p)
+    trial. Otherwise the G(n, M) form is used: M = round(p*n(n-1)/2) uniform
+    endpoint pairs, then self loops and repeats are dropped.
     """
     lib = _load()
     p = avg_degree / (n - 1)
-    if n <= 32768:
+    if pairwise is None:
+        pairwise = n <= 32768
+    if pairwise:
         cap = int(p * n * (n - 1) / 2 * 1.5) + 1024
         eu = np.empty(cap, np.int32)
         ev = np.empty(cap, np.int32)
@@ -181,6 +183,30 @@ def grid(side: int) -> Graph:
     ev = np.empty(M, np.int32)
     m = lib.gg_grid(side, _p(eu), _p(ev))
     return from_edges(side * side, eu[:m], ev[:m], name=f"grid_{side}")
+
+
+def uneven_set(count: int = 256, base_seed: int = 6, n_lo: int = 2000, n_hi: int = 200000):
+    """The uneven multi-graph workload: `count` graphs with sizes log-uniform in
+    [n_lo, n_hi], each an Erdos-Renyi graph (G(n, M) form, average degree
+    uniform in 4..16), an R-MAT graph (2^round(log2 n) vertices, edge factor 8,
+    a=0.57 b=0.19 c=0.19) or a 2D grid of side floor(sqrt(n)), the family and
+    every parameter drawn from the generator's hash of (base_seed, stream, i).
+    Returns a list of (family, Graph)."""
+    out = []
+    lo, hi = math.log(n_lo), math.log(n_hi)
+    for i in range(count):
+        u = (rand64(base_seed, 1, i) >> 11) / float(1 << 53)
+        n = int(round(math.exp(lo + u * (hi - lo))))
+        fam = rand64(base_seed, 2, i) % 3
+        seed = rand64(base_seed, 3, i) & 0x7FFFFFFF
+        if fam == 0:
+            deg = 4 + rand64(base_seed, 4, i) % 13
+            out.append(("er", erdos_renyi(n, float(deg), seed, pairwise=False)))
+        elif fam == 1:
+            out.append(("rmat", rmat(max(1, int(round(math.log2(n)))), 8, 0.57, 0.19, 0.19, seed)))
+        else:
+            out.append(("grid", grid(max(1, int(math.isqrt(n))))))
+    return out
 
 
 def uniform_targets(n: int, T: int, seed: int) -> np.ndarray:

@@ -286,11 +286,13 @@ __global__ void k_validate(int32_t n, const int32_t *__restrict__ rp, const int3
 
 // Key of a vertex for grouping sampled sources: its distance from the graph's
 // highest-degree vertex (capped at 254), 255 when unreachable from it.
-__global__ void k_make_key(int32_t n, const int32_t *__restrict__ dist, uint8_t *__restrict__ key) {
+__global__ void k_make_key(int32_t n, const int32_t *__restrict__ dist, uint8_t *__restrict__ key,
+                           int *__restrict__ maxd) {
   const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v < n) {
     const int32_t d = dist[v];
     key[v] = d < 0 ? 255 : (uint8_t)(d > 254 ? 254 : d);
+    if (d > 0) atomicMax(maxd, d);
   }
 }
 
@@ -422,6 +424,7 @@ static void copy_scan_out(bc_ctx *ctx, int32_t T, const ScanState &st, double sc
 // vertices ordered by key; computed on first use with one BFS from the hub.
 struct KeyMeta {
   DevBuf key, order;
+  int32_t ecc = 0;  // largest finite distance from the hub
 };
 static std::map<const int32_t *, KeyMeta> g_keys;
 static std::mutex g_keys_mu;
@@ -446,16 +449,20 @@ static KeyMeta &key_meta(bc_ctx *ctx, const Graph &g, bool need_order) {
     BCG_CUDA(cudaMemcpyAsync(ws.sources.p, &hub, 4, cudaMemcpyHostToDevice, ctx->stream));
     const int64_t s0 = ctx->samples, b0 = ctx->batches;
     DevBuf dist;
-    dist.ensure(n * 4);
+    dist.ensure(n * 4 + 4);  // distances, then the largest one
     try {
       plain_distances(ctx, g, ws.sources.as<int32_t>(), dist.as<int32_t>());  // any depth
       ctx->samples = s0;
       ctx->batches = b0;
       {
         LaunchScope ls(ctx, F_MISC);
-        k_make_key<<<(g.n + 255) / 256, 256, 0, ctx->stream>>>(g.n, dist.as<int32_t>(), km.key.as<uint8_t>());
+        int *d_maxd = reinterpret_cast<int *>(dist.as<int32_t>() + n);
+        BCG_CUDA(cudaMemsetAsync(d_maxd, 0, 4, ctx->stream));
+        k_make_key<<<(g.n + 255) / 256, 256, 0, ctx->stream>>>(g.n, dist.as<int32_t>(), km.key.as<uint8_t>(), d_maxd);
+        BCG_CUDA(cudaMemcpyAsync(ws.pinned, d_maxd, 4, cudaMemcpyDeviceToHost, ctx->stream));
       }
       sync(ctx);
+      km.ecc = *static_cast<int32_t *>(ws.pinned);
     } catch (...) {
       dist.release();
       throw;
@@ -539,6 +546,12 @@ static void do_exact_or_uniform(bc_ctx *ctx, const Graph &g, bool exact, int64_t
   }
   check_err_bits(ctx);
   BCG_CUDA(cudaMemcpy(out, ws.misc2.p, n * 8, cudaMemcpyDeviceToHost));
+}
+
+int graph_depth_hint(bc_ctx *ctx, const Graph &g) { return key_meta(ctx, g, false).ecc; }
+
+void uniform_one(bc_ctx *ctx, const Graph &g, int64_t k, uint64_t seed, uint64_t qid, double *out) {
+  do_exact_or_uniform(ctx, g, false, k, seed, qid, out);
 }
 
 // Bader's loop over windows of draws: each window's draws run grouped by source
@@ -787,6 +800,8 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
     if (const char *sl = std::getenv("BCG_SEGMENT")) ctx->seg_len = std::atoi(sl);
     if (const char *bv = std::getenv("BCG_BWD_VARIANT")) ctx->bwd_variant = std::atoi(bv);
     if (const char *fv = std::getenv("BCG_FWD_VARIANT")) ctx->fwd_variant = std::atoi(fv);
+    if (const char *dl = std::getenv("BCG_DEEP_LEVELS")) ctx->deep_levels = std::atoi(dl);
+    if (const char *mc = std::getenv("BCG_MULTI_CAP")) ctx->multi_cap = std::atoi(mc);
     BCG_CUDA(cudaMallocHost(&ctx->ws.pinned, 4096));
     ctx->ws.enable.ensure(64);   // [0] lane enable mask, [1] pair continuation word
     ctx->ws.sources.ensure(64 * 4);
@@ -831,6 +846,7 @@ void bc_destroy(bc_ctx *ctx) {
     if (ws.pinned) cudaFreeHost(ws.pinned);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
   }
   delete ctx;
 }

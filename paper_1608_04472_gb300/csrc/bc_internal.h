@@ -130,6 +130,7 @@ struct bc_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t stream2 = nullptr;  // second stream (persistent multi-graph work), made on first use
   int32_t batch_width = 0;
   std::recursive_mutex mu;
   std::string err = "no error";
@@ -152,6 +153,9 @@ struct bc_ctx {
   int32_t bwd_variant = 1;
   // forward kernel form: 0 = fused scan and sigma gather, 1 = two-phase packed
   int32_t fwd_variant = 0;
+  // multi-graph split: hub eccentricity above which a graph goes to the
+  // persistent kernel, and its CTAs per SM while the batched engine runs beside
+  int32_t deep_levels = 32, multi_cap = 4;
 };
 
 namespace bcg {
@@ -223,6 +227,10 @@ inline bool batch_width_is_plain(bc_ctx *ctx) { return ctx->batch_width == 1; }
 void do_uniform_multi(bc_ctx *ctx, const std::vector<bc_graph> &handles, const std::vector<const Graph *> &gs,
                       const int64_t *k, const uint64_t *seed, const uint64_t *qid, double *est_out);
 void forget_multi_plan(bc_ctx *ctx);
+// (bc_capi.cu) the largest finite distance from the graph's hub (cached), and
+// one graph's uniform estimate on the batched/plain engine
+int graph_depth_hint(bc_ctx *ctx, const Graph &g);
+void uniform_one(bc_ctx *ctx, const Graph &g, int64_t k, uint64_t seed, uint64_t qid, double *out);
 bool multi_plan_uses_graph(bc_ctx *ctx, bc_graph g);
 
 // query server lifetime (bc_serve.cu)

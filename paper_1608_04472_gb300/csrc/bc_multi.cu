@@ -13,6 +13,11 @@
 // exact partial sums per vertex and rounds once; the two launches are replayed
 // from a captured CUDA graph.
 //
+// bc_uniform_sources_multi splits the graphs by depth (the hub's eccentricity):
+// deep ones go to this persistent kernel on a second stream, sized to leave
+// room on every SM, while shallow ones run concurrently on the 64-lane batched
+// engine, which amortises its traversal over 64 sources and wins there.
+//
 // Arithmetic per source is the library's: exact uint64 counts and exact
 // successor sums (order-free); a source whose counts exceed 2^64-1 has its
 // counts re-pulled and its dependencies computed in the extended form
@@ -290,6 +295,7 @@ __global__ void k_multi_reduce(const MGraph *__restrict__ graphs, const int32_t 
 
 struct MultiPlan {
   std::vector<bc_graph> handles;
+  int cap_per_sm = 0;
   std::vector<int64_t> k;
   std::vector<uint64_t> seed, qid;
   int ncta = 0, nitems = 0, G = 0;
@@ -326,7 +332,9 @@ bool multi_plan_uses_graph(bc_ctx *ctx, bc_graph g) {
   return false;
 }
 
-static int multi_ctas() {
+// Resident CTAs: every slot the SMs have, or at most `cap_per_sm` per SM when
+// other kernels run beside it.
+static int multi_ctas(int cap_per_sm) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -334,6 +342,7 @@ static int multi_ctas() {
     cudaGetLastError();
     per = 1;
   }
+  if (cap_per_sm > 0) per = std::min(per, cap_per_sm);
   return std::max(1, sms) * per;
 }
 
@@ -354,7 +363,7 @@ static void enqueue_multi(bc_ctx *ctx, MultiPlan &P) {
 static void build_plan(bc_ctx *ctx, MultiPlan &P, const std::vector<const Graph *> &gs) {
   const int G = (int)gs.size();
   P.G = G;
-  P.ncta = multi_ctas();
+  P.ncta = multi_ctas(P.cap_per_sm);
   double total = 0.0;
   P.nmax = 1;
   P.total_n = 0;
@@ -446,29 +455,88 @@ static void build_plan(bc_ctx *ctx, MultiPlan &P, const std::vector<const Graph 
 
 void do_uniform_multi(bc_ctx *ctx, const std::vector<bc_graph> &handles, const std::vector<const Graph *> &gs,
                       const int64_t *k, const uint64_t *seed, const uint64_t *qid, double *est_out) {
+  const int G = (int)gs.size();
+  std::vector<int64_t> off(G + 1, 0);
+  for (int g = 0; g < G; ++g) off[g + 1] = off[g] + gs[g]->n;
+  std::vector<int> deep, shallow;
+  for (int g = 0; g < G; ++g) (graph_depth_hint(ctx, *gs[g]) > ctx->deep_levels ? deep : shallow).push_back(g);
   std::lock_guard<std::mutex> lk(g_plans_mu);
   MultiPlan &P = g_plans[ctx];
-  const int G = (int)gs.size();
-  const bool same = P.nitems > 0 && P.handles == handles && std::equal(k, k + G, P.k.begin()) &&
-                    std::equal(seed, seed + G, P.seed.begin()) && std::equal(qid, qid + G, P.qid.begin());
-  if (!same) {
-    P.release();
-    P.handles = handles;
-    P.k.assign(k, k + G);
-    P.seed.assign(seed, seed + G);
-    P.qid.assign(qid, qid + G);
-    build_plan(ctx, P, gs);
+  cudaEvent_t done = nullptr;
+  if (!deep.empty()) {
+    std::vector<bc_graph> dh;
+    std::vector<const Graph *> dg;
+    std::vector<int64_t> dk;
+    std::vector<uint64_t> ds, dq;
+    for (int g : deep) {
+      dh.push_back(handles[g]);
+      dg.push_back(gs[g]);
+      dk.push_back(k[g]);
+      ds.push_back(seed[g]);
+      dq.push_back(qid[g]);
+    }
+    const int cap = shallow.empty() ? 0 : ctx->multi_cap;
+    const bool same = P.nitems > 0 && P.handles == dh && P.k == dk && P.seed == ds && P.qid == dq &&
+                      P.cap_per_sm == cap;
+    if (!ctx->stream2) BCG_CUDA(cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking));
+    cudaStream_t main = ctx->stream;
+    if (!same) {
+      P.release();
+      P.handles = dh;
+      P.k = dk;
+      P.seed = ds;
+      P.qid = dq;
+      P.cap_per_sm = cap;
+      ctx->stream = ctx->stream2;  // the plan's sequence is captured on the second stream
+      try {
+        build_plan(ctx, P, dg);
+      } catch (...) {
+        ctx->stream = main;
+        throw;
+      }
+      ctx->stream = main;
+    }
+    // the second stream starts after everything already queued on the main one
+    cudaEvent_t ready = nullptr;
+    BCG_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    BCG_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    BCG_CUDA(cudaEventRecord(ready, main));
+    BCG_CUDA(cudaStreamWaitEvent(ctx->stream2, ready, 0));
+    cudaEventDestroy(ready);
+    if (P.exec) {
+      BCG_CUDA(cudaGraphLaunch(P.exec, ctx->stream2));
+    } else {
+      ctx->stream = ctx->stream2;
+      enqueue_multi(ctx, P);
+      ctx->stream = main;
+    }
+    BCG_CUDA(cudaGetLastError());
+    BCG_CUDA(cudaEventRecord(done, ctx->stream2));
+    ctx->launches += 2;
+    ctx->batches += P.nitems;
+    for (int g : deep) ctx->samples += k[g];
   }
-  if (P.exec)
-    BCG_CUDA(cudaGraphLaunch(P.exec, ctx->stream));
-  else
-    enqueue_multi(ctx, P);
-  BCG_CUDA(cudaGetLastError());
-  ctx->launches += 2;
-  for (int g = 0; g < G; ++g) ctx->samples += k[g];
-  ctx->batches += P.nitems;
-  BCG_CUDA(cudaMemcpyAsync(est_out, P.est.p, 8 * (size_t)P.total_n, cudaMemcpyDeviceToHost, ctx->stream));
-  BCG_CUDA(cudaStreamSynchronize(ctx->stream));
+  try {
+    for (int g : shallow) uniform_one(ctx, *gs[g], k[g], seed[g], qid[g], est_out + off[g]);
+  } catch (...) {
+    if (done) {
+      cudaEventSynchronize(done);
+      cudaEventDestroy(done);
+    }
+    throw;
+  }
+  if (done) {
+    BCG_CUDA(cudaStreamWaitEvent(ctx->stream, done, 0));
+    cudaEventDestroy(done);
+    int64_t poff = 0;
+    for (size_t i = 0; i < deep.size(); ++i) {
+      const int g = deep[i];
+      BCG_CUDA(cudaMemcpyAsync(est_out + off[g], P.est.as<double>() + poff, 8 * (size_t)gs[g]->n,
+                               cudaMemcpyDeviceToHost, ctx->stream));
+      poff += gs[g]->n;
+    }
+    BCG_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
 }
 
 }  // namespace bcg

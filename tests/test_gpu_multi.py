@@ -66,3 +66,31 @@ def test_multi_rejects_bad_arguments():
         h2 = ctx.load_graph(g.row_ptr, g.col)
         out = ctx.uniform_sources_multi([h2], [4], [1], [1])
         assert np.array_equal(out[0], oracle.uniform_sources(g, 4, 1, 1))
+
+
+def test_uneven_set_full_size_sampled():
+    """The full uneven workload (256 graphs, 1024 draws each) in one call; the
+    two smallest graphs of each family and one deeper grid are checked against
+    the oracle."""
+    import paper_1608_04472_gb300 as pkg
+
+    S = gg.uneven_set()
+    G = len(S)
+    seeds = [6000 + i for i in range(G)]
+    qids = list(range(G))
+    with pkg.Context(0, batch_width=64) as ctx:
+        hs = [ctx.load_graph(g.row_ptr, g.col) for _, g in S]
+        out = ctx.uniform_sources_multi(hs, [1024] * G, seeds, qids)
+    checked = 0
+    for fam in ["er", "rmat", "grid"]:
+        order = sorted((i for i, (f, _) in enumerate(S) if f == fam), key=lambda i: S[i][1].n)
+        idx = order[:2]
+        if fam == "grid":  # and one deeper grid (side ~90, ~180 levels)
+            idx.append(next(i for i in order if S[i][1].n > 8000))
+        for i in idx:
+            ref = oracle.uniform_sources(S[i][1], 1024, seeds[i], qids[i])
+            assert np.array_equal(out[i], ref), (fam, i, np.sum(out[i] != ref))
+            checked += 1
+    assert checked == 7
+    for i, (_, g) in enumerate(S):
+        assert out[i].shape == (g.n,) and np.all(np.isfinite(out[i])) and np.all(out[i] >= 0)
