@@ -235,7 +235,7 @@ def measure_pairs(pkg, torch, local, stream, cap=2048, T=256):
             "note": "includes one BFS per target (256) before the pair draws"}
 
 
-def measure_uneven(pkg, torch, local, stream, k=1024, reps=2):
+def measure_uneven(pkg, torch, local, stream, k=1024, reps=2, count=256, n_hi=200000):
     """Uniform 1024-draw estimates for 256 graphs of uneven size and depth
     (log-uniform 2k-200k vertices; ER, R-MAT ef 8 or 2D grid, from base seed 6)
     in one bc_uniform_sources_multi call: deep graphs on the persistent kernel,
@@ -243,7 +243,7 @@ def measure_uneven(pkg, torch, local, stream, k=1024, reps=2):
     bc_uniform_sources call per graph on every 4th graph (the same graphs
     through both paths)."""
     import graphgen as gg
-    S = gg.uneven_set()
+    S = gg.uneven_set(count=count, n_hi=n_hi)
     G = len(S)
     seeds = [6000 + i for i in range(G)]
     qids = list(range(G))
@@ -270,10 +270,15 @@ def measure_uneven(pkg, torch, local, stream, k=1024, reps=2):
     t_per, out_p = timed(lambda: [ctx.uniform_sources(h, k, s_, q) for h, s_, q in zip(hsub, ssub, qsub)])
     same = all(np.array_equal(a, b) for a, b in zip(out_m, out_p))
     fam = {f: sum(1 for x, _ in S if x == f) for f in ("er", "rmat", "grid")}
+    # algorithmic bytes per sample, lane-major: per directed edge and pass
+    # (discovery, count pull, dependency pull) a 4 B column and a 4 B distance;
+    # per vertex an 8 B count, an 8 B coefficient and an 8 B partial sum
+    alg = sum(k * (3 * 8 * g.nnz + 24 * g.n) for _, g in S)
     ctx.close()
     return {"workload": f"{G} graphs (ER {fam['er']}, R-MAT {fam['rmat']}, grid {fam['grid']}), "
                         f"{sum(g.n for _, g in S)} vertices, {k} draws each",
             "samples_per_s": G * k / best, "seconds": best,
+            "algorithmic_gb_per_s": alg / best / 1e9,
             "per_graph_subset": {"graphs": len(sub), "one_call_s": t_multi, "per_graph_calls_s": t_per,
                                  "speedup": t_per / t_multi, "identical_estimates": bool(same)}}
 
@@ -338,9 +343,21 @@ def main():
                     help="override the Bader cap (default n/20); for short profiling runs only")
     ap.add_argument("--uniform-k", type=int, default=K_UNIFORM,
                     help="override the uniform sample count; for short profiling runs only")
+    ap.add_argument("--uneven-only", action="store_true",
+                    help="run only the uneven multi-graph measurement and print its JSON object")
+    ap.add_argument("--uneven-count", type=int, default=256, help="graphs in the uneven workload")
+    ap.add_argument("--uneven-nmax", type=int, default=200000, help="largest graph size in the uneven workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.uneven_only:
+        import torch
+        import paper_1608_04472_gb300 as pkg
+        torch.cuda.set_device(0)
+        r = measure_uneven(pkg, torch, 0, torch.cuda.current_stream(), count=args.uneven_count,
+                           n_hi=args.uneven_nmax)
+        print(json.dumps(r))
+        return 0
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
