@@ -67,6 +67,7 @@ def _load():
         "orc_source_dependencies_xf": (ctypes.c_int, [_i32, _i32p, _i32p, _i32, _f64p, _i32p,
                                                       _f64p, _i64p]),
         "orc_xf_add_pair": (None, [_f64, _i64, _f64, _i64, _f64p, _i64p]),
+        "orc_pair_value_of": (_f64, [_i32, _i32p, _i32p, _i32, _i32, _i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -223,6 +224,13 @@ def pair_value(v: int, s: int, t: int, dist_v, sigma_v, d_st: int, sigma_st: int
     dv = np.ascontiguousarray(dist_v, dtype=np.int32)
     sv = np.ascontiguousarray(sigma_v, dtype=np.uint64)
     return float(_load().orc_pair_value(v, s, t, _p(dv, _i32p), _p(sv, _u64p), d_st, sigma_st))
+
+
+def pair_value_of(g, v: int, s: int, t: int) -> float:
+    """sigma_st(v)/sigma_st for one ordered pair, each count in the form the
+    estimator uses (exact uint64, or extended when it overflows)."""
+    n, rp, col = _csr(g)
+    return float(_load().orc_pair_value_of(n, _p(rp, _i32p), _p(col, _i32p), v, s, t))
 
 
 def pair_sequence(g, v: int, seed: int, qid: int, i0: int, count: int):

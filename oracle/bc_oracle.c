@@ -33,6 +33,8 @@
  *   R11 sigma is exact uint64 while every count of the sample fits. A sample
  *       in which some count exceeds 2^64-1 is recomputed in the extended
  *       form (R17) and the call reports that it happened (return value 1).
+ *       For pairs: a target's counts are extended when its BFS overflows; a
+ *       pair's sigma_st when a count at distance <= d(s,t) from s overflows.
  *   R17 extended form: sigma and coef are doubles with an unbounded exponent
  *       (value = m * 2^e, m in [1,2)); every operation rounds once to 53 bits
  *       as IEEE round-to-nearest-even would with no exponent limit. Path
@@ -207,9 +209,24 @@ double orc_exact_sum(const double *x, int64_t count) {
  * order[0..*nreached) lists reached vertices by non-decreasing distance.
  * Returns ORC_SIGMA_OVERFLOW if some sigma does not fit in 64 bits.
  */
+static int orc_bfs_depth(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
+                         int32_t *dist, uint64_t *sigma, int32_t *order, int32_t *nreached,
+                         int32_t *ovf_depth);
+
 int orc_bfs(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
             int32_t *dist, uint64_t *sigma, int32_t *order, int32_t *nreached) {
+  int32_t depth;
+  return orc_bfs_depth(n, row_ptr, col, s, dist, sigma, order, nreached, &depth);
+}
+
+/* orc_bfs that also reports the smallest distance of a vertex whose count
+ * exceeded 2^64-1 (*ovf_depth, -1 when none): levels are processed in order,
+ * so the first overflow detected is at the smallest such distance. */
+static int orc_bfs_depth(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
+                         int32_t *dist, uint64_t *sigma, int32_t *order, int32_t *nreached,
+                         int32_t *ovf_depth) {
   int overflow = 0;
+  *ovf_depth = -1;
   for (int32_t v = 0; v < n; ++v) { dist[v] = -1; sigma[v] = 0; }
   int32_t head = 0, tail = 0;
   dist[s] = 0;
@@ -223,7 +240,10 @@ int orc_bfs(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
       if (dist[w] == dist[v] + 1) { /* v is in P_s(w) */
         uint64_t before = sigma[w];
         sigma[w] = before + sigma[v];
-        if (sigma[w] < before) overflow = 1;
+        if (sigma[w] < before) {
+          if (!overflow) *ovf_depth = dist[w];
+          overflow = 1;
+        }
       }
     }
   }
@@ -348,6 +368,19 @@ static double orc_xf_mul_to_double(orc_xf a, orc_xf b) {
 
 /* RN(x / b) for a double x > 0 and b > 0. */
 static orc_xf orc_xf_div(double x, orc_xf b) { return orc_xf_make(x / b.m, -b.e); }
+
+/* RN(a * b), RN(a / b) in the extended form, and the value as a double
+ * (rounded once, by orc_scale2). */
+static orc_xf orc_xf_mul(orc_xf a, orc_xf b) {
+  if (a.m == 0.0 || b.m == 0.0) return orc_xf_make(0.0, 0);
+  return orc_xf_make(a.m * b.m, a.e + b.e);
+}
+static orc_xf orc_xf_div_xf(orc_xf a, orc_xf b) {
+  if (a.m == 0.0) return orc_xf_make(0.0, 0);
+  return orc_xf_make(a.m / b.m, a.e - b.e);
+}
+static double orc_xf_to_double(orc_xf a) { return a.m == 0.0 ? 0.0 : orc_scale2(a.m, a.e); }
+static orc_xf orc_xf_of_u64(uint64_t x) { return orc_xf_make((double)x, 0); }
 
 /* Test hook: (m1 2^e1) + (m2 2^e2) in the extended form. */
 void orc_xf_add_pair(double m1, int64_t e1, double m2, int64_t e2, double *m, int64_t *e) {
@@ -544,6 +577,43 @@ double orc_pair_value(int32_t v, int32_t s, int32_t t, const int32_t *dist_v,
 }
 
 /*
+ * The pair dependency when a count it uses exceeded 2^64-1 (R11, R17): the
+ * target's counts xsig_v (NULL: exact uint64 sig_v) and sigma_st (xst, NULL:
+ * exact sig_st) in the extended form, value RN(RN(sigma_sv * sigma_vt) /
+ * sigma_st). With neither extended this is orc_pair_value, and the two agree
+ * wherever the double range is not left.
+ */
+static double orc_pair_y(int32_t v, int32_t s, int32_t t, const int32_t *dist_v, const uint64_t *sig_v,
+                         const orc_xf *xsig_v, int32_t d_st, uint64_t sig_st, const orc_xf *xst) {
+  if (!xsig_v && !xst) return orc_pair_value(v, s, t, dist_v, sig_v, d_st, sig_st);
+  if (v == s || v == t || d_st < 0) return 0.0;
+  orc_xf c = xst ? *xst : orc_xf_of_u64(sig_st);
+  if (c.m == 0.0) return 0.0;
+  if (dist_v[s] < 0 || dist_v[t] < 0 || dist_v[s] + dist_v[t] != d_st) return 0.0;
+  orc_xf a = xsig_v ? xsig_v[s] : orc_xf_of_u64(sig_v[s]);
+  orc_xf b = xsig_v ? xsig_v[t] : orc_xf_of_u64(sig_v[t]);
+  return orc_xf_to_double(orc_xf_div_xf(orc_xf_mul(a, b), c));
+}
+
+/* BFS from s for a pair (s, t): d(s,t) in *d_st, sigma_st exact in *sig_st, and
+ * in the extended form (*xst, return 1) when a count at distance <= d(s,t)
+ * exceeded 2^64-1. xsig/dist2 are n-long scratch. */
+static int orc_pair_bfs(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s, int32_t t,
+                        int32_t *dist, uint64_t *sigma, int32_t *order, int32_t *dist2, orc_xf *xsig,
+                        int32_t *d_st, uint64_t *sig_st, orc_xf *xst) {
+  int32_t nr, od;
+  int rc = orc_bfs_depth(n, row_ptr, col, s, dist, sigma, order, &nr, &od);
+  *d_st = dist[t];
+  *sig_st = sigma[t];
+  if (rc == ORC_SIGMA_OVERFLOW && dist[t] >= 0 && od <= dist[t]) {
+    orc_bfs_xf(n, row_ptr, col, s, dist2, xsig, order, &nr);
+    *xst = xsig[t];
+    return 1;
+  }
+  return 0;
+}
+
+/*
  * Algorithm 1 for each target v: S <- 0, k <- 0; while S <= c*n: draw an
  * ordered pair (s,t) of different vertices, S <- S + sigma_st(v)/sigma_st,
  * k <- k+1; return n(n-1)S/k. All targets share the pair stream; a target also
@@ -565,29 +635,46 @@ int orc_adaptive_pairs(int32_t n, const int32_t *row_ptr, const int32_t *col, in
   uint64_t *sigma = (uint64_t *)malloc(sizeof(uint64_t) * nn);
   int32_t *order = (int32_t *)malloc(sizeof(int32_t) * nn);
   int32_t *done = (int32_t *)calloc((size_t)(T ? T : 1), sizeof(int32_t));
-  if (!dist_t || !sig_t || !dist || !sigma || !order || !done) {
+  int32_t *dist2 = (int32_t *)malloc(sizeof(int32_t) * nn);
+  orc_xf *xsig = (orc_xf *)malloc(sizeof(orc_xf) * nn);
+  orc_xf **xt = (orc_xf **)calloc((size_t)(T ? T : 1), sizeof(orc_xf *));
+  if (!dist_t || !sig_t || !dist || !sigma || !order || !done || !dist2 || !xsig || !xt) {
     free(dist_t); free(sig_t); free(dist); free(sigma); free(order); free(done);
+    free(dist2); free(xsig); free(xt);
     return ORC_E_NOMEM;
   }
   int status = ORC_OK;
   int32_t nr;
   for (int32_t j = 0; j < T; ++j) {
     if (orc_bfs(n, row_ptr, col, targets[j], dist_t + (size_t)j * nn, sig_t + (size_t)j * nn,
-                order, &nr) == ORC_SIGMA_OVERFLOW)
+                order, &nr) == ORC_SIGMA_OVERFLOW) {
+      /* R11: this target's counts in the extended form */
       status = ORC_SIGMA_OVERFLOW;
+      xt[j] = (orc_xf *)malloc(sizeof(orc_xf) * nn);
+      if (!xt[j]) { status = ORC_E_NOMEM; break; }
+      orc_bfs_xf(n, row_ptr, col, targets[j], dist2, xt[j], order, &nr);
+    }
+  }
+  if (status == ORC_E_NOMEM) {
+    for (int32_t j = 0; j < T; ++j) free(xt[j]);
+    free(dist_t); free(sig_t); free(dist); free(sigma); free(order); free(done);
+    free(dist2); free(xsig); free(xt);
+    return ORC_E_NOMEM;
   }
   const double cn = c * (double)n;
   for (int32_t j = 0; j < T; ++j) { S_out[j] = 0.0; k_out[j] = 0; stop_status[j] = ORC_CAPPED; }
   int32_t remaining = T;
   for (int64_t i = 0; i < cap && remaining > 0; ++i) {
-    int32_t s, t;
+    int32_t s, t, d_st;
+    uint64_t sig_st;
+    orc_xf xst;
     orc_draw_pair(seed, qid, (uint64_t)i, n, &s, &t);
-    if (orc_bfs(n, row_ptr, col, s, dist, sigma, order, &nr) == ORC_SIGMA_OVERFLOW)
-      status = ORC_SIGMA_OVERFLOW;
+    const int ext = orc_pair_bfs(n, row_ptr, col, s, t, dist, sigma, order, dist2, xsig, &d_st, &sig_st, &xst);
+    if (ext) status = ORC_SIGMA_OVERFLOW;
     for (int32_t j = 0; j < T; ++j) {
       if (done[j]) continue;
-      double y = orc_pair_value(targets[j], s, t, dist_t + (size_t)j * nn,
-                                sig_t + (size_t)j * nn, dist[t], sigma[t]);
+      double y = orc_pair_y(targets[j], s, t, dist_t + (size_t)j * nn, sig_t + (size_t)j * nn, xt[j],
+                            d_st, sig_st, ext ? &xst : NULL);
       S_out[j] = S_out[j] + y;
       k_out[j] = i + 1;
       if (S_out[j] * threshold_scale > cn) {
@@ -597,8 +684,38 @@ int orc_adaptive_pairs(int32_t n, const int32_t *row_ptr, const int32_t *col, in
   }
   const double nn1 = (double)n * (double)(n - 1);
   for (int32_t j = 0; j < T; ++j) est[j] = (nn1 * S_out[j]) / (double)k_out[j];
+  for (int32_t j = 0; j < T; ++j) free(xt[j]);
   free(dist_t); free(sig_t); free(dist); free(sigma); free(order); free(done);
+  free(dist2); free(xsig); free(xt);
   return status;
+}
+
+/* The pair dependency of v for one explicit ordered pair (s, t), each count
+ * in the form the estimator would use (test hook). NAN when out of memory. */
+double orc_pair_value_of(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t v, int32_t s,
+                         int32_t t) {
+  size_t nn = (size_t)n;
+  int32_t *dist_v = (int32_t *)malloc(sizeof(int32_t) * nn);
+  uint64_t *sig_v = (uint64_t *)malloc(sizeof(uint64_t) * nn);
+  int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * nn);
+  uint64_t *sigma = (uint64_t *)malloc(sizeof(uint64_t) * nn);
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *dist2 = (int32_t *)malloc(sizeof(int32_t) * nn);
+  orc_xf *xsig = (orc_xf *)malloc(sizeof(orc_xf) * nn);
+  orc_xf *xv = (orc_xf *)malloc(sizeof(orc_xf) * nn);
+  double y = NAN;
+  if (dist_v && sig_v && dist && sigma && order && dist2 && xsig && xv) {
+    int32_t nr, d_st;
+    uint64_t sig_st;
+    orc_xf xst;
+    const int vext = orc_bfs(n, row_ptr, col, v, dist_v, sig_v, order, &nr) == ORC_SIGMA_OVERFLOW;
+    if (vext) orc_bfs_xf(n, row_ptr, col, v, dist2, xv, order, &nr);
+    const int ext = orc_pair_bfs(n, row_ptr, col, s, t, dist, sigma, order, dist2, xsig, &d_st, &sig_st, &xst);
+    y = orc_pair_y(v, s, t, dist_v, sig_v, vext ? xv : NULL, d_st, sig_st, ext ? &xst : NULL);
+  }
+  free(dist_v); free(sig_v); free(dist); free(sigma); free(order);
+  free(dist2); free(xsig); free(xv);
+  return y;
 }
 
 /* Pair values y_i(v) for explicit draws i in [i0, i0+count) of (seed, qid), for
@@ -612,21 +729,30 @@ int orc_pair_sequence(int32_t n, const int32_t *row_ptr, const int32_t *col, int
   int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * nn);
   uint64_t *sigma = (uint64_t *)malloc(sizeof(uint64_t) * nn);
   int32_t *order = (int32_t *)malloc(sizeof(int32_t) * nn);
-  if (!dist_v || !sig_v || !dist || !sigma || !order) {
+  int32_t *dist2 = (int32_t *)malloc(sizeof(int32_t) * nn);
+  orc_xf *xsig = (orc_xf *)malloc(sizeof(orc_xf) * nn);
+  orc_xf *xv = (orc_xf *)malloc(sizeof(orc_xf) * nn);
+  if (!dist_v || !sig_v || !dist || !sigma || !order || !dist2 || !xsig || !xv) {
     free(dist_v); free(sig_v); free(dist); free(sigma); free(order);
+    free(dist2); free(xsig); free(xv);
     return ORC_E_NOMEM;
   }
   int32_t nr;
   int status = orc_bfs(n, row_ptr, col, v, dist_v, sig_v, order, &nr);
+  const int vext = status == ORC_SIGMA_OVERFLOW;
+  if (vext) orc_bfs_xf(n, row_ptr, col, v, dist2, xv, order, &nr);
   for (int64_t q = 0; q < count; ++q) {
-    int32_t s, t;
+    int32_t s, t, d_st;
+    uint64_t sig_st;
+    orc_xf xst;
     orc_draw_pair(seed, qid, (uint64_t)(i0 + q), n, &s, &t);
-    if (orc_bfs(n, row_ptr, col, s, dist, sigma, order, &nr) == ORC_SIGMA_OVERFLOW)
-      status = ORC_SIGMA_OVERFLOW;
-    y[q] = orc_pair_value(v, s, t, dist_v, sig_v, dist[t], sigma[t]);
+    const int ext = orc_pair_bfs(n, row_ptr, col, s, t, dist, sigma, order, dist2, xsig, &d_st, &sig_st, &xst);
+    if (ext) status = ORC_SIGMA_OVERFLOW;
+    y[q] = orc_pair_y(v, s, t, dist_v, sig_v, vext ? xv : NULL, d_st, sig_st, ext ? &xst : NULL);
     if (s_out) s_out[q] = s;
     if (t_out) t_out[q] = t;
   }
   free(dist_v); free(sig_v); free(dist); free(sigma); free(order);
+  free(dist2); free(xsig); free(xv);
   return status;
 }

@@ -197,3 +197,46 @@ def test_exact_bc_on_overflowing_grid_invariant():
     # symmetry of the grid: BC is invariant under the 8 symmetries of the square
     B = bc.reshape(side, side)
     assert np.allclose(B, B.T, rtol=1e-11) and np.allclose(B, B[::-1, :], rtol=1e-11)
+
+
+def _grid_pair_exact(side, v, s, t):
+    """sigma_sv sigma_vt / sigma_st on a grid from binomials (exact rational)."""
+    (vi, vj), (si, sj), (ti, tj) = divmod(v, side), divmod(s, side), divmod(t, side)
+    dst = abs(ti - si) + abs(tj - sj)
+    dsv = abs(vi - si) + abs(vj - sj)
+    dvt = abs(ti - vi) + abs(tj - vj)
+    if v in (s, t) or dsv + dvt != dst:
+        return Fraction(0)
+    c = lambda a, b: math.comb(a + b, a)
+    return Fraction(c(abs(vi - si), abs(vj - sj)) * c(abs(ti - vi), abs(tj - vj)), c(abs(ti - si), abs(tj - sj)))
+
+
+@pytest.mark.parametrize("side", [40, 60])
+def test_pair_values_on_overflowing_grid_against_binomials(side):
+    # corner-to-corner counts C(2(side-1), side-1) exceed 2^64: the pair BFS and
+    # (for central targets) the target BFS use the extended form
+    g = gg.grid(side)
+    rng = random.Random(side)
+    s, t = 0, g.n - 1
+    cases = [(rng.randrange(g.n), s, t) for _ in range(40)]
+    cases += [((side // 2) * side + side // 2, s, t), (side + 1, s, t), (g.n - 2, s, t)]
+    cases += [(rng.randrange(g.n), rng.randrange(g.n), rng.randrange(g.n)) for _ in range(40)]
+    for v, a, b in cases:
+        if a == b:
+            continue
+        exact = _grid_pair_exact(side, v, a, b)
+        got = oracle.pair_value_of(g, v, a, b)
+        if exact == 0:
+            assert got == 0.0, (v, a, b)
+        else:
+            assert abs(Fraction(got) - exact) <= exact * Fraction(4 * 2 * side * U), (v, a, b, got, float(exact))
+
+
+def test_pair_values_match_uint64_formula_where_counts_fit():
+    # a 12x12 grid never overflows: the extended path is not taken and the value
+    # is the plain double formula on exact counts
+    g = gg.grid(12)
+    for v, s, t in [(13, 0, 143), (50, 0, 143), (5, 3, 140), (77, 60, 80)]:
+        exact = _grid_pair_exact(12, v, s, t)
+        got = oracle.pair_value_of(g, v, s, t)
+        assert abs(Fraction(got) - exact) <= exact * Fraction(2 * U)
