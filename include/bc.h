@@ -39,8 +39,11 @@
  *     over the predecessors and coefficients over the successors in the CSR
  *     order of the vertex; delta = RN(sigma * sum) is an ordinary double. The
  *     choice is made per sample, so it does not depend on batching either.
- *     The pair estimator (bc_adaptive_pairs, BC_QUERY_PAIRS) has no extended
- *     form: a pair or target count beyond 2^64-1 fails with BC_E_SIGMA_OVERFLOW.
+ *     For pair sampling a target's counts are extended when its BFS
+ *     overflows, and a pair's sigma_st when a count at distance <= d(s,t)
+ *     from s overflows; the pair value is then RN(RN(sigma_sv * sigma_vt) /
+ *     sigma_st) with unbounded exponents (the double formula wherever the
+ *     double range holds).
  */
 #ifndef BC_GB300_H
 #define BC_GB300_H

@@ -1200,7 +1200,8 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
       read_u64x2(ctx, cont_word, ws.enable.as<uint64_t>() + 3, cont, ovf);
     else
       cont = read_u64(ctx, cont_word);
-    const bool all_ovf = watch && ovf != 0ull && (ovf & lanes_of(count)) == lanes_of(count);
+    // stop once every lane still going has overflowed (finished lanes are complete)
+    const bool all_ovf = watch && ovf != 0ull && (cont & ~ovf) == 0ull;
     if (!cont || all_ovf) {
       // largest sigma and overflowed lanes, adjacent words
       uint64_t *h = static_cast<uint64_t *>(ws.pinned);

@@ -14,12 +14,12 @@
 #include <vector>
 
 #include "bc_internal.h"
+#include "bc_xf.cuh"
 
 namespace bcg {
 
 void forget_heavy_meta(const int32_t *rp);
 void forget_key_meta(const int32_t *rp);
-void plain_pair(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dest);
 
 const char *kFamilyName[F_NFAM] = {"draw", "init",      "fwd",       "bwd",     "scan",   "pair",
                                    "misc", "plain_fwd", "plain_bwd", "ext_fwd", "ext_bwd"};
@@ -213,11 +213,15 @@ __global__ void k_finalize_vertices(int32_t n, const Acc *__restrict__ acc, doub
 
 // y = sigma_sv*sigma_vt/sigma_st if d(s,v)+d(v,t) = d(s,t) and v not in {s,t}
 // (Algorithm 1 with the pair-dependency of Eq. 2), else 0.
+// texp/tx (may be null): exponents [n][tstride] and flags [T] of targets whose
+// counts are in the extended form (tsig then holds mantissa bits); pexp and
+// pxmask: the same for pair lanes.
 __global__ void k_pair_values(int T, int count, const int32_t *__restrict__ targets,
                               const int32_t *__restrict__ ps, const int32_t *__restrict__ pt,
                               const int32_t *__restrict__ pd, const uint64_t *__restrict__ psig,
                               const int32_t *__restrict__ tdist, const uint64_t *__restrict__ tsig, int tstride,
-                              double *__restrict__ vals) {
+                              const int32_t *__restrict__ texp, const int32_t *__restrict__ tx,
+                              const int32_t *__restrict__ pexp, uint64_t pxmask, double *__restrict__ vals) {
   const int i = threadIdx.x;           // pair lane
   const int j = blockIdx.x;            // target
   if (j >= T || i >= 64) return;
@@ -227,11 +231,17 @@ __global__ void k_pair_values(int T, int count, const int32_t *__restrict__ targ
     const int32_t dst = pd[i];
     const uint64_t sst = psig[i];
     if (v != s && v != t && sst != 0ull && dst >= 0) {
-      const int32_t ds = tdist[(size_t)s * tstride + j], dt = tdist[(size_t)t * tstride + j];
+      const size_t is = (size_t)s * tstride + j, it = (size_t)t * tstride + j;
+      const int32_t ds = tdist[is], dt = tdist[it];
       if (ds >= 0 && dt >= 0 && ds + dt == dst) {
-        const double a = sigma_to_double(tsig[(size_t)s * tstride + j]);
-        const double b = sigma_to_double(tsig[(size_t)t * tstride + j]);
-        y = __ddiv_rn(__dmul_rn(a, b), sigma_to_double(sst));
+        const bool vx = tx && tx[j], px = (pxmask >> i) & 1ull;
+        if (vx || px) {
+          y = pair_y(vx, tsig[is], vx ? texp[is] : 0, tsig[it], vx ? texp[it] : 0, px, sst, px ? pexp[i] : 0);
+        } else {
+          const double a = sigma_to_double(tsig[is]);
+          const double b = sigma_to_double(tsig[it]);
+          y = __ddiv_rn(__dmul_rn(a, b), sigma_to_double(sst));
+        }
       }
     }
   }
@@ -602,6 +612,43 @@ static void do_adaptive_sources(bc_ctx *ctx, const Graph &g, const int32_t *targ
   copy_scan_out(ctx, T, ss, (double)g.n, est, k, S, status);
 }
 
+// Per-target BFS into [n][Tp] layouts (d(v_j, .) and sigma_{v_j .}). A target
+// whose counts exceed 2^64-1 is recomputed in the extended form: its tsig
+// entries then hold mantissa bits, texp (allocated on first need, [n][Tp])
+// the exponents, and tx[j] = 1.
+void target_bfs(bc_ctx *ctx, const Graph &g, const int32_t *d_targets, int T, int Tp, int32_t *tdist,
+                uint64_t *tsig, DevBuf &texp, std::vector<int32_t> &tx) {
+  Workspace &ws = ctx->ws;
+  const size_t n = (size_t)g.n;
+  tx.assign((size_t)Tp, 0);
+  for (int j0 = 0; j0 < T; j0 += 64) {
+    const int count = std::min(64, T - j0);
+    BCG_CUDA(cudaMemcpyAsync(ws.sources.p, d_targets + j0, (size_t)count * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    batch_ensure(ctx, g);
+    const int maxl = batch_forward(ctx, g, count, false, OVF_EXTEND);
+    batch_extract(ctx, g, count, maxl, tdist + j0, tsig + j0, Tp, 1);
+    const uint64_t ovf = ws.last_ovf & lanes_of(count);
+    if (ovf) {
+      if (!texp.p) texp.ensure(n * (size_t)Tp * 4);
+      ext_forward(ctx, g, ws.sources.as<int32_t>(), ovf);
+      ext_extract(ctx, g, ovf, tdist + j0, reinterpret_cast<double *>(tsig + j0), texp.as<int32_t>() + j0, Tp, 1);
+      for (int t = 0; t < count; ++t)
+        if ((ovf >> t) & 1ull) tx[(size_t)j0 + t] = 1;
+    }
+  }
+}
+
+// One batch of pair lanes (ws.sources -> ws.targets); returns the lanes whose
+// sigma_st is in the extended form (ws.pair_exp holds their exponents).
+uint64_t pair_batch(bc_ctx *ctx, const Graph &g, int count) {
+  Workspace &ws = ctx->ws;
+  if (batch_width(ctx) == 1) return plain_pair(ctx, g, ws.sources.as<int32_t>(), ws.targets.as<int32_t>()) ? 1ull : 0ull;
+  batch_forward(ctx, g, count, true, OVF_EXTEND);
+  const uint64_t ovf = ws.last_ovf & lanes_of(count);
+  if (ovf) ext_pair_lanes(ctx, g, ws.sources.as<int32_t>(), ws.targets.as<int32_t>(), ovf);
+  return ovf;
+}
+
 static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *targets, int32_t T, double c,
                               int64_t cap, uint64_t seed, uint64_t qid, double scale, double *est, int64_t *k,
                               double *S, int32_t *status) {
@@ -610,18 +657,19 @@ static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *target
   cudaStream_t st = ctx->stream;
   const int Tp = std::max(T, 1);
   // Per-target BFS (distance and sigma from every target), layout [n][Tp].
-  DevBuf tdist, tsig;
+  DevBuf tdist, tsig, texp, dtx;
   tdist.ensure(n * Tp * 4);
   tsig.ensure(n * Tp * 8);
   ws.misc.ensure((size_t)Tp * 4 + 64);
   int32_t *d_targets = dev_upload(ctx, ws.misc, targets, (size_t)T);
   try {
-    for (int j0 = 0; j0 < T; j0 += 64) {
-      const int count = std::min(64, T - j0);
-      BCG_CUDA(cudaMemcpyAsync(ws.sources.p, d_targets + j0, (size_t)count * 4, cudaMemcpyDeviceToDevice, st));
-      batch_ensure(ctx, g);
-      const int maxl = batch_forward(ctx, g, count, false);
-      batch_extract(ctx, g, count, maxl, tdist.as<int32_t>() + j0, tsig.as<uint64_t>() + j0, Tp, 1);
+    std::vector<int32_t> tx;
+    target_bfs(ctx, g, d_targets, T, Tp, tdist.as<int32_t>(), tsig.as<uint64_t>(), texp, tx);
+    const int32_t *d_tx = nullptr;
+    if (texp.p) {
+      dtx.ensure((size_t)Tp * 4);
+      BCG_CUDA(cudaMemcpyAsync(dtx.p, tx.data(), (size_t)Tp * 4, cudaMemcpyHostToDevice, st));
+      d_tx = dtx.as<int32_t>();
     }
     ws.tdelta.ensure((size_t)Tp * 64 * 8);
     ScanState ss = make_scan(ctx, T);
@@ -635,16 +683,13 @@ static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *target
         k_draw_pairs<<<1, 64, 0, st>>>(seed, qid, (uint64_t)i0, count, g.n, ws.sources.as<int32_t>(),
                                        ws.targets.as<int32_t>());
       }
-      if (width == 1) {
-        plain_pair(ctx, g, ws.sources.as<int32_t>(), ws.targets.as<int32_t>());
-      } else {
-        batch_forward(ctx, g, count, true);
-      }
+      const uint64_t px = pair_batch(ctx, g, count);
       if (T > 0) {
         LaunchScope ls(ctx, F_PAIR);
         k_pair_values<<<T, 64, 0, st>>>(T, count, d_targets, ws.sources.as<int32_t>(), ws.targets.as<int32_t>(),
                                         ws.pair_d.as<int32_t>(), ws.pair_sig.as<uint64_t>(), tdist.as<int32_t>(),
-                                        tsig.as<uint64_t>(), Tp, ws.tdelta.as<double>());
+                                        tsig.as<uint64_t>(), Tp, texp.as<int32_t>(), d_tx,
+                                        ws.pair_exp.as<int32_t>(), px, ws.tdelta.as<double>());
       }
       {
         LaunchScope ls(ctx, F_SCAN);
@@ -658,11 +703,15 @@ static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *target
     cudaStreamSynchronize(st);
     tdist.release();
     tsig.release();
+    texp.release();
+    dtx.release();
     throw;
   }
   sync(ctx);
   tdist.release();
   tsig.release();
+  texp.release();
+  dtx.release();
 }
 
 // Per-source outputs. Sources whose counts exceed 2^64-1 are computed in the
@@ -808,6 +857,7 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
     ctx->ws.targets.ensure(64 * 4);
     ctx->ws.pair_d.ensure(64 * 4);
     ctx->ws.pair_sig.ensure(64 * 8);
+    ctx->ws.pair_exp.ensure(64 * 4);
     ctx->ws.err.ensure(16);
     BCG_CUDA(cudaMemset(ctx->ws.err.p, 0, 16));
     ctx->ws.cnt.ensure(16);
@@ -838,7 +888,7 @@ void bc_destroy(bc_ctx *ctx) {
     ctx->graphs.clear();
     Workspace &ws = ctx->ws;
     for (DevBuf *b : {&ws.lm, &ws.visited, &ws.sigma, &ws.active, &ws.wq, &ws.enable, &ws.sources, &ws.targets, &ws.pair_d,
-                      &ws.pair_sig, &ws.err, &ws.cnt, &ws.acc, &ws.tslot, &ws.tdelta, &ws.scan, &ws.misc, &ws.misc2,
+                      &ws.pair_sig, &ws.pair_exp, &ws.err, &ws.cnt, &ws.acc, &ws.tslot, &ws.tdelta, &ws.scan, &ws.misc, &ws.misc2,
                       &ws.delta_lm, &ws.coefx, &ws.p_dist, &ws.p_sigma, &ws.p_coef, &ws.p_queue, &ws.p_ctr,
                       &ws.x_dist, &ws.x_m, &ws.x_e, &ws.x_vis, &ws.x_nm, &ws.x_list, &ws.x_lmask, &ws.x_ctr,
                       &ws.x_off})

@@ -191,21 +191,37 @@ k_x_back(int d, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
   if (er) atomicOr(err, er);
 }
 
-// Per-lane distances and counts of the lanes in `mask` into [t][v] rows
-// (row stride n): dist, sigma mantissa and exponent.
+// Per-lane distances and counts of the lanes in `mask`: element (t, v) goes to
+// t * lane_stride + v * row_stride of dist, sigma mantissa and exponent.
 __global__ void k_x_extract(int32_t n, uint64_t mask, const int32_t *__restrict__ dist, const double *__restrict__ xm,
                             const int32_t *__restrict__ xe, int32_t *__restrict__ dist_out,
-                            double *__restrict__ sm_out, int32_t *__restrict__ se_out) {
+                            double *__restrict__ sm_out, int32_t *__restrict__ se_out, int64_t row_stride,
+                            int64_t lane_stride) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long long)n * 64) return;
   const int t = (int)(i / n);
   const int32_t v = (int32_t)(i % n);
   if (!((mask >> t) & 1ull)) return;
   const size_t src = (size_t)v * 64 + t;
+  const int64_t o = (int64_t)t * lane_stride + (int64_t)v * row_stride;
   const int32_t dv = dist[src];
-  if (dist_out) dist_out[i] = dv;
-  if (sm_out) sm_out[i] = dv >= 0 ? xm[src] : 0.0;
-  if (se_out) se_out[i] = dv >= 0 ? xe[src] : 0;
+  if (dist_out) dist_out[o] = dv;
+  if (sm_out) sm_out[o] = dv >= 0 ? xm[src] : 0.0;
+  if (se_out) se_out[o] = dv >= 0 ? xe[src] : 0;
+}
+
+// Pair lanes in the extended form: d(s,t) and sigma_st (mantissa bits,
+// exponent) of lane t's destination dest[t].
+__global__ void k_x_pair(uint64_t mask, const int32_t *__restrict__ dest, const int32_t *__restrict__ dist,
+                         const double *__restrict__ xm, const int32_t *__restrict__ xe, int32_t *__restrict__ pair_d,
+                         uint64_t *__restrict__ pair_sig, int32_t *__restrict__ pair_exp) {
+  const int t = threadIdx.x;
+  if (t >= 64 || !((mask >> t) & 1ull)) return;
+  const size_t src = (size_t)dest[t] * 64 + t;
+  const int32_t d = dist[src];
+  pair_d[t] = d;
+  pair_sig[t] = d >= 0 ? (uint64_t)__double_as_longlong(xm[src]) : 0ull;
+  pair_exp[t] = d >= 0 ? xe[src] : 0;
 }
 
 // Rows of lanes whose counts do not fit 64 bits: UINT64_MAX at reached vertices.
@@ -314,13 +330,23 @@ void ext_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink) {
   }
 }
 
-void ext_extract(bc_ctx *ctx, const Graph &g, uint64_t mask, int32_t *dist_out, double *sm_out, int32_t *se_out) {
+void ext_extract(bc_ctx *ctx, const Graph &g, uint64_t mask, int32_t *dist_out, double *sm_out, int32_t *se_out,
+                 int64_t row_stride, int64_t lane_stride) {
+  if (lane_stride < 0) lane_stride = g.n;
   const long long tot = (long long)g.n * 64;
   LaunchScope ls(ctx, F_MISC);
-  k_x_extract<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(g.n, mask, ctx->ws.x_dist.as<int32_t>(),
-                                                                      ctx->ws.x_m.as<double>(),
-                                                                      ctx->ws.x_e.as<int32_t>(), dist_out, sm_out,
-                                                                      se_out);
+  k_x_extract<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(
+      g.n, mask, ctx->ws.x_dist.as<int32_t>(), ctx->ws.x_m.as<double>(), ctx->ws.x_e.as<int32_t>(), dist_out, sm_out,
+      se_out, row_stride, lane_stride);
+}
+
+void ext_pair_lanes(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, const int32_t *d_dest, uint64_t mask) {
+  ext_forward(ctx, g, d_sources, mask);
+  Workspace &ws = ctx->ws;
+  LaunchScope ls(ctx, F_PAIR);
+  k_x_pair<<<1, 64, 0, ctx->stream>>>(mask, d_dest, ws.x_dist.as<int32_t>(), ws.x_m.as<double>(),
+                                      ws.x_e.as<int32_t>(), ws.pair_d.as<int32_t>(), ws.pair_sig.as<uint64_t>(),
+                                      ws.pair_exp.as<int32_t>());
 }
 
 void ext_mark_sigma(bc_ctx *ctx, const Graph &g, uint64_t mask, const int32_t *dist, uint64_t *sig) {

@@ -100,7 +100,8 @@ struct Workspace {
   DevBuf sources;  // [64] i32
   DevBuf targets;  // [64] i32 pair destinations
   DevBuf pair_d;   // [64] i32 d(s,t) of pair lanes
-  DevBuf pair_sig; // [64] u64 sigma_st of pair lanes
+  DevBuf pair_sig; // [64] u64 sigma_st of pair lanes (extended lanes: mantissa bits)
+  DevBuf pair_exp; // [64] i32 exponent of extended sigma_st
   DevBuf err;      // u32 error bits
   DevBuf cnt;      // u64[2]: shortest-path DAG triples, reached (vertex, lane) pairs
   DevBuf acc;      // [n] Acc
@@ -196,8 +197,13 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
 int ext_forward(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, uint64_t mask);
 void ext_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink);
 void ext_source_batch(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, uint64_t mask, const Sink &sink);
-// After ext_forward: rows [t][v] (stride n) of dist, sigma mantissa, exponent for lanes in mask.
-void ext_extract(bc_ctx *ctx, const Graph &g, uint64_t mask, int32_t *dist_out, double *sm_out, int32_t *se_out);
+// After ext_forward: dist, sigma mantissa, exponent of the lanes in mask, element
+// (t, v) at t * lane_stride + v * row_stride (default: rows [t][v] of length n).
+void ext_extract(bc_ctx *ctx, const Graph &g, uint64_t mask, int32_t *dist_out, double *sm_out, int32_t *se_out,
+                 int64_t row_stride = 1, int64_t lane_stride = -1);
+// Pair lanes in `mask` (sources d_sources[t], destinations d_dest[t]) in the
+// extended form: ws.pair_d / ws.pair_sig (mantissa bits) / ws.pair_exp.
+void ext_pair_lanes(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, const int32_t *d_dest, uint64_t mask);
 // Rows [t][v] (stride n) of lanes in mask: sig = UINT64_MAX where dist >= 0, else 0.
 void ext_mark_sigma(bc_ctx *ctx, const Graph &g, uint64_t mask, const int32_t *dist, uint64_t *sig);
 // u64 counts to (mantissa, exponent), elementwise.
@@ -232,6 +238,13 @@ void forget_multi_plan(bc_ctx *ctx);
 int graph_depth_hint(bc_ctx *ctx, const Graph &g);
 void uniform_one(bc_ctx *ctx, const Graph &g, int64_t k, uint64_t seed, uint64_t qid, double *out);
 bool multi_plan_uses_graph(bc_ctx *ctx, bc_graph g);
+
+// ---- pair sampling helpers (bc_capi.cu), shared with the server ----
+void target_bfs(bc_ctx *ctx, const Graph &g, const int32_t *d_targets, int T, int Tp, int32_t *tdist,
+                uint64_t *tsig, DevBuf &texp, std::vector<int32_t> &tx);
+uint64_t pair_batch(bc_ctx *ctx, const Graph &g, int count);
+// Plain pair lane; true when its sigma_st is in the extended form.
+bool plain_pair(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dest);
 
 // query server lifetime (bc_serve.cu)
 void server_shutdown(bc_ctx *ctx);

@@ -305,14 +305,19 @@ void plain_distances(bc_ctx *ctx, const Graph &g, const int32_t *d_src, int32_t 
 
 // Plain pair lane: BFS from *d_src truncated at the level that reaches *d_dest;
 // leaves d(s,t) and sigma_st in ws.pair_d[0], ws.pair_sig[0].
-void plain_pair(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dest) {
+bool plain_pair(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dest) {
   std::vector<int32_t> offs;
   bool overflow = false;
   plain_forward(ctx, g, d_src, d_dest, offs, overflow);
-  if (overflow) raise_err_bits(ctx, ERR_SIGMA_OVERFLOW);
+  if (overflow) {
+    // a count at distance <= d(s,t) overflowed: sigma_st in the extended form
+    ext_pair_lanes(ctx, g, d_src, d_dest, 1ull);
+    return true;
+  }
   LaunchScope ls(ctx, F_PAIR);
   k_pplain_pair<<<1, 1, 0, ctx->stream>>>(d_dest, ctx->ws.p_dist.as<int32_t>(), ctx->ws.p_sigma.as<uint64_t>(),
                                           ctx->ws.pair_d.as<int32_t>(), ctx->ws.pair_sig.as<uint64_t>());
+  return false;
 }
 
 }  // namespace bcg

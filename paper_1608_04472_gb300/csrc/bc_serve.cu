@@ -23,11 +23,11 @@
 #include <vector>
 
 #include "bc_internal.h"
+#include "bc_xf.cuh"
 
 namespace bcg {
 
 void run_source_batch(bc_ctx *ctx, const Graph &g, int count, const Sink &sink);
-void plain_pair(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dest);
 
 namespace {
 
@@ -60,6 +60,8 @@ struct SQuery {
   size_t mem = 0;
   DevBuf dstate;      // S[T] f64 | k[T] i64 | done[T] i32 | remaining i32
   DevBuf tdist, tsig; // pairs: [n][T]
+  DevBuf dtarg, texp, dtx;  // pairs: targets on the device; extended-form exponents [n][T] and flags [T]
+  std::vector<int32_t> tx;
   DevBuf acc;         // uniform: [n] Acc
   Clock::time_point t_submit, t_admit;
   int64_t samples = 0, batches = 0;
@@ -97,6 +99,8 @@ struct ScanEntry {
 struct PairEntry {
   const int32_t *tdist;
   const uint64_t *tsig;
+  const int32_t *texp;  // null unless some target of the query is in the extended form
+  const int32_t *tx;
   int32_t v, j, T, a, c, pad;
 };
 
@@ -147,7 +151,8 @@ __global__ void k_stop_scan_multi(int E, const ScanEntry *__restrict__ ent, cons
 
 __global__ void k_pair_values_multi(int E, const PairEntry *__restrict__ ent, const int32_t *__restrict__ ps,
                                     const int32_t *__restrict__ pt, const int32_t *__restrict__ pd,
-                                    const uint64_t *__restrict__ psig, double *__restrict__ vals) {
+                                    const uint64_t *__restrict__ psig, const int32_t *__restrict__ pexp,
+                                    uint64_t pxmask, double *__restrict__ vals) {
   const int e = blockIdx.x, i = threadIdx.x;
   if (e >= E || i >= 64) return;
   const PairEntry d = ent[e];
@@ -156,11 +161,17 @@ __global__ void k_pair_values_multi(int E, const PairEntry *__restrict__ ent, co
     const int32_t v = d.v, s = ps[i], t = pt[i], dst = pd[i];
     const uint64_t sst = psig[i];
     if (v != s && v != t && sst != 0ull && dst >= 0) {
-      const int32_t ds = d.tdist[(size_t)s * d.T + d.j], dt = d.tdist[(size_t)t * d.T + d.j];
+      const size_t is = (size_t)s * d.T + d.j, it = (size_t)t * d.T + d.j;
+      const int32_t ds = d.tdist[is], dt = d.tdist[it];
       if (ds >= 0 && dt >= 0 && ds + dt == dst) {
-        const double a = sigma_to_double(d.tsig[(size_t)s * d.T + d.j]);
-        const double b = sigma_to_double(d.tsig[(size_t)t * d.T + d.j]);
-        y = __ddiv_rn(__dmul_rn(a, b), sigma_to_double(sst));
+        const bool vx = d.tx && d.tx[d.j], px = (pxmask >> i) & 1ull;
+        if (vx || px) {
+          y = pair_y(vx, d.tsig[is], vx ? d.texp[is] : 0, d.tsig[it], vx ? d.texp[it] : 0, px, sst, px ? pexp[i] : 0);
+        } else {
+          const double a = sigma_to_double(d.tsig[is]);
+          const double b = sigma_to_double(d.tsig[it]);
+          y = __ddiv_rn(__dmul_rn(a, b), sigma_to_double(sst));
+        }
       }
     }
   }
@@ -260,13 +271,12 @@ bool Server::prepare(SQuery &q) {
     const size_t n = (size_t)q.g.n;
     q.tdist.ensure(n * T * 4);
     q.tsig.ensure(n * T * 8);
-    Workspace &ws = ctx->ws;
-    for (int j0 = 0; j0 < q.T(); j0 += 64) {
-      const int count = std::min(64, q.T() - j0);
-      BCG_CUDA(cudaMemcpyAsync(ws.sources.p, q.targets.data() + j0, (size_t)count * 4, cudaMemcpyHostToDevice,
-                               ctx->stream));
-      const int maxl = batch_forward(ctx, q.g, count, false);
-      batch_extract(ctx, q.g, count, maxl, q.tdist.as<int32_t>() + j0, q.tsig.as<uint64_t>() + j0, (int64_t)T, 1);
+    q.dtarg.ensure((size_t)T * 4);
+    BCG_CUDA(cudaMemcpyAsync(q.dtarg.p, q.targets.data(), (size_t)q.T() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    target_bfs(ctx, q.g, q.dtarg.as<int32_t>(), q.T(), T, q.tdist.as<int32_t>(), q.tsig.as<uint64_t>(), q.texp, q.tx);
+    if (q.texp.p) {
+      q.dtx.ensure((size_t)T * 4);
+      BCG_CUDA(cudaMemcpyAsync(q.dtx.p, q.tx.data(), (size_t)T * 4, cudaMemcpyHostToDevice, ctx->stream));
     }
   }
   sync(ctx);
@@ -351,8 +361,9 @@ void Server::run_group(std::vector<std::shared_ptr<SQuery>> &part, std::vector<i
         se.push_back(ScanEntry{q.S(), q.K(), q.Done(), q.Rem(), j, a[b], lanes[b], 0, q.issued,
                                q.c * (double)g.n, kind == BC_QUERY_PAIRS ? q.scale : 1.0});
         if (kind == BC_QUERY_PAIRS)
-          pe.push_back(PairEntry{q.tdist.as<int32_t>(), q.tsig.as<uint64_t>(), v, j, std::max(q.T(), 1), a[b],
-                                 lanes[b], 0});
+          pe.push_back(PairEntry{q.tdist.as<int32_t>(), q.tsig.as<uint64_t>(), q.texp.as<int32_t>(),
+                                 q.texp.p ? q.dtx.as<int32_t>() : nullptr, v, j, std::max(q.T(), 1), a[b], lanes[b],
+                                 0});
       }
     }
     const int E = (int)enext.size();
@@ -389,18 +400,15 @@ void Server::run_group(std::vector<std::shared_ptr<SQuery>> &part, std::vector<i
       sink.tdelta = d_tdelta.as<double>();
       run_source_batch(ctx, g, L, sink);
     } else {
-      if (batch_width_is_plain(ctx)) {
-        // the plain pair path handles one lane; keep batches of one in that mode
-        plain_pair(ctx, g, ws.sources.as<int32_t>(), ws.targets.as<int32_t>());
-      } else {
-        batch_forward(ctx, g, L, true);
-      }
+      // (the plain pair path handles one lane; batches are of one in that mode)
+      const uint64_t px = pair_batch(ctx, g, L);
       d_pair.ensure((size_t)std::max(E, 1) * sizeof(PairEntry));
       BCG_CUDA(cudaMemcpyAsync(d_pair.p, pe.data(), (size_t)E * sizeof(PairEntry), cudaMemcpyHostToDevice, st));
       LaunchScope ls(ctx, F_PAIR);
       k_pair_values_multi<<<E, 64, 0, st>>>(E, d_pair.as<PairEntry>(), ws.sources.as<int32_t>(),
                                             ws.targets.as<int32_t>(), ws.pair_d.as<int32_t>(),
-                                            ws.pair_sig.as<uint64_t>(), d_tdelta.as<double>());
+                                            ws.pair_sig.as<uint64_t>(), ws.pair_exp.as<int32_t>(), px,
+                                            d_tdelta.as<double>());
     }
     d_scan.ensure((size_t)std::max(E, 1) * sizeof(ScanEntry));
     BCG_CUDA(cudaMemcpyAsync(d_scan.p, se.data(), (size_t)E * sizeof(ScanEntry), cudaMemcpyHostToDevice, st));
@@ -497,6 +505,9 @@ void Server::loop() {
       q->dstate.release();
       q->tdist.release();
       q->tsig.release();
+      q->dtarg.release();
+      q->texp.release();
+      q->dtx.release();
       q->acc.release();
       std::lock_guard<std::mutex> lk(mu);
       if (fcode == BC_OK) {
@@ -610,6 +621,9 @@ void server_shutdown(bc_ctx *ctx) {
     kv.second->dstate.release();
     kv.second->tdist.release();
     kv.second->tsig.release();
+    kv.second->dtarg.release();
+    kv.second->texp.release();
+    kv.second->dtx.release();
     kv.second->acc.release();
   }
   delete s;

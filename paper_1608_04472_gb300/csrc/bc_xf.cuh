@@ -66,4 +66,29 @@ __device__ __forceinline__ void xf_store(double *xm, int32_t *xe, size_t i, Xf x
   xe[i] = x.e;
 }
 
+// RN(a * b) and RN(a / b) in the extended form; the value as a double (only
+// the last power-of-two step can round).
+__device__ __forceinline__ Xf xf_mul(Xf a, Xf b) {
+  if (a.m == 0.0 || b.m == 0.0) return Xf{0.0, 0};
+  return xf_make(__dmul_rn(a.m, b.m), a.e + b.e);
+}
+__device__ __forceinline__ Xf xf_div_xf(Xf a, Xf b) {
+  if (a.m == 0.0) return Xf{0.0, 0};
+  return xf_make(__ddiv_rn(a.m, b.m), a.e - b.e);
+}
+__device__ __forceinline__ double xf_to_double(Xf a) { return xf_mul_to_double(a, Xf{1.0, 0}); }
+__device__ __forceinline__ Xf xf_of_u64(uint64_t x) { return xf_make(__ull2double_rn(x), 0); }
+
+// Pair dependency sigma_sv * sigma_vt / sigma_st (Eq. 2) from counts that are
+// exact uint64 or, when flagged, extended (mantissa bits + exponent):
+// RN(RN(a * b) / c) without an exponent limit; with no flag set this equals
+// the double formula RN(RN(a * b) / c) on the rounded counts.
+__device__ __forceinline__ double pair_y(bool vx, uint64_t a, int ae, uint64_t b, int be, bool px, uint64_t c,
+                                         int ce) {
+  const Xf A = vx ? Xf{__longlong_as_double((long long)a), ae} : xf_of_u64(a);
+  const Xf B = vx ? Xf{__longlong_as_double((long long)b), be} : xf_of_u64(b);
+  const Xf C = px ? Xf{__longlong_as_double((long long)c), ce} : xf_of_u64(c);
+  return xf_to_double(xf_div_xf(xf_mul(A, B), C));
+}
+
 }  // namespace bcg

@@ -99,13 +99,27 @@ def test_uniform_and_bader_on_grid(pkg):
         assert np.array_equal(served[key], ref_b[key]), key
 
 
-def test_pairs_on_overflowing_grid_report_overflow(pkg):
-    g = gg.grid(40)
-    with pkg.Context(0, batch_width=64) as ctx:
+@pytest.mark.parametrize("width", [1, 64])
+def test_pairs_on_overflowing_grid(pkg, width):
+    # corner targets and far pairs (distance > ~70 on a 60x60 grid) have counts
+    # beyond 2^64: targets and pair lanes are recomputed in the extended form
+    g = gg.grid(60)
+    targets = [0, g.n - 1, 30 * 60 + 30, 61, 5 * 60 + 53]
+    far = sum(1 for s, t in (oracle.draw_pair(1, 1, i, g.n) for i in range(60))
+              if abs(s // 60 - t // 60) + abs(s % 60 - t % 60) > 75)
+    assert far >= 1  # the draws include pairs whose sigma_st overflows
+    cap = 200 if width == 64 else 60
+    ref = oracle.adaptive_pairs(g, targets, 1.0, cap, 1, 1)
+    ref2 = oracle.adaptive_pairs(g, targets, 2.0, 3 * cap, 2, 5, float(g.n - 1))
+    with pkg.Context(0, batch_width=width) as ctx:
         h = ctx.load_graph(g.row_ptr, g.col)
-        with pytest.raises(pkg.BCError) as e:
-            ctx.adaptive_pairs(h, [0, g.n - 1], 1.0, 64, 1, 1)
-        assert e.value.code == -9
-        # the context stays usable
-        d, _, _ = ctx.source_dependencies(h, [5])
-        assert np.array_equal(d[0], oracle.dependencies(g, 5)[0])
+        got = ctx.adaptive_pairs(h, targets, 1.0, cap, 1, 1)
+        got2 = ctx.adaptive_pairs(h, targets, 2.0, 3 * cap, 2, 5, float(g.n - 1))
+        tk = ctx.submit(h, pkg.BC_QUERY_PAIRS, targets=targets, c=1.0, cap=cap, seed=1, qid=1)
+        assert ctx.poll(tk, -1) == pkg.BC_OK
+        served = tk.outputs()
+    for key in ["est", "k", "S", "status"]:
+        assert np.array_equal(got[key], ref[key]), key
+        assert np.array_equal(got2[key], ref2[key]), key
+        assert np.array_equal(served[key], ref[key]), key
+    assert np.sum(ref["S"] > 0) >= 2
