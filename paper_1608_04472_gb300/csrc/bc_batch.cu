@@ -47,6 +47,12 @@ __device__ __forceinline__ uint64_t warp_max64(uint64_t x) {
   return x;
 }
 
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
+  return x;
+}
+
 __device__ __forceinline__ void block_or_to(uint64_t x, uint64_t *dst) {
   __shared__ unsigned long long s_or;
   if (threadIdx.x == 0) s_or = 0ull;
@@ -136,6 +142,103 @@ __global__ void k_fwd_level1(int count, const int32_t *__restrict__ sources, con
   }
 }
 
+struct Packed {
+  int glog;  // log2 of the group width G
+  int p0;    // lane owned by this thread (-1: none)
+  int p1;    // second lane when |L| > 32 (G = 32), else -1
+  bool two;
+};
+
+// Active lane positions in increasing order: each set lane writes its position
+// at its rank in a per-warp table, then thread i reads entry i.
+__device__ __forceinline__ Packed pack_lanes(uint64_t lanes, int8_t *tab) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lo = (unsigned)lanes, hi = (unsigned)(lanes >> 32);
+  const unsigned lt = (1u << lane) - 1u;
+  const int nlo = __popc(lo), L = nlo + __popc(hi);
+  if ((lo >> lane) & 1u) tab[__popc(lo & lt)] = (int8_t)lane;
+  if ((hi >> lane) & 1u) tab[nlo + __popc(hi & lt)] = (int8_t)(lane + 32);
+  __syncwarp();
+  Packed pk;
+  pk.glog = L > 16 ? 5 : (L > 8 ? 4 : (L > 4 ? 3 : 2));
+  const int slot = lane & ((1 << pk.glog) - 1);
+  pk.p0 = slot < L ? (int)tab[slot] : -1;
+  pk.p1 = (pk.glog == 5 && lane + 32 < L) ? (int)tab[lane + 32] : -1;
+  pk.two = L > 32;
+  __syncwarp();
+  return pk;
+}
+
+
+// Predecessor counts for one 32-neighbour chunk of v, packed: the lanes of cm
+// (the OR of the chunk's masks) are spread over groups of G >= |cm| threads and
+// each group takes a different predecessor per step, so a chunk with many
+// predecessors over few lanes costs a few steps instead of one 64-slot step per
+// predecessor. The chunk's per-lane sums are then added into the owners' sums
+// (thread t owns lanes t and t + 32). Integer sums: exact, order-free.
+__device__ __forceinline__ void chunk_packed(uint64_t m, int32_t w, uint64_t cm, unsigned bal,
+                                             const uint64_t *__restrict__ sigma, int8_t *tab, int32_t *list,
+                                             uint64_t &s0, uint64_t &s1, uint64_t &ovf) {
+  const int lane = threadIdx.x & 31;
+  const Packed pk = pack_lanes(cm, tab);
+  const int NG = 32 >> pk.glog, g = lane >> pk.glog;
+  const int cnt = __popc(bal);
+  if (m != 0ull) list[__popc(bal & ((1u << lane) - 1u))] = lane;
+  __syncwarp();
+  const uint64_t b0 = pk.p0 >= 0 ? (1ull << pk.p0) : 0ull, b1 = pk.p1 >= 0 ? (1ull << pk.p1) : 0ull;
+  const int q0 = pk.p0 < 0 ? 0 : pk.p0, q1 = pk.p1 < 0 ? 0 : pk.p1;
+  uint64_t a0 = 0ull, a1 = 0ull;
+  for (int r = 0; r < cnt; r += 2 * NG) {
+    const int i0 = r + g, i1 = r + NG + g;
+    const bool h0 = i0 < cnt, h1 = i1 < cnt;
+    const int x0s = h0 ? list[i0] : 0, x1s = h1 ? list[i1] : 0;
+    const uint64_t m0 = __shfl_sync(FULL, m, x0s), m1 = __shfl_sync(FULL, m, x1s);
+    const int32_t w0 = __shfl_sync(FULL, w, x0s), w1 = __shfl_sync(FULL, w, x1s);
+    const uint64_t y0 = (h0 && (m0 & b0)) ? sigma[(size_t)w0 * 64 + q0] : 0ull;
+    const uint64_t y1 = (h1 && (m1 & b0)) ? sigma[(size_t)w1 * 64 + q0] : 0ull;
+    if (pk.two) {
+      const uint64_t z0 = (h0 && (m0 & b1)) ? sigma[(size_t)w0 * 64 + q1] : 0ull;
+      const uint64_t z1 = (h1 && (m1 & b1)) ? sigma[(size_t)w1 * 64 + q1] : 0ull;
+      uint64_t t = a1 + z0;
+      if (t < a1) ovf |= b1;
+      a1 = t + z1;
+      if (a1 < t) ovf |= b1;
+    }
+    uint64_t t = a0 + y0;
+    if (t < a0) ovf |= b0;
+    a0 = t + y1;
+    if (a0 < t) ovf |= b0;
+  }
+  __syncwarp();
+  for (int off = 1 << pk.glog; off < 32; off <<= 1) {
+    const uint64_t o = __shfl_xor_sync(FULL, a0, off);
+    const uint64_t t = a0 + o;
+    if (t < a0) ovf |= b0;
+    a0 = t;
+  }
+  // lane X of cm has rank r in the packed order: its sum is a0 of thread r
+  // (r < 32) or a1 of thread r - 32
+  const unsigned lo = (unsigned)cm, hi = (unsigned)(cm >> 32), lt = (1u << lane) - 1u;
+  const int nlo = __popc(lo);
+  const int r0 = __popc(lo & lt), r1 = nlo + __popc(hi & lt);
+  uint64_t v0 = __shfl_sync(FULL, a0, r0 & 31), v1 = __shfl_sync(FULL, a0, r1 & 31);
+  if (pk.two) {
+    const uint64_t u0 = __shfl_sync(FULL, a1, r0 & 31), u1 = __shfl_sync(FULL, a1, r1 & 31);
+    if (r0 >= 32) v0 = u0;
+    if (r1 >= 32) v1 = u1;
+  }
+  if ((lo >> lane) & 1u) {
+    const uint64_t t = s0 + v0;
+    if (t < s0) ovf |= 1ull << lane;
+    s0 = t;
+  }
+  if ((hi >> lane) & 1u) {
+    const uint64_t t = s1 + v1;
+    if (t < s1) ovf |= 1ull << (lane + 32);
+    s1 = t;
+  }
+}
+
 // --------------------------------------------------------------- forward --
 // One warp per vertex (grid-stride); heavy vertices only get lm_cur[v] = 0 here.
 __global__ void __launch_bounds__(FWD_THREADS)
@@ -144,10 +247,11 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
             uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
             const uint64_t *__restrict__ active_prev, uint64_t *__restrict__ enable,
             uint64_t *__restrict__ active_cur, unsigned *__restrict__ err,
-            unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq, int heavy_deg) {
+            unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq, int heavy_deg, int pk_maxl,
+            int pk_mincnt) {
+  __shared__ int32_t lists[FWD_THREADS / 32][32];
+  __shared__ int8_t tabs[FWD_THREADS / 32][64];
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint64_t act = *active_prev & *enable;
   uint64_t any_new = 0ull, smax = 0ull;
   unsigned long long tri = 0ull, rch = 0ull;
@@ -186,7 +290,16 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
           m = lm_prev[w] & pend;
         }
         newm |= m;
+        tri += (unsigned long long)__popcll((long long)m);
         unsigned bal = __ballot_sync(FULL, m != 0ull);
+        if (pk_maxl > 0 && __popc(bal) >= pk_mincnt) {
+          // many predecessors over few lanes: packed groups do several per step
+          const uint64_t cm = warp_or64(m);
+          if (__popcll((long long)cm) <= pk_maxl) {
+            chunk_packed(m, w, cm, bal, sigma, tabs[threadIdx.x >> 5], lists[threadIdx.x >> 5], s0, s1, ovf);
+            bal = 0u;
+          }
+        }
         while (bal) {
           uint64_t mk[UNR];
           int32_t wk[UNR];
@@ -197,7 +310,6 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
             const uint64_t *row = sigma + (size_t)wk[k] * 64;
             x0[k] = ((mk[k] >> lane) & 1ull) ? row[lane] : 0ull;
             x1[k] = ((mk[k] >> (lane + 32)) & 1ull) ? row[lane + 32] : 0ull;
-            tri += (unsigned long long)__popcll((long long)mk[k]);
           }
 #pragma unroll
           for (int k = 0; k < UNR; ++k) {
@@ -231,6 +343,7 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
   ovf = warp_or64(ovf);
   if (lane == 0 && ovf) atomicOr((unsigned long long *)(enable + 3), (unsigned long long)ovf);
   (void)err;
+  tri = warp_sum64(tri);
   if (lane == 0 && (tri | rch)) {
     atomicAdd(cnt, tri);
     atomicAdd(cnt + 1, rch);
@@ -267,6 +380,7 @@ k_fwd_heavy(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restri
         m = lm_prev[w] & pend;
       }
       newm |= m;
+      tri += (unsigned long long)__popcll((long long)m);
       unsigned bal = __ballot_sync(FULL, m != 0ull);
       while (bal) {
         uint64_t mk[UNR];
@@ -278,7 +392,6 @@ k_fwd_heavy(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restri
           const uint64_t *row = sigma + (size_t)wk[k] * 64;
           x0[k] = ((mk[k] >> lane) & 1ull) ? row[lane] : 0ull;
           x1[k] = ((mk[k] >> (lane + 32)) & 1ull) ? row[lane + 32] : 0ull;
-          tri += (unsigned long long)__popcll((long long)mk[k]);
         }
 #pragma unroll
         for (int k = 0; k < UNR; ++k) {
@@ -307,18 +420,25 @@ k_fwd_heavy(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restri
   ovf = warp_or64(ovf);
   if (lane == 0 && ovf) atomicOr((unsigned long long *)(enable + 3), (unsigned long long)ovf);
   (void)err;
+  tri = warp_sum64(tri);
   if (lane == 0 && tri) atomicAdd(cnt, tri);
 }
 
+// Also records, for the host, whether any heavy vertex has lanes at this level
+// (*hflag) and the lanes in which some heavy vertex is still unvisited (*hpend):
+// levels without heavy work then skip the heavy kernels.
 __global__ void k_fwd_heavy_fin(int nh, const int32_t *__restrict__ heavy,
                                 const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ visited,
                                 uint64_t *__restrict__ active_cur, unsigned long long *__restrict__ cnt,
-                                const uint64_t *__restrict__ sigma, uint64_t *__restrict__ enable) {
+                                const uint64_t *__restrict__ sigma, uint64_t *__restrict__ enable,
+                                unsigned *__restrict__ hflag, unsigned long long *__restrict__ hpend) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
-  uint64_t newm = 0ull;
+  const uint64_t en = *enable;
+  uint64_t newm = 0ull, pend = 0ull;
   if (h < nh) {
     const int32_t v = heavy[h];
     newm = lm_cur[v];
+    pend = ~(visited[v] | newm) & en;
     if (newm) {
       visited[v] |= newm;
       atomicAdd(cnt + 1, (unsigned long long)__popcll((long long)newm));
@@ -333,7 +453,14 @@ __global__ void k_fwd_heavy_fin(int nh, const int32_t *__restrict__ heavy,
     }
   }
   newm = warp_or64(newm);
-  if ((threadIdx.x & 31) == 0 && newm) atomicOr((unsigned long long *)active_cur, (unsigned long long)newm);
+  pend = warp_or64(pend);
+  if ((threadIdx.x & 31) == 0) {
+    if (newm) {
+      atomicOr((unsigned long long *)active_cur, (unsigned long long)newm);
+      atomicOr(hflag, 1u);
+    }
+    if (pend) atomicOr(hpend, (unsigned long long)pend);
+  }
 }
 
 // Pair lanes: lane i is finished once its destination appears at this level.
@@ -660,33 +787,6 @@ k_bwd_heavy_fin(int nh, const int32_t *__restrict__ heavy, const int32_t *__rest
 // groups of G >= |L| threads and each group takes a different listed
 // successor per step (thread (g, s) owns the s-th active lane).
 
-struct Packed {
-  int glog;  // log2 of the group width G
-  int p0;    // lane owned by this thread (-1: none)
-  int p1;    // second lane when |L| > 32 (G = 32), else -1
-  bool two;
-};
-
-// Active lane positions in increasing order: each set lane writes its position
-// at its rank in a per-warp table, then thread i reads entry i.
-__device__ __forceinline__ Packed pack_lanes(uint64_t lanes, int8_t *tab) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lo = (unsigned)lanes, hi = (unsigned)(lanes >> 32);
-  const unsigned lt = (1u << lane) - 1u;
-  const int nlo = __popc(lo), L = nlo + __popc(hi);
-  if ((lo >> lane) & 1u) tab[__popc(lo & lt)] = (int8_t)lane;
-  if ((hi >> lane) & 1u) tab[nlo + __popc(hi & lt)] = (int8_t)(lane + 32);
-  __syncwarp();
-  Packed pk;
-  pk.glog = L > 16 ? 5 : (L > 8 ? 4 : (L > 4 ? 3 : 2));
-  const int slot = lane & ((1 << pk.glog) - 1);
-  pk.p0 = slot < L ? (int)tab[slot] : -1;
-  pk.p1 = (pk.glog == 5 && lane + 32 < L) ? (int)tab[lane + 32] : -1;
-  pk.two = L > 32;
-  __syncwarp();
-  return pk;
-}
-
 __device__ __forceinline__ void acc2_add_u4(Acc2 &a, const uint4 &x) { acc2_add4(a, x.x, x.y, x.z, x.w); }
 
 __device__ __forceinline__ void acc2_shfl_xor_add(Acc2 &a, int off) {
@@ -801,7 +901,7 @@ k_fwd_light_pk(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restr
                uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
                const uint64_t *__restrict__ active_prev, uint64_t *__restrict__ enable,
                uint64_t *__restrict__ active_cur, unsigned *__restrict__ err,
-               unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq, int heavy_deg) {
+               unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq, int heavy_deg, int, int) {
   __shared__ int32_t lists[FWD_THREADS / 32][32];
   __shared__ int8_t tabs[FWD_THREADS / 32][64];
   int32_t *list = lists[threadIdx.x >> 5];
@@ -1119,6 +1219,7 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
   ctx->batches += 1;
   const int blocks = grid_blocks();
   int l = 0;
+  bool heavy_done = false;
   {
     // level 1 straight from the sources' adjacency; heavy sigma rows were zeroed
     // above and only receive stores here, so the atomics-based heavy path is not needed
@@ -1143,6 +1244,7 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
     ws.last_ovf = 0ull;
     if (!cont1) {  // no vertex at distance 1 (or, for pairs, every destination found)
       ws.last_sigmax = 1ull;
+      ws.hlev.assign(3, 1);
       return pairs ? 1 : 0;
     }
     l = 1;
@@ -1166,9 +1268,10 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
                                                  ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(), act + l,
                                                  ws.enable.as<uint64_t>(), act + l + 1, ws.err.as<unsigned>(),
                                                  ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 0,
-                                                 hm.heavy_deg);
+                                                 hm.heavy_deg, ctx->pk_maxl, ctx->pk_mincnt);
     }
-    if (hm.nseg) {
+    const bool heavy_now = hm.nseg && !heavy_done;
+    if (heavy_now) {
       LaunchScope ls(ctx, F_FWD);
       k_fwd_heavy<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
           hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
@@ -1176,12 +1279,14 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
           act + l, ws.enable.as<uint64_t>(), ws.err.as<unsigned>(), ws.cnt.as<unsigned long long>(),
           ws.wq.as<unsigned>() + 8 * l + 1);
     }
-    if (hm.nseg) {
+    unsigned *hw = ws.wq.as<unsigned>() + 8 * (l + 1);  // slot 5: heavy lanes at l+1; 6-7: heavy pending lanes
+    if (heavy_now) {
       LaunchScope ls(ctx, F_FWD);
       k_fwd_heavy_fin<<<(hm.nh + 255) / 256, 256, 0, st>>>(hm.nh, hm.heavy.as<int32_t>(), lm + (size_t)(l + 1) * n,
                                                           ws.visited.as<uint64_t>(), act + l + 1,
                                                           ws.cnt.as<unsigned long long>(), ws.sigma.as<uint64_t>(),
-                                                          ws.enable.as<uint64_t>());
+                                                          ws.enable.as<uint64_t>(), hw + 5,
+                                                          reinterpret_cast<unsigned long long *>(hw + 6));
     }
     // Deep traversals also watch the overflowed lanes every level: once every
     // lane has overflowed the integer pass has nothing left to give (and its
@@ -1196,10 +1301,16 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
                                      ws.pair_sig.as<uint64_t>(), act + l + 1, ws.enable.as<uint64_t>() + 1);
       cont_word = ws.enable.as<uint64_t>() + 1;
     }
+    uint64_t hpend = 0ull;
     if (watch)
       read_u64x2(ctx, cont_word, ws.enable.as<uint64_t>() + 3, cont, ovf);
+    else if (heavy_now)
+      read_u64x2(ctx, cont_word, reinterpret_cast<const uint64_t *>(hw + 6), cont, hpend);
     else
       cont = read_u64(ctx, cont_word);
+    // no heavy vertex is unvisited in a lane that goes on: the heavy kernels
+    // have nothing left to do in this batch (the lanes going on only shrink)
+    if (heavy_now && !watch && (hpend & cont) == 0ull) heavy_done = true;
     // stop once every lane still going has overflowed (finished lanes are complete)
     const bool all_ovf = watch && ovf != 0ull && (cont & ~ovf) == 0ull;
     if (!cont || all_ovf) {
@@ -1209,12 +1320,24 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
       BCG_CUDA(cudaStreamSynchronize(st));
       ws.last_sigmax = h[0];
       ws.last_ovf = h[1];
+      // per level: did any heavy vertex get lanes there (level 1 is filled
+      // without the heavy kernels: assume yes)
+      ws.hlev.assign((size_t)l + 2, 1);
+      if (hm.nseg) {
+        std::vector<unsigned> fl((size_t)(l + 2) * 8);
+        BCG_CUDA(cudaMemcpyAsync(fl.data(), ws.wq.p, fl.size() * 4, cudaMemcpyDeviceToHost, st));
+        BCG_CUDA(cudaStreamSynchronize(st));
+        for (int k = 2; k <= l + 1; ++k) ws.hlev[k] = fl[(size_t)k * 8 + 5] != 0u;
+      }
       if (ws.last_ovf && mode == OVF_ERROR) raise_err_bits(ctx, ERR_SIGMA_OVERFLOW);
       return l;
     }
     ++l;
   }
 }
+
+// Whether a heavy vertex has lanes at level l in the last forward pass.
+static inline bool heavy_at(const Workspace &ws, int l) { return l >= (int)ws.hlev.size() || ws.hlev[l]; }
 
 void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink, uint64_t keep) {
   Workspace &ws = ctx->ws;
@@ -1234,7 +1357,7 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
                                                       ws.sigma.as<uint64_t>(), coefx, sink, ws.err.as<unsigned>(),
                                                       ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg, keep);
       }
-      if (hm.nseg) {
+      if (hm.nseg && heavy_at(ws, l)) {
         {
           LaunchScope ls(ctx, F_BWD);
           k_bwd_heavy_seg_fx<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
@@ -1262,7 +1385,7 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
             g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), sink,
             ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg, keep);
     }
-    if (hm.nseg) {
+    if (hm.nseg && heavy_at(ws, l)) {
       LaunchScope ls(ctx, F_BWD);
       auto kseg = narrow ? k_bwd_heavy_seg<NarrowAcc> : k_bwd_heavy_seg<WideAcc>;
       kseg<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(

@@ -850,6 +850,8 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
     if (const char *bv = std::getenv("BCG_BWD_VARIANT")) ctx->bwd_variant = std::atoi(bv);
     if (const char *fv = std::getenv("BCG_FWD_VARIANT")) ctx->fwd_variant = std::atoi(fv);
     if (const char *dl = std::getenv("BCG_DEEP_LEVELS")) ctx->deep_levels = std::atoi(dl);
+    if (const char *pm = std::getenv("BCG_PK_MAXL")) ctx->pk_maxl = std::atoi(pm);
+    if (const char *pc = std::getenv("BCG_PK_MINCNT")) ctx->pk_mincnt = std::atoi(pc);
     if (const char *mc = std::getenv("BCG_MULTI_CAP")) ctx->multi_cap = std::atoi(mc);
     BCG_CUDA(cudaMallocHost(&ctx->ws.pinned, 4096));
     ctx->ws.enable.ensure(64);   // [0] lane enable mask, [1] pair continuation word

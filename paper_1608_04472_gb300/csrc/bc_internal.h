@@ -114,6 +114,7 @@ struct Workspace {
   DevBuf coefx;    // [n][64] uint4: coefficients as 128-bit fixed point (unit 2^-96)
   DevBuf win;      // draw window: draws[W] | sorted sources[W] | sorted positions[W]
   uint64_t last_ovf = 0ull;  // lanes of the last batched forward whose counts exceeded 2^64-1
+  std::vector<uint8_t> hlev;  // per level of the last batched forward: a heavy vertex has lanes there
   // extended-form engine (bc_ext.cu): dist [n][64] i32, sigma/coef as
   // mantissa [n][64] f64 + exponent [n][64] i32, visited / next masks [n],
   // level entry lists with lane masks, level offsets (device and host copies)
@@ -154,6 +155,9 @@ struct bc_ctx {
   int32_t bwd_variant = 1;
   // forward kernel form: 0 = fused scan and sigma gather, 1 = two-phase packed
   int32_t fwd_variant = 0;
+  // light forward: a 32-neighbour chunk with at least pk_mincnt predecessors
+  // over at most pk_maxl lanes is summed in packed groups (0 disables)
+  int32_t pk_maxl = 16, pk_mincnt = 6;
   // multi-graph split: hub eccentricity above which a graph goes to the
   // persistent kernel, and its CTAs per SM while the batched engine runs beside
   int32_t deep_levels = 32, multi_cap = 4;
