@@ -29,8 +29,13 @@ namespace bcg {
 constexpr int HEAVY_DEFAULT = 256;   // vertices above this degree are split into segments
 constexpr int SEG_DEFAULT = 256;     // neighbours per heavy segment
 constexpr int GRAB = 16;     // vertices taken per work-queue grab
-constexpr int UNR = 4;       // neighbours gathered per unrolled step
+constexpr int UNR = 3;       // neighbours gathered per unrolled step (measured: 2-3 best, 1 and 8 slower)
 constexpr int FWD_THREADS = 256;
+// The packed backward kernels are latency-bound; five resident blocks per SM
+// (at most 51 registers a thread; a few bytes spill in the heavy finisher)
+// measured 5 % faster than the register-limited four. The forward kernels
+// measured slower that way.
+constexpr int BWD_MIN_BLOCKS = 5;
 
 __device__ __forceinline__ uint64_t warp_or64(uint64_t x) {
   const unsigned lo = __reduce_or_sync(FULL, (unsigned)x);
@@ -973,7 +978,7 @@ __device__ __forceinline__ void ring_append_fx(Ring &R, unsigned &tail, int32_t 
   tail += (unsigned)__popcll((long long)lanes);
 }
 
-__global__ void __launch_bounds__(FWD_THREADS)
+__global__ void __launch_bounds__(FWD_THREADS, BWD_MIN_BLOCKS)
 k_bwd_light_fx(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
                uint64_t *__restrict__ sigma, uint4 *__restrict__ coefx, Sink sink, unsigned *__restrict__ err,
@@ -1008,7 +1013,7 @@ k_bwd_light_fx(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restr
   if (e) atomicOr(err, e);
 }
 
-__global__ void __launch_bounds__(FWD_THREADS)
+__global__ void __launch_bounds__(FWD_THREADS, BWD_MIN_BLOCKS)
 k_bwd_heavy_seg_fx(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restrict__ seg_b,
                    const int32_t *__restrict__ seg_e, const int32_t *__restrict__ col,
                    const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
@@ -1033,7 +1038,7 @@ k_bwd_heavy_seg_fx(int nseg, const int32_t *__restrict__ seg_v, const int32_t *_
   if (e) atomicOr(err, e);
 }
 
-__global__ void __launch_bounds__(FWD_THREADS)
+__global__ void __launch_bounds__(FWD_THREADS, BWD_MIN_BLOCKS)
 k_bwd_heavy_fin_fx(int nh, const int32_t *__restrict__ heavy, const int32_t *__restrict__ hseg0,
                    const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ sigma, uint4 *__restrict__ coefx,
                    const uint4 *__restrict__ part, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq, uint64_t keep) {
