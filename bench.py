@@ -307,19 +307,23 @@ def measure_uneven(pkg, torch, local, stream, k=1024, reps=2, count=256, n_hi=20
                                  "speedup": t_per / t_multi, "identical_estimates": bool(same)}}
 
 
-def measure_serving(pkg, g, h_ctx, rng_seed=7, nq=48, cap=1024):
-    """Continuous batching on the resident R-MAT s20 graph: a mix of Bader
-    queries (75 %) and pair queries (25 %), 1-64 uniform targets each, c in
-    {2, 5, 10}, cap draws each. Saturation rate from submitting all at once, then
-    Poisson arrivals at 0.5 and 0.8 of it; latency = submit -> result written."""
+def measure_serving(pkg, g, h_ctx, rng_seed=7, nq=48, cap=1024, graphs=None, label=None):
+    """Continuous batching on resident graphs: a mix of Bader queries (75 %) and
+    pair queries (25 %), each on a graph chosen uniformly (default: the one
+    graph g), 1-64 uniform targets, c in {2, 5, 10}, cap draws each. Saturation
+    rate from submitting all at once, then Poisson arrivals at 0.5 and 0.8 of
+    it; latency = submit -> result written."""
     import graphgen as gg
     ctx, h = h_ctx
+    graphs = graphs or [(g, h)]
     rng = np.random.default_rng(rng_seed)
     specs = []
     for i in range(nq):
         T = int(rng.integers(1, 65))
-        specs.append(dict(kind=pkg.BC_QUERY_PAIRS if rng.random() < 0.25 else pkg.BC_QUERY_SOURCES,
-                          targets=gg.uniform_targets(g.n, T, 1000 + i), c=float(rng.choice([2.0, 5.0, 10.0])),
+        gi = int(rng.integers(0, len(graphs)))
+        gq, hq = graphs[gi]
+        specs.append(dict(h=hq, kind=pkg.BC_QUERY_PAIRS if rng.random() < 0.25 else pkg.BC_QUERY_SOURCES,
+                          targets=gg.uniform_targets(gq.n, T, 1000 + i), c=float(rng.choice([2.0, 5.0, 10.0])),
                           cap=cap, seed=SEED, qid=5_000_000 + i))
 
     def run(rate):
@@ -330,7 +334,8 @@ def measure_serving(pkg, g, h_ctx, rng_seed=7, nq=48, cap=1024):
                 time.sleep(float(rng.exponential(1.0 / rate)))
             kw = dict(sp)
             kw["qid"] = sp["qid"] + int(rate * 1000)
-            tks.append(ctx.submit(h, kw.pop("kind"), **kw))
+            hq = kw.pop("h")
+            tks.append(ctx.submit(hq, kw.pop("kind"), **kw))
         for tk in tks:
             ctx.poll(tk, -1)
         wall = time.perf_counter() - t0
@@ -341,7 +346,7 @@ def measure_serving(pkg, g, h_ctx, rng_seed=7, nq=48, cap=1024):
     run(0)  # warm-up (per-query state allocation paths)
     wall, lat, samples = run(0)
     lam = nq / wall
-    out = {"workload": f"R-MAT s20 resident; {nq} queries, 75% Bader / 25% pairs, 1-64 targets, "
+    out = {"workload": f"{label or 'R-MAT s20'} resident; {nq} queries, 75% Bader / 25% pairs, 1-64 targets, "
                        f"c in {{2,5,10}}, cap {cap}",
            "saturation_queries_per_s": lam, "saturation_samples_per_s": samples / wall,
            "saturation_p50_ms": float(np.percentile(lat, 50)), "saturation_p99_ms": float(np.percentile(lat, 99))}
@@ -367,6 +372,12 @@ def main():
                     help="override the Bader cap (default n/20); for short profiling runs only")
     ap.add_argument("--uniform-k", type=int, default=K_UNIFORM,
                     help="override the uniform sample count; for short profiling runs only")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="run only the serving measurement on resident R-MAT s21 and s22 (about a minute "
+                         "of graph generation first) and print its JSON object")
+    ap.add_argument("--serving-queries", type=int, default=48, help="queries in the --serving-full stream")
+    ap.add_argument("--serving-grid", type=int, default=0,
+                    help="also serve a 2D grid of this side in --serving-full (0: none)")
     ap.add_argument("--uneven-only", action="store_true",
                     help="run only the uneven multi-graph measurement and print its JSON object")
     ap.add_argument("--uneven-count", type=int, default=256, help="graphs in the uneven workload")
@@ -374,6 +385,25 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving_full:
+        import torch
+        import graphgen as gg
+        import paper_1608_04472_gb300 as pkg
+        torch.cuda.set_device(0)
+        t0 = time.perf_counter()
+        gs = [gg.rmat(21, EF, 0.57, 0.19, 0.19, 4), gg.rmat(22, EF, 0.57, 0.19, 0.19, 5)]
+        if args.serving_grid:
+            gs.append(gg.grid(args.serving_grid))
+        gen_s = time.perf_counter() - t0
+        ctx = pkg.Context(0, batch_width=64, stream=torch.cuda.current_stream().cuda_stream)
+        hs = [ctx.load_graph(x.row_ptr, x.col) for x in gs]
+        r = measure_serving(pkg, gs[0], (ctx, hs[0]), nq=args.serving_queries, graphs=list(zip(gs, hs)),
+                            label="R-MAT s21 (seed 4) + R-MAT s22 (seed 5)"
+                                  + (f" + {args.serving_grid}x{args.serving_grid} grid" if args.serving_grid else ""))
+        r["graph_generation_s"] = gen_s
+        ctx.close()
+        print(json.dumps(r))
+        return 0
     if args.uneven_only:
         import torch
         import paper_1608_04472_gb300 as pkg
