@@ -360,9 +360,14 @@ static void launch_draw_sources(bc_ctx *ctx, uint64_t seed, uint64_t qid, uint64
 
 // Lanes whose path counts exceed 2^64-1 skip the integer backward pass and are
 // recomputed in the extended form (bc_ext.cu); the others are unaffected.
+// Deep graphs (the hub's eccentricity above ctx->deep_levels, e.g. grids) go
+// lane-major: level masks and 64-lane rows cost O(levels * n) there, while each
+// lane's own BFS costs O(n + nnz).
 void run_source_batch(bc_ctx *ctx, const Graph &g, int count, const Sink &sink) {
   if (batch_width(ctx) == 1) {
     plain_source(ctx, g, ctx->ws.sources.as<int32_t>(), sink, nullptr, nullptr);
+  } else if (graph_depth_hint(ctx, g) > ctx->deep_levels) {
+    lane_sink(ctx, g, ctx->ws.sources.as<int32_t>(), count, sink);
   } else {
     const int maxl = batch_forward(ctx, g, count, false, OVF_EXTEND);
     const uint64_t all = lanes_of(count), ovf = ctx->ws.last_ovf & all;
@@ -456,12 +461,13 @@ static KeyMeta &key_meta(bc_ctx *ctx, const Graph &g, bool need_order) {
   if (!km.key.p) {
     km.key.ensure(n);
     const int32_t hub = g.hub;
-    BCG_CUDA(cudaMemcpyAsync(ws.sources.p, &hub, 4, cudaMemcpyHostToDevice, ctx->stream));
     const int64_t s0 = ctx->samples, b0 = ctx->batches;
     DevBuf dist;
-    dist.ensure(n * 4 + 4);  // distances, then the largest one
+    dist.ensure(n * 4 + 8);  // distances, the largest one, the hub (ws.sources may hold a batch)
     try {
-      plain_distances(ctx, g, ws.sources.as<int32_t>(), dist.as<int32_t>());  // any depth
+      int32_t *d_hub = dist.as<int32_t>() + n + 1;
+      BCG_CUDA(cudaMemcpyAsync(d_hub, &hub, 4, cudaMemcpyHostToDevice, ctx->stream));
+      plain_distances(ctx, g, d_hub, dist.as<int32_t>());  // any depth
       ctx->samples = s0;
       ctx->batches = b0;
       {
@@ -880,6 +886,7 @@ void bc_destroy(bc_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     forget_multi_plan(ctx);
+    forget_lane_scratch(ctx);
     resolve_events(ctx);
     for (auto &kv : ctx->graphs) {
       forget_heavy_meta(kv.second.rp);

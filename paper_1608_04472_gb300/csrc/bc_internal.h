@@ -237,6 +237,10 @@ inline bool batch_width_is_plain(bc_ctx *ctx) { return ctx->batch_width == 1; }
 void do_uniform_multi(bc_ctx *ctx, const std::vector<bc_graph> &handles, const std::vector<const Graph *> &gs,
                       const int64_t *k, const uint64_t *seed, const uint64_t *qid, double *est_out);
 void forget_multi_plan(bc_ctx *ctx);
+// One batch of sources on a deep graph, lane-major (persistent CTAs, one lane
+// at a time each, CTA barriers between levels), delivering to the sink.
+void lane_sink(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, int count, const Sink &sink);
+void forget_lane_scratch(bc_ctx *ctx);
 // (bc_capi.cu) the largest finite distance from the graph's hub (cached), and
 // one graph's uniform estimate on the batched/plain engine
 int graph_depth_hint(bc_ctx *ctx, const Graph &g);

@@ -136,9 +136,11 @@ __device__ __forceinline__ void for_level(const MScratch &S, const int32_t *__re
   }
 }
 
-// One source on the whole CTA; its dependencies are added to part[].
-__device__ void multi_source(const MGraph &G, int32_t s, const MScratch &S, Acc *__restrict__ part, unsigned &err,
-                             int *s_tail, int *s_ovf) {
+// One source on the whole CTA; every dependency delta_s(v) (v at distance >= 1)
+// is handed to deliver(v, delta) by one thread.
+template <class D>
+__device__ void multi_source(const MGraph &G, int32_t s, const MScratch &S, unsigned &err, int *s_tail, int *s_ovf,
+                             D deliver) {
   const int tid = threadIdx.x, lane = tid & 31;
   const int32_t *__restrict__ rp = G.rp;
   const int32_t *__restrict__ col = G.col;
@@ -244,11 +246,7 @@ __device__ void multi_source(const MGraph &G, int32_t s, const MScratch &S, Acc 
         delta = __dmul_rn(sigma_to_double(sg), acc_round(a));
         if (!coop || lane == 0) S.coef[v] = coef_of(delta, sg);
       }
-      if (!coop || lane == 0) {
-        Acc cur = part[v];
-        acc_add(cur, delta, err);
-        part[v] = cur;
-      }
+      if (!coop || lane == 0) deliver(v, delta);
     });
     __syncthreads();
   }
@@ -271,10 +269,57 @@ k_multi(const MGraph *__restrict__ graphs, const MItem *__restrict__ items, int 
     Acc *part = partials + item.part;
     for (int32_t v = threadIdx.x; v < G.n; v += MT) part[v] = acc_zero();
     for (int64_t i = item.i0; i < item.i1; ++i)
-      multi_source(G, draw_source(G.seed, G.qid, (uint64_t)i, G.n), S, part, e, &s_tail, &s_ovf);
+      multi_source(G, draw_source(G.seed, G.qid, (uint64_t)i, G.n), S, e, &s_tail, &s_ovf,
+                   [&](int32_t v, double delta) {
+                     Acc cur = part[v];
+                     acc_add(cur, delta, e);
+                     part[v] = cur;
+                   });
     __syncthreads();  // s_item is rewritten only after every thread has used it
   }
   if (e) atomicOr(err, e);
+}
+
+// The lanes of one batch (sources[t], t < count) of a deep graph, lane-major:
+// persistent CTAs take lanes one at a time and deliver each dependency to the
+// batch's sink as the 64-lane engine would (target entries, per-lane rows);
+// all-vertex sums go to per-CTA exact partials, added into sink.acc after.
+__global__ void __launch_bounds__(MT)
+k_lane_sink(MGraph G, const int32_t *__restrict__ sources, int count, unsigned *__restrict__ next,
+            unsigned char *__restrict__ scratch, size_t stride, int32_t nmax, Acc *__restrict__ partials, Sink sink,
+            unsigned *__restrict__ err) {
+  __shared__ int s_item, s_tail, s_ovf;
+  const MScratch S = mscratch_of(scratch + (size_t)blockIdx.x * stride, nmax);
+  Acc *part = partials ? partials + (size_t)blockIdx.x * G.n : nullptr;
+  if (part)
+    for (int32_t v = threadIdx.x; v < G.n; v += MT) part[v] = acc_zero();
+  unsigned e = 0u;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(next, 1u);
+    __syncthreads();
+    const int t = s_item;
+    if (t >= count) break;
+    multi_source(G, sources[t], S, e, &s_tail, &s_ovf, [&](int32_t v, double delta) {
+      if (sink.delta_lm) sink.delta_lm[(size_t)v * 64 + t] = delta;
+      if (sink.tslot) sink_targets(sink, v, t, delta);
+      if (part) {
+        Acc cur = part[v];
+        acc_add(cur, delta, e);
+        part[v] = cur;
+      }
+    });
+    __syncthreads();
+  }
+  if (e) atomicOr(err, e);
+}
+
+// sink.acc[v] += the CTAs' partial sums (exact).
+__global__ void k_lane_acc(int32_t n, int nparts, const Acc *__restrict__ partials, Acc *__restrict__ acc) {
+  const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  Acc a = acc[v];
+  for (int c = 0; c < nparts; ++c) acc_add_acc(a, partials[(size_t)c * n + v]);
+  acc[v] = a;
 }
 
 // est[off_g + v] = (n * RN(sum of the items' exact partial sums)) / k
@@ -451,6 +496,53 @@ static void build_plan(bc_ctx *ctx, MultiPlan &P, const std::vector<const Graph 
   const cudaError_t ie = cudaGraphInstantiate(&P.exec, graph, 0);
   cudaGraphDestroy(graph);
   cuda_check(ie, "cudaGraphInstantiate");
+}
+
+// Per-context scratch of the lane-major path (grown on demand).
+struct LaneScratch {
+  DevBuf scratch, partials, next;
+};
+static std::map<bc_ctx *, LaneScratch> g_lane;
+
+void forget_lane_scratch(bc_ctx *ctx) {
+  std::lock_guard<std::mutex> lk(g_plans_mu);
+  auto it = g_lane.find(ctx);
+  if (it == g_lane.end()) return;
+  it->second.scratch.release();
+  it->second.partials.release();
+  it->second.next.release();
+  g_lane.erase(it);
+}
+
+void lane_sink(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, int count, const Sink &sink) {
+  if (count < 1) return;
+  std::unique_lock<std::mutex> lk(g_plans_mu);
+  LaneScratch &L = g_lane[ctx];
+  lk.unlock();
+  const size_t stride = mscratch_stride(g.n);
+  const size_t per = stride + (sink.acc ? sizeof(Acc) * (size_t)g.n : 0);
+  // resident CTAs, at most one per lane, and at most ~8 GB of scratch
+  const int ncta = std::max(1, std::min({count, multi_ctas(0), (int)std::max<size_t>(1, ((size_t)8 << 30) / per)}));
+  L.scratch.ensure(stride * ncta);
+  if (sink.acc) L.partials.ensure(sizeof(Acc) * (size_t)g.n * ncta);
+  L.next.ensure(16);
+  cudaStream_t st = ctx->stream;
+  BCG_CUDA(cudaMemsetAsync(L.next.p, 0, 16, st));
+  MGraph G{};
+  G.rp = g.rp;
+  G.col = g.col;
+  G.n = g.n;
+  {
+    LaunchScope ls(ctx, F_XFWD);
+    k_lane_sink<<<ncta, MT, 0, st>>>(G, d_sources, count, L.next.as<unsigned>(), L.scratch.as<unsigned char>(), stride,
+                                     g.n, sink.acc ? L.partials.as<Acc>() : nullptr, sink, ctx->ws.err.as<unsigned>());
+  }
+  if (sink.acc) {
+    LaunchScope ls(ctx, F_XBWD);
+    k_lane_acc<<<(g.n + 255) / 256, 256, 0, st>>>(g.n, ncta, L.partials.as<Acc>(), sink.acc);
+  }
+  ctx->samples += count;
+  ctx->batches += 1;
 }
 
 void do_uniform_multi(bc_ctx *ctx, const std::vector<bc_graph> &handles, const std::vector<const Graph *> &gs,
