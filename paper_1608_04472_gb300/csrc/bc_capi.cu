@@ -627,6 +627,23 @@ void target_bfs(bc_ctx *ctx, const Graph &g, const int32_t *d_targets, int T, in
   Workspace &ws = ctx->ws;
   const size_t n = (size_t)g.n;
   tx.assign((size_t)Tp, 0);
+  if (T > 0 && graph_depth_hint(ctx, g) > ctx->deep_levels) {
+    // deep graph: one lane-major BFS per target
+    if (!texp.p) texp.ensure(n * (size_t)Tp * 4);
+    DevBuf dtx;
+    dtx.ensure((size_t)Tp * 4);
+    try {
+      lane_targets(ctx, g, d_targets, T, Tp, tdist, tsig, texp.as<int32_t>(), dtx.as<int32_t>());
+      BCG_CUDA(cudaMemcpyAsync(tx.data(), dtx.p, (size_t)T * 4, cudaMemcpyDeviceToHost, ctx->stream));
+      sync(ctx);
+    } catch (...) {
+      cudaStreamSynchronize(ctx->stream);
+      dtx.release();
+      throw;
+    }
+    dtx.release();
+    return;
+  }
   for (int j0 = 0; j0 < T; j0 += 64) {
     const int count = std::min(64, T - j0);
     BCG_CUDA(cudaMemcpyAsync(ws.sources.p, d_targets + j0, (size_t)count * 4, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -649,6 +666,7 @@ void target_bfs(bc_ctx *ctx, const Graph &g, const int32_t *d_targets, int T, in
 uint64_t pair_batch(bc_ctx *ctx, const Graph &g, int count) {
   Workspace &ws = ctx->ws;
   if (batch_width(ctx) == 1) return plain_pair(ctx, g, ws.sources.as<int32_t>(), ws.targets.as<int32_t>()) ? 1ull : 0ull;
+  if (graph_depth_hint(ctx, g) > ctx->deep_levels) return lane_pairs(ctx, g, count);
   batch_forward(ctx, g, count, true, OVF_EXTEND);
   const uint64_t ovf = ws.last_ovf & lanes_of(count);
   if (ovf) ext_pair_lanes(ctx, g, ws.sources.as<int32_t>(), ws.targets.as<int32_t>(), ovf);

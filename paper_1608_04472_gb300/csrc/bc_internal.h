@@ -241,6 +241,13 @@ void forget_multi_plan(bc_ctx *ctx);
 // at a time each, CTA barriers between levels), delivering to the sink.
 void lane_sink(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, int count, const Sink &sink);
 void forget_lane_scratch(bc_ctx *ctx);
+// Pair sampling on a deep graph, lane-major: the targets' full BFS into the
+// [n][Tp] tables (d_tx[j] = 1 where the extended form was needed), and one
+// batch of pair lanes (ws.sources -> ws.targets) into ws.pair_*; returns the
+// lanes whose sigma_st is in the extended form.
+void lane_targets(bc_ctx *ctx, const Graph &g, const int32_t *d_targets, int T, int Tp, int32_t *tdist,
+                  uint64_t *tsig, int32_t *texp, int32_t *d_tx);
+uint64_t lane_pairs(bc_ctx *ctx, const Graph &g, int count);
 // (bc_capi.cu) the largest finite distance from the graph's hub (cached), and
 // one graph's uniform estimate on the batched/plain engine
 int graph_depth_hint(bc_ctx *ctx, const Graph &g);

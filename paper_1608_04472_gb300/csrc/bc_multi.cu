@@ -136,11 +136,11 @@ __device__ __forceinline__ void for_level(const MScratch &S, const int32_t *__re
   }
 }
 
-// One source on the whole CTA; every dependency delta_s(v) (v at distance >= 1)
-// is handed to deliver(v, delta) by one thread.
-template <class D>
-__device__ void multi_source(const MGraph &G, int32_t s, const MScratch &S, unsigned &err, int *s_tail, int *s_ovf,
-                             D deliver) {
+// Forward pass of one source on the whole CTA: distances, exact counts and the
+// level offsets; with dest >= 0 it stops once dest's level is settled. Returns
+// the deepest settled level; *s_ovf says whether a count of those levels
+// exceeded 2^64-1.
+__device__ int lane_forward(const MGraph &G, int32_t s, int32_t dest, const MScratch &S, int *s_tail, int *s_ovf) {
   const int tid = threadIdx.x, lane = tid & 31;
   const int32_t *__restrict__ rp = G.rp;
   const int32_t *__restrict__ col = G.col;
@@ -201,26 +201,44 @@ __device__ void multi_source(const MGraph &G, int32_t s, const MScratch &S, unsi
     });
     __syncthreads();
     ++L;
+    if (dest >= 0 && S.dist[dest] >= 0) break;  // dest settled at level L
   }
-  const bool ext = *s_ovf != 0;
-  if (ext) {
-    // the counts again, in the extended form (pull order)
-    if (tid == 0) {
-      S.sig[s] = (uint64_t)__double_as_longlong(1.0);
-      S.sige[s] = 0;
-    }
+  return L;
+}
+
+// The counts of levels 1..L again, in the extended form (pull order).
+__device__ void lane_extend(const MGraph &G, int32_t s, const MScratch &S, int L) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int32_t *__restrict__ rp = G.rp;
+  const int32_t *__restrict__ col = G.col;
+  if (tid == 0) {
+    S.sig[s] = (uint64_t)__double_as_longlong(1.0);
+    S.sige[s] = 0;
+  }
+  __syncthreads();
+  for (int d = 1; d <= L; ++d) {
+    for_level(S, rp, S.lo[d], S.lo[d + 1], [&](int32_t w, int beg, int end, bool coop) {
+      const Xf x = xf_pull(S, col, beg, end, d - 1, false, coop);
+      if (!coop || lane == 0) {
+        S.sig[w] = (uint64_t)__double_as_longlong(x.m);
+        S.sige[w] = x.e;
+      }
+    });
     __syncthreads();
-    for (int d = 1; d <= L; ++d) {
-      for_level(S, rp, S.lo[d], S.lo[d + 1], [&](int32_t w, int beg, int end, bool coop) {
-        const Xf x = xf_pull(S, col, beg, end, d - 1, false, coop);
-        if (!coop || lane == 0) {
-          S.sig[w] = (uint64_t)__double_as_longlong(x.m);
-          S.sige[w] = x.e;
-        }
-      });
-      __syncthreads();
-    }
   }
+}
+
+// One source on the whole CTA; every dependency delta_s(v) (v at distance >= 1)
+// is handed to deliver(v, delta) by one thread.
+template <class D>
+__device__ void multi_source(const MGraph &G, int32_t s, const MScratch &S, unsigned &err, int *s_tail, int *s_ovf,
+                             D deliver) {
+  const int lane = threadIdx.x & 31;
+  const int32_t *__restrict__ rp = G.rp;
+  const int32_t *__restrict__ col = G.col;
+  const int L = lane_forward(G, s, -1, S, s_tail, s_ovf);
+  const bool ext = *s_ovf != 0;
+  if (ext) lane_extend(G, s, S, L);
   // Theorem 1 in decreasing distance
   for (int d = L; d >= 1; --d) {
     for_level(S, rp, S.lo[d], S.lo[d + 1], [&](int32_t v, int beg, int end, bool coop) {
@@ -311,6 +329,64 @@ k_lane_sink(MGraph G, const int32_t *__restrict__ sources, int count, unsigned *
     __syncthreads();
   }
   if (e) atomicOr(err, e);
+}
+
+// Pair sampling on a deep graph, lane-major. Targets: the full BFS of each
+// target into the [n][Tp] tables (counts in the extended form, with tx[j] = 1,
+// when the BFS overflows). Pair lanes: the BFS from sources[t] until dests[t]'s
+// level; sigma_st in the extended form (bit t of *pxmask) when a count up to
+// that level overflowed.
+__global__ void __launch_bounds__(MT)
+k_lane_targets(MGraph G, const int32_t *__restrict__ targets, int T, int Tp, unsigned *__restrict__ next,
+               unsigned char *__restrict__ scratch, size_t stride, int32_t nmax, int32_t *__restrict__ tdist,
+               uint64_t *__restrict__ tsig, int32_t *__restrict__ texp, int32_t *__restrict__ tx) {
+  __shared__ int s_item, s_tail, s_ovf;
+  const MScratch S = mscratch_of(scratch + (size_t)blockIdx.x * stride, nmax);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(next, 1u);
+    __syncthreads();
+    const int j = s_item;
+    if (j >= T) break;
+    const int L = lane_forward(G, targets[j], -1, S, &s_tail, &s_ovf);
+    const bool ext = s_ovf != 0;
+    if (ext) lane_extend(G, targets[j], S, L);
+    for (int32_t v = threadIdx.x; v < G.n; v += MT) {
+      const size_t o = (size_t)v * Tp + j;
+      const int32_t d = S.dist[v];
+      tdist[o] = d;
+      tsig[o] = d >= 0 ? S.sig[v] : 0ull;
+      texp[o] = (ext && d >= 0) ? S.sige[v] : 0;
+    }
+    if (threadIdx.x == 0) tx[j] = ext ? 1 : 0;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(MT)
+k_lane_pairs(MGraph G, const int32_t *__restrict__ sources, const int32_t *__restrict__ dests, int count,
+             unsigned *__restrict__ next, unsigned char *__restrict__ scratch, size_t stride, int32_t nmax,
+             int32_t *__restrict__ pair_d, uint64_t *__restrict__ pair_sig, int32_t *__restrict__ pair_exp,
+             unsigned long long *__restrict__ pxmask) {
+  __shared__ int s_item, s_tail, s_ovf;
+  const MScratch S = mscratch_of(scratch + (size_t)blockIdx.x * stride, nmax);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(next, 1u);
+    __syncthreads();
+    const int t = s_item;
+    if (t >= count) break;
+    const int32_t dst = dests[t];
+    const int L = lane_forward(G, sources[t], dst, S, &s_tail, &s_ovf);
+    const bool reached = S.dist[dst] >= 0;
+    const bool ext = reached && s_ovf != 0;
+    if (ext) lane_extend(G, sources[t], S, L);
+    if (threadIdx.x == 0) {
+      pair_d[t] = reached ? S.dist[dst] : -1;
+      pair_sig[t] = reached ? S.sig[dst] : 0ull;
+      pair_exp[t] = ext ? S.sige[dst] : 0;
+      if (ext) atomicOr(pxmask, 1ull << t);
+    }
+    __syncthreads();
+  }
 }
 
 // sink.acc[v] += the CTAs' partial sums (exact).
@@ -498,6 +574,21 @@ static void build_plan(bc_ctx *ctx, MultiPlan &P, const std::vector<const Graph 
   cuda_check(ie, "cudaGraphInstantiate");
 }
 
+// Lane-major scratch budget: a quarter of the free device memory, at most 32 GB
+// (on the 8.4 M-vertex grid a CTA needs ~300 MB; 64 lanes then run at once).
+static size_t lane_budget() {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    fr = (size_t)32 << 30;
+  }
+  return std::min<size_t>(fr / 4, (size_t)32 << 30);
+}
+
+static int lane_ctas(int count, size_t per) {
+  return std::max(1, std::min({count, multi_ctas(0), (int)std::max<size_t>(1, lane_budget() / per)}));
+}
+
 // Per-context scratch of the lane-major path (grown on demand).
 struct LaneScratch {
   DevBuf scratch, partials, next;
@@ -521,8 +612,7 @@ void lane_sink(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, int count,
   lk.unlock();
   const size_t stride = mscratch_stride(g.n);
   const size_t per = stride + (sink.acc ? sizeof(Acc) * (size_t)g.n : 0);
-  // resident CTAs, at most one per lane, and at most ~8 GB of scratch
-  const int ncta = std::max(1, std::min({count, multi_ctas(0), (int)std::max<size_t>(1, ((size_t)8 << 30) / per)}));
+  const int ncta = lane_ctas(count, per);  // resident CTAs, at most one per lane
   L.scratch.ensure(stride * ncta);
   if (sink.acc) L.partials.ensure(sizeof(Acc) * (size_t)g.n * ncta);
   L.next.ensure(16);
@@ -543,6 +633,58 @@ void lane_sink(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, int count,
   }
   ctx->samples += count;
   ctx->batches += 1;
+}
+
+void lane_targets(bc_ctx *ctx, const Graph &g, const int32_t *d_targets, int T, int Tp, int32_t *tdist,
+                  uint64_t *tsig, int32_t *texp, int32_t *d_tx) {
+  if (T < 1) return;
+  std::unique_lock<std::mutex> lk(g_plans_mu);
+  LaneScratch &L = g_lane[ctx];
+  lk.unlock();
+  const size_t stride = mscratch_stride(g.n);
+  const int ncta = lane_ctas(T, stride);
+  L.scratch.ensure(stride * ncta);
+  L.next.ensure(16);
+  cudaStream_t st = ctx->stream;
+  BCG_CUDA(cudaMemsetAsync(L.next.p, 0, 16, st));
+  MGraph G{};
+  G.rp = g.rp;
+  G.col = g.col;
+  G.n = g.n;
+  LaunchScope ls(ctx, F_XFWD);
+  k_lane_targets<<<ncta, MT, 0, st>>>(G, d_targets, T, Tp, L.next.as<unsigned>(), L.scratch.as<unsigned char>(), stride,
+                                      g.n, tdist, tsig, texp, d_tx);
+}
+
+uint64_t lane_pairs(bc_ctx *ctx, const Graph &g, int count) {
+  if (count < 1) return 0ull;
+  std::unique_lock<std::mutex> lk(g_plans_mu);
+  LaneScratch &L = g_lane[ctx];
+  lk.unlock();
+  Workspace &ws = ctx->ws;
+  const size_t stride = mscratch_stride(g.n);
+  const int ncta = lane_ctas(count, stride);
+  L.scratch.ensure(stride * ncta);
+  L.next.ensure(16);
+  cudaStream_t st = ctx->stream;
+  BCG_CUDA(cudaMemsetAsync(L.next.p, 0, 16, st));
+  MGraph G{};
+  G.rp = g.rp;
+  G.col = g.col;
+  G.n = g.n;
+  {
+    LaunchScope ls(ctx, F_PAIR);
+    k_lane_pairs<<<ncta, MT, 0, st>>>(G, ws.sources.as<int32_t>(), ws.targets.as<int32_t>(), count,
+                                      L.next.as<unsigned>(), L.scratch.as<unsigned char>(), stride, g.n,
+                                      ws.pair_d.as<int32_t>(), ws.pair_sig.as<uint64_t>(), ws.pair_exp.as<int32_t>(),
+                                      L.next.as<unsigned long long>() + 1);
+  }
+  uint64_t *h = static_cast<uint64_t *>(ws.pinned);
+  BCG_CUDA(cudaMemcpyAsync(h, L.next.as<unsigned long long>() + 1, 8, cudaMemcpyDeviceToHost, st));
+  BCG_CUDA(cudaStreamSynchronize(st));
+  ctx->samples += count;
+  ctx->batches += 1;
+  return h[0];
 }
 
 void do_uniform_multi(bc_ctx *ctx, const std::vector<bc_graph> &handles, const std::vector<const Graph *> &gs,
