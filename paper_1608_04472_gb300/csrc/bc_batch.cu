@@ -572,11 +572,9 @@ __device__ __forceinline__ void ring_append(Ring &R, unsigned &tail, int32_t v, 
 }
 
 // One warp-wide round over ring records head..head+count-1 (count <= 32).
-// With `coefx` set (128-bit window), the coefficient is stored as its exact
-// fixed-point limbs (unit 2^-96) in coefx[v][t] and sigma stays in place;
-// otherwise the coefficient's double bits overwrite sigma[v][t].
+// The coefficient's double bits overwrite sigma[v][t].
 __device__ __forceinline__ void ring_round(Ring &R, unsigned head, int count, uint64_t *__restrict__ sigma,
-                                           const Sink &sink, unsigned &e, uint4 *__restrict__ coefx = nullptr) {
+                                           const Sink &sink, unsigned &e) {
   const int lane = threadIdx.x & 31;
   int32_t v = -1;
   double d = 0.0;
@@ -587,13 +585,7 @@ __device__ __forceinline__ void ring_round(Ring &R, unsigned head, int count, ui
     const uint64_t sg = R.sig[pos];
     d = delta_of(R.sum[pos], sg);
     const double cf = coef_round(d, sg);
-    if (coefx) {
-      Acc2 z = acc2_zero();
-      acc2_add(z, cf, e);
-      coefx[(size_t)v * 64 + t] = make_uint4(z.l0, z.l1, z.l2, z.l3);
-    } else {
-      sigma[(size_t)v * 64 + t] = (uint64_t)__double_as_longlong(cf);
-    }
+    sigma[(size_t)v * 64 + t] = (uint64_t)__double_as_longlong(cf);
     if (sink.delta_lm) sink.delta_lm[(size_t)v * 64 + t] = d;
     if (sink.tslot) sink_targets(sink, v, t, d);
   }
@@ -843,120 +835,6 @@ __device__ __forceinline__ void gather_packed(int beg, int end, uint64_t lanes, 
   for (int off = 1 << pk.glog; off < 32; off <<= 1) acc2_shfl_xor_add(a0, off);
 }
 
-// Forward, packed: predecessor sigma sums for the lanes `newm` that reach v at
-// this level (thread (g, s) of the packed layout owns the s-th lane of newm).
-__device__ __forceinline__ void gather_sigma_packed(int beg, int end, uint64_t newm, const uint64_t *__restrict__ lm_prev,
-                                                    const int32_t *__restrict__ col, const uint64_t *__restrict__ sigma,
-                                                    const Packed &pk, int32_t *list, uint64_t &s0, uint64_t &s1,
-                                                    uint64_t &ovf, unsigned long long &tri) {
-  const int lane = threadIdx.x & 31;
-  const int NG = 32 >> pk.glog, g = lane >> pk.glog;
-  const uint64_t b0 = pk.p0 >= 0 ? (1ull << pk.p0) : 0ull, b1 = pk.p1 >= 0 ? (1ull << pk.p1) : 0ull;
-  const int q0 = pk.p0 < 0 ? 0 : pk.p0, q1 = pk.p1 < 0 ? 0 : pk.p1;
-  for (int base = beg; base < end; base += 32) {
-    const int j = base + lane;
-    int32_t w = 0;
-    uint64_t m = 0ull;
-    if (j < end) {
-      w = col[j];
-      m = lm_prev[w] & newm;
-    }
-    const unsigned bal = __ballot_sync(FULL, m != 0ull);
-    const int cnt = __popc(bal);
-    tri += (unsigned long long)__reduce_add_sync(FULL, (unsigned)__popcll((long long)m));
-    if (m != 0ull) list[__popc(bal & ((1u << lane) - 1u))] = lane;
-    __syncwarp();
-    for (int r = 0; r < cnt; r += 2 * NG) {
-      const int i0 = r + g, i1 = r + NG + g;
-      const bool h0 = i0 < cnt, h1 = i1 < cnt;
-      const int x0s = h0 ? list[i0] : 0, x1s = h1 ? list[i1] : 0;
-      const uint64_t m0 = __shfl_sync(FULL, m, x0s), m1 = __shfl_sync(FULL, m, x1s);
-      const int32_t w0 = __shfl_sync(FULL, w, x0s), w1 = __shfl_sync(FULL, w, x1s);
-      const uint64_t a0 = (h0 && (m0 & b0)) ? sigma[(size_t)w0 * 64 + q0] : 0ull;
-      const uint64_t a1 = (h1 && (m1 & b0)) ? sigma[(size_t)w1 * 64 + q0] : 0ull;
-      if (pk.two) {
-        const uint64_t c0 = (h0 && (m0 & b1)) ? sigma[(size_t)w0 * 64 + q1] : 0ull;
-        const uint64_t c1 = (h1 && (m1 & b1)) ? sigma[(size_t)w1 * 64 + q1] : 0ull;
-        uint64_t t = s1 + c0;
-        if (t < s1) ovf |= b1;
-        s1 = t + c1;
-        if (s1 < t) ovf |= b1;
-      }
-      uint64_t t = s0 + a0;
-      if (t < s0) ovf |= b0;
-      s0 = t + a1;
-      if (s0 < t) ovf |= b0;
-    }
-    __syncwarp();
-  }
-  for (int off = 1 << pk.glog; off < 32; off <<= 1) {
-    const uint64_t o = __shfl_xor_sync(FULL, s0, off);
-    const uint64_t t = s0 + o;
-    if (t < s0 && pk.p0 >= 0) ovf |= 1ull << pk.p0;
-    s0 = t;
-  }
-}
-
-// Forward level, two phases per vertex: an OR-scan of the neighbours' level
-// masks finds the lanes that reach v at this level; only then are the
-// predecessors' sigma values summed, packed over exactly those lanes.
-__global__ void __launch_bounds__(FWD_THREADS)
-k_fwd_light_pk(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-               const uint64_t *__restrict__ lm_prev, uint64_t *__restrict__ lm_cur,
-               uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
-               const uint64_t *__restrict__ active_prev, uint64_t *__restrict__ enable,
-               uint64_t *__restrict__ active_cur, unsigned *__restrict__ err,
-               unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq, int heavy_deg, int, int) {
-  __shared__ int32_t lists[FWD_THREADS / 32][32];
-  __shared__ int8_t tabs[FWD_THREADS / 32][64];
-  int32_t *list = lists[threadIdx.x >> 5];
-  int8_t *tab = tabs[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
-  const uint64_t act = *active_prev & *enable;
-  uint64_t any_new = 0ull, smax = 0ull, ovf = 0ull;
-  unsigned long long tri = 0ull, rch = 0ull;
-  for (int base = grab(wq); base < n; base = grab(wq))
-    for (int v = base; v < min(base + GRAB, n); ++v) {
-      const int beg = rp[v], end = rp[v + 1];
-      const uint64_t vis = visited[v];
-      const uint64_t pend = ~vis & act;
-      uint64_t newm = 0ull;
-      if (pend && end - beg <= heavy_deg) {
-        for (int j = beg + lane; j < end; j += 32) newm |= lm_prev[col[j]] & pend;
-        newm = warp_or64(newm);
-        if (newm) {
-          const Packed pk = pack_lanes(newm, tab);
-          uint64_t s0 = 0ull, s1 = 0ull;
-          gather_sigma_packed(beg, end, newm, lm_prev, col, sigma, pk, list, s0, s1, ovf, tri);
-          if ((lane >> pk.glog) == 0 && pk.p0 >= 0) {
-            sigma[(size_t)v * 64 + pk.p0] = s0;
-            smax = s0 > smax ? s0 : smax;
-          }
-          if (pk.p1 >= 0) {
-            sigma[(size_t)v * 64 + pk.p1] = s1;
-            smax = s1 > smax ? s1 : smax;
-          }
-        }
-      }
-      if (lane == 0) {
-        lm_cur[v] = newm;
-        if (newm) visited[v] = vis | newm;
-      }
-      rch += (unsigned long long)__popcll((long long)newm);
-      any_new |= newm;
-    }
-  ovf = warp_or64(ovf);
-  if (lane == 0 && ovf) atomicOr((unsigned long long *)(enable + 3), (unsigned long long)ovf);
-  (void)err;
-  if (lane == 0 && (tri | rch)) {
-    atomicAdd(cnt, tri);
-    atomicAdd(cnt + 1, rch);
-  }
-  smax = warp_max64(smax);
-  if (lane == 0 && smax > 1ull) atomicMax((unsigned long long *)(enable + 2), (unsigned long long)smax);
-  block_or_to(any_new, active_cur);
-}
-
 // Finished lanes of v (threads of group 0 own them) into the ring.
 __device__ __forceinline__ void ring_append_fx(Ring &R, unsigned &tail, int32_t v, uint64_t lanes, const Packed &pk,
                                                const Acc2 &a0, const Acc2 &a1, const uint64_t *__restrict__ row) {
@@ -981,7 +859,7 @@ __device__ __forceinline__ void ring_append_fx(Ring &R, unsigned &tail, int32_t 
 __global__ void __launch_bounds__(FWD_THREADS, BWD_MIN_BLOCKS)
 k_bwd_light_fx(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
-               uint64_t *__restrict__ sigma, uint4 *__restrict__ coefx, Sink sink, unsigned *__restrict__ err,
+               uint64_t *__restrict__ sigma, Sink sink, unsigned *__restrict__ err,
                unsigned *__restrict__ wq, int heavy_deg, uint64_t keep) {
   __shared__ Ring rings[FWD_THREADS / 32];
   __shared__ int32_t lists[FWD_THREADS / 32][32];
@@ -991,7 +869,6 @@ k_bwd_light_fx(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restr
   int8_t *tab = tabs[threadIdx.x >> 5];
   unsigned head = 0u, tail = 0u;
   unsigned e = 0u;
-  (void)coefx;
   for (int base = grab(wq); base < n; base = grab(wq))
     for (int v = base; v < min(base + GRAB, n); ++v) {
       const uint64_t lanes = lm_cur[v] & keep;
@@ -1040,7 +917,7 @@ k_bwd_heavy_seg_fx(int nseg, const int32_t *__restrict__ seg_v, const int32_t *_
 
 __global__ void __launch_bounds__(FWD_THREADS, BWD_MIN_BLOCKS)
 k_bwd_heavy_fin_fx(int nh, const int32_t *__restrict__ heavy, const int32_t *__restrict__ hseg0,
-                   const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ sigma, uint4 *__restrict__ coefx,
+                   const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ sigma,
                    const uint4 *__restrict__ part, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq, uint64_t keep) {
   __shared__ Ring rings[FWD_THREADS / 32];
   Ring &R = rings[threadIdx.x >> 5];
@@ -1268,8 +1145,7 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
     uint64_t *act = ws.active.as<uint64_t>();
     {
       LaunchScope ls(ctx, F_FWD);
-      auto kfwd = ctx->fwd_variant == 1 ? k_fwd_light_pk : k_fwd_light;
-      kfwd<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
+      k_fwd_light<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
                                                  ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(), act + l,
                                                  ws.enable.as<uint64_t>(), act + l + 1, ws.err.as<unsigned>(),
                                                  ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 0,
@@ -1354,12 +1230,11 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
   const bool narrow = ws.last_sigmax <= (1ull << 44);
   if (narrow && ctx->bwd_variant == 1) {
     hm.part2.ensure(std::max<size_t>(hm.nseg, 1) * 64 * sizeof(uint4));
-    uint4 *coefx = nullptr;
     for (int l = maxlevel; l >= 1; --l) {
       {
         LaunchScope ls(ctx, F_BWD);
         k_bwd_light_fx<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
-                                                      ws.sigma.as<uint64_t>(), coefx, sink, ws.err.as<unsigned>(),
+                                                      ws.sigma.as<uint64_t>(), sink, ws.err.as<unsigned>(),
                                                       ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg, keep);
       }
       if (hm.nseg && heavy_at(ws, l)) {
@@ -1373,7 +1248,7 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
         LaunchScope ls(ctx, F_BWD);
         k_bwd_heavy_fin_fx<<<std::min(blocks, (hm.nh + 7) / 8), FWD_THREADS, 0, st>>>(
             hm.nh, hm.heavy.as<int32_t>(), hm.hseg0.as<int32_t>(), lm + (size_t)l * n, ws.sigma.as<uint64_t>(),
-            coefx, hm.part2.as<uint4>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 4, keep);
+            hm.part2.as<uint4>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 4, keep);
       }
     }
     return;

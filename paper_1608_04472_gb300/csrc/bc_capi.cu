@@ -872,7 +872,6 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
     if (const char *hd = std::getenv("BCG_HEAVY_DEGREE")) ctx->heavy_deg = std::atoi(hd);
     if (const char *sl = std::getenv("BCG_SEGMENT")) ctx->seg_len = std::atoi(sl);
     if (const char *bv = std::getenv("BCG_BWD_VARIANT")) ctx->bwd_variant = std::atoi(bv);
-    if (const char *fv = std::getenv("BCG_FWD_VARIANT")) ctx->fwd_variant = std::atoi(fv);
     if (const char *dl = std::getenv("BCG_DEEP_LEVELS")) ctx->deep_levels = std::atoi(dl);
     if (const char *pm = std::getenv("BCG_PK_MAXL")) ctx->pk_maxl = std::atoi(pm);
     if (const char *pc = std::getenv("BCG_PK_MINCNT")) ctx->pk_mincnt = std::atoi(pc);
@@ -916,7 +915,7 @@ void bc_destroy(bc_ctx *ctx) {
     Workspace &ws = ctx->ws;
     for (DevBuf *b : {&ws.lm, &ws.visited, &ws.sigma, &ws.active, &ws.wq, &ws.enable, &ws.sources, &ws.targets, &ws.pair_d,
                       &ws.pair_sig, &ws.pair_exp, &ws.err, &ws.cnt, &ws.acc, &ws.tslot, &ws.tdelta, &ws.scan, &ws.misc, &ws.misc2,
-                      &ws.delta_lm, &ws.coefx, &ws.p_dist, &ws.p_sigma, &ws.p_coef, &ws.p_queue, &ws.p_ctr,
+                      &ws.delta_lm, &ws.p_dist, &ws.p_sigma, &ws.p_coef, &ws.p_queue, &ws.p_ctr,
                       &ws.x_dist, &ws.x_m, &ws.x_e, &ws.x_vis, &ws.x_nm, &ws.x_list, &ws.x_lmask, &ws.x_ctr,
                       &ws.x_off})
       b->release();

@@ -111,7 +111,6 @@ struct Workspace {
   DevBuf misc;     // scratch
   DevBuf misc2;
   DevBuf delta_lm; // [n][64] f64
-  DevBuf coefx;    // [n][64] uint4: coefficients as 128-bit fixed point (unit 2^-96)
   DevBuf win;      // draw window: draws[W] | sorted sources[W] | sorted positions[W]
   uint64_t last_ovf = 0ull;  // lanes of the last batched forward whose counts exceeded 2^64-1
   std::vector<uint8_t> hlev;  // per level of the last batched forward: a heavy vertex has lanes there
@@ -153,8 +152,6 @@ struct bc_ctx {
   // backward kernel form (128-bit window only): 1 = packed lane groups (default),
   // 0 = two lane halves per thread
   int32_t bwd_variant = 1;
-  // forward kernel form: 0 = fused scan and sigma gather, 1 = two-phase packed
-  int32_t fwd_variant = 0;
   // light forward: a 32-neighbour chunk with at least pk_mincnt predecessors
   // over at most pk_maxl lanes is summed in packed groups (0 disables)
   int32_t pk_maxl = 16, pk_mincnt = 6;
