@@ -21,7 +21,7 @@ for a uniform source s has mean A/n exactly (every source's dependencies are
 computed), and the model's variance (n-1)/(n^2 (n+1)) A^2 is set beside the
 exact variance.
 
-Usage: python accuracy.py [--seeds 100] [--json out.json]
+Usage: python accuracy.py [--seeds 100] [--json out.json] [--paper-shaped]
 """
 import argparse
 import json
@@ -134,6 +134,58 @@ def run(seeds: int):
     return out
 
 
+def run_paper_shaped(seeds: int):
+    """c sweep on synthetic stand-ins shaped like the paper's two datasets
+    (Sec. 7, Table 1: 10,670 vertices / 22,002 edges and 4,039 / 88,234 edges):
+    Barabasi-Albert graphs with 2 and 22 edges per new vertex. Targets: the 8
+    highest-degree vertices and 8 uniform ones; cap 8 n draws. Per c: mean draws,
+    share of runs stopped before the cap, median and p90 of the factor difference
+    |est/BC - 1| (Sec. 7's measures: number of samples and factor against c)."""
+    import paper_1608_04472_gb300 as pkg
+
+    graphs = [("oregon-shaped BA(n=10670, m=2)", gg.barabasi_albert(10670, 2, 7)),
+              ("facebook-shaped BA(n=4039, m=22)", gg.barabasi_albert(4039, 22, 7, m0=23))]
+    out = []
+    with pkg.Context(0, batch_width=64) as ctx:
+        for name, g in graphs:
+            n = g.n
+            h = ctx.load_graph(g.row_ptr, g.col)
+            bc = ctx.exact(h)
+            deg = np.diff(g.row_ptr)
+            top = np.argsort(-deg, kind="stable")[:8]
+            rest = [int(v) for v in gg.uniform_targets(n, 24, 3) if v not in set(top.tolist())][:8]
+            targets = np.array(top.tolist() + rest, np.int32)
+            A = bc[targets]
+            keep = A > 0
+            for est_kind, cs in (("sources", (1.0, 2.0, 5.0, 10.0, 20.0)), ("pairs", (1.0, 2.0, 5.0, 10.0, 20.0))):
+                for c in cs:
+                    rel, ks, st = [], [], []
+                    for s_ in range(seeds):
+                        if est_kind == "sources":
+                            r = ctx.adaptive_sources(h, targets, c, 8 * n, 3000 + s_, s_)
+                        else:  # the rescaled pair threshold S (n-1) > c n
+                            r = ctx.adaptive_pairs(h, targets, c, 8 * n, 4000 + s_, s_, float(n - 1))
+                        rel.append(np.abs(r["est"][keep] / A[keep] - 1.0))
+                        ks.append(r["k"][keep])
+                        st.append(r["status"][keep] == pkg.BC_STOPPED)
+                    rel, ks, st = np.concatenate(rel), np.concatenate(ks), np.concatenate(st)
+                    out.append(dict(graph=name, n=n, m=int(g.nnz // 2), estimator=est_kind, c=c, runs=int(rel.size),
+                                    mean_k=float(ks.mean()), stopped=float(st.mean()),
+                                    median=float(np.median(rel)), p90=float(np.quantile(rel, 0.9))))
+                    print(json.dumps(out[-1]), flush=True)
+            ctx.free_graph(h)
+    return out
+
+
+def markdown_paper(rows):
+    lines = ["| graph | estimator | c | runs | mean draws | stopped | median factor diff | p90 |",
+             "|---|---|---|---|---|---|---|---|"]
+    for r in rows:
+        lines.append(f"| {r['graph']} | {r['estimator']} | {r['c']:g} | {r['runs']} | {r['mean_k']:.0f} | "
+                     f"{100 * r['stopped']:.0f} % | {r['median']:.4f} | {r['p90']:.4f} |")
+    return "\n".join(lines)
+
+
 def markdown(res):
     lines = ["| estimator | c | threshold | runs | stopped | mean k | median rel err | p90 | max |",
              "|---|---|---|---|---|---|---|---|---|"]
@@ -162,7 +214,16 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--seeds", type=int, default=100)
     ap.add_argument("--json", default=None)
+    ap.add_argument("--paper-shaped", action="store_true",
+                    help="c sweep on stand-ins shaped like the paper's two datasets instead")
     a = ap.parse_args()
+    if a.paper_shaped:
+        rows = run_paper_shaped(a.seeds)
+        if a.json:
+            with open(a.json, "w") as f:
+                json.dump(rows, f, indent=1)
+        print(markdown_paper(rows))
+        return
     res = run(a.seeds)
     if a.json:
         with open(a.json, "w") as f:
