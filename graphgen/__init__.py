@@ -125,6 +125,54 @@ def from_edges(n: int, eu, ev, name: str = "graph") -> Graph:
     return Graph(row_ptr, col, name)
 
 
+def from_edges_directed(n: int, eu, ev, name: str = "digraph") -> Graph:
+    """A directed CSR from an edge list u -> v: self loops and repeated edges
+    dropped, each row (the out-neighbours) sorted; no symmetrisation."""
+    eu = np.asarray(eu, dtype=np.int64)
+    ev = np.asarray(ev, dtype=np.int64)
+    keep = eu != ev
+    key = np.unique(eu[keep] * n + ev[keep])
+    src = (key // n).astype(np.int32)
+    col = (key % n).astype(np.int32)
+    row_ptr = np.zeros(n + 1, dtype=np.int32)
+    np.add.at(row_ptr, src.astype(np.int64) + 1, 1)
+    row_ptr = np.cumsum(row_ptr, dtype=np.int64).astype(np.int32)
+    return Graph(row_ptr, col, name)
+
+
+def directed_rmat(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int) -> Graph:
+    """R-MAT edges read as directed (row -> column quadrant), not symmetrised."""
+    lib = _load()
+    n = 1 << scale
+    M = edge_factor * n
+    eu = np.empty(M, np.int32)
+    ev = np.empty(M, np.int32)
+    lib.gg_rmat(scale, M, a, b, c, seed, _p(eu), _p(ev))
+    return from_edges_directed(n, eu, ev, name=f"drmat_s{scale}_ef{edge_factor}_s{seed}")
+
+
+def directed_er(n: int, avg_out_degree: float, seed: int) -> Graph:
+    """Directed G(n, M): M = round(avg_out_degree * n) uniform ordered pairs."""
+    lib = _load()
+    M = int(round(avg_out_degree * n))
+    eu = np.empty(M, np.int32)
+    ev = np.empty(M, np.int32)
+    lib.gg_er_m(n, M, seed, _p(eu), _p(ev))
+    return from_edges_directed(n, eu, ev, name=f"der_n{n}_d{avg_out_degree:g}_s{seed}")
+
+
+def directed_grid(side: int) -> Graph:
+    """side x side lattice with edges pointing right and down only (from the
+    corner 0, sigma to (i, j) is the binomial C(i+j, i))."""
+    v = np.arange(side * side, dtype=np.int64)
+    i, j = v // side, v % side
+    right = v[j + 1 < side]
+    down = v[i + 1 < side]
+    eu = np.concatenate([right, down])
+    ev = np.concatenate([right + 1, down + side])
+    return from_edges_directed(side * side, eu, ev, name=f"dgrid_{side}")
+
+
 def erdos_renyi(n: int, avg_degree: float, seed: int, pairwise=None) -> Graph:
     """G(n, p) with p = avg_degree/(n-1).
 

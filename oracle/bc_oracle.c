@@ -43,6 +43,12 @@
  *       order of the vertex, one rounding per addition; delta = RN(sigma *
  *       sum) is then an ordinary double.
  *
+ * Graphs: a CSR row lists the out-neighbours of a vertex. For an undirected
+ * graph every edge appears in both rows; the per-source step, exact BC and the
+ * source-sampling estimators also take a directed graph as it is (paths follow
+ * the edges' direction). Pair sampling assumes an undirected graph (it reads
+ * d(s,v) from the BFS at v).
+ *
  * Random draws: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11) with key = (seed, qid) and counter =
  * (i, 0, 0, 0) for the i-th draw (0-based). A source is floor(x0*n/2^64); an
@@ -390,14 +396,37 @@ void orc_xf_add_pair(double m1, int64_t e1, double m2, int64_t e2, double *m, in
   *e = r.e;
 }
 
+/* In-neighbour lists of a CSR (edge u -> w lists u under w), each in increasing
+ * u; for an undirected graph with sorted rows this is the CSR itself. */
+static int orc_transpose(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t **rp_in,
+                         int32_t **col_in) {
+  int64_t m = row_ptr[n];
+  int32_t *rp = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+  int32_t *cl = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m ? m : 1));
+  int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+  if (!rp || !cl || !fill) { free(rp); free(cl); free(fill); return ORC_E_NOMEM; }
+  for (int64_t j = 0; j < m; ++j) rp[col[j] + 1]++;
+  for (int32_t v = 0; v < n; ++v) rp[v + 1] += rp[v];
+  for (int32_t v = 0; v < n; ++v) fill[v] = rp[v];
+  for (int32_t u = 0; u < n; ++u)
+    for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) cl[fill[col[j]]++] = u;
+  free(fill);
+  *rp_in = rp;
+  *col_in = cl;
+  return ORC_OK;
+}
+
 /*
  * BFS from s with path counts in the extended form (Sec. 3 step 1, Def. 3):
  * distances by a FIFO queue as in orc_bfs, then for the reached vertices in
- * queue order (non-decreasing distance) sigma_sw = sum over CSR neighbours v of
- * w with d(s,v) = d(s,w) - 1 of sigma_sv, added in CSR order.
+ * queue order (non-decreasing distance) sigma_sw = sum over the in-neighbours v
+ * of w with d(s,v) = d(s,w) - 1 of sigma_sv, added in increasing v (for an
+ * undirected graph: w's CSR row).
  */
 static void orc_bfs_xf(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
                        int32_t *dist, orc_xf *sigma, int32_t *order, int32_t *nreached) {
+  int32_t *rp_in = NULL, *col_in = NULL;
+  if (orc_transpose(n, row_ptr, col, &rp_in, &col_in) != ORC_OK) { *nreached = -1; return; }
   for (int32_t v = 0; v < n; ++v) { dist[v] = -1; sigma[v].m = 0.0; sigma[v].e = 0; }
   int32_t head = 0, tail = 0;
   dist[s] = 0;
@@ -413,12 +442,14 @@ static void orc_bfs_xf(int32_t n, const int32_t *row_ptr, const int32_t *col, in
   for (int32_t idx = 1; idx < tail; ++idx) {
     int32_t w = order[idx];
     orc_xf acc = orc_xf_make(0.0, 0);
-    for (int32_t j = row_ptr[w]; j < row_ptr[w + 1]; ++j) {
-      int32_t v = col[j];
+    for (int32_t j = rp_in[w]; j < rp_in[w + 1]; ++j) {
+      int32_t v = col_in[j];
       if (dist[v] >= 0 && dist[v] == dist[w] - 1) acc = orc_xf_add(acc, sigma[v]); /* v in P_s(w) */
     }
     sigma[w] = acc;
   }
+  free(rp_in);
+  free(col_in);
   *nreached = tail;
 }
 
@@ -461,6 +492,10 @@ int orc_source_dependencies_xf(int32_t n, const int32_t *row_ptr, const int32_t 
   }
   int32_t nr = 0;
   orc_bfs_xf(n, row_ptr, col, s, dist, sigma, order, &nr);
+  if (nr < 0) {
+    free(dist); free(order); free(sigma); free(coef);
+    return ORC_E_NOMEM;
+  }
   for (int32_t v = 0; v < n; ++v) {
     if (sigma_m) sigma_m[v] = sigma[v].m;
     if (sigma_e) sigma_e[v] = sigma[v].e;
