@@ -16,9 +16,10 @@
  *   - All pointers are HOST pointers unless the name says "device". Arrays are
  *     caller-owned; synchronous calls copy their inputs and have finished with
  *     them on return.
- *   - Vertices are int32 in [0, n). Graphs are undirected and unweighted, in
- *     CSR form: row_ptr[n+1] (row_ptr[0] = 0, non-decreasing), col[nnz]; every
- *     undirected edge appears in both rows.
+ *   - Vertices are int32 in [0, n). Graphs are unweighted, in CSR form:
+ *     row_ptr[n+1] (row_ptr[0] = 0, non-decreasing), col[nnz]. An undirected
+ *     graph lists every edge in both rows; a directed one (BC_DIRECTED) lists
+ *     out-neighbours.
  *   - Errors are returned as negative bc_status codes; bc_last_error() gives a
  *     message. No C++ exception crosses this boundary. A context serialises the
  *     calls made on it (calls on one context from several threads are safe).
@@ -74,8 +75,10 @@ typedef int32_t bc_status;
 #define BC_CAPPED 1                /* k reached cap before S exceeded c*n */
 
 /* graph load flags */
-#define BC_UNDIRECTED 1u           /* required: the CSR is an undirected adjacency */
-#define BC_VALIDATE 2u             /* check symmetry, sorted rows, no loops or duplicates */
+#define BC_UNDIRECTED 1u           /* the CSR is an undirected adjacency (each edge in both rows) */
+#define BC_VALIDATE 2u             /* check sorted rows, no loops or duplicates, and (undirected)
+                                      symmetry */
+#define BC_DIRECTED 4u             /* the CSR lists out-neighbours; paths follow the edges' direction */
 
 typedef struct bc_ctx bc_ctx;
 typedef int64_t bc_graph;          /* graph handle, valid in the context that made it */
@@ -106,8 +109,17 @@ bc_status bc_set_batch_width(bc_ctx *ctx, int32_t width);
 /* ------------------------------------------------------------------ graphs -- */
 
 /* Copies a CSR graph to the device and returns a handle. flags must contain
- * BC_UNDIRECTED; with BC_VALIDATE the CSR is checked first (BC_E_BAD_GRAPH on
- * failure). nnz = row_ptr[n] must be < 2^31 (BC_E_TOO_LARGE). n >= 1.
+ * exactly one of BC_UNDIRECTED and BC_DIRECTED (else BC_E_INVALID); with
+ * BC_VALIDATE the CSR is checked first (BC_E_BAD_GRAPH on failure).
+ * nnz = row_ptr[n] must be < 2^31 (BC_E_TOO_LARGE). n >= 1.
+ * A directed graph (Def. 1 with ordered pairs and directed paths) also gets
+ * its in-neighbour CSR, built on the host at load (a stable transpose, so each
+ * in-row is in increasing order when the rows are sorted; a column outside
+ * [0, n) is BC_E_BAD_GRAPH even without BC_VALIDATE); path counts are pulled
+ * over it. The per-source step, exact BC, the uniform and multi-graph
+ * estimates and adaptive source sampling (also served) take directed graphs;
+ * pair sampling (bc_adaptive_pairs, BC_QUERY_PAIRS) reads d(s,v) from a BFS
+ * at v and needs an undirected graph (BC_E_INVALID otherwise).
  * The caller keeps ownership of row_ptr and col. */
 bc_status bc_graph_load_csr(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col,
                             int64_t nnz, uint32_t flags, bc_graph *out);
@@ -185,7 +197,9 @@ bc_status bc_adaptive_sources(bc_ctx *ctx, bc_graph g, const int32_t *targets, i
  * (BC_CAPPED); est = (n(n-1)*S)/k. sigma_st(v)/sigma_st is
  * sigma_sv*sigma_vt/sigma_st when d(s,v)+d(v,t) = d(s,t) and v not in {s,t},
  * else 0. threshold_scale = 1 is the paper's test; other values (> 0) rescale
- * S only in the stop test. n >= 2, c >= 1, cap >= 1. */
+ * S only in the stop test. n >= 2, c >= 1, cap >= 1. The graph must be
+ * undirected (BC_E_INVALID for a BC_DIRECTED graph): sigma_vt and d(v,t) are
+ * read from the BFS at t. */
 bc_status bc_adaptive_pairs(bc_ctx *ctx, bc_graph g, const int32_t *targets, int32_t T,
                             double c, int64_t cap, uint64_t seed, uint64_t qid,
                             double threshold_scale, double *est, int64_t *k, double *S,

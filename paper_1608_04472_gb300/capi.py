@@ -24,6 +24,7 @@ BC_STOPPED = 0
 BC_CAPPED = 1
 BC_UNDIRECTED = 1
 BC_VALIDATE = 2
+BC_DIRECTED = 4
 BC_PENDING = 1
 BC_QUERY_SOURCES = 1
 BC_QUERY_PAIRS = 2
@@ -401,8 +402,8 @@ class Context:
         except Exception:
             pass
 
-    def load_graph(self, row_ptr, col, validate: bool = False) -> int:
-        flags = BC_UNDIRECTED | (BC_VALIDATE if validate else 0)
+    def load_graph(self, row_ptr, col, validate: bool = False, directed: bool = False) -> int:
+        flags = (BC_DIRECTED if directed else BC_UNDIRECTED) | (BC_VALIDATE if validate else 0)
         h = bc_graph_load_csr(self.ptr, row_ptr, col, flags)
         self.graphs.add(h)
         return h

@@ -269,7 +269,7 @@ __global__ void k_exact_sum(int64_t count, const double *__restrict__ x, double 
 
 // Graph validation: symmetric, sorted, no loops, no duplicates, in range.
 __global__ void k_validate(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                           int64_t nnz, unsigned *__restrict__ bad) {
+                           int64_t nnz, int symmetric, unsigned *__restrict__ bad) {
   const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   const int b = rp[v], e = rp[v + 1];
@@ -281,6 +281,7 @@ __global__ void k_validate(int32_t n, const int32_t *__restrict__ rp, const int3
     const int32_t w = col[j];
     if (w < 0 || w >= n || w == v) { atomicOr(bad, 2u); return; }
     if (j > b && col[j - 1] >= w) { atomicOr(bad, 4u); return; }
+    if (!symmetric) continue;
     // symmetric: binary search v in row w
     int lo = rp[w], hi = rp[w + 1] - 1;
     bool found = false;
@@ -564,7 +565,11 @@ static void do_exact_or_uniform(bc_ctx *ctx, const Graph &g, bool exact, int64_t
   BCG_CUDA(cudaMemcpy(out, ws.misc2.p, n * 8, cudaMemcpyDeviceToHost));
 }
 
-int graph_depth_hint(bc_ctx *ctx, const Graph &g) { return key_meta(ctx, g, false).ecc; }
+// A directed graph reports an unbounded depth, which sends its batches to the
+// lane-major engine: the level-mask engine pulls counts over the out-CSR.
+int graph_depth_hint(bc_ctx *ctx, const Graph &g) {
+  return g.directed ? INT32_MAX : key_meta(ctx, g, false).ecc;
+}
 
 void uniform_one(bc_ctx *ctx, const Graph &g, int64_t k, uint64_t seed, uint64_t qid, double *out) {
   do_exact_or_uniform(ctx, g, false, k, seed, qid, out);
@@ -751,7 +756,8 @@ static void do_source_dependencies(bc_ctx *ctx, const Graph &g, const int32_t *s
     if (sources[i] < 0 || sources[i] >= g.n) fail(BC_E_INVALID, "source out of range");
   ws.delta_lm.ensure(n * 64 * 8);
   DevBuf dd, ddist, dsig, dsm, dse;
-  const int width = batch_width(ctx);
+  // a directed graph runs one source at a time on the plain engine
+  const int width = g.directed ? 1 : batch_width(ctx);
   const int chunk = std::min<int>(64, std::max(1, count));
   const bool want_xf = sm_out || se_out;
   dd.ensure(n * chunk * 8);
@@ -910,6 +916,10 @@ void bc_destroy(bc_ctx *ctx) {
       forget_key_meta(kv.second.rp);
       cudaFree(kv.second.rp);
       cudaFree(kv.second.col);
+      if (kv.second.directed) {
+        cudaFree(kv.second.rp_in);
+        cudaFree(kv.second.col_in);
+      }
     }
     ctx->graphs.clear();
     Workspace &ws = ctx->ws;
@@ -943,7 +953,9 @@ bc_status bc_graph_load_csr(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, cons
                             uint32_t flags, bc_graph *out) {
   BC_GUARD_BEGIN
   if (!out || !row_ptr) fail(BC_E_INVALID, "NULL argument");
-  if (!(flags & BC_UNDIRECTED)) fail(BC_E_INVALID, "only undirected graphs (BC_UNDIRECTED) are supported");
+  const bool directed = (flags & BC_DIRECTED) != 0;
+  if (directed == ((flags & BC_UNDIRECTED) != 0))
+    fail(BC_E_INVALID, "flags need exactly one of BC_UNDIRECTED and BC_DIRECTED");
   if (n < 1) fail(BC_E_INVALID, "n must be >= 1");
   if (n > (1 << 30)) fail(BC_E_TOO_LARGE, "n too large");
   if (nnz < 0 || nnz >= ((int64_t)1 << 31)) fail(BC_E_TOO_LARGE, "nnz must be < 2^31");
@@ -955,10 +967,27 @@ bc_status bc_graph_load_csr(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, cons
     if (d < 0) fail(BC_E_BAD_GRAPH, "row_ptr must be non-decreasing");
     maxdeg = std::max(maxdeg, d);
   }
+  // directed: the in-neighbour CSR by a stable counting transpose (row u's
+  // columns are visited in increasing u, so in-rows come out sorted)
+  std::vector<int32_t> rp_in, col_in;
+  if (directed) {
+    rp_in.assign((size_t)n + 1, 0);
+    for (int64_t j = 0; j < nnz; ++j) {
+      const int32_t w = col[j];
+      if (w < 0 || w >= n) fail(BC_E_BAD_GRAPH, "column out of range");
+      ++rp_in[(size_t)w + 1];
+    }
+    for (int32_t v = 0; v < n; ++v) rp_in[(size_t)v + 1] += rp_in[v];
+    col_in.resize((size_t)std::max<int64_t>(nnz, 1));
+    std::vector<int32_t> pos(rp_in.begin(), rp_in.end() - 1);
+    for (int32_t u = 0; u < n; ++u)
+      for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) col_in[(size_t)pos[col[j]]++] = u;
+  }
   Graph g;
   g.n = n;
   g.nnz = nnz;
   g.max_deg = maxdeg;
+  g.directed = directed;
   for (int32_t v = 0; v < n; ++v)
     if (row_ptr[v + 1] - row_ptr[v] == maxdeg) {
       g.hub = v;
@@ -970,16 +999,36 @@ bc_status bc_graph_load_csr(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, cons
     cudaFree(g.rp);
     fail(BC_E_NOMEM, "out of device memory for col");
   }
+  g.rp_in = g.rp;
+  g.col_in = g.col;
+  if (directed) {
+    g.rp_in = g.col_in = nullptr;
+    if (cudaMalloc(&g.rp_in, sizeof(int32_t) * ((size_t)n + 1)) != cudaSuccess ||
+        cudaMalloc(&g.col_in, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(g.rp);
+      cudaFree(g.col);
+      cudaFree(g.rp_in);
+      fail(BC_E_NOMEM, "out of device memory for the in-neighbour CSR");
+    }
+  }
   try {
     BCG_CUDA(cudaMemcpyAsync(g.rp, row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, ctx->stream));
     if (nnz > 0)
       BCG_CUDA(cudaMemcpyAsync(g.col, col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, ctx->stream));
+    if (directed) {
+      BCG_CUDA(cudaMemcpyAsync(g.rp_in, rp_in.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice,
+                               ctx->stream));
+      if (nnz > 0)
+        BCG_CUDA(cudaMemcpyAsync(g.col_in, col_in.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    }
     if (flags & BC_VALIDATE) {
       unsigned *d_bad = ctx->ws.err.as<unsigned>() + 1;
       BCG_CUDA(cudaMemsetAsync(d_bad, 0, 4, ctx->stream));
       {
         LaunchScope ls(ctx, F_MISC);
-        k_validate<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, g.rp, g.col, nnz, d_bad);
+        k_validate<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, g.rp, g.col, nnz, directed ? 0 : 1, d_bad);
       }
       unsigned *h = static_cast<unsigned *>(ctx->ws.pinned);
       BCG_CUDA(cudaMemcpyAsync(h, d_bad, 4, cudaMemcpyDeviceToHost, ctx->stream));
@@ -994,6 +1043,10 @@ bc_status bc_graph_load_csr(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, cons
   } catch (...) {
     cudaFree(g.rp);
     cudaFree(g.col);
+    if (directed) {
+      cudaFree(g.rp_in);
+      cudaFree(g.col_in);
+    }
     throw;
   }
   const bc_graph h = ctx->next_handle++;
@@ -1013,6 +1066,10 @@ bc_status bc_graph_free(bc_ctx *ctx, bc_graph g) {
   forget_key_meta(it->second.rp);
   cudaFree(it->second.rp);
   cudaFree(it->second.col);
+  if (it->second.directed) {
+    cudaFree(it->second.rp_in);
+    cudaFree(it->second.col_in);
+  }
   ctx->graphs.erase(it);
   BC_GUARD_END
 }
@@ -1108,6 +1165,7 @@ bc_status bc_adaptive_pairs(bc_ctx *ctx, bc_graph g, const int32_t *targets, int
   BC_GUARD_BEGIN
   const Graph &gr = get_graph(ctx, g);
   if (gr.n < 2) fail(BC_E_INVALID, "pair sampling needs n >= 2");
+  if (gr.directed) fail(BC_E_INVALID, "pair sampling needs an undirected graph");
   if (!(c >= 1.0) || !(c < 1e300)) fail(BC_E_INVALID, "c must be >= 1 and finite");
   if (!(threshold_scale > 0.0) || !(threshold_scale < 1e300)) fail(BC_E_INVALID, "threshold_scale must be > 0");
   if (cap < 1 || cap > ((int64_t)1 << 32)) fail(BC_E_INVALID, "cap must be in [1, 2^32]");

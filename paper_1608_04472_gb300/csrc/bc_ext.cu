@@ -48,7 +48,8 @@ __global__ void k_x_init(uint64_t mask, const int32_t *__restrict__ sources, uin
 }
 
 // Settles level d: entries [off[d], ctr) take their lane masks from nm, record
-// the distance and pull sigma from the previous level in CSR order. Block 0
+// the distance and pull sigma from the previous level in the CSR order of the
+// in-neighbours (rp/col here are the in-neighbour CSR). Block 0
 // also closes the level (off[d+1] = ctr).
 __global__ void __launch_bounds__(XTHREADS)
 k_x_settle(int d, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
@@ -291,7 +292,7 @@ int ext_forward(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, uint64_t 
     for (int k = 0; k < XCHUNK; ++k, ++d) {
       {
         LaunchScope ls(ctx, F_XFWD);
-        k_x_settle<<<blocks, XTHREADS, 0, st>>>(d, g.rp, g.col, off, ctr, ws.x_list.as<int32_t>(),
+        k_x_settle<<<blocks, XTHREADS, 0, st>>>(d, g.rp_in, g.col_in, off, ctr, ws.x_list.as<int32_t>(),
                                                 ws.x_lmask.as<uint64_t>(), ws.x_nm.as<uint64_t>(),
                                                 ws.x_vis.as<uint64_t>(), ws.x_dist.as<int32_t>(),
                                                 ws.x_m.as<double>(), ws.x_e.as<int32_t>());

@@ -46,8 +46,13 @@ struct Graph {
   int32_t hub = 0;                 // a vertex of maximum degree
   uint8_t *key = nullptr;          // device [n]: min(d(hub, v), 254), 255 if unreachable (lazy)
   int32_t *order = nullptr;        // device [n]: all vertices sorted by key (lazy, exact BC)
-  int32_t *rp = nullptr;   // device row_ptr[n+1]
+  int32_t *rp = nullptr;   // device row_ptr[n+1] (out-neighbours)
   int32_t *col = nullptr;  // device col[nnz]
+  // in-neighbour CSR, over which path counts are pulled: a separate device copy
+  // for a directed graph, the same arrays as rp/col for an undirected one
+  bool directed = false;
+  int32_t *rp_in = nullptr;
+  int32_t *col_in = nullptr;
 };
 
 // Kernel families timed separately when profiling is on.

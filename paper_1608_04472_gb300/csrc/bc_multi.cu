@@ -37,8 +37,10 @@ constexpr int MWARPS = MT / 32;
 constexpr int MHEAVY = 32;  // vertices above this degree are processed by a whole warp
 
 struct MGraph {
-  const int32_t *rp;
+  const int32_t *rp;     // out-neighbours: discovery, successors in the backward pass
   const int32_t *col;
+  const int32_t *rp_in;  // in-neighbours: predecessors whose counts are pulled
+  const int32_t *col_in; // (the same arrays as rp/col for an undirected graph)
   int32_t n;
   int32_t pad;
   int64_t k;
@@ -172,13 +174,14 @@ __device__ int lane_forward(const MGraph &G, int32_t s, int32_t dest, const MScr
     const int nt = *s_tail;
     if (nt == e) break;  // no vertex at distance L+1
     if (tid == 0) S.lo[L + 2] = nt;
-    // exact counts of level L+1, pulled from level L (order-free integer sums)
-    for_level(S, rp, e, nt, [&](int32_t w, int beg, int end, bool coop) {
+    // exact counts of level L+1, pulled from the in-neighbours at level L
+    // (order-free integer sums)
+    for_level(S, G.rp_in, e, nt, [&](int32_t w, int beg, int end, bool coop) {
       uint64_t sum = 0ull;
       bool ov = false;
       const int step = coop ? 32 : 1;
       for (int j = beg + (coop ? lane : 0); j < end; j += step) {
-        const int32_t u = col[j];
+        const int32_t u = G.col_in[j];
         if (S.dist[u] == L) {
           const uint64_t t = sum + S.sig[u];
           ov |= t < sum;
@@ -206,11 +209,12 @@ __device__ int lane_forward(const MGraph &G, int32_t s, int32_t dest, const MScr
   return L;
 }
 
-// The counts of levels 1..L again, in the extended form (pull order).
+// The counts of levels 1..L again, in the extended form (pull order over the
+// in-neighbours).
 __device__ void lane_extend(const MGraph &G, int32_t s, const MScratch &S, int L) {
   const int tid = threadIdx.x, lane = tid & 31;
-  const int32_t *__restrict__ rp = G.rp;
-  const int32_t *__restrict__ col = G.col;
+  const int32_t *__restrict__ rp = G.rp_in;
+  const int32_t *__restrict__ col = G.col_in;
   if (tid == 0) {
     S.sig[s] = (uint64_t)__double_as_longlong(1.0);
     S.sige[s] = 0;
@@ -532,6 +536,8 @@ static void build_plan(bc_ctx *ctx, MultiPlan &P, const std::vector<const Graph 
   for (int g = 0; g < G; ++g) {
     mg[g].rp = gs[g]->rp;
     mg[g].col = gs[g]->col;
+    mg[g].rp_in = gs[g]->rp_in;
+    mg[g].col_in = gs[g]->col_in;
     mg[g].n = gs[g]->n;
     mg[g].pad = 0;
     mg[g].k = P.k[g];
@@ -621,6 +627,8 @@ void lane_sink(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, int count,
   MGraph G{};
   G.rp = g.rp;
   G.col = g.col;
+  G.rp_in = g.rp_in;
+  G.col_in = g.col_in;
   G.n = g.n;
   {
     LaunchScope ls(ctx, F_XFWD);
@@ -650,6 +658,8 @@ void lane_targets(bc_ctx *ctx, const Graph &g, const int32_t *d_targets, int T, 
   MGraph G{};
   G.rp = g.rp;
   G.col = g.col;
+  G.rp_in = g.rp_in;
+  G.col_in = g.col_in;
   G.n = g.n;
   LaunchScope ls(ctx, F_XFWD);
   k_lane_targets<<<ncta, MT, 0, st>>>(G, d_targets, T, Tp, L.next.as<unsigned>(), L.scratch.as<unsigned char>(), stride,
@@ -671,6 +681,8 @@ uint64_t lane_pairs(bc_ctx *ctx, const Graph &g, int count) {
   MGraph G{};
   G.rp = g.rp;
   G.col = g.col;
+  G.rp_in = g.rp_in;
+  G.col_in = g.col_in;
   G.n = g.n;
   {
     LaunchScope ls(ctx, F_PAIR);

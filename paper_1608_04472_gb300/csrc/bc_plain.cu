@@ -86,7 +86,8 @@ k_ptd(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, const int
 }
 
 __global__ void __launch_bounds__(PTHREADS)
-k_pbu(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t level,
+k_pbu(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ rp_in,
+      const int32_t *__restrict__ col_in, int32_t level,
       int32_t *__restrict__ dist, uint64_t *__restrict__ sigma, int32_t *__restrict__ queue_out,
       PlainCtr *__restrict__ ctr, unsigned *__restrict__ err, unsigned long long *__restrict__ cnt) {
   const int lane = threadIdx.x & 31;
@@ -96,10 +97,10 @@ k_pbu(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col
   unsigned long long edges = 0ull, tri = 0ull, rch = 0ull;
   for (int32_t v = warp; v < n; v += nwarps) {
     if (dist[v] != -1) continue;
-    const int beg = rp[v], end = rp[v + 1];
+    const int beg = rp_in[v], end = rp_in[v + 1];  // predecessors are in-neighbours
     uint64_t s = 0ull;
     for (int j = beg + lane; j < end; j += 32) {
-      const int32_t w = col[j];
+      const int32_t w = col_in[j];
       if (dist[w] == level) {
         const uint64_t x = sigma[w];
         const uint64_t t = s + x;
@@ -120,7 +121,7 @@ k_pbu(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col
       sigma[v] = s;
       const int pos = atomicAdd(&ctr->qtail, 1);
       queue_out[pos] = v;
-      edges += (unsigned long long)(end - beg);
+      edges += (unsigned long long)(rp[v + 1] - rp[v]);
       ++rch;
     }
   }
@@ -232,7 +233,7 @@ static int plain_forward(bc_ctx *ctx, const Graph &g, const int32_t *d_src, cons
     BCG_CUDA(cudaMemsetAsync(&ctr->next_edges, 0, sizeof(unsigned long long), st));
     if (frontier_edges * ALPHA > unexplored) {
       LaunchScope ls(ctx, F_PFWD);
-      k_pbu<<<blocks, PTHREADS, 0, st>>>(g.n, g.rp, g.col, level, dist, sigma, queue, ctr, ws.err.as<unsigned>(),
+      k_pbu<<<blocks, PTHREADS, 0, st>>>(g.n, g.rp, g.rp_in, g.col_in, level, dist, sigma, queue, ctr, ws.err.as<unsigned>(),
                                          ws.cnt.as<unsigned long long>());
     } else {
       LaunchScope ls(ctx, F_PFWD);
@@ -403,7 +404,7 @@ static bc_status run(const int32_t *rp, const int32_t *col, int32_t n, int64_t n
       explored += frontier_edges;
       if (cudaMemsetAsync(&ctr->next_edges, 0, sizeof(unsigned long long), st) != cudaSuccess) return BC_E_DEVICE;
       if (frontier_edges * ALPHA > nnz - explored) {
-        k_pbu<<<blocks, PTHREADS, 0, st>>>(n, rp, col, level, dist, sigma, queue, ctr, err, cnt);
+        k_pbu<<<blocks, PTHREADS, 0, st>>>(n, rp, rp, col, level, dist, sigma, queue, ctr, err, cnt);
       } else {
         const int nb = std::max(1, std::min(blocks, (qe - qb + 7) / 8));
         k_ptd<<<nb, PTHREADS, 0, st>>>(rp, col, queue, qb, qe, level, dist, sigma, queue, ctr, err, cnt);

@@ -41,6 +41,16 @@ def test_binding_wraps_every_declared_symbol(lib_path):
     assert sorted(mod.EXPORTED) == declared_functions()
 
 
+def test_binding_constants_match_header():
+    from paper_1608_04472_gb300 import capi as mod
+    text = open(HEADER).read()
+    defs = dict(re.findall(r"#define\s+(BC_[A-Z_]+)\s+(-?\d+)u?\b", text))
+    names = ["BC_UNDIRECTED", "BC_VALIDATE", "BC_DIRECTED", "BC_STOPPED", "BC_CAPPED"]
+    for name in names:
+        assert name in defs, name
+        assert getattr(mod, name) == int(defs[name]), name
+
+
 def test_null_context_is_rejected(lib_path):
     lib = ctypes.CDLL(lib_path)
     lib.bc_set_batch_width.restype = ctypes.c_int32
