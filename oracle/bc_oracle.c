@@ -34,7 +34,8 @@
  *       in which some count exceeds 2^64-1 is recomputed in the extended
  *       form (R17) and the call reports that it happened (return value 1).
  *       For pairs: a target's counts are extended when its BFS overflows; a
- *       pair's sigma_st when a count at distance <= d(s,t) from s overflows.
+ *       pair's sigma_st when sigma_st itself is 2^64 or more (a property of
+ *       the pair alone, whatever other counts of the BFS from s do).
  *   R17 extended form: sigma and coef are doubles with an unbounded exponent
  *       (value = m * 2^e, m in [1,2)); every operation rounds once to 53 bits
  *       as IEEE round-to-nearest-even would with no exponent limit. Path
@@ -215,25 +216,28 @@ double orc_exact_sum(const double *x, int64_t count) {
  * order[0..*nreached) lists reached vertices by non-decreasing distance.
  * Returns ORC_SIGMA_OVERFLOW if some sigma does not fit in 64 bits.
  */
-static int orc_bfs_depth(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
-                         int32_t *dist, uint64_t *sigma, int32_t *order, int32_t *nreached,
-                         int32_t *ovf_depth);
+static int orc_bfs_big(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
+                       int32_t *dist, uint64_t *sigma, int32_t *order, int32_t *nreached,
+                       uint8_t *big);
 
 int orc_bfs(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
             int32_t *dist, uint64_t *sigma, int32_t *order, int32_t *nreached) {
-  int32_t depth;
-  return orc_bfs_depth(n, row_ptr, col, s, dist, sigma, order, nreached, &depth);
+  return orc_bfs_big(n, row_ptr, col, s, dist, sigma, order, nreached, NULL);
 }
 
-/* orc_bfs that also reports the smallest distance of a vertex whose count
- * exceeded 2^64-1 (*ovf_depth, -1 when none): levels are processed in order,
- * so the first overflow detected is at the smallest such distance. */
-static int orc_bfs_depth(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
-                         int32_t *dist, uint64_t *sigma, int32_t *order, int32_t *nreached,
-                         int32_t *ovf_depth) {
+/* orc_bfs that also marks (big != NULL) every vertex whose count is 2^64 or
+ * more: big[w] = 1 when a predecessor's count is, or when adding a
+ * predecessor's count carries out of 64 bits (all terms are non-negative, so
+ * a carry means the exact sum is at least 2^64); sigma[w] is then
+ * meaningless. A vertex is popped only after all its predecessors, so its
+ * mark is final when it is propagated. */
+static int orc_bfs_big(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s,
+                       int32_t *dist, uint64_t *sigma, int32_t *order, int32_t *nreached,
+                       uint8_t *big) {
   int overflow = 0;
-  *ovf_depth = -1;
   for (int32_t v = 0; v < n; ++v) { dist[v] = -1; sigma[v] = 0; }
+  if (big)
+    for (int32_t v = 0; v < n; ++v) big[v] = 0;
   int32_t head = 0, tail = 0;
   dist[s] = 0;
   sigma[s] = 1;
@@ -247,9 +251,10 @@ static int orc_bfs_depth(int32_t n, const int32_t *row_ptr, const int32_t *col, 
         uint64_t before = sigma[w];
         sigma[w] = before + sigma[v];
         if (sigma[w] < before) {
-          if (!overflow) *ovf_depth = dist[w];
           overflow = 1;
+          if (big) big[w] = 1;
         }
+        if (big && big[v]) big[w] = 1;
       }
     }
   }
@@ -630,17 +635,21 @@ static double orc_pair_y(int32_t v, int32_t s, int32_t t, const int32_t *dist_v,
   return orc_xf_to_double(orc_xf_div_xf(orc_xf_mul(a, b), c));
 }
 
-/* BFS from s for a pair (s, t): d(s,t) in *d_st, sigma_st exact in *sig_st, and
- * in the extended form (*xst, return 1) when a count at distance <= d(s,t)
- * exceeded 2^64-1. xsig/dist2 are n-long scratch. */
+/* BFS from s for a pair (s, t): d(s,t) in *d_st and sigma_st exact in
+ * *sig_st; when sigma_st itself is 2^64 or more (R11: the choice depends on
+ * sigma_st alone, not on other counts of the BFS) it is given in the extended
+ * form instead (*xst, return 1). dist2 (n int32) and xsig (n orc_xf) are
+ * scratch; dist2 also holds the n marks of orc_bfs_big until the extended
+ * BFS reuses it. */
 static int orc_pair_bfs(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t s, int32_t t,
                         int32_t *dist, uint64_t *sigma, int32_t *order, int32_t *dist2, orc_xf *xsig,
                         int32_t *d_st, uint64_t *sig_st, orc_xf *xst) {
-  int32_t nr, od;
-  int rc = orc_bfs_depth(n, row_ptr, col, s, dist, sigma, order, &nr, &od);
+  int32_t nr;
+  uint8_t *big = (uint8_t *)dist2;
+  orc_bfs_big(n, row_ptr, col, s, dist, sigma, order, &nr, big);
   *d_st = dist[t];
   *sig_st = sigma[t];
-  if (rc == ORC_SIGMA_OVERFLOW && dist[t] >= 0 && od <= dist[t]) {
+  if (dist[t] >= 0 && big[t]) {
     orc_bfs_xf(n, row_ptr, col, s, dist2, xsig, order, &nr);
     *xst = xsig[t];
     return 1;

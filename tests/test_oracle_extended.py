@@ -240,3 +240,30 @@ def test_pair_values_match_uint64_formula_where_counts_fit():
         exact = _grid_pair_exact(12, v, s, t)
         got = oracle.pair_value_of(g, v, s, t)
         assert abs(Fraction(got) - exact) <= exact * Fraction(2 * U)
+
+
+def test_pair_sigma_st_extended_only_when_it_is_2_to_64_or_more():
+    # R11 for pairs: the form of sigma_st depends on sigma_st alone. On a 90x90
+    # grid from the corner, t = (14, 81) has sigma_st = C(95, 14), between 2^53
+    # and 2^64, while counts in the middle of the same level, C(95, 47), exceed
+    # 2^64. sigma_st is then the exact count rounded once, and the value is the
+    # double formula on binomials; the pull-order extended sum of that count
+    # differs from RN(C(95, 14)) in the last place, so the test tells the two
+    # choices apart.
+    side = 90
+    g = gg.grid(side)
+    ti, tj = 14, 81
+    t = ti * side + tj
+    c = math.comb(ti + tj, ti)
+    assert 2**53 < c < 2**64 and math.comb(ti + tj, (ti + tj) // 2) >= 2**64
+    _, _, sm, se = oracle.dependencies_xf(g, 0)
+    assert Fraction(sm[t]) * Fraction(2) ** int(se[t]) != Fraction(float(c))
+    for vi, vj in [(7, 40), (3, 20), (10, 60), (1, 1), (13, 80), (0, 5), (14, 2)]:
+        a = float(math.comb(vi + vj, vi))
+        b = float(math.comb(ti - vi + tj - vj, ti - vi))
+        assert oracle.pair_value_of(g, vi * side + vj, 0, t) == (a * b) / float(c), (vi, vj)
+    # and when sigma_st itself is beyond 2^64 the extended form is used: far corner
+    far = g.n - 1
+    exact = _grid_pair_exact(side, 45 * side + 45, 0, far)
+    got = oracle.pair_value_of(g, 45 * side + 45, 0, far)
+    assert abs(Fraction(got) - exact) <= exact * Fraction(4 * 2 * side * U)
