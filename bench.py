@@ -235,28 +235,68 @@ def cpu_multicore(g, budget_s=10.0):
             "sample": f"{done} per-sample Brandes steps (source draws of R-MAT s20), one per thread"}
 
 
-def measure_pairs(pkg, torch, local, stream, cap=2048, T=256):
+def measure_pairs(pkg, torch, local, stream, caps=(2048, 16384), T=256):
     """Algorithm 1 on BA n=2,000,000 (4 edges per new vertex, seed 3) with 256
     degree-proportional targets and the paper's threshold c*n (c=1): every
-    target runs to the cap, so the run is `cap` pair draws plus one BFS per
-    target. Returns pair draws per second."""
+    target runs to the cap, so a run is `cap` pair draws plus one BFS per
+    target. Timed at two caps, so that the marginal cost of a pair draw is
+    separated from the targets' BFS, for the bidirectional pair search (the
+    default) and the one-sided BFS truncated at t's level (BCG_PAIR_ENGINE=1).
+    Returns pair draws per second."""
     import graphgen as gg
     g = gg.barabasi_albert(2_000_000, 4, 3)
     targets = gg.degree_targets(g, T, 3)
-    ctx = pkg.Context(local, batch_width=64, stream=stream.cuda_stream)
-    h = ctx.load_graph(g.row_ptr, g.col)
-    ctx.adaptive_pairs(h, targets[:8], 1.0, 64, 3, 1)  # warm-up
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    res = ctx.adaptive_pairs(h, targets, 1.0, cap, 3, 2)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    ctx.close()
-    return {"workload": f"BA n=2e6 m=4 seed 3, {T} degree-proportional targets, c=1 (threshold c*n), cap {cap}",
-            "pair_draws_per_s": cap / (ms / 1e3), "ms": ms, "targets_capped": int((res["status"] == 1).sum()),
-            "note": "includes one BFS per target (256) before the pair draws"}
+    out = {"workload": f"BA n=2e6 m=4 seed 3, {T} degree-proportional targets, c=1 (threshold c*n), "
+                       f"caps {caps[0]} and {caps[1]}"}
+    prev = os.environ.get("BCG_PAIR_ENGINE")
+    try:
+        for engine, name in (("0", "bidirectional"), ("1", "one_sided")):
+            os.environ["BCG_PAIR_ENGINE"] = engine  # read when the context is made
+            ctx = pkg.Context(local, batch_width=64, stream=stream.cuda_stream)
+            h = ctx.load_graph(g.row_ptr, g.col)
+            ctx.adaptive_pairs(h, targets[:8], 1.0, 64, 3, 1)  # warm-up
+            ms = []
+            for cap in caps:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                res = ctx.adaptive_pairs(h, targets, 1.0, cap, 3, 2)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                assert int((res["status"] == 1).sum()) == T  # every target ran to the cap
+            # per-family device time of the longer run (profiling on: not a timed number)
+            ctx.set_profiling(True)
+            ctx.reset_stats()
+            ctx.adaptive_pairs(h, targets, 1.0, caps[1], 3, 2)
+            st = ctx.stats()
+            # vertices in the two balls per pair: the counter also takes the
+            # target's BFS, so a one-draw run is subtracted
+            ctx.reset_stats()
+            ctx.adaptive_pairs(h, targets[:1], 1.0, 1, 3, 2)
+            r1 = ctx.stats()["reached"]
+            ctx.reset_stats()
+            ctx.adaptive_pairs(h, targets[:1], 1.0, caps[1], 3, 2)
+            rk = ctx.stats()["reached"]
+            ctx.set_profiling(False)
+            ctx.close()
+            out[name] = {"ms": ms, "pair_draws_per_s_with_targets": caps[0] / (ms[0] / 1e3),
+                         "pair_draws_per_s_marginal": (caps[1] - caps[0]) / ((ms[1] - ms[0]) / 1e3),
+                         "profile_cap": caps[1],
+                         "family_ms": {k: round(v["ms"], 2) for k, v in st["kernels"].items() if v["launches"]},
+                         "family_launches": {k: v["launches"] for k, v in st["kernels"].items() if v["launches"]}}
+            if engine == "0":
+                out[name]["ball_vertices_per_pair"] = (rk - r1) / (caps[1] - 1)
+    finally:
+        if prev is None:
+            os.environ.pop("BCG_PAIR_ENGINE", None)
+        else:
+            os.environ["BCG_PAIR_ENGINE"] = prev
+    out["pair_draws_per_s"] = out["bidirectional"]["pair_draws_per_s_with_targets"]
+    out["marginal_speedup"] = (out["bidirectional"]["pair_draws_per_s_marginal"]
+                               / out["one_sided"]["pair_draws_per_s_marginal"])
+    out["note"] = "with_targets includes one BFS per target (256) before the pair draws"
+    return out
 
 
 def measure_uneven(pkg, torch, local, stream, k=1024, reps=2, count=256, n_hi=200000):
@@ -380,6 +420,8 @@ def main():
                     help="also serve a 2D grid of this side in --serving-full (0: none)")
     ap.add_argument("--uneven-only", action="store_true",
                     help="run only the uneven multi-graph measurement and print its JSON object")
+    ap.add_argument("--pairs-only", action="store_true",
+                    help="run only the pair-sampling measurement (BA 2M, both pair engines) and print it")
     ap.add_argument("--uneven-count", type=int, default=256, help="graphs in the uneven workload")
     ap.add_argument("--uneven-nmax", type=int, default=200000, help="largest graph size in the uneven workload")
     args = ap.parse_args()
@@ -403,6 +445,12 @@ def main():
         r["graph_generation_s"] = gen_s
         ctx.close()
         print(json.dumps(r))
+        return 0
+    if args.pairs_only:
+        import torch
+        import paper_1608_04472_gb300 as pkg
+        torch.cuda.set_device(0)
+        print(json.dumps(measure_pairs(pkg, torch, 0, torch.cuda.current_stream())))
         return 0
     if args.uneven_only:
         import torch

@@ -212,40 +212,46 @@ __global__ void k_finalize_vertices(int32_t n, const Acc *__restrict__ acc, doub
 }
 
 // y = sigma_sv*sigma_vt/sigma_st if d(s,v)+d(v,t) = d(s,t) and v not in {s,t}
-// (Algorithm 1 with the pair-dependency of Eq. 2), else 0.
+// (Algorithm 1 with the pair-dependency of Eq. 2), else 0, for target j
+// (blockIdx.x) and pair lane i of a window of `count` lanes; vals[j][vstride].
 // texp/tx (may be null): exponents [n][tstride] and flags [T] of targets whose
 // counts are in the extended form (tsig then holds mantissa bits); pexp and
-// pxmask: the same for pair lanes.
+// pxf (per-lane flags, may be null): the same for pair lanes.
 __global__ void k_pair_values(int T, int count, const int32_t *__restrict__ targets,
                               const int32_t *__restrict__ ps, const int32_t *__restrict__ pt,
                               const int32_t *__restrict__ pd, const uint64_t *__restrict__ psig,
                               const int32_t *__restrict__ tdist, const uint64_t *__restrict__ tsig, int tstride,
                               const int32_t *__restrict__ texp, const int32_t *__restrict__ tx,
-                              const int32_t *__restrict__ pexp, uint64_t pxmask, double *__restrict__ vals) {
-  const int i = threadIdx.x;           // pair lane
-  const int j = blockIdx.x;            // target
-  if (j >= T || i >= 64) return;
+                              const int32_t *__restrict__ pexp, const int32_t *__restrict__ pxf,
+                              double *__restrict__ vals, int vstride) {
+  const int i = blockIdx.y * blockDim.x + threadIdx.x;  // pair lane
+  const int j = blockIdx.x;                             // target
+  if (j >= T || i >= count) return;
   double y = 0.0;
-  if (i < count) {
-    const int32_t v = targets[j], s = ps[i], t = pt[i];
-    const int32_t dst = pd[i];
-    const uint64_t sst = psig[i];
-    if (v != s && v != t && sst != 0ull && dst >= 0) {
-      const size_t is = (size_t)s * tstride + j, it = (size_t)t * tstride + j;
-      const int32_t ds = tdist[is], dt = tdist[it];
-      if (ds >= 0 && dt >= 0 && ds + dt == dst) {
-        const bool vx = tx && tx[j], px = (pxmask >> i) & 1ull;
-        if (vx || px) {
-          y = pair_y(vx, tsig[is], vx ? texp[is] : 0, tsig[it], vx ? texp[it] : 0, px, sst, px ? pexp[i] : 0);
-        } else {
-          const double a = sigma_to_double(tsig[is]);
-          const double b = sigma_to_double(tsig[it]);
-          y = __ddiv_rn(__dmul_rn(a, b), sigma_to_double(sst));
-        }
+  const int32_t v = targets[j], s = ps[i], t = pt[i];
+  const int32_t dst = pd[i];
+  const uint64_t sst = psig[i];
+  if (v != s && v != t && sst != 0ull && dst >= 0) {
+    const size_t is = (size_t)s * tstride + j, it = (size_t)t * tstride + j;
+    const int32_t ds = tdist[is], dt = tdist[it];
+    if (ds >= 0 && dt >= 0 && ds + dt == dst) {
+      const bool vx = tx && tx[j], px = pxf && pxf[i];
+      if (vx || px) {
+        y = pair_y(vx, tsig[is], vx ? texp[is] : 0, tsig[it], vx ? texp[it] : 0, px, sst, px ? pexp[i] : 0);
+      } else {
+        const double a = sigma_to_double(tsig[is]);
+        const double b = sigma_to_double(tsig[it]);
+        y = __ddiv_rn(__dmul_rn(a, b), sigma_to_double(sst));
       }
     }
   }
-  vals[(size_t)j * 64 + i] = y;
+  vals[(size_t)j * vstride + i] = y;
+}
+
+// pxf[i] = bit i of mask, i < c
+__global__ void k_mask_flags(int c, uint64_t mask, int32_t *__restrict__ pxf) {
+  const int i = threadIdx.x;
+  if (i < c) pxf[i] = (int32_t)((mask >> i) & 1ull);
 }
 
 __global__ void k_transpose_delta(int32_t n, int count, const double *__restrict__ delta_lm,
@@ -668,14 +674,23 @@ void target_bfs(bc_ctx *ctx, const Graph &g, const int32_t *d_targets, int T, in
 
 // One batch of pair lanes (ws.sources -> ws.targets); returns the lanes whose
 // sigma_st is in the extended form (ws.pair_exp holds their exponents).
+// The one-sided form (ctx->pair_engine = 1) runs the BFS from s up to t's
+// level; a lane where a count of that BFS overflowed may still have sigma_st
+// below 2^64, so such a batch is redone by the bidirectional search, which
+// decides the form of sigma_st exactly (R11).
 uint64_t pair_batch(bc_ctx *ctx, const Graph &g, int count) {
   Workspace &ws = ctx->ws;
-  if (batch_width(ctx) == 1) return plain_pair(ctx, g, ws.sources.as<int32_t>(), ws.targets.as<int32_t>()) ? 1ull : 0ull;
-  if (graph_depth_hint(ctx, g) > ctx->deep_levels) return lane_pairs(ctx, g, count);
-  batch_forward(ctx, g, count, true, OVF_EXTEND);
-  const uint64_t ovf = ws.last_ovf & lanes_of(count);
-  if (ovf) ext_pair_lanes(ctx, g, ws.sources.as<int32_t>(), ws.targets.as<int32_t>(), ovf);
-  return ovf;
+  if (ctx->pair_engine == 0) return pair_batch_bidir(ctx, g, count);
+  uint64_t ovf;
+  if (batch_width(ctx) == 1) {
+    ovf = plain_pair(ctx, g, ws.sources.as<int32_t>(), ws.targets.as<int32_t>()) ? 1ull : 0ull;
+  } else if (graph_depth_hint(ctx, g) > ctx->deep_levels) {
+    ovf = lane_pairs(ctx, g, count);
+  } else {
+    batch_forward(ctx, g, count, true, OVF_EXTEND);
+    ovf = ws.last_ovf & lanes_of(count);
+  }
+  return ovf ? pair_batch_bidir(ctx, g, count) : 0ull;
 }
 
 static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *targets, int32_t T, double c,
@@ -686,7 +701,7 @@ static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *target
   cudaStream_t st = ctx->stream;
   const int Tp = std::max(T, 1);
   // Per-target BFS (distance and sigma from every target), layout [n][Tp].
-  DevBuf tdist, tsig, texp, dtx;
+  DevBuf tdist, tsig, texp, dtx, wsrc, wdst, wpd, wpsig, wpexp, wpxf;
   tdist.ensure(n * Tp * 4);
   tsig.ensure(n * Tp * 8);
   ws.misc.ensure((size_t)Tp * 4 + 64);
@@ -700,47 +715,65 @@ static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *target
       BCG_CUDA(cudaMemcpyAsync(dtx.p, tx.data(), (size_t)Tp * 4, cudaMemcpyHostToDevice, st));
       d_tx = dtx.as<int32_t>();
     }
-    ws.tdelta.ensure((size_t)Tp * 64 * 8);
+    ws.tdelta.ensure((size_t)Tp * WMAX * 8);
     ScanState ss = make_scan(ctx, T);
     const double cn = c * (double)g.n;
     const int width = batch_width(ctx);
+    for (DevBuf *b : {&wsrc, &wdst, &wpd, &wpexp, &wpxf}) b->ensure(WMAX * 4);
+    wpsig.ensure(WMAX * 8);
     int32_t remaining = T;
-    for (int64_t i0 = 0; i0 < cap && remaining > 0; i0 += width) {
-      const int count = (int)std::min<int64_t>(width, cap - i0);
+    // windows of draws as in Bader's loop (64 .. 1024, growing with the draws
+    // made; one draw at a time with the plain width); the stop scan walks each
+    // window in draw order
+    for (int64_t i0 = 0; i0 < cap && remaining > 0;) {
+      const int64_t want = width == 1 ? 1 : std::max<int64_t>(64, i0 / 2);
+      const int W = (int)std::min<int64_t>(std::min<int64_t>(WMAX, want), cap - i0);
       {
         LaunchScope ls(ctx, F_DRAW);
-        k_draw_pairs<<<1, 64, 0, st>>>(seed, qid, (uint64_t)i0, count, g.n, ws.sources.as<int32_t>(),
-                                       ws.targets.as<int32_t>());
+        k_draw_pairs<<<(W + 63) / 64, 64, 0, st>>>(seed, qid, (uint64_t)i0, W, g.n, wsrc.as<int32_t>(),
+                                                   wdst.as<int32_t>());
       }
-      const uint64_t px = pair_batch(ctx, g, count);
+      if (ctx->pair_engine == 0) {
+        pair_lanes(ctx, g, wsrc.as<int32_t>(), wdst.as<int32_t>(), W, wpd.as<int32_t>(), wpsig.as<uint64_t>(),
+                   wpexp.as<int32_t>(), wpxf.as<int32_t>());
+      } else {
+        for (int b = 0; b < W; b += 64) {
+          const int cnt = std::min(64, W - b);
+          BCG_CUDA(cudaMemcpyAsync(ws.sources.p, wsrc.as<int32_t>() + b, (size_t)cnt * 4, cudaMemcpyDeviceToDevice, st));
+          BCG_CUDA(cudaMemcpyAsync(ws.targets.p, wdst.as<int32_t>() + b, (size_t)cnt * 4, cudaMemcpyDeviceToDevice, st));
+          const uint64_t px = pair_batch(ctx, g, cnt);
+          BCG_CUDA(cudaMemcpyAsync(wpd.as<int32_t>() + b, ws.pair_d.p, (size_t)cnt * 4, cudaMemcpyDeviceToDevice, st));
+          BCG_CUDA(cudaMemcpyAsync(wpsig.as<uint64_t>() + b, ws.pair_sig.p, (size_t)cnt * 8, cudaMemcpyDeviceToDevice,
+                                   st));
+          BCG_CUDA(cudaMemcpyAsync(wpexp.as<int32_t>() + b, ws.pair_exp.p, (size_t)cnt * 4, cudaMemcpyDeviceToDevice,
+                                   st));
+          LaunchScope ls(ctx, F_PAIR);
+          k_mask_flags<<<1, 64, 0, st>>>(cnt, px, wpxf.as<int32_t>() + b);
+        }
+      }
       if (T > 0) {
         LaunchScope ls(ctx, F_PAIR);
-        k_pair_values<<<T, 64, 0, st>>>(T, count, d_targets, ws.sources.as<int32_t>(), ws.targets.as<int32_t>(),
-                                        ws.pair_d.as<int32_t>(), ws.pair_sig.as<uint64_t>(), tdist.as<int32_t>(),
-                                        tsig.as<uint64_t>(), Tp, texp.as<int32_t>(), d_tx,
-                                        ws.pair_exp.as<int32_t>(), px, ws.tdelta.as<double>());
+        k_pair_values<<<dim3((unsigned)T, (unsigned)((W + 63) / 64)), 64, 0, st>>>(
+            T, W, d_targets, wsrc.as<int32_t>(), wdst.as<int32_t>(), wpd.as<int32_t>(), wpsig.as<uint64_t>(),
+            tdist.as<int32_t>(), tsig.as<uint64_t>(), Tp, texp.as<int32_t>(), d_tx, wpexp.as<int32_t>(),
+            wpxf.as<int32_t>(), ws.tdelta.as<double>(), W);
       }
       {
         LaunchScope ls(ctx, F_SCAN);
-        k_stop_scan<<<(T + 127) / 128, 128, 0, st>>>(T, count, ws.tdelta.as<double>(), ss, i0, cn, scale, 64);
+        k_stop_scan<<<(T + 127) / 128, 128, 0, st>>>(T, W, ws.tdelta.as<double>(), ss, i0, cn, scale, W);
       }
       remaining = read_remaining(ctx, ss);
+      i0 += W;
     }
     check_err_bits(ctx);
     copy_scan_out(ctx, T, ss, (double)g.n * (double)(g.n - 1), est, k, S, status);
   } catch (...) {
     cudaStreamSynchronize(st);
-    tdist.release();
-    tsig.release();
-    texp.release();
-    dtx.release();
+    for (DevBuf *b : {&tdist, &tsig, &texp, &dtx, &wsrc, &wdst, &wpd, &wpsig, &wpexp, &wpxf}) b->release();
     throw;
   }
   sync(ctx);
-  tdist.release();
-  tsig.release();
-  texp.release();
-  dtx.release();
+  for (DevBuf *b : {&tdist, &tsig, &texp, &dtx, &wsrc, &wdst, &wpd, &wpsig, &wpexp, &wpxf}) b->release();
 }
 
 // Per-source outputs. Sources whose counts exceed 2^64-1 are computed in the
@@ -882,6 +915,7 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
     if (const char *pm = std::getenv("BCG_PK_MAXL")) ctx->pk_maxl = std::atoi(pm);
     if (const char *pc = std::getenv("BCG_PK_MINCNT")) ctx->pk_mincnt = std::atoi(pc);
     if (const char *mc = std::getenv("BCG_MULTI_CAP")) ctx->multi_cap = std::atoi(mc);
+    if (const char *pe = std::getenv("BCG_PAIR_ENGINE")) ctx->pair_engine = std::atoi(pe) == 1 ? 1 : 0;
     BCG_CUDA(cudaMallocHost(&ctx->ws.pinned, 4096));
     ctx->ws.enable.ensure(64);   // [0] lane enable mask, [1] pair continuation word
     ctx->ws.sources.ensure(64 * 4);
@@ -910,6 +944,7 @@ void bc_destroy(bc_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     forget_multi_plan(ctx);
     forget_lane_scratch(ctx);
+    forget_bidir_scratch(ctx);
     resolve_events(ctx);
     for (auto &kv : ctx->graphs) {
       forget_heavy_meta(kv.second.rp);

@@ -163,6 +163,9 @@ struct bc_ctx {
   // multi-graph split: hub eccentricity above which a graph goes to the
   // persistent kernel, and its CTAs per SM while the batched engine runs beside
   int32_t deep_levels = 32, multi_cap = 4;
+  // pair lanes of Algorithm 1: 0 = bidirectional search (bc_bidir.cu), 1 = the
+  // one-sided BFS from s truncated at t's level (kept for comparison)
+  int32_t pair_engine = 0;
 };
 
 namespace bcg {
@@ -255,6 +258,17 @@ uint64_t lane_pairs(bc_ctx *ctx, const Graph &g, int count);
 int graph_depth_hint(bc_ctx *ctx, const Graph &g);
 void uniform_one(bc_ctx *ctx, const Graph &g, int64_t k, uint64_t seed, uint64_t qid, double *out);
 bool multi_plan_uses_graph(bc_ctx *ctx, bc_graph g);
+
+// ---- bidirectional pair search (bc_bidir.cu) ----
+// d(s,t) and sigma_st for pair lanes [0, count) (device arrays d_src, d_dst)
+// into pd / psig / pexp; pxf[i] = 1 where sigma_st >= 2^64 (then in the extended
+// form: psig holds mantissa bits, pexp the exponent). Returns those lanes. Uses
+// ws.sources / ws.targets / ws.pair_* as scratch when it returns any.
+std::vector<int32_t> pair_lanes(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dst, int count,
+                                int32_t *pd, uint64_t *psig, int32_t *pexp, int32_t *pxf);
+// pair_batch's bidirectional form (ws.sources / ws.targets kept).
+uint64_t pair_batch_bidir(bc_ctx *ctx, const Graph &g, int count);
+void forget_bidir_scratch(bc_ctx *ctx);
 
 // ---- pair sampling helpers (bc_capi.cu), shared with the server ----
 void target_bfs(bc_ctx *ctx, const Graph &g, const int32_t *d_targets, int T, int Tp, int32_t *tdist,
