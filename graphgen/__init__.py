@@ -63,6 +63,9 @@ def _load():
         lib.gg_degree_targets.restype = ctypes.c_int
         lib.gg_degree_targets.argtypes = [ctypes.c_int32, _i32p, ctypes.c_int32,
                                           ctypes.c_uint64, _i32p]
+        lib.gg_edge_lengths.restype = None
+        lib.gg_edge_lengths.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32)]
         lib.gg_rand.restype = ctypes.c_uint64
         lib.gg_rand.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
         _lib = lib
@@ -278,3 +281,16 @@ def degree_targets(g: Graph, T: int, seed: int) -> np.ndarray:
 def rand64(seed: int, stream: int, idx: int) -> int:
     """The generator's 64-bit hash (exposed for tests and derived seeds)."""
     return int(_load().gg_rand(seed, stream, idx))
+
+
+def edge_lengths(g: Graph, lo: int, hi: int, seed: int, symmetric: bool = True) -> np.ndarray:
+    """uint32 lengths in [lo, hi], one per CSR entry, from a hash of the edge
+    (the unordered pair when symmetric, so both rows of an undirected edge
+    agree) and the seed."""
+    if not (1 <= lo <= hi < 2**32):
+        raise ValueError("need 1 <= lo <= hi < 2^32")
+    lib = _load()
+    w = np.empty(max(1, g.col.shape[0]), np.uint32)
+    lib.gg_edge_lengths(g.n, _p(g.row_ptr), _p(g.col) if g.col.size else _p(np.zeros(1, np.int32)), lo, hi,
+                        seed, 1 if symmetric else 0, w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    return w[: g.col.shape[0]]

@@ -243,3 +243,20 @@ int gg_degree_targets(int32_t n, const int32_t *row_ptr, int32_t T, uint64_t see
   }
   return GG_OK;
 }
+
+/* ------------------------------------------------------- edge lengths -- */
+
+/* Integer lengths in [lo, hi] for the CSR entries (edge u -> col[j]): a hash of
+ * (seed, the unordered pair {u, v} when symmetric, else the ordered pair), so
+ * both rows of an undirected edge get the same length. */
+void gg_edge_lengths(int32_t n, const int32_t *row_ptr, const int32_t *col, uint32_t lo, uint32_t hi,
+                     uint64_t seed, int symmetric, uint32_t *w) {
+  const uint64_t span = (uint64_t)hi - (uint64_t)lo + 1u;
+  for (int32_t u = 0; u < n; ++u)
+    for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
+      const int32_t v = col[j];
+      const int32_t a = (symmetric && v < u) ? v : u, b = (symmetric && v < u) ? u : v;
+      const uint64_t key = (uint64_t)(uint32_t)a * (uint64_t)(uint32_t)n + (uint64_t)(uint32_t)b;
+      w[j] = lo + (uint32_t)gg_below(gg_rand(seed, 7u, key), span);
+    }
+}

@@ -27,6 +27,7 @@ CAPPED = 1
 SIGMA_OVERFLOW = 1
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 _f64p = ctypes.POINTER(ctypes.c_double)
@@ -68,6 +69,12 @@ def _load():
                                                       _f64p, _i64p]),
         "orc_xf_add_pair": (None, [_f64, _i64, _f64, _i64, _f64p, _i64p]),
         "orc_pair_value_of": (_f64, [_i32, _i32p, _i32p, _i32, _i32, _i32]),
+        "orc_source_dependencies_w": (ctypes.c_int, [_i32, _i32p, _i32p, _u32p, _i32, _f64p, _i64p, _u64p,
+                                                     _f64p, _i64p]),
+        "orc_exact_bc_w": (ctypes.c_int, [_i32, _i32p, _i32p, _u32p, _f64p]),
+        "orc_uniform_sources_w": (ctypes.c_int, [_i32, _i32p, _i32p, _u32p, _i64, _u64, _u64, _f64p]),
+        "orc_adaptive_sources_w": (ctypes.c_int, [_i32, _i32p, _i32p, _u32p, _i32, _i32p, _f64, _i64, _u64,
+                                                  _u64, _f64p, _i64p, _f64p, _i32p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -242,3 +249,62 @@ def pair_sequence(g, v: int, seed: int, qid: int, i0: int, count: int):
     _check(_load().orc_pair_sequence(n, _p(rp, _i32p), _p(col, _i32p), v, seed, qid, i0, count,
                                      _p(y, _f64p), _p(s, _i32p), _p(t, _i32p)))
     return y, s, t
+
+
+# ---- weighted graphs: positive integer lengths w[j] of CSR entry j (Sec. 3, R19) ----
+
+def _wts(g, w):
+    w = np.ascontiguousarray(w, dtype=np.uint32)
+    if w.shape[0] != np.asarray(g.col).shape[0]:
+        raise ValueError("one length per CSR entry")
+    return w if w.size else np.ones(1, np.uint32)
+
+
+def dependencies_w(g, w, s: int):
+    """One source on a weighted graph: (delta, dist int64, sigma u64, overflow,
+    sigma mantissa, sigma exponent). With overflow the sample is in the
+    extended form and sigma holds UINT64_MAX at reached vertices."""
+    n, rp, col = _csr(g)
+    wt = _wts(g, w)
+    delta = np.empty(n, np.float64)
+    dist = np.empty(n, np.int64)
+    sig = np.empty(n, np.uint64)
+    sm = np.empty(n, np.float64)
+    se = np.empty(n, np.int64)
+    rc = _check(_load().orc_source_dependencies_w(n, _p(rp, _i32p), _p(col, _i32p), _p(wt, _u32p), s,
+                                                  _p(delta, _f64p), _p(dist, _i64p), _p(sig, _u64p),
+                                                  _p(sm, _f64p), _p(se, _i64p)))
+    return delta, dist, sig, rc == SIGMA_OVERFLOW, sm, se
+
+
+def exact_bc_w(g, w) -> np.ndarray:
+    n, rp, col = _csr(g)
+    wt = _wts(g, w)
+    bc = np.empty(n, np.float64)
+    _check(_load().orc_exact_bc_w(n, _p(rp, _i32p), _p(col, _i32p), _p(wt, _u32p), _p(bc, _f64p)))
+    return bc
+
+
+def uniform_sources_w(g, w, k: int, seed: int, qid: int) -> np.ndarray:
+    n, rp, col = _csr(g)
+    wt = _wts(g, w)
+    est = np.empty(n, np.float64)
+    _check(_load().orc_uniform_sources_w(n, _p(rp, _i32p), _p(col, _i32p), _p(wt, _u32p), k, seed, qid,
+                                         _p(est, _f64p)))
+    return est
+
+
+def adaptive_sources_w(g, w, targets, c: float, cap: int, seed: int, qid: int):
+    n, rp, col = _csr(g)
+    wt = _wts(g, w)
+    tg = np.ascontiguousarray(targets, dtype=np.int32)
+    T = tg.size
+    est = np.empty(T, np.float64)
+    k = np.empty(T, np.int64)
+    S = np.empty(T, np.float64)
+    st = np.empty(T, np.int32)
+    tgp = tg if T else np.zeros(1, np.int32)
+    _check(_load().orc_adaptive_sources_w(n, _p(rp, _i32p), _p(col, _i32p), _p(wt, _u32p), T, _p(tgp, _i32p),
+                                          c, cap, seed, qid, _p(est, _f64p), _p(k, _i64p), _p(S, _f64p),
+                                          _p(st, _i32p)))
+    return dict(est=est, k=k, S=S, status=st)

@@ -511,17 +511,220 @@ int orc_source_dependencies_xf(int32_t n, const int32_t *row_ptr, const int32_t 
   return ORC_OK;
 }
 
+/* ------------------------------------------ weighted graphs (Sec. 3, R19) -- */
+/*
+ * Edge lengths are positive integers: w[j] >= 1 is the length of CSR entry j
+ * (edge u -> col[j]); an undirected graph lists each edge in both rows with
+ * the same length. Distances are exact int64 sums (-1: unreachable). u is in
+ * P_s(v) (Def. 3) when (u, v) is an edge and d(s,u) + w(u,v) = d(s,v); since
+ * lengths are >= 1 a predecessor is strictly closer to s, so vertices of equal
+ * distance never depend on each other. With unit lengths every function
+ * below equals its unweighted counterpart.
+ */
+
+/* Dijkstra from s (Sec. 3 step 1): a binary heap of (distance, vertex) with
+ * lazy deletion (a popped entry whose distance is no longer current is
+ * skipped). order[0..*nreached) lists the settled vertices by non-decreasing
+ * distance. */
+static int orc_dijkstra(int32_t n, const int32_t *row_ptr, const int32_t *col, const uint32_t *w,
+                        int32_t s, int64_t *dist, int32_t *order, int32_t *nreached) {
+  int64_t m = row_ptr[n];
+  size_t cap = (size_t)m + 1;
+  int64_t *hk = (int64_t *)malloc(sizeof(int64_t) * cap);
+  int32_t *hv = (int32_t *)malloc(sizeof(int32_t) * cap);
+  uint8_t *done = (uint8_t *)calloc((size_t)(n ? n : 1), 1);
+  if (!hk || !hv || !done) { free(hk); free(hv); free(done); return ORC_E_NOMEM; }
+  for (int32_t v = 0; v < n; ++v) dist[v] = -1;
+  size_t hn = 0;
+  int32_t tail = 0;
+  dist[s] = 0;
+  hk[0] = 0; hv[0] = s; hn = 1;
+  while (hn > 0) {
+    /* pop the smallest (distance, vertex) */
+    int64_t dk = hk[0];
+    int32_t v = hv[0];
+    --hn;
+    if (hn > 0) {
+      int64_t xk = hk[hn];
+      int32_t xv = hv[hn];
+      size_t i = 0;
+      for (;;) {
+        size_t c = 2 * i + 1;
+        if (c >= hn) break;
+        if (c + 1 < hn && (hk[c + 1] < hk[c] || (hk[c + 1] == hk[c] && hv[c + 1] < hv[c]))) ++c;
+        if (hk[c] < xk || (hk[c] == xk && hv[c] < xv)) { hk[i] = hk[c]; hv[i] = hv[c]; i = c; }
+        else break;
+      }
+      hk[i] = xk; hv[i] = xv;
+    }
+    if (done[v] || dk != dist[v]) continue;
+    done[v] = 1;
+    order[tail++] = v;
+    for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) {
+      int32_t x = col[j];
+      int64_t nd = dk + (int64_t)w[j];
+      if (!done[x] && (dist[x] < 0 || nd < dist[x])) {
+        dist[x] = nd;
+        /* push (nd, x); each edge pushes at most once, so m + 1 entries suffice */
+        size_t i = hn++;
+        while (i > 0) {
+          size_t p = (i - 1) / 2;
+          if (hk[p] > nd || (hk[p] == nd && hv[p] > x)) { hk[i] = hk[p]; hv[i] = hv[p]; i = p; }
+          else break;
+        }
+        hk[i] = nd; hv[i] = x;
+      }
+    }
+  }
+  free(hk); free(hv); free(done);
+  *nreached = tail;
+  return ORC_OK;
+}
+
+/* In-neighbour lists with their lengths (edge u -> x lists u under x), each
+ * in increasing u. */
+static int orc_transpose_w(int32_t n, const int32_t *row_ptr, const int32_t *col, const uint32_t *w,
+                           int32_t **rp_in, int32_t **col_in, uint32_t **w_in) {
+  int64_t m = row_ptr[n];
+  int32_t *rp = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+  int32_t *cl = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m ? m : 1));
+  uint32_t *wl = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(m ? m : 1));
+  int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+  if (!rp || !cl || !wl || !fill) { free(rp); free(cl); free(wl); free(fill); return ORC_E_NOMEM; }
+  for (int64_t j = 0; j < m; ++j) rp[col[j] + 1]++;
+  for (int32_t v = 0; v < n; ++v) rp[v + 1] += rp[v];
+  for (int32_t v = 0; v < n; ++v) fill[v] = rp[v];
+  for (int32_t u = 0; u < n; ++u)
+    for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
+      int32_t k = fill[col[j]]++;
+      cl[k] = u;
+      wl[k] = w[j];
+    }
+  free(fill);
+  *rp_in = rp; *col_in = cl; *w_in = wl;
+  return ORC_OK;
+}
+
+/*
+ * One source on a weighted graph: Dijkstra, then sigma_sv = sum over P_s(v)
+ * of sigma_su for the settled vertices in order (exact uint64; pulled over
+ * the in-neighbours in CSR order), then Theorem 1 in non-increasing distance
+ * as in orc_dependencies (exact successor sums, rounded once). When a count
+ * exceeds 2^64-1 the sample is recomputed in the extended form (R11, R17:
+ * counts pulled over the in-neighbours in CSR order, successor coefficients
+ * added in CSR order) and ORC_SIGMA_OVERFLOW is returned; sigma_out then holds
+ * UINT64_MAX at every reached vertex. dist_out (int64), sigma_out, sigma_m and
+ * sigma_e (extended counts; RN of the exact count otherwise) may be NULL.
+ */
+int orc_source_dependencies_w(int32_t n, const int32_t *row_ptr, const int32_t *col, const uint32_t *w,
+                              int32_t s, double *delta, int64_t *dist_out, uint64_t *sigma_out,
+                              double *sigma_m, int64_t *sigma_e) {
+  size_t nn = (size_t)(n ? n : 1);
+  int64_t *dist = (int64_t *)malloc(sizeof(int64_t) * nn);
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * nn);
+  uint64_t *sigma = (uint64_t *)malloc(sizeof(uint64_t) * nn);
+  orc_xf *xs = (orc_xf *)malloc(sizeof(orc_xf) * nn);
+  orc_xf *xc = (orc_xf *)malloc(sizeof(orc_xf) * nn);
+  double *coef = (double *)malloc(sizeof(double) * nn);
+  orc_acc *acc = (orc_acc *)malloc(sizeof(orc_acc));
+  int32_t *rp_in = NULL, *col_in = NULL;
+  uint32_t *w_in = NULL;
+  int rc = ORC_E_NOMEM;
+  if (!dist || !order || !sigma || !xs || !xc || !coef || !acc) goto out;
+  if (orc_transpose_w(n, row_ptr, col, w, &rp_in, &col_in, &w_in) != ORC_OK) goto out;
+  int32_t nr = 0;
+  if (orc_dijkstra(n, row_ptr, col, w, s, dist, order, &nr) != ORC_OK) goto out;
+  int overflow = 0;
+  for (int32_t v = 0; v < n; ++v) sigma[v] = 0;
+  sigma[s] = 1;
+  for (int32_t idx = 1; idx < nr; ++idx) {
+    int32_t v = order[idx];
+    uint64_t sum = 0;
+    for (int32_t j = rp_in[v]; j < rp_in[v + 1]; ++j) {
+      int32_t u = col_in[j];
+      if (dist[u] >= 0 && dist[u] + (int64_t)w_in[j] == dist[v]) { /* u in P_s(v) */
+        uint64_t t = sum + sigma[u];
+        if (t < sum) overflow = 1;
+        sum = t;
+      }
+    }
+    sigma[v] = sum;
+  }
+  for (int32_t v = 0; v < n; ++v) delta[v] = 0.0;
+  if (!overflow) {
+    orc_acc_clear(acc);
+    for (int32_t idx = nr - 1; idx >= 0; --idx) {
+      int32_t v = order[idx];
+      for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) {
+        int32_t x = col[j];
+        if (dist[x] >= 0 && dist[x] == dist[v] + (int64_t)w[j]) orc_acc_add(acc, coef[x]); /* v in P_s(x) */
+      }
+      double sum = orc_acc_round(acc);
+      orc_acc_clear(acc);
+      double sv = (double)sigma[v];
+      double d = sv * sum;
+      if (v == s) d = 0.0;
+      delta[v] = d;
+      coef[v] = (1.0 + d) / sv;
+    }
+    for (int32_t v = 0; v < n; ++v) xs[v] = orc_xf_of_u64(sigma[v]);
+  } else {
+    for (int32_t v = 0; v < n; ++v) xs[v] = orc_xf_make(0.0, 0);
+    xs[s] = orc_xf_make(1.0, 0);
+    for (int32_t idx = 1; idx < nr; ++idx) {
+      int32_t v = order[idx];
+      orc_xf sum = orc_xf_make(0.0, 0);
+      for (int32_t j = rp_in[v]; j < rp_in[v + 1]; ++j) {
+        int32_t u = col_in[j];
+        if (dist[u] >= 0 && dist[u] + (int64_t)w_in[j] == dist[v]) sum = orc_xf_add(sum, xs[u]);
+      }
+      xs[v] = sum;
+    }
+    for (int32_t idx = nr - 1; idx >= 0; --idx) {
+      int32_t v = order[idx];
+      orc_xf sum = orc_xf_make(0.0, 0);
+      for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) {
+        int32_t x = col[j];
+        if (dist[x] >= 0 && dist[x] == dist[v] + (int64_t)w[j]) sum = orc_xf_add(sum, xc[x]);
+      }
+      double d = orc_xf_mul_to_double(xs[v], sum);
+      if (v == s) d = 0.0;
+      delta[v] = d;
+      xc[v] = orc_xf_div(1.0 + d, xs[v]);
+    }
+    for (int32_t v = 0; v < n; ++v) sigma[v] = dist[v] >= 0 ? UINT64_MAX : 0;
+  }
+  if (dist_out) memcpy(dist_out, dist, sizeof(int64_t) * (size_t)n);
+  if (sigma_out) memcpy(sigma_out, sigma, sizeof(uint64_t) * (size_t)n);
+  for (int32_t v = 0; v < n; ++v) {
+    if (sigma_m) sigma_m[v] = xs[v].m;
+    if (sigma_e) sigma_e[v] = xs[v].e;
+  }
+  rc = overflow ? ORC_SIGMA_OVERFLOW : ORC_OK;
+out:
+  free(dist); free(order); free(sigma); free(xs); free(xc); free(coef); free(acc);
+  free(rp_in); free(col_in); free(w_in);
+  return rc;
+}
+
+/* delta_s(.) of one source, weighted (w != NULL) or not. */
+static int orc_deps_of(int32_t n, const int32_t *row_ptr, const int32_t *col, const uint32_t *w, int32_t s,
+                       double *delta) {
+  if (w) return orc_source_dependencies_w(n, row_ptr, col, w, s, delta, NULL, NULL, NULL, NULL);
+  return orc_source_dependencies(n, row_ptr, col, s, delta, NULL, NULL);
+}
+
 /* --------------------------------------------------------------- exact BC -- */
 /* BC(x) = sum over sources s != x of delta_s(x) (Eq. 4, Brandes' algorithm of
  * Sec. 3), the sum over s exact and rounded once. */
-int orc_exact_bc(int32_t n, const int32_t *row_ptr, const int32_t *col, double *bc) {
+int orc_exact_bc_w(int32_t n, const int32_t *row_ptr, const int32_t *col, const uint32_t *w, double *bc) {
   double *delta = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
   orc_acc *acc = (orc_acc *)malloc(sizeof(orc_acc) * (size_t)(n ? n : 1));
   if (!delta || !acc) { free(delta); free(acc); return ORC_E_NOMEM; }
   for (int32_t v = 0; v < n; ++v) orc_acc_clear(&acc[v]);
   int status = ORC_OK;
   for (int32_t s = 0; s < n; ++s) {
-    int rc = orc_source_dependencies(n, row_ptr, col, s, delta, NULL, NULL);
+    int rc = orc_deps_of(n, row_ptr, col, w, s, delta);
     if (rc < 0) { free(delta); free(acc); return rc; }
     if (rc == ORC_SIGMA_OVERFLOW) status = ORC_SIGMA_OVERFLOW;
     for (int32_t v = 0; v < n; ++v) orc_acc_add(&acc[v], delta[v]);
@@ -531,12 +734,15 @@ int orc_exact_bc(int32_t n, const int32_t *row_ptr, const int32_t *col, double *
   free(acc);
   return status;
 }
+int orc_exact_bc(int32_t n, const int32_t *row_ptr, const int32_t *col, double *bc) {
+  return orc_exact_bc_w(n, row_ptr, col, NULL, bc);
+}
 
 /* ----------------------------------------------------- uniform estimate -- */
 /* est(x) = n/k * sum_{i<k} delta_{s_i}(x), s_i the first k source draws of
  * (seed, qid); the sum over i exact and rounded once, then (n*S)/k. */
-int orc_uniform_sources(int32_t n, const int32_t *row_ptr, const int32_t *col, int64_t k,
-                        uint64_t seed, uint64_t qid, double *est) {
+int orc_uniform_sources_w(int32_t n, const int32_t *row_ptr, const int32_t *col, const uint32_t *w, int64_t k,
+                          uint64_t seed, uint64_t qid, double *est) {
   if (k < 1 || n < 1) return ORC_E_INVALID;
   double *delta = (double *)malloc(sizeof(double) * (size_t)n);
   orc_acc *acc = (orc_acc *)malloc(sizeof(orc_acc) * (size_t)n);
@@ -545,7 +751,7 @@ int orc_uniform_sources(int32_t n, const int32_t *row_ptr, const int32_t *col, i
   int status = ORC_OK;
   for (int64_t i = 0; i < k; ++i) {
     int32_t s = orc_draw_source(seed, qid, (uint64_t)i, n);
-    int rc = orc_source_dependencies(n, row_ptr, col, s, delta, NULL, NULL);
+    int rc = orc_deps_of(n, row_ptr, col, w, s, delta);
     if (rc < 0) { free(delta); free(acc); return rc; }
     if (rc == ORC_SIGMA_OVERFLOW) status = ORC_SIGMA_OVERFLOW;
     for (int32_t v = 0; v < n; ++v) orc_acc_add(&acc[v], delta[v]);
@@ -558,6 +764,10 @@ int orc_uniform_sources(int32_t n, const int32_t *row_ptr, const int32_t *col, i
   free(acc);
   return status;
 }
+int orc_uniform_sources(int32_t n, const int32_t *row_ptr, const int32_t *col, int64_t k,
+                        uint64_t seed, uint64_t qid, double *est) {
+  return orc_uniform_sources_w(n, row_ptr, col, NULL, k, seed, qid, est);
+}
 
 /* ---------------------------------------------------- Bader (Sec. 4) ----- */
 /*
@@ -566,10 +776,10 @@ int orc_uniform_sources(int32_t n, const int32_t *row_ptr, const int32_t *col, i
  * same draw stream. The loop for a target also ends at k = cap (status CAPPED).
  * S is the running double sum in draw order.
  */
-int orc_adaptive_sources(int32_t n, const int32_t *row_ptr, const int32_t *col,
-                         int32_t T, const int32_t *targets, double c, int64_t cap,
-                         uint64_t seed, uint64_t qid, double *est, int64_t *k_out,
-                         double *S_out, int32_t *stop_status) {
+int orc_adaptive_sources_w(int32_t n, const int32_t *row_ptr, const int32_t *col, const uint32_t *w,
+                           int32_t T, const int32_t *targets, double c, int64_t cap,
+                           uint64_t seed, uint64_t qid, double *est, int64_t *k_out,
+                           double *S_out, int32_t *stop_status) {
   if (n < 1 || T < 0 || cap < 1 || !(c >= 1.0)) return ORC_E_INVALID;
   for (int32_t j = 0; j < T; ++j)
     if (targets[j] < 0 || targets[j] >= n) return ORC_E_INVALID;
@@ -582,7 +792,7 @@ int orc_adaptive_sources(int32_t n, const int32_t *row_ptr, const int32_t *col,
   int status = ORC_OK;
   for (int64_t i = 0; i < cap && remaining > 0; ++i) {
     int32_t s = orc_draw_source(seed, qid, (uint64_t)i, n);
-    int rc = orc_source_dependencies(n, row_ptr, col, s, delta, NULL, NULL);
+    int rc = orc_deps_of(n, row_ptr, col, w, s, delta);
     if (rc < 0) { free(delta); free(done); return rc; }
     if (rc == ORC_SIGMA_OVERFLOW) status = ORC_SIGMA_OVERFLOW;
     for (int32_t j = 0; j < T; ++j) {
@@ -597,6 +807,13 @@ int orc_adaptive_sources(int32_t n, const int32_t *row_ptr, const int32_t *col,
   free(delta);
   free(done);
   return status;
+}
+int orc_adaptive_sources(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                         int32_t T, const int32_t *targets, double c, int64_t cap,
+                         uint64_t seed, uint64_t qid, double *est, int64_t *k_out,
+                         double *S_out, int32_t *stop_status) {
+  return orc_adaptive_sources_w(n, row_ptr, col, NULL, T, targets, c, cap, seed, qid, est, k_out, S_out,
+                                stop_status);
 }
 
 /* ------------------------------------------------ pairs (Algorithm 1) ---- */

@@ -248,6 +248,35 @@ __global__ void k_pair_values(int T, int count, const int32_t *__restrict__ targ
   vals[(size_t)j * vstride + i] = y;
 }
 
+// Target tables from a 64-lane forward pass: row v of tdist/tsig ([n][tstride],
+// columns j0 + t) gets d(s_t, v) from the level masks (-1 when unreached) and
+// sigma (0 when unreached). One warp per vertex, two lanes per thread, so each
+// row is written with coalesced stores.
+__global__ void k_target_rows(int32_t n, int count, int maxlevel, const uint64_t *__restrict__ lm,
+                              const uint64_t *__restrict__ sigma, int32_t *__restrict__ tdist,
+                              uint64_t *__restrict__ tsig, int tstride) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long v = warp; v < n; v += nwarps) {
+    int32_t d0 = -1, d1 = -1;
+    for (int l = 0; l <= maxlevel; ++l) {
+      const uint64_t m = lm[(size_t)l * n + v];
+      if ((m >> lane) & 1ull) d0 = l;
+      if ((m >> (lane + 32)) & 1ull) d1 = l;
+    }
+    const size_t row = (size_t)v * tstride;
+    if (lane < count) {
+      tdist[row + lane] = d0;
+      tsig[row + lane] = d0 >= 0 ? sigma[(size_t)v * 64 + lane] : 0ull;
+    }
+    if (lane + 32 < count) {
+      tdist[row + lane + 32] = d1;
+      tsig[row + lane + 32] = d1 >= 0 ? sigma[(size_t)v * 64 + lane + 32] : 0ull;
+    }
+  }
+}
+
 // pxf[i] = bit i of mask, i < c
 __global__ void k_mask_flags(int c, uint64_t mask, int32_t *__restrict__ pxf) {
   const int i = threadIdx.x;
@@ -660,7 +689,11 @@ void target_bfs(bc_ctx *ctx, const Graph &g, const int32_t *d_targets, int T, in
     BCG_CUDA(cudaMemcpyAsync(ws.sources.p, d_targets + j0, (size_t)count * 4, cudaMemcpyDeviceToDevice, ctx->stream));
     batch_ensure(ctx, g);
     const int maxl = batch_forward(ctx, g, count, false, OVF_EXTEND);
-    batch_extract(ctx, g, count, maxl, tdist + j0, tsig + j0, Tp, 1);
+    {
+      LaunchScope ls(ctx, F_MISC);
+      k_target_rows<<<1216, 256, 0, ctx->stream>>>(g.n, count, maxl, ws.lm.as<uint64_t>(), ws.sigma.as<uint64_t>(),
+                                                   tdist + j0, tsig + j0, Tp);
+    }
     const uint64_t ovf = ws.last_ovf & lanes_of(count);
     if (ovf) {
       if (!texp.p) texp.ensure(n * (size_t)Tp * 4);
