@@ -124,6 +124,23 @@ bc_status bc_set_batch_width(bc_ctx *ctx, int32_t width);
 bc_status bc_graph_load_csr(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col,
                             int64_t nnz, uint32_t flags, bc_graph *out);
 
+/* A graph with edge lengths (Sec. 3 step 1: shortest paths by Dijkstra; Def. 3
+ * with lengths: u is in P_s(v) when (u, v) is an edge and d(s,u) + w(u,v) =
+ * d(s,v)). lengths[j] >= 1 is the length of CSR entry j (BC_E_BAD_GRAPH for a
+ * 0), caller-owned; an undirected graph must give both rows of an edge the
+ * same length (checked with BC_VALIDATE). Distances are exact int64 sums.
+ * Everything else as bc_graph_load_csr. On a weighted graph the per-source
+ * step, exact BC, the uniform and multi-graph estimates and adaptive source
+ * sampling (also served) run on the weighted engine: one source per
+ * persistent CTA, distances by near-far label correcting, counts and
+ * dependencies over the shortest-path DAG in topological rounds (counts beyond
+ * 2^64-1 in the extended form, pulled in CSR order). Pair sampling needs an
+ * unweighted graph (BC_E_INVALID); bc_source_dependencies and
+ * bc_source_dependencies_ext need dist_out = NULL (int32 cannot hold the
+ * distances; bc_source_dependencies_weighted gives them). */
+bc_status bc_graph_load_csr_weighted(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                     const uint32_t *lengths, int64_t nnz, uint32_t flags, bc_graph *out);
+
 /* Releases a graph's device memory. */
 bc_status bc_graph_free(bc_ctx *ctx, bc_graph g);
 
@@ -154,6 +171,19 @@ bc_status bc_source_dependencies(bc_ctx *ctx, bc_graph g, const int32_t *sources
 bc_status bc_source_dependencies_ext(bc_ctx *ctx, bc_graph g, const int32_t *sources, int32_t count,
                                      double *delta_out, int32_t *dist_out, double *sigma_mant_out,
                                      int32_t *sigma_exp_out, int32_t *tier_out);
+
+/* The per-sample step on the weighted engine (Sec. 3 steps 1-2 with edge
+ * lengths; any graph: one without lengths runs with unit lengths and gives
+ * the results of bc_source_dependencies bit for bit), with int64 distances:
+ *   delta_out[i*n + v]       delta_{s_i}(v)
+ *   dist_out[i*n + v]        d(s_i, v), -1 when unreachable      (may be NULL)
+ *   sigma_out[i*n + v]       sigma as in bc_source_dependencies  (may be NULL)
+ *   sigma_mant_out/exp_out   sigma in the extended form           (may be NULL)
+ *   tier_out[i]              1 when source i is in the extended form (may be NULL)
+ * count >= 0; every source in [0, n). */
+bc_status bc_source_dependencies_weighted(bc_ctx *ctx, bc_graph g, const int32_t *sources, int32_t count,
+                                          double *delta_out, int64_t *dist_out, uint64_t *sigma_out,
+                                          double *sigma_mant_out, int32_t *sigma_exp_out, int32_t *tier_out);
 
 /* ----------------------------------------------------------- estimators -- */
 
@@ -198,8 +228,10 @@ bc_status bc_adaptive_sources(bc_ctx *ctx, bc_graph g, const int32_t *targets, i
  * sigma_sv*sigma_vt/sigma_st when d(s,v)+d(v,t) = d(s,t) and v not in {s,t},
  * else 0. threshold_scale = 1 is the paper's test; other values (> 0) rescale
  * S only in the stop test. n >= 2, c >= 1, cap >= 1. The graph must be
- * undirected (BC_E_INVALID for a BC_DIRECTED graph): sigma_vt and d(v,t) are
- * read from the BFS at t. */
+ * undirected and unweighted (BC_E_INVALID for a BC_DIRECTED graph or one with
+ * edge lengths): sigma_vt and d(v,t) are read from the BFS at t. d(s,t) and
+ * sigma_st come from a bidirectional search (balls around s and t grown
+ * until they meet). */
 bc_status bc_adaptive_pairs(bc_ctx *ctx, bc_graph g, const int32_t *targets, int32_t T,
                             double c, int64_t cap, uint64_t seed, uint64_t qid,
                             double threshold_scale, double *est, int64_t *k, double *S,

@@ -71,10 +71,12 @@ _SIGS = {
     "bc_last_error": (ctypes.c_char_p, [_vp]),
     "bc_set_batch_width": (_i32, [_vp, _i32]),
     "bc_graph_load_csr": (_i32, [_vp, _i32, _i32p, _i32p, _i64, _u32, _i64p]),
+    "bc_graph_load_csr_weighted": (_i32, [_vp, _i32, _i32p, _i32p, ctypes.POINTER(_u32), _i64, _u32, _i64p]),
     "bc_graph_free": (_i32, [_vp, _i64]),
     "bc_graph_info": (_i32, [_vp, _i64, _i32p, _i64p]),
     "bc_source_dependencies": (_i32, [_vp, _i64, _i32p, _i32, _f64p, _i32p, _u64p]),
     "bc_source_dependencies_ext": (_i32, [_vp, _i64, _i32p, _i32, _f64p, _i32p, _f64p, _i32p, _i32p]),
+    "bc_source_dependencies_weighted": (_i32, [_vp, _i64, _i32p, _i32, _f64p, _i64p, _u64p, _f64p, _i32p, _i32p]),
     "bc_uniform_sources_multi": (_i32, [_vp, _i32, _i64p, _i64p, _u64p, _u64p, _f64p]),
     "bc_exact": (_i32, [_vp, _i64, _f64p]),
     "bc_uniform_sources": (_i32, [_vp, _i64, _i64, _u64, _u64, _f64p]),
@@ -157,6 +159,22 @@ def bc_graph_load_csr(ctx, row_ptr, col, flags: int = BC_UNDIRECTED) -> int:
     return int(h.value)
 
 
+def bc_graph_load_csr_weighted(ctx, row_ptr, col, lengths, flags: int = BC_UNDIRECTED) -> int:
+    rp = _i32arr(row_ptr)
+    cl = _i32arr(col)
+    wl = np.ascontiguousarray(lengths, dtype=np.uint32)
+    if wl.shape[0] != cl.shape[0]:
+        raise ValueError("one length per CSR entry")
+    n = rp.shape[0] - 1
+    cl_ = cl if cl.size else np.zeros(1, np.int32)
+    wl_ = wl if wl.size else np.ones(1, np.uint32)
+    h = _i64()
+    _ck(ctx, _lib.bc_graph_load_csr_weighted(ctx, n, _p(rp, _i32p), _p(cl_, _i32p),
+                                             wl_.ctypes.data_as(ctypes.POINTER(_u32)), int(cl.size), flags,
+                                             ctypes.byref(h)))
+    return int(h.value)
+
+
 def bc_graph_free(ctx, g: int):
     _ck(ctx, _lib.bc_graph_free(ctx, g))
 
@@ -198,6 +216,26 @@ def bc_source_dependencies_ext(ctx, g: int, sources):
         _ck(ctx, _lib.bc_source_dependencies_ext(ctx, g, _p(src, _i32p), cnt, _p(delta, _f64p), _p(dist, _i32p),
                                                  _p(sm, _f64p), _p(se, _i32p), _p(tier, _i32p)))
     return delta, dist, sm, se, tier
+
+
+def bc_source_dependencies_weighted(ctx, g: int, sources):
+    """(delta [count][n], dist int64 [count][n], sigma [count][n], sigma mantissa,
+    sigma exponent, tier [count]) from the weighted engine (unit lengths on a
+    graph without lengths)."""
+    n, _ = bc_graph_info(ctx, g)
+    src = _i32arr(sources)
+    cnt = src.size
+    delta = np.zeros((cnt, n), np.float64)
+    dist = np.zeros((cnt, n), np.int64)
+    sig = np.zeros((cnt, n), np.uint64)
+    sm = np.zeros((cnt, n), np.float64)
+    se = np.zeros((cnt, n), np.int32)
+    tier = np.zeros(cnt, np.int32)
+    if cnt:
+        _ck(ctx, _lib.bc_source_dependencies_weighted(ctx, g, _p(src, _i32p), cnt, _p(delta, _f64p),
+                                                      _p(dist, _i64p), _p(sig, _u64p), _p(sm, _f64p),
+                                                      _p(se, _i32p), _p(tier, _i32p)))
+    return delta, dist, sig, sm, se, tier
 
 
 def bc_uniform_sources_multi(ctx, graphs, k, seeds, qids):
@@ -402,9 +440,12 @@ class Context:
         except Exception:
             pass
 
-    def load_graph(self, row_ptr, col, validate: bool = False, directed: bool = False) -> int:
+    def load_graph(self, row_ptr, col, validate: bool = False, directed: bool = False, lengths=None) -> int:
         flags = (BC_DIRECTED if directed else BC_UNDIRECTED) | (BC_VALIDATE if validate else 0)
-        h = bc_graph_load_csr(self.ptr, row_ptr, col, flags)
+        if lengths is None:
+            h = bc_graph_load_csr(self.ptr, row_ptr, col, flags)
+        else:
+            h = bc_graph_load_csr_weighted(self.ptr, row_ptr, col, lengths, flags)
         self.graphs.add(h)
         return h
 
@@ -420,6 +461,9 @@ class Context:
 
     def source_dependencies_ext(self, g, sources):
         return bc_source_dependencies_ext(self.ptr, g, sources)
+
+    def source_dependencies_weighted(self, g, sources):
+        return bc_source_dependencies_weighted(self.ptr, g, sources)
 
     def uniform_sources_multi(self, graphs, k, seeds, qids):
         return bc_uniform_sources_multi(self.ptr, graphs, k, seeds, qids)

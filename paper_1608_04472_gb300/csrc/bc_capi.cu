@@ -302,9 +302,10 @@ __global__ void k_exact_sum(int64_t count, const double *__restrict__ x, double 
   if (e) atomicOr(err, e);
 }
 
-// Graph validation: symmetric, sorted, no loops, no duplicates, in range.
+// Graph validation: symmetric (with equal lengths in both rows when len is
+// given), sorted, no loops, no duplicates, in range.
 __global__ void k_validate(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                           int64_t nnz, int symmetric, unsigned *__restrict__ bad) {
+                           const uint32_t *__restrict__ len, int64_t nnz, int symmetric, unsigned *__restrict__ bad) {
   const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   const int b = rp[v], e = rp[v + 1];
@@ -323,7 +324,11 @@ __global__ void k_validate(int32_t n, const int32_t *__restrict__ rp, const int3
     while (lo <= hi) {
       const int mid = (lo + hi) >> 1;
       const int32_t x = col[mid];
-      if (x == v) { found = true; break; }
+      if (x == v) {
+        found = true;
+        if (len && len[mid] != len[j]) { atomicOr(bad, 16u); return; }  // lengths of both rows must agree
+        break;
+      }
       if (x < v) lo = mid + 1; else hi = mid - 1;
     }
     if (!found) { atomicOr(bad, 8u); return; }
@@ -400,7 +405,9 @@ static void launch_draw_sources(bc_ctx *ctx, uint64_t seed, uint64_t qid, uint64
 // lane-major: level masks and 64-lane rows cost O(levels * n) there, while each
 // lane's own BFS costs O(n + nnz).
 void run_source_batch(bc_ctx *ctx, const Graph &g, int count, const Sink &sink) {
-  if (batch_width(ctx) == 1) {
+  if (g.w) {  // edge lengths: the weighted engine at any width
+    wlane_sink(ctx, g, ctx->ws.sources.as<int32_t>(), count, sink);
+  } else if (batch_width(ctx) == 1) {
     plain_source(ctx, g, ctx->ws.sources.as<int32_t>(), sink, nullptr, nullptr);
   } else if (graph_depth_hint(ctx, g) > ctx->deep_levels) {
     lane_sink(ctx, g, ctx->ws.sources.as<int32_t>(), count, sink);
@@ -812,9 +819,57 @@ static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *target
 // Per-source outputs. Sources whose counts exceed 2^64-1 are computed in the
 // extended form: their sigma rows hold UINT64_MAX at reached vertices, and the
 // extended outputs (sm_out, se_out; tier_out = 1) carry the counts.
+// The per-source rows on the weighted engine (any graph; unit lengths when it
+// has none), 64 sources per launch.
+static void do_source_rows_weighted(bc_ctx *ctx, const Graph &g, const int32_t *sources, int32_t count,
+                                    double *delta_out, int64_t *dist_out, uint64_t *sigma_out, double *sm_out,
+                                    int32_t *se_out, int32_t *tier_out) {
+  Workspace &ws = ctx->ws;
+  const size_t n = (size_t)g.n;
+  cudaStream_t st = ctx->stream;
+  for (int32_t i = 0; i < count; ++i)
+    if (sources[i] < 0 || sources[i] >= g.n) fail(BC_E_INVALID, "source out of range");
+  const int chunk = std::min<int>(64, std::max(1, count));
+  DevBuf dd, ddist, dsig, dsm, dse, dtier;
+  try {
+    dd.ensure(n * chunk * 8);
+    if (dist_out) ddist.ensure(n * chunk * 8);
+    if (sigma_out) dsig.ensure(n * chunk * 8);
+    if (sm_out) dsm.ensure(n * chunk * 8);
+    if (se_out) dse.ensure(n * chunk * 4);
+    dtier.ensure(64 * 4);
+    for (int32_t i0 = 0; i0 < count; i0 += 64) {
+      const int cnt = std::min<int>(64, count - i0);
+      BCG_CUDA(cudaMemcpyAsync(ws.sources.p, sources + i0, (size_t)cnt * 4, cudaMemcpyHostToDevice, st));
+      wlane_rows(ctx, g, ws.sources.as<int32_t>(), cnt, dd.as<double>(), dist_out ? ddist.as<int64_t>() : nullptr,
+                 sigma_out ? dsig.as<uint64_t>() : nullptr, sm_out ? dsm.as<double>() : nullptr,
+                 se_out ? dse.as<int32_t>() : nullptr, dtier.as<int32_t>());
+      sync(ctx);
+      BCG_CUDA(cudaMemcpy(delta_out + (size_t)i0 * n, dd.p, n * cnt * 8, cudaMemcpyDeviceToHost));
+      if (dist_out) BCG_CUDA(cudaMemcpy(dist_out + (size_t)i0 * n, ddist.p, n * cnt * 8, cudaMemcpyDeviceToHost));
+      if (sigma_out) BCG_CUDA(cudaMemcpy(sigma_out + (size_t)i0 * n, dsig.p, n * cnt * 8, cudaMemcpyDeviceToHost));
+      if (sm_out) BCG_CUDA(cudaMemcpy(sm_out + (size_t)i0 * n, dsm.p, n * cnt * 8, cudaMemcpyDeviceToHost));
+      if (se_out) BCG_CUDA(cudaMemcpy(se_out + (size_t)i0 * n, dse.p, n * cnt * 4, cudaMemcpyDeviceToHost));
+      if (tier_out) BCG_CUDA(cudaMemcpy(tier_out + i0, dtier.p, (size_t)cnt * 4, cudaMemcpyDeviceToHost));
+    }
+    check_err_bits(ctx);
+  } catch (...) {
+    cudaStreamSynchronize(st);
+    for (DevBuf *b : {&dd, &ddist, &dsig, &dsm, &dse, &dtier}) b->release();
+    throw;
+  }
+  for (DevBuf *b : {&dd, &ddist, &dsig, &dsm, &dse, &dtier}) b->release();
+}
+
 static void do_source_dependencies(bc_ctx *ctx, const Graph &g, const int32_t *sources, int32_t count,
                                    double *delta_out, int32_t *dist_out, uint64_t *sigma_out, double *sm_out,
                                    int32_t *se_out, int32_t *tier_out) {
+  if (g.w) {
+    // lengths: int64 distances (bc_source_dependencies_weighted gives them)
+    if (dist_out) fail(BC_E_INVALID, "a weighted graph's distances need bc_source_dependencies_weighted");
+    do_source_rows_weighted(ctx, g, sources, count, delta_out, nullptr, sigma_out, sm_out, se_out, tier_out);
+    return;
+  }
   Workspace &ws = ctx->ws;
   const size_t n = (size_t)g.n;
   cudaStream_t st = ctx->stream;
@@ -916,6 +971,152 @@ using namespace bcg;
     return BC_E_DEVICE;                                                \
   }
 
+namespace bcg {
+
+static void load_graph(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col, const uint32_t *wts,
+                       int64_t nnz, uint32_t flags, bc_graph *out) {
+  if (!out || !row_ptr) fail(BC_E_INVALID, "NULL argument");
+  const bool directed = (flags & BC_DIRECTED) != 0;
+  if (directed == ((flags & BC_UNDIRECTED) != 0))
+    fail(BC_E_INVALID, "flags need exactly one of BC_UNDIRECTED and BC_DIRECTED");
+  if (n < 1) fail(BC_E_INVALID, "n must be >= 1");
+  if (n > (1 << 30)) fail(BC_E_TOO_LARGE, "n too large");
+  if (nnz < 0 || nnz >= ((int64_t)1 << 31)) fail(BC_E_TOO_LARGE, "nnz must be < 2^31");
+  if (row_ptr[0] != 0 || (int64_t)row_ptr[n] != nnz) fail(BC_E_BAD_GRAPH, "row_ptr[0] must be 0 and row_ptr[n] == nnz");
+  if (nnz > 0 && !col) fail(BC_E_INVALID, "col is NULL");
+  int32_t maxdeg = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    const int32_t d = row_ptr[v + 1] - row_ptr[v];
+    if (d < 0) fail(BC_E_BAD_GRAPH, "row_ptr must be non-decreasing");
+    maxdeg = std::max(maxdeg, d);
+  }
+  if (wts) {
+    for (int64_t j = 0; j < nnz; ++j)
+      if (wts[j] == 0u) fail(BC_E_BAD_GRAPH, "edge lengths must be >= 1");
+  }
+  // directed: the in-neighbour CSR by a stable counting transpose (row u's
+  // columns are visited in increasing u, so in-rows come out sorted), with
+  // the lengths of the entries
+  std::vector<int32_t> rp_in, col_in;
+  std::vector<uint32_t> w_in;
+  if (directed) {
+    rp_in.assign((size_t)n + 1, 0);
+    for (int64_t j = 0; j < nnz; ++j) {
+      const int32_t w = col[j];
+      if (w < 0 || w >= n) fail(BC_E_BAD_GRAPH, "column out of range");
+      ++rp_in[(size_t)w + 1];
+    }
+    for (int32_t v = 0; v < n; ++v) rp_in[(size_t)v + 1] += rp_in[v];
+    col_in.resize((size_t)std::max<int64_t>(nnz, 1));
+    if (wts) w_in.resize((size_t)std::max<int64_t>(nnz, 1));
+    std::vector<int32_t> pos(rp_in.begin(), rp_in.end() - 1);
+    for (int32_t u = 0; u < n; ++u)
+      for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
+        const int32_t k = pos[col[j]]++;
+        col_in[(size_t)k] = u;
+        if (wts) w_in[(size_t)k] = wts[j];
+      }
+  }
+  Graph g;
+  g.n = n;
+  g.nnz = nnz;
+  g.max_deg = maxdeg;
+  g.directed = directed;
+  for (int32_t v = 0; v < n; ++v)
+    if (row_ptr[v + 1] - row_ptr[v] == maxdeg) {
+      g.hub = v;
+      break;
+    }
+  BCG_CUDA(cudaMalloc(&g.rp, sizeof(int32_t) * ((size_t)n + 1)));
+  if (cudaMalloc(&g.col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(g.rp);
+    fail(BC_E_NOMEM, "out of device memory for col");
+  }
+  g.rp_in = g.rp;
+  g.col_in = g.col;
+  if (directed) {
+    g.rp_in = g.col_in = nullptr;
+    if (cudaMalloc(&g.rp_in, sizeof(int32_t) * ((size_t)n + 1)) != cudaSuccess ||
+        cudaMalloc(&g.col_in, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(g.rp);
+      cudaFree(g.col);
+      cudaFree(g.rp_in);
+      fail(BC_E_NOMEM, "out of device memory for the in-neighbour CSR");
+    }
+  }
+  auto free_all = [&]() {
+    cudaFree(g.rp);
+    cudaFree(g.col);
+    if (directed) {
+      cudaFree(g.rp_in);
+      cudaFree(g.col_in);
+    }
+    cudaFree(g.w);
+    if (directed) cudaFree(g.w_in);
+  };
+  if (wts) {
+    const size_t wb = sizeof(uint32_t) * (size_t)std::max<int64_t>(nnz, 1);
+    if (cudaMalloc(&g.w, wb) != cudaSuccess || (directed && cudaMalloc(&g.w_in, wb) != cudaSuccess)) {
+      cudaGetLastError();
+      free_all();
+      fail(BC_E_NOMEM, "out of device memory for the edge lengths");
+    }
+    if (!directed) g.w_in = g.w;
+    // near-far threshold increment: four times the mean length (at least 1)
+    long double sum = 0.0L;
+    for (int64_t j = 0; j < nnz; ++j) sum += (long double)wts[j];
+    const uint64_t mean = nnz > 0 ? (uint64_t)(sum / (long double)nnz + 0.5L) : 1ull;
+    g.w_step = ctx->w_step > 0 ? (uint64_t)ctx->w_step : std::max<uint64_t>(1ull, 4ull * mean);
+  }
+  try {
+    if (wts && nnz > 0) {
+      BCG_CUDA(cudaMemcpyAsync(g.w, wts, sizeof(uint32_t) * (size_t)nnz, cudaMemcpyHostToDevice, ctx->stream));
+      if (directed)
+        BCG_CUDA(cudaMemcpyAsync(g.w_in, w_in.data(), sizeof(uint32_t) * (size_t)nnz, cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    }
+    BCG_CUDA(cudaMemcpyAsync(g.rp, row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, ctx->stream));
+    if (nnz > 0)
+      BCG_CUDA(cudaMemcpyAsync(g.col, col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, ctx->stream));
+    if (directed) {
+      BCG_CUDA(cudaMemcpyAsync(g.rp_in, rp_in.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice,
+                               ctx->stream));
+      if (nnz > 0)
+        BCG_CUDA(cudaMemcpyAsync(g.col_in, col_in.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    }
+    if (flags & BC_VALIDATE) {
+      unsigned *d_bad = ctx->ws.err.as<unsigned>() + 1;
+      BCG_CUDA(cudaMemsetAsync(d_bad, 0, 4, ctx->stream));
+      {
+        LaunchScope ls(ctx, F_MISC);
+        k_validate<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, g.rp, g.col, directed ? nullptr : g.w, nnz,
+                                                             directed ? 0 : 1, d_bad);
+      }
+      unsigned *h = static_cast<unsigned *>(ctx->ws.pinned);
+      BCG_CUDA(cudaMemcpyAsync(h, d_bad, 4, cudaMemcpyDeviceToHost, ctx->stream));
+      sync(ctx);
+      if (*h) {
+        const unsigned b = *h;
+        fail(BC_E_BAD_GRAPH, (b & 1u) ? "bad row_ptr" : (b & 2u) ? "column out of range or self loop"
+                                          : (b & 4u) ? "row not sorted or duplicate edge"
+                                          : (b & 8u) ? "adjacency not symmetric" : "edge lengths not symmetric");
+      }
+    }
+    sync(ctx);
+  } catch (...) {
+    free_all();
+    throw;
+  }
+  const bc_graph h = ctx->next_handle++;
+  ctx->graphs[h] = g;
+  *out = h;
+}
+
+}  // namespace bcg
+
 extern "C" {
 
 bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
@@ -949,6 +1150,7 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
     if (const char *pc = std::getenv("BCG_PK_MINCNT")) ctx->pk_mincnt = std::atoi(pc);
     if (const char *mc = std::getenv("BCG_MULTI_CAP")) ctx->multi_cap = std::atoi(mc);
     if (const char *pe = std::getenv("BCG_PAIR_ENGINE")) ctx->pair_engine = std::atoi(pe) == 1 ? 1 : 0;
+    if (const char *ws = std::getenv("BCG_W_STEP")) ctx->w_step = std::atoll(ws);
     BCG_CUDA(cudaMallocHost(&ctx->ws.pinned, 4096));
     ctx->ws.enable.ensure(64);   // [0] lane enable mask, [1] pair continuation word
     ctx->ws.sources.ensure(64 * 4);
@@ -978,6 +1180,7 @@ void bc_destroy(bc_ctx *ctx) {
     forget_multi_plan(ctx);
     forget_lane_scratch(ctx);
     forget_bidir_scratch(ctx);
+    forget_weighted_scratch(ctx);
     resolve_events(ctx);
     for (auto &kv : ctx->graphs) {
       forget_heavy_meta(kv.second.rp);
@@ -987,7 +1190,9 @@ void bc_destroy(bc_ctx *ctx) {
       if (kv.second.directed) {
         cudaFree(kv.second.rp_in);
         cudaFree(kv.second.col_in);
+        cudaFree(kv.second.w_in);
       }
+      cudaFree(kv.second.w);
     }
     ctx->graphs.clear();
     Workspace &ws = ctx->ws;
@@ -1020,106 +1225,15 @@ bc_status bc_set_batch_width(bc_ctx *ctx, int32_t width) {
 bc_status bc_graph_load_csr(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col, int64_t nnz,
                             uint32_t flags, bc_graph *out) {
   BC_GUARD_BEGIN
-  if (!out || !row_ptr) fail(BC_E_INVALID, "NULL argument");
-  const bool directed = (flags & BC_DIRECTED) != 0;
-  if (directed == ((flags & BC_UNDIRECTED) != 0))
-    fail(BC_E_INVALID, "flags need exactly one of BC_UNDIRECTED and BC_DIRECTED");
-  if (n < 1) fail(BC_E_INVALID, "n must be >= 1");
-  if (n > (1 << 30)) fail(BC_E_TOO_LARGE, "n too large");
-  if (nnz < 0 || nnz >= ((int64_t)1 << 31)) fail(BC_E_TOO_LARGE, "nnz must be < 2^31");
-  if (row_ptr[0] != 0 || (int64_t)row_ptr[n] != nnz) fail(BC_E_BAD_GRAPH, "row_ptr[0] must be 0 and row_ptr[n] == nnz");
-  if (nnz > 0 && !col) fail(BC_E_INVALID, "col is NULL");
-  int32_t maxdeg = 0;
-  for (int32_t v = 0; v < n; ++v) {
-    const int32_t d = row_ptr[v + 1] - row_ptr[v];
-    if (d < 0) fail(BC_E_BAD_GRAPH, "row_ptr must be non-decreasing");
-    maxdeg = std::max(maxdeg, d);
-  }
-  // directed: the in-neighbour CSR by a stable counting transpose (row u's
-  // columns are visited in increasing u, so in-rows come out sorted)
-  std::vector<int32_t> rp_in, col_in;
-  if (directed) {
-    rp_in.assign((size_t)n + 1, 0);
-    for (int64_t j = 0; j < nnz; ++j) {
-      const int32_t w = col[j];
-      if (w < 0 || w >= n) fail(BC_E_BAD_GRAPH, "column out of range");
-      ++rp_in[(size_t)w + 1];
-    }
-    for (int32_t v = 0; v < n; ++v) rp_in[(size_t)v + 1] += rp_in[v];
-    col_in.resize((size_t)std::max<int64_t>(nnz, 1));
-    std::vector<int32_t> pos(rp_in.begin(), rp_in.end() - 1);
-    for (int32_t u = 0; u < n; ++u)
-      for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) col_in[(size_t)pos[col[j]]++] = u;
-  }
-  Graph g;
-  g.n = n;
-  g.nnz = nnz;
-  g.max_deg = maxdeg;
-  g.directed = directed;
-  for (int32_t v = 0; v < n; ++v)
-    if (row_ptr[v + 1] - row_ptr[v] == maxdeg) {
-      g.hub = v;
-      break;
-    }
-  BCG_CUDA(cudaMalloc(&g.rp, sizeof(int32_t) * ((size_t)n + 1)));
-  if (cudaMalloc(&g.col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)) != cudaSuccess) {
-    cudaGetLastError();
-    cudaFree(g.rp);
-    fail(BC_E_NOMEM, "out of device memory for col");
-  }
-  g.rp_in = g.rp;
-  g.col_in = g.col;
-  if (directed) {
-    g.rp_in = g.col_in = nullptr;
-    if (cudaMalloc(&g.rp_in, sizeof(int32_t) * ((size_t)n + 1)) != cudaSuccess ||
-        cudaMalloc(&g.col_in, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)) != cudaSuccess) {
-      cudaGetLastError();
-      cudaFree(g.rp);
-      cudaFree(g.col);
-      cudaFree(g.rp_in);
-      fail(BC_E_NOMEM, "out of device memory for the in-neighbour CSR");
-    }
-  }
-  try {
-    BCG_CUDA(cudaMemcpyAsync(g.rp, row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, ctx->stream));
-    if (nnz > 0)
-      BCG_CUDA(cudaMemcpyAsync(g.col, col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, ctx->stream));
-    if (directed) {
-      BCG_CUDA(cudaMemcpyAsync(g.rp_in, rp_in.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice,
-                               ctx->stream));
-      if (nnz > 0)
-        BCG_CUDA(cudaMemcpyAsync(g.col_in, col_in.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice,
-                                 ctx->stream));
-    }
-    if (flags & BC_VALIDATE) {
-      unsigned *d_bad = ctx->ws.err.as<unsigned>() + 1;
-      BCG_CUDA(cudaMemsetAsync(d_bad, 0, 4, ctx->stream));
-      {
-        LaunchScope ls(ctx, F_MISC);
-        k_validate<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, g.rp, g.col, nnz, directed ? 0 : 1, d_bad);
-      }
-      unsigned *h = static_cast<unsigned *>(ctx->ws.pinned);
-      BCG_CUDA(cudaMemcpyAsync(h, d_bad, 4, cudaMemcpyDeviceToHost, ctx->stream));
-      sync(ctx);
-      if (*h) {
-        const unsigned b = *h;
-        fail(BC_E_BAD_GRAPH, (b & 1u) ? "bad row_ptr" : (b & 2u) ? "column out of range or self loop"
-                                          : (b & 4u) ? "row not sorted or duplicate edge" : "adjacency not symmetric");
-      }
-    }
-    sync(ctx);
-  } catch (...) {
-    cudaFree(g.rp);
-    cudaFree(g.col);
-    if (directed) {
-      cudaFree(g.rp_in);
-      cudaFree(g.col_in);
-    }
-    throw;
-  }
-  const bc_graph h = ctx->next_handle++;
-  ctx->graphs[h] = g;
-  *out = h;
+  load_graph(ctx, n, row_ptr, col, nullptr, nnz, flags, out);
+  BC_GUARD_END
+}
+
+bc_status bc_graph_load_csr_weighted(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                     const uint32_t *lengths, int64_t nnz, uint32_t flags, bc_graph *out) {
+  BC_GUARD_BEGIN
+  if (!lengths) fail(BC_E_INVALID, "lengths is NULL");
+  load_graph(ctx, n, row_ptr, col, lengths, nnz, flags, out);
   BC_GUARD_END
 }
 
@@ -1137,7 +1251,9 @@ bc_status bc_graph_free(bc_ctx *ctx, bc_graph g) {
   if (it->second.directed) {
     cudaFree(it->second.rp_in);
     cudaFree(it->second.col_in);
+    cudaFree(it->second.w_in);
   }
+  cudaFree(it->second.w);
   ctx->graphs.erase(it);
   BC_GUARD_END
 }
@@ -1174,6 +1290,20 @@ bc_status bc_source_dependencies_ext(bc_ctx *ctx, bc_graph g, const int32_t *sou
   if (count > 0)
     do_source_dependencies(ctx, gr, sources, count, delta_out, dist_out, nullptr, sigma_mant_out, sigma_exp_out,
                            tier_out);
+  BC_GUARD_END
+}
+
+bc_status bc_source_dependencies_weighted(bc_ctx *ctx, bc_graph g, const int32_t *sources, int32_t count,
+                                          double *delta_out, int64_t *dist_out, uint64_t *sigma_out,
+                                          double *sigma_mant_out, int32_t *sigma_exp_out, int32_t *tier_out) {
+  BC_GUARD_BEGIN
+  const Graph &gr = get_graph(ctx, g);
+  if (count < 0) fail(BC_E_INVALID, "count must be >= 0");
+  if (count > 0 && (!sources || !delta_out)) fail(BC_E_INVALID, "NULL argument");
+  BCG_CUDA(cudaSetDevice(ctx->device));
+  if (count > 0)
+    do_source_rows_weighted(ctx, gr, sources, count, delta_out, dist_out, sigma_out, sigma_mant_out, sigma_exp_out,
+                            tier_out);
   BC_GUARD_END
 }
 
@@ -1234,6 +1364,7 @@ bc_status bc_adaptive_pairs(bc_ctx *ctx, bc_graph g, const int32_t *targets, int
   const Graph &gr = get_graph(ctx, g);
   if (gr.n < 2) fail(BC_E_INVALID, "pair sampling needs n >= 2");
   if (gr.directed) fail(BC_E_INVALID, "pair sampling needs an undirected graph");
+  if (gr.w) fail(BC_E_INVALID, "pair sampling needs an unweighted graph");
   if (!(c >= 1.0) || !(c < 1e300)) fail(BC_E_INVALID, "c must be >= 1 and finite");
   if (!(threshold_scale > 0.0) || !(threshold_scale < 1e300)) fail(BC_E_INVALID, "threshold_scale must be > 0");
   if (cap < 1 || cap > ((int64_t)1 << 32)) fail(BC_E_INVALID, "cap must be in [1, 2^32]");

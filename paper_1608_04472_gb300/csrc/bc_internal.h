@@ -53,6 +53,12 @@ struct Graph {
   bool directed = false;
   int32_t *rp_in = nullptr;
   int32_t *col_in = nullptr;
+  // edge lengths (weighted graphs; nullptr: unweighted): w[j] of CSR entry j,
+  // w_in[j] of in-CSR entry j (the same array for an undirected graph), and
+  // the near-far threshold increment of the weighted engine
+  uint32_t *w = nullptr;
+  uint32_t *w_in = nullptr;
+  uint64_t w_step = 0;
 };
 
 // Kernel families timed separately when profiling is on.
@@ -166,6 +172,9 @@ struct bc_ctx {
   // pair lanes of Algorithm 1: 0 = bidirectional search (bc_bidir.cu), 1 = the
   // one-sided BFS from s truncated at t's level (kept for comparison)
   int32_t pair_engine = 0;
+  // weighted graphs: near-far threshold increment for graphs loaded later
+  // (0 = four times the graph's mean edge length)
+  long long w_step = 0;
 };
 
 namespace bcg {
@@ -258,6 +267,16 @@ uint64_t lane_pairs(bc_ctx *ctx, const Graph &g, int count);
 int graph_depth_hint(bc_ctx *ctx, const Graph &g);
 void uniform_one(bc_ctx *ctx, const Graph &g, int64_t k, uint64_t seed, uint64_t qid, double *out);
 bool multi_plan_uses_graph(bc_ctx *ctx, bc_graph g);
+
+// ---- weighted graphs (bc_weighted.cu): one source per persistent CTA ----
+// A batch of sources delivering to a sink, as lane_sink does.
+void wlane_sink(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, int count, const Sink &sink);
+// Per-source rows [count][n] (device): delta, dist (int64, -1 unreachable),
+// sigma (UINT64_MAX at reached vertices of an extended sample), the counts as
+// mantissa/exponent, tier; any output but delta may be null.
+void wlane_rows(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, int count, double *delta, int64_t *dist,
+                uint64_t *sig, double *sm, int32_t *se, int32_t *tier);
+void forget_weighted_scratch(bc_ctx *ctx);
 
 // ---- bidirectional pair search (bc_bidir.cu) ----
 // d(s,t) and sigma_st for pair lanes [0, count) (device arrays d_src, d_dst)

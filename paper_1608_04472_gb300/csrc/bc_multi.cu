@@ -705,7 +705,9 @@ void do_uniform_multi(bc_ctx *ctx, const std::vector<bc_graph> &handles, const s
   std::vector<int64_t> off(G + 1, 0);
   for (int g = 0; g < G; ++g) off[g + 1] = off[g] + gs[g]->n;
   std::vector<int> deep, shallow;
-  for (int g = 0; g < G; ++g) (graph_depth_hint(ctx, *gs[g]) > ctx->deep_levels ? deep : shallow).push_back(g);
+  // weighted graphs run per graph (the weighted engine); the persistent kernel takes unit lengths only
+  for (int g = 0; g < G; ++g)
+    (!gs[g]->w && graph_depth_hint(ctx, *gs[g]) > ctx->deep_levels ? deep : shallow).push_back(g);
   std::lock_guard<std::mutex> lk(g_plans_mu);
   MultiPlan &P = g_plans[ctx];
   cudaEvent_t done = nullptr;

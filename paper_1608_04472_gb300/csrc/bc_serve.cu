@@ -665,6 +665,7 @@ bc_status bc_submit(bc_ctx *ctx, const bc_query *q, bc_ticket *out) {
         if (q->cap < 1 || q->cap > ((int64_t)1 << 32)) fail(BC_E_INVALID, "cap must be in [1, 2^32]");
         if (q->kind == BC_QUERY_PAIRS && g.n < 2) fail(BC_E_INVALID, "pair sampling needs n >= 2");
         if (q->kind == BC_QUERY_PAIRS && g.directed) fail(BC_E_INVALID, "pair sampling needs an undirected graph");
+        if (q->kind == BC_QUERY_PAIRS && g.w) fail(BC_E_INVALID, "pair sampling needs an unweighted graph");
         const double sc = q->threshold_scale == 0.0 ? 1.0 : q->threshold_scale;
         if (!(sc > 0.0) || !(sc < 1e300)) fail(BC_E_INVALID, "threshold_scale must be > 0");
         std::vector<int32_t> t(q->targets, q->targets + q->T);
