@@ -235,7 +235,7 @@ def cpu_multicore(g, budget_s=10.0):
             "sample": f"{done} per-sample Brandes steps (source draws of R-MAT s20), one per thread"}
 
 
-def measure_pairs(pkg, torch, local, stream, caps=(2048, 16384), T=256):
+def measure_pairs(pkg, torch, local, stream, caps=(2048, 16384), T=256, n=2_000_000):
     """Algorithm 1 on BA n=2,000,000 (4 edges per new vertex, seed 3) with 256
     degree-proportional targets and the paper's threshold c*n (c=1): every
     target runs to the cap, so a run is `cap` pair draws plus one BFS per
@@ -244,9 +244,9 @@ def measure_pairs(pkg, torch, local, stream, caps=(2048, 16384), T=256):
     default) and the one-sided BFS truncated at t's level (BCG_PAIR_ENGINE=1).
     Returns pair draws per second."""
     import graphgen as gg
-    g = gg.barabasi_albert(2_000_000, 4, 3)
+    g = gg.barabasi_albert(n, 4, 3)
     targets = gg.degree_targets(g, T, 3)
-    out = {"workload": f"BA n=2e6 m=4 seed 3, {T} degree-proportional targets, c=1 (threshold c*n), "
+    out = {"workload": f"BA n={n} m=4 seed 3, {T} degree-proportional targets, c=1 (threshold c*n), "
                        f"caps {caps[0]} and {caps[1]}"}
     prev = os.environ.get("BCG_PAIR_ENGINE")
     try:
@@ -296,6 +296,59 @@ def measure_pairs(pkg, torch, local, stream, caps=(2048, 16384), T=256):
     out["marginal_speedup"] = (out["bidirectional"]["pair_draws_per_s_marginal"]
                                / out["one_sided"]["pair_draws_per_s_marginal"])
     out["note"] = "with_targets includes one BFS per target (256) before the pair draws"
+    return out
+
+
+def measure_variants(pkg, torch, local, stream, k=512):
+    """The uniform k-source estimate (the per-sample step of Sec. 3 summed over
+    k draws) on R-MAT s20 with edge lengths 1-100 (weighted engine: near-far
+    distances, Kahn rounds over the shortest-path DAG) and on R-MAT s20 read
+    as a directed graph (lane-major engine, counts pulled over the
+    in-neighbour CSR), each beside the same graph's unit-length/undirected
+    figure and the oracle on one host core for a few draws of the same
+    stream."""
+    import graphgen as gg
+    import oracle
+    g = gg.rmat(SCALE, EF, A, B, C, SEED)
+    w = gg.edge_lengths(g, 1, 100, 9)
+    gd = gg.directed_rmat(SCALE, EF, A, B, C, SEED)
+    out = {"k": k}
+
+    def timed(ctx, h):
+        ctx.uniform_sources(h, 64, 1, 1)  # warm-up (scratch sized once)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.uniform_sources(h, k, 3, 4)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def oracle_rate(fn, n_draws=3):
+        t0 = time.perf_counter()
+        for i in range(n_draws):
+            fn(oracle.draw_source(3, 4, i, g.n))
+        return n_draws / (time.perf_counter() - t0)
+
+    ctx = pkg.Context(local, batch_width=64, stream=stream.cuda_stream)
+    hw = ctx.load_graph(g.row_ptr, g.col, lengths=w)
+    ms_w = timed(ctx, hw)
+    ctx.free_graph(hw)
+    h1 = ctx.load_graph(g.row_ptr, g.col, lengths=np.ones(g.col.shape[0], np.uint32))
+    ms_1 = timed(ctx, h1)
+    ctx.free_graph(h1)
+    hd = ctx.load_graph(gd.row_ptr, gd.col, directed=True)
+    ms_d = timed(ctx, hd)
+    ctx.close()
+    out["weighted"] = {
+        "workload": f"R-MAT s20 (seed {SEED}), lengths uniform 1-100 (graphgen.edge_lengths seed 9), uniform k={k}",
+        "samples_per_s": k / (ms_w / 1e3), "ms": ms_w,
+        "unit_lengths_samples_per_s": k / (ms_1 / 1e3),
+        "oracle_1core_samples_per_s": oracle_rate(lambda s: oracle.dependencies_w(g, w, s))}
+    out["directed"] = {
+        "workload": f"R-MAT s20 edges read row -> column (seed {SEED}, {gd.col.shape[0]} arcs), uniform k={k}",
+        "samples_per_s": k / (ms_d / 1e3), "ms": ms_d,
+        "oracle_1core_samples_per_s": oracle_rate(lambda s: oracle.dependencies(gd, s))}
     return out
 
 
@@ -420,8 +473,13 @@ def main():
                     help="also serve a 2D grid of this side in --serving-full (0: none)")
     ap.add_argument("--uneven-only", action="store_true",
                     help="run only the uneven multi-graph measurement and print its JSON object")
+    ap.add_argument("--variants-only", action="store_true",
+                    help="run only the weighted / directed R-MAT s20 measurements and print them")
     ap.add_argument("--pairs-only", action="store_true",
                     help="run only the pair-sampling measurement (BA 2M, both pair engines) and print it")
+    ap.add_argument("--pairs-n", type=int, default=2_000_000,
+                    help="BA size of --pairs-only (smaller for profiling captures)")
+    ap.add_argument("--pairs-targets", type=int, default=256, help="targets of --pairs-only")
     ap.add_argument("--uneven-count", type=int, default=256, help="graphs in the uneven workload")
     ap.add_argument("--uneven-nmax", type=int, default=200000, help="largest graph size in the uneven workload")
     args = ap.parse_args()
@@ -446,11 +504,18 @@ def main():
         ctx.close()
         print(json.dumps(r))
         return 0
+    if args.variants_only:
+        import torch
+        import paper_1608_04472_gb300 as pkg
+        torch.cuda.set_device(0)
+        print(json.dumps(measure_variants(pkg, torch, 0, torch.cuda.current_stream())))
+        return 0
     if args.pairs_only:
         import torch
         import paper_1608_04472_gb300 as pkg
         torch.cuda.set_device(0)
-        print(json.dumps(measure_pairs(pkg, torch, 0, torch.cuda.current_stream())))
+        print(json.dumps(measure_pairs(pkg, torch, 0, torch.cuda.current_stream(), T=args.pairs_targets,
+                                       n=args.pairs_n)))
         return 0
     if args.uneven_only:
         import torch
