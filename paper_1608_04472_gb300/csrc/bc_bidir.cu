@@ -38,7 +38,9 @@ namespace bcg {
 
 constexpr int BT = 256;  // threads per CTA
 constexpr int BWARPS = BT / 32;
-constexpr int BHEAVY = 32;  // vertices above this degree are handled by a whole warp
+constexpr int BHEAVY = 32;   // vertices above this degree are handled by a whole warp
+constexpr int BHUGE = 512;   // ... and above this one by the whole CTA
+constexpr int BHUGE_CAP = 64;  // CTA-wide vertices per pass (the rest fall back to a warp)
 
 // Per-CTA scratch: side 0 grows from s, side 1 from t.
 struct BScr {
@@ -68,11 +70,15 @@ __device__ inline BScr bscr_of(unsigned char *base, int32_t nmax) {
   return s;
 }
 
-// fn(v, beg, end, coop) for the list entries [b, e): light vertices one per
-// thread, heavy ones (degree > BHEAVY) by the whole warp (every lane calls fn).
+// fn(v, beg, end, off, step) for the list entries [b, e), where fn visits the
+// row entries beg + off, beg + off + step, ... below end: light vertices one
+// per thread (off 0, step 1), heavy ones (degree > BHEAVY) by a whole warp
+// (lane, 32), huge ones (degree > BHUGE, up to BHUGE_CAP of them) by the whole
+// CTA after the others (thread, BT). Called by every thread of the CTA; ends
+// with a CTA barrier. s_huge / s_nhuge: shared scratch, *s_nhuge = 0 on entry.
 template <class F>
 __device__ __forceinline__ void for_list(const int32_t *__restrict__ q, const int32_t *__restrict__ rp, int b, int e,
-                                         F fn) {
+                                         int32_t *s_huge, int *s_nhuge, F fn) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int cb = b + warp * 32; cb < e; cb += BWARPS * 32) {
     const int idx = cb + lane;
@@ -83,13 +89,29 @@ __device__ __forceinline__ void for_list(const int32_t *__restrict__ q, const in
       beg = rp[v];
       end = rp[v + 1];
     }
-    const bool heavy = v >= 0 && end - beg > BHEAVY;
-    if (v >= 0 && !heavy) fn(v, beg, end, false);
+    bool queued = false;
+    if (v >= 0 && end - beg > BHUGE) {
+      const int k = atomicAdd(s_nhuge, 1);
+      if (k < BHUGE_CAP) {
+        s_huge[k] = v;
+        queued = true;
+      }
+    }
+    const bool heavy = v >= 0 && !queued && end - beg > BHEAVY;
+    if (v >= 0 && !queued && !heavy) fn(v, beg, end, 0, 1);
     for (unsigned hb = __ballot_sync(FULL, heavy); hb; hb &= hb - 1u) {
       const int k = __ffs(hb) - 1;
-      fn(__shfl_sync(FULL, v, k), __shfl_sync(FULL, beg, k), __shfl_sync(FULL, end, k), true);
+      fn(__shfl_sync(FULL, v, k), __shfl_sync(FULL, beg, k), __shfl_sync(FULL, end, k), lane, 32);
     }
   }
+  __syncthreads();
+  const int nh = min(*s_nhuge, BHUGE_CAP);
+  for (int k = 0; k < nh; ++k) {
+    const int32_t v = s_huge[k];
+    fn(v, rp[v], rp[v + 1], (int)threadIdx.x, BT);
+  }
+  __syncthreads();  // every thread has read *s_nhuge and s_huge
+  if (threadIdx.x == 0) *s_nhuge = 0;
 }
 
 // Pair lanes [0, count): persistent CTAs take lanes from *next. Outputs per
@@ -101,11 +123,13 @@ k_pair_bidir(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, co
              const int32_t *__restrict__ dst, int count, unsigned *__restrict__ next, unsigned char *__restrict__ scratch,
              size_t stride, int32_t nmax, int32_t *__restrict__ pair_d, uint64_t *__restrict__ pair_sig,
              int32_t *__restrict__ pair_big, unsigned *__restrict__ nbig, unsigned long long *__restrict__ visited) {
-  __shared__ int s_item, s_met, s_big, s_dmeet;
+  __shared__ int s_item, s_met, s_big, s_dmeet, s_nhuge;
+  __shared__ int32_t s_huge[BHUGE_CAP];
   __shared__ int s_tail[2], s_fb[2], s_lev[2];
   __shared__ unsigned long long s_fedges[2], s_sum;
   const BScr S = bscr_of(scratch + (size_t)blockIdx.x * stride, nmax);
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_nhuge = 0;
   for (;;) {
     if (tid == 0) s_item = (int)atomicAdd(next, 1u);
     __syncthreads();
@@ -153,11 +177,10 @@ k_pair_bidir(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, co
       // frontier's edges (exact integer sums in any order; a carry out of 64
       // bits or a marked predecessor marks the vertex)
       unsigned long long my_edges = 0ull;
-      for_list(qX, rp, fb, fe, [&](int32_t v, int beg, int end, bool coop) {
+      for_list(qX, rp, fb, fe, s_huge, &s_nhuge, [&](int32_t v, int beg, int end, int off, int step) {
         const uint64_t sv = sX[v];
         const bool bv = bX[v] != 0;
-        const int step = coop ? 32 : 1;
-        for (int j = beg + (coop ? lane : 0); j < end; j += step) {
+        for (int j = beg + off; j < end; j += step) {
           const int32_t w = col[j];
           int32_t dw = dX[w];
           if (dw == -1) {
@@ -175,7 +198,7 @@ k_pair_bidir(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, co
         }
       });
       if (my_edges) atomicAdd(fedX, my_edges);
-      __syncthreads();
+      __syncthreads();  // (for_list ended with a barrier; this one covers the edge sums)
       const int ne = *tailX;
       if (ne == fe) break;  // side x's component is exhausted without meeting: t unreachable
       // vertices of the new level inside the other ball: the balls meet there

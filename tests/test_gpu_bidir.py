@@ -1,7 +1,8 @@
 """GPU parity of pair sampling (Algorithm 1) through the bidirectional pair
 search: d(s,t) and sigma_st from two balls meeting in the middle must give
 estimates, draw counts, sums and stop states equal to the oracle's bit for bit.
-Cases: a small-world graph over windows of up to 1024 draws; a sparse graph
+Cases: a small-world graph over windows of up to 1024 draws; an R-MAT graph
+whose hubs are expanded by whole CTAs; a sparse graph
 with many unreachable pairs and isolated vertices; tiny graphs (adjacent
 pairs); a 90x90 grid where many sigma_st exceed 2^64 (extended form) and others
 lie below 2^64 while counts elsewhere at the same depth do not (R11 for pairs).
@@ -51,6 +52,18 @@ def test_small_world_windows(pkg, monkeypatch, engine):
     _same(got, ref, "batched")
     _same(served, ref, "served")
     assert np.all(ref["k"] == 3000)  # every target ran through windows of up to 1024 draws
+
+
+def test_hub_vertices_expanded_by_the_whole_cta(pkg):
+    # R-MAT s13 has 27 vertices of degree above 512 (up to 2,204): frontiers
+    # holding them are expanded by all threads of the CTA
+    g = gg.rmat(13, 16, 0.57, 0.19, 0.19, 46)
+    assert int(np.diff(g.row_ptr).max()) > 2000
+    targets = gg.degree_targets(g, 12, 47)
+    ref = oracle.adaptive_pairs(g, targets, 1.0, 2500, 11, 3)
+    got, served = _run(pkg, g, targets, 1.0, 2500, 11, 3, served=True)
+    _same(got, ref, "batched")
+    _same(served, ref, "served")
 
 
 def test_small_world_stops_and_plain_width(pkg):
