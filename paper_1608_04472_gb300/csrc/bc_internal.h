@@ -173,7 +173,7 @@ struct bc_ctx {
   // one-sided BFS from s truncated at t's level (kept for comparison)
   int32_t pair_engine = 0;
   // weighted graphs: near-far threshold increment for graphs loaded later
-  // (0 = four times the graph's mean edge length)
+  // (0 = a sixth of the graph's mean edge length)
   long long w_step = 0;
 };
 
