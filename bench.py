@@ -235,6 +235,18 @@ def cpu_multicore(g, budget_s=10.0):
             "sample": f"{done} per-sample Brandes steps (source draws of R-MAT s20), one per thread"}
 
 
+def oracle_pair_rate(g, targets, draws=4):
+    """The oracle's marginal cost of a pair draw of Algorithm 1 (one BFS from s)
+    on one host core: a run of `draws` draws minus a run of one, same stream."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.adaptive_pairs(g, targets[:1], 1.0, 1, 3, 2)
+    t1 = time.perf_counter()
+    oracle.adaptive_pairs(g, targets[:1], 1.0, draws, 3, 2)
+    t2 = time.perf_counter()
+    return (draws - 1) / max(1e-9, (t2 - t1) - (t1 - t0))
+
+
 def measure_pairs(pkg, torch, local, stream, caps=(2048, 16384), T=256, n=2_000_000):
     """Algorithm 1 on BA n=2,000,000 (4 edges per new vertex, seed 3) with 256
     degree-proportional targets and the paper's threshold c*n (c=1): every
@@ -292,6 +304,7 @@ def measure_pairs(pkg, torch, local, stream, caps=(2048, 16384), T=256, n=2_000_
             os.environ.pop("BCG_PAIR_ENGINE", None)
         else:
             os.environ["BCG_PAIR_ENGINE"] = prev
+    out["oracle_1core_pair_draws_per_s"] = oracle_pair_rate(g, targets)
     out["pair_draws_per_s"] = out["bidirectional"]["pair_draws_per_s_with_targets"]
     out["marginal_speedup"] = (out["bidirectional"]["pair_draws_per_s_marginal"]
                                / out["one_sided"]["pair_draws_per_s_marginal"])
