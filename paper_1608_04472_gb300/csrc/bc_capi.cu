@@ -6,8 +6,12 @@
 //   bc_uniform_sources   first k draws, exact per-vertex sums, est = n*S/k
 //   bc_adaptive_sources  Bader's loop (Sec. 4): per batch, the dependencies of the
 //                        targets go through a sequential per-target stop scan
-//   bc_adaptive_pairs    Algorithm 1: one BFS per target, then batched pair BFS
-//                        truncated at the destination's level, pair values, scan
+//   bc_adaptive_pairs    Algorithm 1: one BFS per target, then windows of pair
+//                        draws whose d(s,t), sigma_st come from the bidirectional
+//                        search (bc_bidir.cu), pair values, scan
+// Directed graphs run on the plain and lane-major engines (counts pulled over
+// the in-neighbour CSR); graphs with edge lengths on the weighted engine
+// (bc_weighted.cu).
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>

@@ -6,8 +6,9 @@
 //   * picks a (graph, kind) group round-robin and fills one 64-lane batch with
 //     the next draws of the group's active queries (each query's lanes
 //     contiguous and in its own draw order);
-//   * runs the batched Brandes step (sources) or the truncated pair BFS
-//     (pairs), routes each lane's per-target values to its query, and runs each
+//   * runs the batched Brandes step (sources; the weighted or lane-major
+//     engine for graphs with lengths or direction) or the bidirectional pair
+//     search (pairs), routes each lane's per-target values to its query, and runs each
 //     query's sequential stop scan on the device (Sec. 4 step 3; Algorithm 1);
 //   * writes a finished query's outputs into the caller's buffers.
 // Because every query keeps its own draw stream and every sum is exact, a query's
