@@ -4,8 +4,8 @@ bit for bit (including samples in the extended form), networkx's weighted
 betweenness, subdividing every edge of length k into k unit edges keeps the
 distances and path counts between original vertices, brute-force enumeration
 of every shortest path on small graphs with many ties, invariance under
-scaling all lengths, and binomial counts on a grid of equal lengths beyond
-2^64."""
+scaling all lengths, binomial counts on a grid of equal lengths beyond 2^64,
+and closed forms on a triangle and a square with unequal sides."""
 import math
 import random
 from fractions import Fraction
@@ -188,3 +188,47 @@ def test_equal_length_grid_counts_are_binomials(side):
             assert abs(got - exact) <= Fraction(exact) * Fraction(1.01 * (i + j) * U)
     d1, _, _, _ = oracle.dependencies(g, 0)
     assert np.array_equal(delta, d1)
+
+
+def _wgraph(n, edges):
+    """Undirected graph from (u, v, length) triples: CSR rows sorted, lengths
+    on both rows."""
+    adj = [dict() for _ in range(n)]
+    for u, v, k in edges:
+        adj[u][v] = k
+        adj[v][u] = k
+    rp = np.zeros(n + 1, np.int32)
+    col, w = [], []
+    for u in range(n):
+        for v in sorted(adj[u]):
+            col.append(v)
+            w.append(adj[u][v])
+        rp[u + 1] = len(col)
+    g = gg.from_edges(n, np.array([e[0] for e in edges], np.int32), np.array([e[1] for e in edges], np.int32))
+    assert np.array_equal(g.row_ptr, rp) and np.array_equal(g.col, np.array(col, np.int32))
+    return g, np.array(w, np.uint32)
+
+
+@pytest.mark.parametrize("long_side,bc_b", [(3, 2.0), (2, 1.0), (1, 0.0)])
+def test_weighted_triangle_closed_forms(long_side, bc_b):
+    # a-b and b-c of length 1, a-c of length L: for L = 3 both ordered pairs
+    # (a,c), (c,a) go through b (BC(b) = 2); for L = 2 the direct edge ties the
+    # path through b (each pair splits 1/2, BC(b) = 1); for L = 1 the direct
+    # edge wins (BC(b) = 0). Ordered pairs, R1.
+    g, w = _wgraph(3, [(0, 1, 1), (1, 2, 1), (0, 2, long_side)])
+    bc = oracle.exact_bc_w(g, w)
+    assert bc[1] == bc_b and bc[0] == 0.0 and bc[2] == 0.0
+    _, dist, sig, _, _, _ = oracle.dependencies_w(g, w, 0)
+    assert dist.tolist() == [0, 1, min(2, long_side)]
+    assert sig[2] == (2 if long_side == 2 else 1)
+
+
+def test_weighted_square_with_unequal_sides():
+    # the 4-cycle a-b-c-d-a with lengths ab = 1, bc = 1, cd = 2, da = 2:
+    # a to c is 2 through b (through d it is 4), so b carries (a,c) and (c,a);
+    # b to d is 3 both through a and through c, so a and c each carry half of
+    # (b,d) and of (d,b); every other pair is an edge that is a shortest path.
+    g, w = _wgraph(4, [(0, 1, 1), (1, 2, 1), (2, 3, 2), (3, 0, 2)])
+    bc = oracle.exact_bc_w(g, w)
+    assert bc.tolist() == [1.0, 2.0, 1.0, 0.0]
+    assert math.isclose(float(np.sum(bc)), 4.0)
