@@ -312,7 +312,7 @@ def measure_pairs(pkg, torch, local, stream, caps=(2048, 16384), T=256, n=2_000_
     return out
 
 
-def measure_variants(pkg, torch, local, stream, k=512):
+def measure_variants(pkg, torch, local, stream, k=512, scale=SCALE):
     """The uniform k-source estimate (the per-sample step of Sec. 3 summed over
     k draws) on R-MAT s20 with edge lengths 1-100 (weighted engine: near-far
     distances, Kahn rounds over the shortest-path DAG) and on R-MAT s20 read
@@ -322,10 +322,10 @@ def measure_variants(pkg, torch, local, stream, k=512):
     stream."""
     import graphgen as gg
     import oracle
-    g = gg.rmat(SCALE, EF, A, B, C, SEED)
+    g = gg.rmat(scale, EF, A, B, C, SEED)
     w = gg.edge_lengths(g, 1, 100, 9)
-    gd = gg.directed_rmat(SCALE, EF, A, B, C, SEED)
-    out = {"k": k}
+    gd = gg.directed_rmat(scale, EF, A, B, C, SEED)
+    out = {"k": k, "scale": scale}
 
     def timed(ctx, h):
         ctx.uniform_sources(h, 64, 1, 1)  # warm-up (scratch sized once)
@@ -354,12 +354,13 @@ def measure_variants(pkg, torch, local, stream, k=512):
     ms_d = timed(ctx, hd)
     ctx.close()
     out["weighted"] = {
-        "workload": f"R-MAT s20 (seed {SEED}), lengths uniform 1-100 (graphgen.edge_lengths seed 9), uniform k={k}",
+        "workload": f"R-MAT s{scale} (seed {SEED}), lengths uniform 1-100 (graphgen.edge_lengths seed 9), "
+                    f"uniform k={k}",
         "samples_per_s": k / (ms_w / 1e3), "ms": ms_w,
         "unit_lengths_samples_per_s": k / (ms_1 / 1e3),
         "oracle_1core_samples_per_s": oracle_rate(lambda s: oracle.dependencies_w(g, w, s))}
     out["directed"] = {
-        "workload": f"R-MAT s20 edges read row -> column (seed {SEED}, {gd.col.shape[0]} arcs), uniform k={k}",
+        "workload": f"R-MAT s{scale} edges read row -> column (seed {SEED}, {gd.col.shape[0]} arcs), uniform k={k}",
         "samples_per_s": k / (ms_d / 1e3), "ms": ms_d,
         "oracle_1core_samples_per_s": oracle_rate(lambda s: oracle.dependencies(gd, s))}
     return out
@@ -488,6 +489,8 @@ def main():
                     help="run only the uneven multi-graph measurement and print its JSON object")
     ap.add_argument("--variants-only", action="store_true",
                     help="run only the weighted / directed R-MAT s20 measurements and print them")
+    ap.add_argument("--variants-scale", type=int, default=SCALE,
+                    help="R-MAT scale of --variants-only (smaller for profiling captures)")
     ap.add_argument("--pairs-only", action="store_true",
                     help="run only the pair-sampling measurement (BA 2M, both pair engines) and print it")
     ap.add_argument("--pairs-n", type=int, default=2_000_000,
@@ -521,7 +524,7 @@ def main():
         import torch
         import paper_1608_04472_gb300 as pkg
         torch.cuda.set_device(0)
-        print(json.dumps(measure_variants(pkg, torch, 0, torch.cuda.current_stream())))
+        print(json.dumps(measure_variants(pkg, torch, 0, torch.cuda.current_stream(), scale=args.variants_scale)))
         return 0
     if args.pairs_only:
         import torch
