@@ -562,11 +562,31 @@ static void draw_window(bc_ctx *ctx, const Graph &g, const KeyMeta &km, uint64_t
 
 // Runs the window's sources in batches of the context's width; lane t of the
 // batch starting at position b is the window's sorted entry b + t.
+// Engines that run one source per persistent CTA (edge lengths; deep or
+// directed graphs) take a whole window in one launch, so every resident CTA
+// has a source; the 64-lane engine and the plain width take 64 or 1 at a time.
+static bool one_source_per_cta(bc_ctx *ctx, const Graph &g) {
+  return batch_width(ctx) != 1 && (g.w || graph_depth_hint(ctx, g) > ctx->deep_levels);
+}
+
+static void run_sources_per_cta(bc_ctx *ctx, const Graph &g, const int32_t *d_sources, int count, const Sink &sink) {
+  if (g.w)
+    wlane_sink(ctx, g, d_sources, count, sink);
+  else
+    lane_sink(ctx, g, d_sources, count, sink);
+}
+
 static void run_window(bc_ctx *ctx, const Graph &g, int W, Sink sink) {
   Workspace &ws = ctx->ws;
   const int width = batch_width(ctx);
   const int32_t *sorted_src = ws.win.as<int32_t>() + WMAX;
   const int32_t *sorted_pos = ws.win.as<int32_t>() + 2 * WMAX;
+  if (one_source_per_cta(ctx, g)) {
+    Sink sk = sink;
+    if (sk.tslot) sk.lane_col = sorted_pos;
+    run_sources_per_cta(ctx, g, sorted_src, W, sk);
+    return;
+  }
   for (int b = 0; b < W; b += width) {
     const int count = std::min(width, W - b);
     BCG_CUDA(cudaMemcpyAsync(ws.sources.p, sorted_src + b, (size_t)count * 4, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -586,7 +606,13 @@ static void do_exact_or_uniform(bc_ctx *ctx, const Graph &g, bool exact, int64_t
   sink.acc = ws.acc.as<Acc>();
   const int width = batch_width(ctx);
   KeyMeta &km = key_meta(ctx, g, exact);
-  if (exact) {
+  if (exact && one_source_per_cta(ctx, g)) {
+    // all n sources, up to a window's worth per launch
+    for (int64_t i0 = 0; i0 < (int64_t)g.n; i0 += WMAX) {
+      const int count = (int)std::min<int64_t>(WMAX, (int64_t)g.n - i0);
+      run_sources_per_cta(ctx, g, km.order.as<int32_t>() + i0, count, sink);
+    }
+  } else if (exact) {
     // all n sources, grouped by key (the sum over sources is exact, so any order)
     for (int64_t i0 = 0; i0 < (int64_t)g.n; i0 += width) {
       const int count = (int)std::min<int64_t>(width, (int64_t)g.n - i0);
