@@ -232,3 +232,24 @@ def test_weighted_square_with_unequal_sides():
     bc = oracle.exact_bc_w(g, w)
     assert bc.tolist() == [1.0, 2.0, 1.0, 0.0]
     assert math.isclose(float(np.sum(bc)), 4.0)
+
+
+def test_edge_length_generator():
+    # inputs, not arithmetic of the method: both rows of an undirected edge get
+    # the same length, lengths stay in [lo, hi], cover it, and repeat per seed
+    g = gg.erdos_renyi(500, 6, 95)
+    w = gg.edge_lengths(g, 3, 9, 96)
+    assert w.dtype == np.uint32 and w.shape == g.col.shape
+    assert w.min() == 3 and w.max() == 9
+    pos = {}
+    for u in range(g.n):
+        for j in range(g.row_ptr[u], g.row_ptr[u + 1]):
+            pos[(u, int(g.col[j]))] = int(w[j])
+    assert all(pos[(v, u)] == k for (u, v), k in pos.items())
+    assert np.array_equal(w, gg.edge_lengths(g, 3, 9, 96))
+    assert not np.array_equal(w, gg.edge_lengths(g, 3, 9, 97))
+    d = gg.directed_er(500, 6, 98)
+    wd = gg.edge_lengths(d, 1, 1000, 99, symmetric=False)
+    assert wd.min() >= 1 and wd.max() <= 1000 and len(np.unique(wd)) > 900
+    with pytest.raises(ValueError):
+        gg.edge_lengths(g, 0, 5, 1)
