@@ -137,7 +137,11 @@ bc_status bc_graph_load_csr(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, cons
  * 2^64-1 in the extended form, pulled in CSR order). Pair sampling needs an
  * unweighted graph (BC_E_INVALID); bc_source_dependencies and
  * bc_source_dependencies_ext need dist_out = NULL (int32 cannot hold the
- * distances; bc_source_dependencies_weighted gives them). */
+ * distances; bc_source_dependencies_weighted gives them). Errors as
+ * bc_graph_load_csr, plus BC_E_INVALID for lengths = NULL, BC_E_BAD_GRAPH for
+ * a length of 0 (or, with BC_VALIDATE, rows of an undirected edge whose lengths
+ * differ) and BC_E_NOMEM when the lengths do not fit on the device. The
+ * lengths are copied; the caller keeps ownership. */
 bc_status bc_graph_load_csr_weighted(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col,
                                      const uint32_t *lengths, int64_t nnz, uint32_t flags, bc_graph *out);
 
@@ -180,7 +184,11 @@ bc_status bc_source_dependencies_ext(bc_ctx *ctx, bc_graph g, const int32_t *sou
  *   sigma_out[i*n + v]       sigma as in bc_source_dependencies  (may be NULL)
  *   sigma_mant_out/exp_out   sigma in the extended form           (may be NULL)
  *   tier_out[i]              1 when source i is in the extended form (may be NULL)
- * count >= 0; every source in [0, n). */
+ * count >= 0; every source in [0, n) (BC_E_INVALID otherwise, also for NULL
+ * sources or delta_out with count > 0); BC_E_UNKNOWN_HANDLE for an unknown
+ * graph. All arrays are caller-owned host memory, [count][n] row-major; the
+ * call is synchronous. Device scratch: about 96 B x n per resident CTA, sized
+ * once per context (a quarter of free memory at most). */
 bc_status bc_source_dependencies_weighted(bc_ctx *ctx, bc_graph g, const int32_t *sources, int32_t count,
                                           double *delta_out, int64_t *dist_out, uint64_t *sigma_out,
                                           double *sigma_mant_out, int32_t *sigma_exp_out, int32_t *tier_out);
