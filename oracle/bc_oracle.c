@@ -9,13 +9,17 @@
  *
  * Every function follows the paper's definitions in the paper's order:
  *   - BFS distances and shortest-path counts sigma (Sec. 3, step 1 of Brandes'
- *     algorithm; predecessor sets of Def. 3).
+ *     algorithm; predecessor sets of Def. 3); with edge lengths, Dijkstra
+ *     (the algorithm Sec. 3 step 1 names) and the predecessor test of Def. 3
+ *     with lengths (R19).
  *   - Dependencies by the recursion of Theorem 1, visiting vertices in
  *     non-increasing distance (Sec. 3, step 2).
  *   - Exact BC as the sum of dependencies over all sources (Eq. 4).
  *   - Bader's adaptive source sampling (Sec. 4, steps 1-3).
  *   - Adaptive pair sampling (Algorithm 1, Sec. 6.1).
  *   - Uniform k-source all-vertex estimate (n/k times the summed dependencies).
+ *   The source-based functions take directed graphs as given (R18) and, in
+ *   their _w forms, positive integer edge lengths.
  *
  * Readings where the paper is silent (the same list appears in the design notes):
  *   R1 pairs are ordered; BC(v) ranges over [0, n^2] (Def. 1).
@@ -44,11 +48,12 @@
  *       order of the vertex, one rounding per addition; delta = RN(sigma *
  *       sum) is then an ordinary double.
  *
- * Graphs: a CSR row lists the out-neighbours of a vertex. For an undirected
- * graph every edge appears in both rows; the per-source step, exact BC and the
- * source-sampling estimators also take a directed graph as it is (paths follow
- * the edges' direction). Pair sampling assumes an undirected graph (it reads
- * d(s,v) from the BFS at v).
+ * Graphs (R18): a CSR row lists the out-neighbours of a vertex. For an
+ * undirected graph every edge appears in both rows; the per-source step, exact
+ * BC and the source-sampling estimators also take a directed graph as it is
+ * (paths follow the edges' direction; counts are pulled over in-neighbours).
+ * Pair sampling assumes an undirected unweighted graph (it reads d(s,v) from
+ * the BFS at v).
  *
  * Random draws: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11) with key = (seed, qid) and counter =
