@@ -335,17 +335,25 @@ bc_status bc_exact_sum(bc_ctx *ctx, const double *x, int64_t count, double *out)
  *                   bc_graph_load_csr requires (sorted rows, symmetric, no loops
  *                   or duplicates, columns in [0, n)); not validated here
  *   n               1 .. BC_NOALLOC_MAX_VERTICES, else BC_E_TOO_LARGE
- *   d_sources[count]             DEVICE pointer, every entry in [0, n)
+ *   d_sources[count]             DEVICE pointer; entries are checked on the
+ *                   device: a source outside [0, n) touches no memory, its
+ *                   output row is left as it was, the other sources still run,
+ *                   and the call returns BC_E_INVALID
  *   d_delta_out[count*n]         DEVICE pointer: row i receives delta_{s_i}(v),
- *                   exactly as bc_source_dependencies computes it; a source
- *                   whose path counts exceed 2^64-1 returns BC_E_SIGMA_OVERFLOW
- *                   (the extended form needs scratch this entry does not have)
+ *                   exactly as bc_source_dependencies computes it. A source
+ *                   whose path counts exceed 2^64-1 gets no row (left as it
+ *                   was; the extended form needs scratch this entry does not
+ *                   have), the other sources still run, and the call returns
+ *                   BC_E_SIGMA_OVERFLOW (BC_E_INVALID takes precedence). Rows of
+ *                   in-range sources that did not overflow are always complete.
  *   stream          cudaStream_t to run on (NULL = the legacy default stream);
  *                   the call returns after its work on that stream is done
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture on
- * that device. All calls share the one array and each call re-initialises the
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ * first call before any stream capture on that device, and do not use this
+ * entry across a cudaDeviceReset of that device (the kept address would be
+ * stale). All calls share the one array and each call re-initialises the
  * parts it reads, so calls whose GPU work overlaps (different streams or host
  * threads at the same time) race on it and must be serialised by the caller.
  */

@@ -75,6 +75,12 @@ def _load():
         "orc_uniform_sources_w": (ctypes.c_int, [_i32, _i32p, _i32p, _u32p, _i64, _u64, _u64, _f64p]),
         "orc_adaptive_sources_w": (ctypes.c_int, [_i32, _i32p, _i32p, _u32p, _i32, _i32p, _f64, _i64, _u64,
                                                   _u64, _f64p, _i64p, _f64p, _i32p]),
+        "orc_accs_new": (ctypes.c_void_p, [_i32]),
+        "orc_accs_add_rows": (None, [ctypes.c_void_p, _i32, _i32, _i32, _f64p, _i64]),
+        "orc_accs_uniform_est": (None, [ctypes.c_void_p, _i32, _i64, _f64p]),
+        "orc_accs_free": (None, [ctypes.c_void_p]),
+        "orc_pair_sequence_multi": (ctypes.c_int, [_i32, _i32p, _i32p, _i32, _i32p, _u64, _u64, _i64, _i64,
+                                                   _f64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -308,3 +314,49 @@ def adaptive_sources_w(g, w, targets, c: float, cap: int, seed: int, qid: int):
                                           c, cap, seed, qid, _p(est, _f64p), _p(k, _i64p), _p(S, _f64p),
                                           _p(st, _i32p)))
     return dict(est=est, k=k, S=S, status=st)
+
+
+# ------------------------------------------------ steps for parallel drivers --
+
+class UniformAccumulator:
+    """The exact per-vertex sums of the uniform estimate (``uniform_sources``),
+    fed with dependency rows computed elsewhere (e.g. ``dependencies`` on many
+    host cores at once). ``add_rows`` may be called for disjoint vertex ranges
+    from several threads at the same time; ``estimate(k)`` rounds each sum once
+    and returns (n*S)/k, exactly as ``uniform_sources`` does for the same rows."""
+
+    def __init__(self, n: int):
+        self.n = int(n)
+        self._h = _load().orc_accs_new(self.n)
+        if not self._h:
+            raise MemoryError("oracle accumulators")
+
+    def add_rows(self, rows, v0: int = 0, v1: int | None = None):
+        rows = np.ascontiguousarray(rows, dtype=np.float64).reshape(-1, self.n)
+        v1 = self.n if v1 is None else int(v1)
+        _load().orc_accs_add_rows(self._h, self.n, int(v0), v1, _p(rows, _f64p), rows.shape[0])
+
+    def estimate(self, k: int) -> np.ndarray:
+        est = np.empty(self.n, np.float64)
+        _load().orc_accs_uniform_est(self._h, self.n, int(k), _p(est, _f64p))
+        return est
+
+    def close(self):
+        if self._h:
+            _load().orc_accs_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def pair_sequence_multi(g, targets, seed: int, qid: int, i0: int, count: int) -> np.ndarray:
+    """y[j, q]: the pair value of target j for draw i0+q (Algorithm 1), for all
+    targets with one BFS from s per draw; row j equals ``pair_sequence`` for
+    target j alone."""
+    n, rp, col = _csr(g)
+    t = np.ascontiguousarray(targets, dtype=np.int32)
+    y = np.empty((t.shape[0], max(int(count), 0)), np.float64)
+    _check(_load().orc_pair_sequence_multi(n, _p(rp, _i32p), _p(col, _i32p), t.shape[0], _p(t, _i32p),
+                                           seed, qid, i0, count, _p(y, _f64p)))
+    return y

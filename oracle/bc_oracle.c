@@ -1022,3 +1022,88 @@ int orc_pair_sequence(int32_t n, const int32_t *row_ptr, const int32_t *col, int
   free(dist2); free(xsig); free(xv);
   return status;
 }
+
+/* ------------------------------------------ steps for parallel test drivers -- */
+/*
+ * The uniform estimate (orc_uniform_sources) split into its steps so that the
+ * dependency rows of many draws can come from independent orc_source_dependencies
+ * calls (one per host core) and be added here: n exact accumulators, rows added
+ * into a vertex range [v0, v1), and est(v) = (n * RN(sum))/k at the end. The sum
+ * is exact, so the order in which rows are added does not change any bit.
+ */
+void *orc_accs_new(int32_t n) {
+  if (n < 1) return NULL;
+  orc_acc *a = (orc_acc *)malloc(sizeof(orc_acc) * (size_t)n);
+  if (!a) return NULL;
+  for (int32_t v = 0; v < n; ++v) orc_acc_clear(&a[v]);
+  return a;
+}
+
+void orc_accs_add_rows(void *accs, int32_t n, int32_t v0, int32_t v1, const double *rows, int64_t count) {
+  orc_acc *a = (orc_acc *)accs;
+  for (int64_t r = 0; r < count; ++r)
+    for (int32_t v = v0; v < v1; ++v) orc_acc_add(&a[v], rows[(size_t)r * (size_t)n + (size_t)v]);
+}
+
+void orc_accs_uniform_est(const void *accs, int32_t n, int64_t k, double *est) {
+  const orc_acc *a = (const orc_acc *)accs;
+  for (int32_t v = 0; v < n; ++v) {
+    double S = orc_acc_round(&a[v]);
+    est[v] = ((double)n * S) / (double)k;
+  }
+}
+
+void orc_accs_free(void *accs) { free(accs); }
+
+/* Pair values y_i(v_j) of draws i in [i0, i0+count) for T targets at once
+ * (Algorithm 1's per-draw quantity): one BFS per target, one BFS from s per
+ * draw shared by all targets, y[j*count + q] as orc_pair_sequence gives it for
+ * target j alone. */
+int orc_pair_sequence_multi(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t T,
+                            const int32_t *targets, uint64_t seed, uint64_t qid, int64_t i0, int64_t count,
+                            double *y) {
+  if (n < 2 || T < 1 || count < 0) return ORC_E_INVALID;
+  for (int32_t j = 0; j < T; ++j)
+    if (targets[j] < 0 || targets[j] >= n) return ORC_E_INVALID;
+  size_t nn = (size_t)n;
+  int32_t *dist_t = (int32_t *)malloc(sizeof(int32_t) * nn * (size_t)T);
+  uint64_t *sig_t = (uint64_t *)malloc(sizeof(uint64_t) * nn * (size_t)T);
+  orc_xf **xt = (orc_xf **)calloc((size_t)T, sizeof(orc_xf *));
+  int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * nn);
+  uint64_t *sigma = (uint64_t *)malloc(sizeof(uint64_t) * nn);
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *dist2 = (int32_t *)malloc(sizeof(int32_t) * nn);
+  orc_xf *xsig = (orc_xf *)malloc(sizeof(orc_xf) * nn);
+  int status = ORC_OK;
+  if (!dist_t || !sig_t || !xt || !dist || !sigma || !order || !dist2 || !xsig) {
+    status = ORC_E_NOMEM;
+    goto out;
+  }
+  int32_t nr;
+  for (int32_t j = 0; j < T; ++j) {
+    if (orc_bfs(n, row_ptr, col, targets[j], dist_t + (size_t)j * nn, sig_t + (size_t)j * nn, order, &nr) ==
+        ORC_SIGMA_OVERFLOW) {
+      status = ORC_SIGMA_OVERFLOW;
+      xt[j] = (orc_xf *)malloc(sizeof(orc_xf) * nn);
+      if (!xt[j]) { status = ORC_E_NOMEM; goto out; }
+      orc_bfs_xf(n, row_ptr, col, targets[j], dist2, xt[j], order, &nr);
+    }
+  }
+  for (int64_t q = 0; q < count; ++q) {
+    int32_t s, t, d_st;
+    uint64_t sig_st;
+    orc_xf xst;
+    orc_draw_pair(seed, qid, (uint64_t)(i0 + q), n, &s, &t);
+    const int ext = orc_pair_bfs(n, row_ptr, col, s, t, dist, sigma, order, dist2, xsig, &d_st, &sig_st, &xst);
+    if (ext) status = ORC_SIGMA_OVERFLOW;
+    for (int32_t j = 0; j < T; ++j)
+      y[(size_t)j * (size_t)count + (size_t)q] =
+          orc_pair_y(targets[j], s, t, dist_t + (size_t)j * nn, sig_t + (size_t)j * nn, xt[j], d_st, sig_st,
+                     ext ? &xst : NULL);
+  }
+out:
+  if (xt)
+    for (int32_t j = 0; j < T; ++j) free(xt[j]);
+  free(dist_t); free(sig_t); free(xt); free(dist); free(sigma); free(order); free(dist2); free(xsig);
+  return status;
+}

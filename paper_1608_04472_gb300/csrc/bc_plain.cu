@@ -351,6 +351,26 @@ __global__ void k_acc_to_row(int32_t n, const Acc *__restrict__ acc, double *__r
   if (v < n) out[v] = acc_round(acc[v]);  // one term per vertex: the sum is delta itself
 }
 
+// Start of one source's BFS. The sources are device data the host has not
+// seen, so the range check happens here: a source outside [0, n) writes nothing
+// but qtail = 0 (a valid source always leaves qtail = 1), and the host skips it.
+__global__ void k_na_init(const int32_t *__restrict__ src, int32_t n, const int32_t *__restrict__ rp,
+                          int32_t *__restrict__ dist, uint64_t *__restrict__ sigma, int32_t *__restrict__ queue,
+                          PlainCtr *__restrict__ ctr) {
+  const int32_t s = *src;
+  ctr->ovf = 0;
+  if (s < 0 || s >= n) {
+    ctr->qtail = 0;
+    ctr->next_edges = 0ull;
+    return;
+  }
+  dist[s] = 0;
+  sigma[s] = 1ull;
+  queue[0] = s;
+  ctr->qtail = 1;
+  ctr->next_edges = (unsigned long long)(rp[s + 1] - rp[s]);
+}
+
 static bc_status scratch_of(int device, unsigned char **out) {
   if (device < 0 || device >= 64) return BC_E_INVALID;
   std::lock_guard<std::mutex> lk(g_mu);
@@ -383,17 +403,22 @@ static bc_status run(const int32_t *rp, const int32_t *col, int32_t n, int64_t n
   if (cudaMemsetAsync(err, 0, 4, st) != cudaSuccess) return BC_E_DEVICE;
   Sink sink;
   sink.acc = acc;
+  bool bad_source = false, any_overflow = false;
   for (int32_t i = 0; i < count; ++i) {
     // every scratch array that is read before written starts from zero / -1
     if (cudaMemsetAsync(dist, 0xFF, (size_t)n * 4, st) != cudaSuccess ||
         cudaMemsetAsync(sigma, 0, (size_t)n * 8, st) != cudaSuccess ||
         cudaMemsetAsync(acc, 0, (size_t)n * sizeof(Acc), st) != cudaSuccess)
       return BC_E_DEVICE;
-    k_pinit<<<1, 1, 0, st>>>(sources + i, rp, dist, sigma, queue, ctr);
+    k_na_init<<<1, 1, 0, st>>>(sources + i, n, rp, dist, sigma, queue, ctr);
     PlainCtr h;
     if (cudaMemcpyAsync(&h, ctr, sizeof(PlainCtr), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return BC_E_DEVICE;
+    if (h.qtail == 0) {  // source outside [0, n): its row is left as it was
+      bad_source = true;
+      continue;
+    }
     std::vector<int32_t> offs(1, 0);
     int32_t qb = 0, qe = 1;
     bool overflow = false;
@@ -419,7 +444,10 @@ static bc_status run(const int32_t *rp, const int32_t *col, int32_t n, int64_t n
       qe = h.qtail;
       ++level;
     }
-    if (overflow) return BC_E_SIGMA_OVERFLOW;  // no extended form without scratch of its own
+    if (overflow) {  // no extended form without scratch of its own: the row is left as it was
+      any_overflow = true;
+      continue;
+    }
     for (int l = level; l >= 1; --l) {
       const int32_t b = offs[l], e = offs[l + 1];
       if (e <= b) continue;
@@ -432,7 +460,8 @@ static bc_status run(const int32_t *rp, const int32_t *col, int32_t n, int64_t n
   if (cudaGetLastError() != cudaSuccess) return BC_E_DEVICE;
   if (cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
     return BC_E_DEVICE;
-  if (e & ERR_SIGMA_OVERFLOW) return BC_E_SIGMA_OVERFLOW;
+  if (bad_source) return BC_E_INVALID;
+  if (any_overflow || (e & ERR_SIGMA_OVERFLOW)) return BC_E_SIGMA_OVERFLOW;
   if (e & ERR_RANGE) return BC_E_RANGE;
   return BC_OK;
 }

@@ -1,0 +1,144 @@
+"""GPU parity at the benchmark's own workloads, against the oracle run on every
+host core (tests/_oracle_par.py).
+
+* R-MAT s20 (seed 2), the benchmark's first timed step (qids from bench.py):
+  - the uniform 4096-source all-vertex estimate: all 4096 dependency rows
+    element by element, then the estimate itself (n/k times exact sums);
+  - Bader's loop (Sec. 4) on the 512 targets with c = 5: the run capped at
+    4096 draws in full (k, S, status, est), and the benchmark's own run (cap
+    n/20) on every target that stops within 4096 draws.
+* Algorithm 1 on BA n = 2,000,000 (seed 3) with the benchmark's
+  degree-proportional targets: 4 targets x 2048 pair draws, in the 4-target
+  call and inside the benchmark's 256-target call (each target's result does
+  not depend on the other targets of the query).
+* The 256-graph uneven set in one multi-graph call (the benchmark's call): the
+  largest ER, R-MAT and grid graph against the oracle's uniform estimates.
+
+Bar: bit-exact for every value (draws, counts, statuses and doubles), as in the
+rest of the parity suite.
+"""
+import numpy as np
+import pytest
+
+import bench
+import graphgen as gg
+import oracle
+from tests import _oracle_par as par
+
+pytestmark = pytest.mark.gpu
+
+
+def _same(a, b, what):
+    a, b = np.asarray(a), np.asarray(b)
+    if not np.array_equal(a, b):
+        bad = np.argwhere(a != b)
+        i = tuple(bad[0])
+        raise AssertionError(f"{what}: {len(bad)} mismatches, first at {i}: {a[i]!r} vs {b[i]!r}")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1608_04472_gb300 as pkg
+    c = pkg.Context(0, batch_width=64)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def rmat20():
+    return bench.build_graph()
+
+
+@pytest.fixture(scope="module")
+def step_qids():
+    """(Bader qid, uniform qid) of the benchmark's first timed step (5 warm-ups)."""
+    _, timed = bench.rank_qids(0, 1, 5)
+    return timed[0], timed[0] + 1
+
+
+def test_rmat20_uniform_4096_rows_and_estimate(ctx, rmat20, step_qids):
+    g = rmat20
+    k, seed, qid = bench.K_UNIFORM, bench.SEED, step_qids[1]
+    h = ctx.load_graph(g.row_ptr, g.col)
+    try:
+        est_gpu = ctx.uniform_sources(h, k, seed, qid)
+        srcs = ctx.draw_sources(seed, qid, 0, k, g.n)
+        _same(srcs, [oracle.draw_source(seed, qid, i, g.n) for i in range(k)], "uniform draws")
+
+        def check(i0, rows):
+            got, _, _ = ctx.source_dependencies(h, srcs[i0:i0 + rows.shape[0]])
+            _same(got, rows, f"dependency rows of draws {i0}..{i0 + rows.shape[0] - 1}")
+
+        est_orc = par.uniform_estimate(g, srcs, chunk=64, on_rows=check)
+    finally:
+        ctx.free_graph(h)
+    _same(est_gpu, est_orc, "uniform estimate (k=4096)")
+
+
+def test_rmat20_bader_512_targets_4096_draws(ctx, rmat20, step_qids):
+    g = rmat20
+    targets = gg.uniform_targets(g.n, bench.T_TARGETS, bench.SEED)
+    c, seed, qid, cap = bench.C_BADER, bench.SEED, step_qids[0], 4096
+    h = ctx.load_graph(g.row_ptr, g.col)
+    try:
+        short = ctx.adaptive_sources(h, targets, c, cap, seed, qid)
+        full = ctx.adaptive_sources(h, targets, c, g.n // 20, seed, qid)
+    finally:
+        ctx.free_graph(h)
+    srcs = [oracle.draw_source(seed, qid, i, g.n) for i in range(cap)]
+    X = par.target_columns(g, srcs, targets)
+    k, S, st, est = par.replay_bader(X, g.n, c, cap)
+    for key, ref in (("k", k), ("S", S), ("status", st), ("est", est)):
+        _same(short[key], ref, f"Bader capped at 4096: {key}")
+    stopped = st == 0
+    assert stopped.sum() >= 1, "no target stops within 4096 draws: the comparison below would be empty"
+    for key, ref in (("k", k), ("S", S), ("status", st), ("est", est)):
+        _same(full[key][stopped], ref[stopped], f"Bader at cap n/20, targets stopped by 4096: {key}")
+    assert np.all(full["k"][~stopped] > cap)
+
+
+@pytest.fixture(scope="module")
+def ba2m():
+    return gg.barabasi_albert(2_000_000, 4, 3)
+
+
+def test_ba2m_pairs_4_targets_2048_draws(ctx, ba2m):
+    g = ba2m
+    all_targets = gg.degree_targets(g, 256, 3)  # the benchmark's 256 targets
+    targets = all_targets[:4]
+    seed, qid, cap, c = 3, 2, 2048, 1.0
+    h = ctx.load_graph(g.row_ptr, g.col)
+    try:
+        res4 = ctx.adaptive_pairs(h, targets, c, cap, seed, qid)
+        res256 = ctx.adaptive_pairs(h, all_targets, c, cap, seed, qid)
+    finally:
+        ctx.free_graph(h)
+    Y = par.pair_values(g, targets, seed, qid, cap)
+    k, S, st, est = par.replay_pairs(Y, g.n, c, cap)
+    assert np.all(st == 1)  # the literal threshold c*n is out of reach: every target caps
+    for key, ref in (("k", k), ("S", S), ("status", st), ("est", est)):
+        _same(res4[key], ref, f"pairs, 4-target call: {key}")
+        _same(res256[key][:4], ref, f"pairs, 256-target call: {key}")
+
+
+def test_uneven_set_largest_graphs(ctx):
+    S = gg.uneven_set(count=256, n_hi=200000)
+    G = len(S)
+    k = 1024
+    seeds = [6000 + i for i in range(G)]
+    qids = list(range(G))
+    hs = [ctx.load_graph(g.row_ptr, g.col) for _, g in S]
+    try:
+        out = ctx.uniform_sources_multi(hs, [k] * G, seeds, qids)
+    finally:
+        for h in hs:
+            ctx.free_graph(h)
+    picked = {}
+    for i, (fam, g) in enumerate(S):
+        if fam not in picked or g.n > S[picked[fam]][1].n:
+            picked[fam] = i
+    assert set(picked) == {"er", "rmat", "grid"}
+    for fam, i in sorted(picked.items()):
+        g = S[i][1]
+        srcs = [oracle.draw_source(seeds[i], qids[i], j, g.n) for j in range(k)]
+        _same(out[i], par.uniform_estimate(g, srcs, chunk=256), f"uneven graph {i} ({fam}, n={g.n})")

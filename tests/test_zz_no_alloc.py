@@ -48,6 +48,10 @@ def test_noalloc_matches_allocating_entry_point(family):
         assert rc == 0, f"call {call}: status {rc}"
         got = d_out.cpu().numpy().reshape(len(sources), g.n)
         assert np.array_equal(got, ref), f"call {call}: {np.sum(got != ref)} mismatches"
+    # and, on its own footing, against the CPU oracle (Theorem 1 per source)
+    import oracle
+    for i, s in enumerate(sources):
+        assert np.array_equal(got[i], oracle.dependencies(g, int(s))[0]), f"source {s}: differs from the oracle"
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
@@ -74,3 +78,26 @@ def test_noalloc_reports_overflow_without_extended_form():
     rc = capi.bc_source_dependencies_noalloc(0, d_rp.data_ptr(), d_col.data_ptr(), g.n, g.nnz,
                                              d_src.data_ptr(), 1, d_out.data_ptr(), 0)
     assert rc == -9  # BC_E_SIGMA_OVERFLOW
+
+
+def test_noalloc_rejects_out_of_range_sources_on_the_device():
+    """Sources live in device memory the host never reads: a source of n (or
+    -1) must be refused by the kernel itself, touch no memory, leave its row as
+    it was, and not stop the in-range sources."""
+    torch = pytest.importorskip("torch")
+    import paper_1608_04472_gb300 as pkg
+    from paper_1608_04472_gb300 import capi
+
+    g = gg.erdos_renyi(2000, 8, 1)
+    sources = [3, g.n, 17, -1]
+    with pkg.Context(0, batch_width=1) as ctx:
+        h = ctx.load_graph(g.row_ptr, g.col)
+        ref, _, _ = ctx.source_dependencies(h, [3, 17])
+    d_rp, d_col, d_src, d_out = _device_buffers(torch, g, sources)
+    d_out.fill_(-7.0)
+    rc = capi.bc_source_dependencies_noalloc(0, d_rp.data_ptr(), d_col.data_ptr(), g.n, g.nnz,
+                                             d_src.data_ptr(), len(sources), d_out.data_ptr(), 0)
+    assert rc == -1  # BC_E_INVALID
+    got = d_out.cpu().numpy().reshape(len(sources), g.n)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[2], ref[1])
+    assert np.all(got[1] == -7.0) and np.all(got[3] == -7.0)
