@@ -4,9 +4,10 @@ host core (tests/_oracle_par.py).
 * R-MAT s20 (seed 2), the benchmark's first timed step (qids from bench.py):
   - the uniform 4096-source all-vertex estimate: all 4096 dependency rows
     element by element, then the estimate itself (n/k times exact sums);
-  - Bader's loop (Sec. 4) on the 512 targets with c = 5: the run capped at
-    4096 draws in full (k, S, status, est), and the benchmark's own run (cap
-    n/20) on every target that stops within 4096 draws.
+  - Bader's loop (Sec. 4) on the 512 targets with c = 5, joined by the 8
+    highest-degree vertices (the uniform targets need more than 4096 draws):
+    the run capped at 4096 draws in full (k, S, status, est), and the run at
+    the benchmark's cap n/20 on every target that stops within 4096 draws.
 * Algorithm 1 on BA n = 2,000,000 (seed 3) with the benchmark's
   degree-proportional targets: 4 targets x 2048 pair draws, in the 4-target
   call and inside the benchmark's 256-target call (each target's result does
