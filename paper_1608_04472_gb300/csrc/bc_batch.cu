@@ -527,7 +527,7 @@ struct Ring {
 };
 
 // delta = RN(RN(sigma) * sum); a power-of-two sigma scales exactly (integer
-// exponent add), everything else is one multiply.
+// exponent add), everything else is one rounded product (integer-only below 2^53).
 __device__ __forceinline__ double delta_of(double sum, uint64_t sg) {
   if ((sg & (sg - 1ull)) == 0ull) {
     const uint64_t b = (uint64_t)__double_as_longlong(sum);
@@ -535,18 +535,11 @@ __device__ __forceinline__ double delta_of(double sum, uint64_t sg) {
     const int k = 63 - __clzll((long long)sg);
     return __longlong_as_double((long long)(b + ((uint64_t)k << 52)));
   }
-  return __dmul_rn(sigma_to_double(sg), sum);
+  return delta_rn(sg, sum);
 }
 
-// coef = RN(RN(1 + delta) / RN(sigma)); power-of-two sigma: exact exponent shift.
-__device__ __forceinline__ double coef_round(double delta, uint64_t sg) {
-  const double x = __dadd_rn(1.0, delta);
-  if ((sg & (sg - 1ull)) == 0ull) {
-    const int k = 63 - __clzll((long long)sg);
-    return __longlong_as_double((long long)((uint64_t)__double_as_longlong(x) - ((uint64_t)k << 52)));
-  }
-  return __ddiv_rn(x, sigma_to_double(sg));
-}
+// coef = RN(RN(1 + delta) / RN(sigma)) (power-of-two sigma: exact exponent shift).
+__device__ __forceinline__ double coef_round(double delta, uint64_t sg) { return coef_of(delta, sg); }
 
 __device__ __forceinline__ void ring_append(Ring &R, unsigned &tail, int32_t v, uint64_t lanes, const Acc &a0,
                                             const Acc &a1, const uint64_t *__restrict__ row) {

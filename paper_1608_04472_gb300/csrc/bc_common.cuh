@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cuda_runtime.h>
 
+#include "bc_rn.h"
+
 namespace bcg {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -126,8 +128,8 @@ __device__ __forceinline__ double acc_round(const Acc &a) {
   else if (a.w1) top = 127 - __clzll((long long)a.w1);
   else if (a.w0) top = 63 - __clzll((long long)a.w0);
   else return 0.0;
-  if (top <= 52) {  // fewer than 54 significant bits: exact
-    return __dmul_rn(__ull2double_rn(a.w0), 0x1p-128);
+  if (top <= 52) {  // fewer than 54 significant bits: exact, w0 * 2^-128
+    return bcrn::double_of(bcrn::bits_of(bcrn::rn_u53_to_double(a.w0)) - (128ull << 52));
   }
   int sh = top - 52;  // 1..139
   uint64_t M = acc_shr64(a, sh) & 0x001FFFFFFFFFFFFFull;
@@ -200,16 +202,29 @@ __device__ __forceinline__ Acc acc2_widen(const Acc2 &a) {
 // ------------------------------------------------------ Brandes arithmetic --
 // The per-vertex step of Theorem 1 in factored form, every operation rounded
 // once: delta = RN(RN(sigma) * sum), coef = RN(RN(1 + delta) / RN(sigma)).
-__device__ __forceinline__ double sigma_to_double(uint64_t s) { return __ull2double_rn(s); }
+// Counts below 2^53 (every count of the narrow backward path) go through the
+// integer-only forms of bc_rn.h, which round exactly as the FP64 instructions
+// do but keep the slow FP64 pipe free; larger counts use the FP64 instructions.
+constexpr uint64_t EXACT53 = 1ull << 53;
 
+__device__ __forceinline__ double sigma_to_double(uint64_t s) {
+  if (s == 0ull) return 0.0;
+  return s < EXACT53 ? bcrn::rn_u53_to_double(s) : __ull2double_rn(s);
+}
+
+// RN(RN(sigma) * sum), sum >= 0 normal or zero, sigma >= 1.
+__device__ __forceinline__ double delta_rn(uint64_t sigma, double sum) {
+  return sigma < EXACT53 ? bcrn::rn_mul_u53(sigma, sum) : __dmul_rn(sigma_to_double(sigma), sum);
+}
+
+// RN(RN(1 + delta) / RN(sigma)), delta >= 0 normal or zero, sigma >= 1.
 __device__ __forceinline__ double coef_of(double delta, uint64_t sigma) {
-  const double x = __dadd_rn(1.0, delta);
+  const double x = bcrn::rn_one_plus(delta);
   if ((sigma & (sigma - 1ull)) == 0ull) {  // power of two: exact scaling
     const int k = 63 - __clzll((long long)sigma);
-    const double inv = __longlong_as_double((long long)((uint64_t)(1023 - k) << 52));
-    return __dmul_rn(x, inv);
+    return __longlong_as_double((long long)((uint64_t)__double_as_longlong(x) - ((uint64_t)k << 52)));
   }
-  return __ddiv_rn(x, sigma_to_double(sigma));
+  return sigma < EXACT53 ? bcrn::rn_div_u53(x, sigma) : __ddiv_rn(x, sigma_to_double(sigma));
 }
 
 }  // namespace bcg

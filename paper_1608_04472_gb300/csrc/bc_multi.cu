@@ -265,7 +265,7 @@ __device__ void multi_source(const MGraph &G, int32_t s, const MScratch &S, unsi
         }
         if (coop) a = acc_warp_sum(a);
         const uint64_t sg = S.sig[v];
-        delta = __dmul_rn(sigma_to_double(sg), acc_round(a));
+        delta = delta_rn(sg, acc_round(a));
         if (!coop || lane == 0) S.coef[v] = coef_of(delta, sg);
       }
       if (!coop || lane == 0) deliver(v, delta);

@@ -152,7 +152,7 @@ k_pbwd(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, const in
     a = acc_warp_sum(a);
     if (lane == 0) {
       const uint64_t sg = sigma[v];
-      const double d = __dmul_rn(sigma_to_double(sg), acc_round(a));
+      const double d = delta_rn(sg, acc_round(a));
       coef[v] = coef_of(d, sg);
       if (sink.delta_lm) sink.delta_lm[(size_t)v * 64] = d;
       if (sink.tslot) sink_targets(sink, v, 0, d);

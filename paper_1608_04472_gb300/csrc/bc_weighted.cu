@@ -381,7 +381,7 @@ __device__ void w_source(const WGraph &G, int32_t s, const WScr &S, WShared &sh,
         }
         if (coop) a = acc_warp_sum(a);
         const uint64_t sg = S.sig[v];
-        delta = __dmul_rn(sigma_to_double(sg), acc_round(a));
+        delta = delta_rn(sg, acc_round(a));
         if (!coop || lane == 0) S.coef[v] = coef_of(delta, sg);
       }
       if (!coop || lane == 0) deliver(v, delta);
