@@ -498,6 +498,11 @@ def main():
     ap.add_argument("--pairs-targets", type=int, default=256, help="targets of --pairs-only")
     ap.add_argument("--uneven-count", type=int, default=256, help="graphs in the uneven workload")
     ap.add_argument("--uneven-nmax", type=int, default=200000, help="largest graph size in the uneven workload")
+    ap.add_argument("--sharded", action="store_true",
+                    help="share each step's two queries among the ranks (blocks of draws dealt round-robin, "
+                         "blocks allgathered, the same stop scan on every rank; strong scaling) instead of "
+                         "running independent queries per rank")
+    ap.add_argument("--shard-block", type=int, default=1024, help="draws per block with --sharded")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -546,6 +551,11 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.gpus != world:
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world}; launch N > 1 ranks with "
+              f"python -m torch.distributed.run --nproc-per-node {args.gpus} bench.py --gpus {args.gpus}",
+              file=sys.stderr)
+        return 2
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -566,12 +576,24 @@ def main():
     ctx = pkg.Context(local, batch_width=64, stream=stream.cuda_stream)
     h = ctx.load_graph(g.row_ptr, g.col)
 
-    def step(qid_base):
-        rb = ctx.adaptive_sources(h, targets, C_BADER, cap, SEED, qid_base)
-        est = ctx.uniform_sources(h, kuni, SEED, qid_base + 1)
-        return rb, est
+    if args.sharded:
+        from paper_1608_04472_gb300 import sharded
+        ag, ar = sharded.torch_collectives(dist, "cuda") if dist else (lambda a: [a], lambda a: a)
 
-    warm_qids, timed_qids = rank_qids(rank, args.steps, args.warmup)
+        def step(qid_base):
+            rb = sharded.adaptive_sources_sharded(ctx, h, targets, C_BADER, cap, SEED, qid_base, rank, world, ag,
+                                                  B=args.shard_block)
+            est = sharded.uniform_sources_sharded(ctx, h, kuni, SEED, qid_base + 1, rank, world, ar,
+                                                  B=args.shard_block)
+            return rb, est
+    else:
+        def step(qid_base):
+            rb = ctx.adaptive_sources(h, targets, C_BADER, cap, SEED, qid_base)
+            est = ctx.uniform_sources(h, kuni, SEED, qid_base + 1)
+            return rb, est
+
+    # sharded: every rank works on the same queries (rank 0's streams)
+    warm_qids, timed_qids = rank_qids(0 if args.sharded else rank, args.steps, args.warmup)
     for q in warm_qids:
         step(q)
     ctx.reset_stats()
@@ -601,6 +623,8 @@ def main():
     for q, km in zip(qids, kmax):
         edges_local += float(ce[ctx.draw_sources(SEED, q, 0, km, n)].sum())
         edges_local += float(ce[ctx.draw_sources(SEED, q + 1, 0, kuni, n)].sum())
+    if args.sharded and rank != 0:  # one shared query: its samples are counted once
+        samples_local, edges_local = 0, 0.0
     ms, samples_total, edges_total = reduce_over_ranks(dist, "cuda", ms, float(samples_local), edges_local)
     value = samples_total / (ms / 1e3)
 
@@ -628,10 +652,12 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "strong" if args.sharded else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "graph": f"R-MAT s{SCALE} ef{EF} a{A} b{B} c{C} seed {SEED}",
                    "n": n, "nnz": g.nnz, "targets": T_TARGETS, "c": C_BADER, "cap": cap,
-                   "uniform_k": kuni, "batch_width": 64, "parallelism": f"replicas x{world}",
+                   "uniform_k": kuni, "batch_width": 64,
+                   "parallelism": (f"one query sharded x{world} (blocks of {args.shard_block} draws)"
+                                   if args.sharded else f"replicas x{world}"),
                    "l2": "inputs larger than L2 (CSR 134 MB + 0.6 GB lane state); no flush"},
         "gteps": edges_total / (ms / 1e3) / 1e9,
         "samples_per_step": samples_total / args.steps,
@@ -682,8 +708,13 @@ def main():
         samp = 0
         for _ in range(e2e_steps):
             h2 = ctx.load_graph(g.row_ptr, g.col)
-            rb = ctx.adaptive_sources(h2, targets, C_BADER, cap, SEED, qid)
-            ctx.uniform_sources(h2, kuni, SEED, qid + 1)
+            if args.sharded:
+                rb = sharded.adaptive_sources_sharded(ctx, h2, targets, C_BADER, cap, SEED, qid, rank, world, ag,
+                                                      B=args.shard_block)
+                sharded.uniform_sources_sharded(ctx, h2, kuni, SEED, qid + 1, rank, world, ar, B=args.shard_block)
+            else:
+                rb = ctx.adaptive_sources(h2, targets, C_BADER, cap, SEED, qid)
+                ctx.uniform_sources(h2, kuni, SEED, qid + 1)
             samp += int(rb["k"].max()) + kuni
             ctx.free_graph(h2)
             qid += 2
@@ -693,7 +724,8 @@ def main():
         if dist:
             t = torch.tensor([dt], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_val = samp * world / float(t.item())
+            # replicas: every rank ran its own queries; sharded: one query per step
+            e2e_val = samp * (1 if args.sharded else world) / float(t.item())
         out["e2e"] = {"value": e2e_val, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
     else:

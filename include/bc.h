@@ -64,7 +64,10 @@ typedef int32_t bc_status;
 #define BC_E_TOO_LARGE (-3)        /* n or nnz beyond int32 limits */
 #define BC_E_BAD_GRAPH (-4)        /* CSR failed validation (asymmetric, loop, duplicate, unsorted, out of range) */
 #define BC_E_DEVICE (-5)           /* CUDA error; the message names the call */
-#define BC_E_DEVICE_TIMEOUT (-6)   /* a bounded device-side wait ran out */
+#define BC_E_DEVICE_TIMEOUT (-6)   /* reserved for a bounded device-side wait that ran out;
+                                      no entry point returns it today: the library never
+                                      waits on the device with a time limit (its only waits
+                                      are stream synchronisations on its own work) */
 #define BC_E_CANCELLED (-7)        /* query cancelled before it finished */
 #define BC_E_UNKNOWN_HANDLE (-8)   /* graph handle or ticket not known to this context */
 #define BC_E_SIGMA_OVERFLOW (-9)   /* a shortest-path count exceeded 2^64-1 */
@@ -79,6 +82,10 @@ typedef int32_t bc_status;
 #define BC_VALIDATE 2u             /* check sorted rows, no loops or duplicates, and (undirected)
                                       symmetry */
 #define BC_DIRECTED 4u             /* the CSR lists out-neighbours; paths follow the edges' direction */
+#define BC_NORMALIZE 8u            /* before anything else, each row is sorted and self-loops and
+                                      duplicate columns are dropped (with edge lengths, a duplicate
+                                      keeps the shortest length); the stored graph's nnz
+                                      (bc_graph_info) can then be smaller than row_ptr[n] */
 
 typedef struct bc_ctx bc_ctx;
 typedef int64_t bc_graph;          /* graph handle, valid in the context that made it */
@@ -110,7 +117,11 @@ bc_status bc_set_batch_width(bc_ctx *ctx, int32_t width);
 
 /* Copies a CSR graph to the device and returns a handle. flags must contain
  * exactly one of BC_UNDIRECTED and BC_DIRECTED (else BC_E_INVALID); with
- * BC_VALIDATE the CSR is checked first (BC_E_BAD_GRAPH on failure).
+ * BC_NORMALIZE the rows are first sorted and cleared of self-loops and
+ * duplicates (a column outside [0, n) is still BC_E_BAD_GRAPH); with
+ * BC_VALIDATE the (normalised) CSR is checked (BC_E_BAD_GRAPH on failure):
+ * normalising does not symmetrise, so an undirected CSR that lists an edge in
+ * one row only still fails validation.
  * nnz = row_ptr[n] must be < 2^31 (BC_E_TOO_LARGE). n >= 1.
  * A directed graph (Def. 1 with ordered pairs and directed paths) also gets
  * its in-neighbour CSR, built on the host at load (a stable transpose, so each
@@ -318,6 +329,60 @@ bc_status bc_draw_pairs(bc_ctx *ctx, uint64_t seed, uint64_t qid, uint64_t i0, i
  * nearest-even (the summation the dependency step uses). Values must lie in
  * [2^-76, 2^63) or be 0 (else BC_E_RANGE). */
 bc_status bc_exact_sum(bc_ctx *ctx, const double *x, int64_t count, double *out);
+
+/* ------------------------------------- one query shared by several ranks -- */
+/*
+ * A query's draws are independent (Sec. 4 step 2 draws each source on its own;
+ * Algorithm 1 each pair), so G ranks with one GPU each can share one query:
+ * rank r computes the blocks of draws b = r, r + G, r + 2G, ... (B draws per
+ * block), the ranks exchange them, and every rank combines them in draw order
+ * with the host calls below, which reproduce the single-GPU arithmetic bit for
+ * bit (the stop test of Sec. 4 step 3 / Algorithm 1's loop, run in draw order;
+ * exact sums rounded once). The stop counts and estimates therefore do not
+ * depend on G or B; at most G*B - 1 draws past the last stop are computed.
+ */
+
+/* The block of Bader's per-draw values for draws [i0, i0+count) of the stream
+ * (seed, qid): out[j*count + i] = delta_{s_{i0+i}}(v_j) for target j (Sec. 4
+ * step 2, Theorem 1), as bc_adaptive_sources accumulates them. targets as in
+ * bc_adaptive_sources (distinct, in [0, n); BC_E_INVALID otherwise);
+ * 0 <= count <= 2^32, i0 >= 0. out[T*count] is caller-owned host memory. */
+bc_status bc_target_dependencies(bc_ctx *ctx, bc_graph g, const int32_t *targets, int32_t T, uint64_t seed,
+                                 uint64_t qid, int64_t i0, int64_t count, double *out);
+
+/* Adds the exact sums over draws [i0, i0+count) of (seed, qid) of the
+ * uniform estimate (sum over sampled sources of delta_s(x), Eq. 4 restricted
+ * to the draws) into parts[6*n] (caller-owned host memory, in/out): vertex v's
+ * sum is the 192-bit fixed-point number (unit 2^-128) whose q-th 32-bit chunk
+ * is parts[6v + q]. Chunks of many partials (other blocks, other ranks) may be
+ * added as plain integers -- up to 2^30 partials per array -- before
+ * bc_acc_estimate resolves the carries. BC_E_RANGE if a dependency left the
+ * exact window. */
+bc_status bc_uniform_partial(bc_ctx *ctx, bc_graph g, uint64_t seed, uint64_t qid, int64_t i0, int64_t count,
+                             int64_t *parts);
+
+/* Host only (no context, no GPU). Adds each of count rows of n doubles (0 or
+ * in [2^-76, 2^63), else BC_E_RANGE) exactly into parts[6*n], in the format of
+ * bc_uniform_partial. */
+bc_status bc_acc_add_rows(int32_t n, const double *rows, int64_t count, int64_t *parts);
+
+/* Host only. est[v] = (n * S_v) / k with S_v the sum held in parts rounded
+ * once to nearest-even: bc_uniform_sources' estimate when parts hold the
+ * sums of draws 0..k-1. BC_E_RANGE if a sum does not fit 192 bits or a chunk
+ * is negative; BC_E_INVALID for k < 1, n < 1 or NULL. */
+bc_status bc_acc_estimate(int32_t n, const int64_t *parts, int64_t k, double *est);
+
+/* Host only. The stop scan over one block of per-draw values, block[j*W + t]
+ * the value of draw i0 + t for target j: for every target not yet done,
+ * S <- S + x, k <- i0 + t + 1, in draw order, until S * threshold_scale > cn
+ * (done; Sec. 4 step 3, Algorithm 1's loop test). Then est[j] = (n_scale *
+ * S[j]) / k[j] (0 while k[j] = 0) and status[j] = BC_STOPPED or BC_CAPPED for
+ * every target, and *remaining = targets not done. S, k, done (zero before the
+ * first block) are caller-owned state carried from block to block, which must
+ * be passed in draw order. n_scale is n for source sampling, n(n-1) for pairs. */
+bc_status bc_scan_block(int32_t T, const double *block, int32_t W, int64_t i0, double cn, double threshold_scale,
+                        double n_scale, double *S, int64_t *k, int32_t *done, double *est, int32_t *status,
+                        int32_t *remaining);
 
 /* ------------------------------------------------- allocation-free entry -- */
 /*

@@ -15,7 +15,7 @@ Two layers are exported:
 import importlib
 
 _EXPORTS = ("Context", "BCError", "capi", "BC_STOPPED", "BC_CAPPED", "BC_UNDIRECTED",
-            "BC_VALIDATE", "BC_DIRECTED", "LIB_PATH", "BC_OK", "BC_PENDING", "BC_QUERY_SOURCES", "BC_QUERY_PAIRS",
+            "BC_VALIDATE", "BC_DIRECTED", "BC_NORMALIZE", "LIB_PATH", "BC_OK", "BC_PENDING", "BC_QUERY_SOURCES", "BC_QUERY_PAIRS",
             "BC_QUERY_UNIFORM")
 __all__ = list(_EXPORTS)
 

@@ -25,6 +25,7 @@ BC_CAPPED = 1
 BC_UNDIRECTED = 1
 BC_VALIDATE = 2
 BC_DIRECTED = 4
+BC_NORMALIZE = 8
 BC_PENDING = 1
 BC_QUERY_SOURCES = 1
 BC_QUERY_PAIRS = 2
@@ -92,6 +93,11 @@ _SIGS = {
     "bc_draw_sources": (_i32, [_vp, _u64, _u64, _u64, _i64, _i32, _i32p]),
     "bc_draw_pairs": (_i32, [_vp, _u64, _u64, _u64, _i64, _i32, _i32p, _i32p]),
     "bc_exact_sum": (_i32, [_vp, _f64p, _i64, _f64p]),
+    "bc_target_dependencies": (_i32, [_vp, _i64, _i32p, _i32, _u64, _u64, _i64, _i64, _f64p]),
+    "bc_uniform_partial": (_i32, [_vp, _i64, _u64, _u64, _i64, _i64, _i64p]),
+    "bc_acc_add_rows": (_i32, [_i32, _f64p, _i64, _i64p]),
+    "bc_acc_estimate": (_i32, [_i32, _i64p, _i64, _f64p]),
+    "bc_scan_block": (_i32, [_i32, _f64p, _i32, _i64, _f64, _f64, _f64, _f64p, _i64p, _i32p, _f64p, _i32p, _i32p]),
     "bc_set_profiling": (_i32, [_vp, _i32]),
     "bc_get_stats": (_i32, [_vp, ctypes.POINTER(bc_stats)]),
     "bc_reset_stats": (_i32, [_vp]),
@@ -392,6 +398,64 @@ def bc_exact_sum(ctx, x) -> float:
     return float(out.value)
 
 
+def bc_target_dependencies(ctx, g: int, targets, seed: int, qid: int, i0: int, count: int) -> np.ndarray:
+    """[T][count] block of delta_{s_i}(v_j) for draws i0 .. i0+count-1."""
+    t = _i32arr(targets)
+    out = np.zeros((t.size, max(int(count), 0)), np.float64)
+    tp = t if t.size else np.zeros(1, np.int32)
+    op = out if out.size else np.zeros(1, np.float64)
+    _ck(ctx, _lib.bc_target_dependencies(ctx, g, _p(tp, _i32p), t.size, seed, qid, i0, int(count), _p(op, _f64p)))
+    return out
+
+
+def bc_uniform_partial(ctx, g: int, seed: int, qid: int, i0: int, count: int, parts: np.ndarray) -> np.ndarray:
+    """Adds the exact sums of draws i0 .. i0+count-1 into parts (int64 [n][6], in place)."""
+    if parts.dtype != np.int64 or not parts.flags.c_contiguous:
+        raise ValueError("parts must be a C-contiguous int64 array [n][6]")
+    _ck(ctx, _lib.bc_uniform_partial(ctx, g, seed, qid, i0, int(count), _p(parts, _i64p)))
+    return parts
+
+
+def _ck_host(rc, what):
+    if rc < 0:
+        raise BCError(rc, what)
+    return rc
+
+
+def bc_acc_add_rows(rows, parts: np.ndarray) -> np.ndarray:
+    """Adds rows (count x n doubles) exactly into parts (int64 [n][6], in place)."""
+    if parts.dtype != np.int64 or not parts.flags.c_contiguous:
+        raise ValueError("parts must be a C-contiguous int64 array [n][6]")
+    n = parts.shape[0]
+    r = np.ascontiguousarray(rows, dtype=np.float64).reshape(-1, n)
+    rp = r if r.size else np.zeros(1, np.float64)
+    _ck_host(_lib.bc_acc_add_rows(n, _p(rp, _f64p), r.shape[0], _p(parts, _i64p)), "bc_acc_add_rows")
+    return parts
+
+
+def bc_acc_estimate(parts: np.ndarray, k: int) -> np.ndarray:
+    parts = np.ascontiguousarray(parts, dtype=np.int64)
+    n = parts.shape[0]
+    est = np.empty(n, np.float64)
+    _ck_host(_lib.bc_acc_estimate(n, _p(parts, _i64p), int(k), _p(est, _f64p)), "bc_acc_estimate")
+    return est
+
+
+def bc_scan_block(block, i0: int, cn: float, threshold_scale: float, n_scale: float, state) -> int:
+    """Stop scan of one [T][W] block in draw order; state (S, k, done, est,
+    status: numpy arrays of T) is updated in place; returns targets not done."""
+    b = np.ascontiguousarray(block, dtype=np.float64)
+    S, k, done, est, status = state
+    T = S.shape[0]
+    W = b.shape[1] if b.ndim == 2 else 0
+    bp = b if b.size else np.zeros(1, np.float64)
+    rem = _i32()
+    _ck_host(_lib.bc_scan_block(T, _p(bp, _f64p), W, int(i0), float(cn), float(threshold_scale), float(n_scale),
+                                _p(S, _f64p), _p(k, _i64p), _p(done, _i32p), _p(est, _f64p), _p(status, _i32p),
+                                ctypes.byref(rem)), "bc_scan_block")
+    return int(rem.value)
+
+
 def bc_set_profiling(ctx, on: bool):
     _ck(ctx, _lib.bc_set_profiling(ctx, 1 if on else 0))
 
@@ -440,8 +504,10 @@ class Context:
         except Exception:
             pass
 
-    def load_graph(self, row_ptr, col, validate: bool = False, directed: bool = False, lengths=None) -> int:
-        flags = (BC_DIRECTED if directed else BC_UNDIRECTED) | (BC_VALIDATE if validate else 0)
+    def load_graph(self, row_ptr, col, validate: bool = False, directed: bool = False, lengths=None,
+                   normalize: bool = False) -> int:
+        flags = ((BC_DIRECTED if directed else BC_UNDIRECTED) | (BC_VALIDATE if validate else 0)
+                 | (BC_NORMALIZE if normalize else 0))
         if lengths is None:
             h = bc_graph_load_csr(self.ptr, row_ptr, col, flags)
         else:
@@ -500,6 +566,12 @@ class Context:
 
     def server_limits(self, max_active=0, mem_budget_bytes=0):
         bc_server_limits(self.ptr, max_active, mem_budget_bytes)
+
+    def target_dependencies(self, g, targets, seed, qid, i0, count):
+        return bc_target_dependencies(self.ptr, g, targets, seed, qid, i0, count)
+
+    def uniform_partial(self, g, seed, qid, i0, count, parts):
+        return bc_uniform_partial(self.ptr, g, seed, qid, i0, count, parts)
 
     def set_profiling(self, on: bool):
         bc_set_profiling(self.ptr, on)

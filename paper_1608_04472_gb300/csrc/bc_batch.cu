@@ -68,6 +68,47 @@ __device__ __forceinline__ void block_or_to(uint64_t x, uint64_t *dst) {
 }
 
 
+// Warp-wide 32x32 bit-matrix transpose: thread j holds row j; afterwards thread
+// i holds column i (bit j set iff bit i of row j was set). Five butterfly
+// stages, each exchanging the off-diagonal half-blocks of 16, 8, 4, 2 and 1 bits.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int k = 16 >> st;
+    const uint32_t m = st == 0 ? 0x0000FFFFu : (st == 1 ? 0x00FF00FFu : (st == 2 ? 0x0F0F0F0Fu : (st == 3 ? 0x33333333u : 0x55555555u)));
+    const uint32_t y = __shfl_xor_sync(FULL, x, k);
+    x = (lane & k) ? (((y >> k) & m) | (x & ~m)) : ((x & m) | ((y & m) << k));
+  }
+  return x;
+}
+
+// Lane ownership for per-lane item loops: thread i owns the i-th and the
+// (i+32)-th set lane of `lanes` in increasing order (-1 when absent); the
+// second one, when present, is always >= 32.
+__device__ __forceinline__ void own_lanes(uint64_t lanes, int8_t *tab, int &p0, int &p1) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lo = (unsigned)lanes, hi = (unsigned)(lanes >> 32);
+  const unsigned lt = (1u << lane) - 1u;
+  const int nlo = __popc(lo), L = nlo + __popc(hi);
+  if ((lo >> lane) & 1u) tab[__popc(lo & lt)] = (int8_t)lane;
+  if ((hi >> lane) & 1u) tab[nlo + __popc(hi & lt)] = (int8_t)(lane + 32);
+  __syncwarp();
+  p0 = lane < L ? (int)tab[lane] : -1;
+  p1 = lane + 32 < L ? (int)tab[lane + 32] : -1;
+  __syncwarp();
+}
+
+// The chunk's neighbour masks m (thread j: neighbour j) seen from lanes p0 and
+// p1: bit j of *c0 is bit p0 of m_j (0 when p0 < 0), likewise *c1 for p1.
+__device__ __forceinline__ void lane_columns(uint64_t m, int p0, int p1, uint32_t &c0, uint32_t &c1) {
+  const uint32_t tl = warp_transpose32((uint32_t)m), th = warp_transpose32((uint32_t)(m >> 32));
+  const uint32_t xl = __shfl_sync(FULL, tl, p0 & 31), xh = __shfl_sync(FULL, th, p0 & 31);
+  const uint32_t yh = __shfl_sync(FULL, th, p1 & 31);
+  c0 = p0 < 0 ? 0u : (p0 < 32 ? xl : xh);
+  c1 = p1 < 0 ? 0u : yh;
+}
+
 // Dynamic work distribution: a warp takes `step` consecutive items per atomic
 // (GRAB light vertices; one heavy segment or heavy vertex, whose work is large).
 __device__ __forceinline__ int grab(unsigned *wq, int step = GRAB) {
@@ -425,6 +466,92 @@ k_fwd_heavy(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restri
   ovf = warp_or64(ovf);
   if (lane == 0 && ovf) atomicOr((unsigned long long *)(enable + 3), (unsigned long long)ovf);
   (void)err;
+  tri = warp_sum64(tri);
+  if (lane == 0 && tri) atomicAdd(cnt, tri);
+}
+
+// The same with per-lane item loops: thread i owns the i-th (and (i+32)-th)
+// pending lane of v; a warp transpose turns the chunk's 32 predecessor masks
+// into one 32-bit column per owned lane, and each thread adds only the counts
+// of the predecessors in its own lanes. A hub-adjacent chunk has predecessors in
+// a fraction of the pending lanes, so this skips the lane slots a 64-wide step
+// per predecessor would leave idle.
+__global__ void __launch_bounds__(FWD_THREADS)
+k_fwd_heavy_lane(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restrict__ seg_b,
+                 const int32_t *__restrict__ seg_e, const int32_t *__restrict__ col,
+                 const uint64_t *__restrict__ lm_prev, uint64_t *__restrict__ lm_cur,
+                 const uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
+                 const uint64_t *__restrict__ active_prev, uint64_t *__restrict__ enable,
+                 unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq) {
+  __shared__ int32_t sws[FWD_THREADS / 32][32];
+  __shared__ int8_t tabs[FWD_THREADS / 32][64];
+  int32_t *sw = sws[threadIdx.x >> 5];
+  int8_t *tab = tabs[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const uint64_t act = *active_prev & *enable;
+  unsigned long long tri = 0ull;
+  uint64_t ovf = 0ull;
+  for (int s = grab(wq, 1); s < nseg; s = grab(wq, 1)) {
+    const int32_t v = seg_v[s];
+    const int beg = seg_b[s], end = seg_e[s];
+    const uint64_t pend = ~visited[v] & act;
+    if (!pend) continue;
+    int p0, p1;
+    own_lanes(pend, tab, p0, p1);
+    uint64_t newm = 0ull, s0 = 0ull, s1 = 0ull;
+    bool o0 = false, o1 = false;
+    for (int base = beg; base < end; base += 32) {
+      const int j = base + lane;
+      int32_t w = 0;
+      uint64_t m = 0ull;
+      if (j < end) {
+        w = col[j];
+        m = lm_prev[w] & pend;
+      }
+      newm |= m;
+      tri += (unsigned long long)__popcll((long long)m);
+      sw[lane] = w;
+      uint32_t c0, c1;
+      lane_columns(m, p0, p1, c0, c1);
+      __syncwarp();
+      while (c0) {
+        const int ja = __ffs(c0) - 1;
+        c0 &= c0 - 1u;
+        const int jb = c0 ? __ffs(c0) - 1 : ja;
+        const bool hb = c0 != 0u;
+        if (hb) c0 &= c0 - 1u;
+        const uint64_t xa = sigma[(size_t)sw[ja] * 64 + p0];
+        const uint64_t xb = hb ? sigma[(size_t)sw[jb] * 64 + p0] : 0ull;
+        uint64_t t = s0 + xa;
+        o0 |= t < s0;
+        s0 = t + xb;
+        o0 |= s0 < t;
+      }
+      while (c1) {
+        const int ja = __ffs(c1) - 1;
+        c1 &= c1 - 1u;
+        const uint64_t xa = sigma[(size_t)sw[ja] * 64 + p1];
+        const uint64_t t = s1 + xa;
+        o1 |= t < s1;
+        s1 = t;
+      }
+      __syncwarp();
+    }
+    newm = warp_or64(newm);
+    if (!newm) continue;
+    unsigned long long *dst = (unsigned long long *)(sigma + (size_t)v * 64);
+    if (p0 >= 0 && ((newm >> p0) & 1ull)) {
+      const unsigned long long old = atomicAdd(dst + p0, (unsigned long long)s0);
+      if (o0 || old + s0 < old) ovf |= 1ull << p0;
+    }
+    if (p1 >= 0 && ((newm >> p1) & 1ull)) {
+      const unsigned long long old = atomicAdd(dst + p1, (unsigned long long)s1);
+      if (o1 || old + s1 < old) ovf |= 1ull << p1;
+    }
+    if (lane == 0) atomicOr((unsigned long long *)&lm_cur[v], (unsigned long long)newm);
+  }
+  ovf = warp_or64(ovf);
+  if (lane == 0 && ovf) atomicOr((unsigned long long *)(enable + 3), (unsigned long long)ovf);
   tri = warp_sum64(tri);
   if (lane == 0 && tri) atomicAdd(cnt, tri);
 }
@@ -908,6 +1035,85 @@ k_bwd_heavy_seg_fx(int nseg, const int32_t *__restrict__ seg_v, const int32_t *_
   if (e) atomicOr(err, e);
 }
 
+// Heavy segments with per-lane item loops (see k_fwd_heavy_lane): thread i
+// owns the i-th (and (i+32)-th) lane of v at this level and adds, exactly, the
+// coefficients of the successors in its own lanes only; the partial sums go to
+// part[s][lane] as in k_bwd_heavy_seg_fx.
+__device__ __forceinline__ void acc2_add_nz(Acc2 &a, uint64_t bits, unsigned &err) {
+  const uint32_t hi = (uint32_t)(bits >> 32), lo = (uint32_t)bits;
+  const int p = (int)(hi >> 20) - 979;  // lowest mantissa bit, in units of 2^-96
+  if ((unsigned)p > 75u) {
+    err |= ERR_RANGE;
+    return;
+  }
+  const uint32_t mh = (hi & 0x000FFFFFu) | 0x00100000u;
+  const int r = p & 31, q = p >> 5;
+  const uint32_t c0 = lo << r;
+  const uint32_t c1 = __funnelshift_l(lo, mh, r);
+  const uint32_t c2 = __funnelshift_l(mh, 0u, r);
+  const uint32_t t0 = (q == 0) ? c0 : 0u;
+  const uint32_t t1 = (q == 0) ? c1 : ((q == 1) ? c0 : 0u);
+  const uint32_t t2 = (q == 0) ? c2 : ((q == 1) ? c1 : c0);
+  const uint32_t t3 = (q == 1) ? c2 : ((q == 2) ? c1 : 0u);
+  acc2_add4(a, t0, t1, t2, t3);
+}
+
+__global__ void __launch_bounds__(FWD_THREADS, BWD_MIN_BLOCKS)
+k_bwd_heavy_seg_lane(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restrict__ seg_b,
+                     const int32_t *__restrict__ seg_e, const int32_t *__restrict__ col,
+                     const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
+                     const uint64_t *__restrict__ coef, uint4 *__restrict__ part, unsigned *__restrict__ wq,
+                     unsigned *__restrict__ err, uint64_t keep) {
+  __shared__ int32_t sws[FWD_THREADS / 32][32];
+  __shared__ int8_t tabs[FWD_THREADS / 32][64];
+  int32_t *sw = sws[threadIdx.x >> 5];
+  int8_t *tab = tabs[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  unsigned e = 0u;
+  for (int s = grab(wq, 1); s < nseg; s = grab(wq, 1)) {
+    const int32_t v = seg_v[s];
+    const uint64_t lanes = lm_cur[v] & keep;
+    if (!lanes) continue;
+    int p0, p1;
+    own_lanes(lanes, tab, p0, p1);
+    Acc2 a0 = acc2_zero(), a1 = acc2_zero();
+    const int end = seg_e[s];
+    for (int base = seg_b[s]; base < end; base += 32) {
+      const int j = base + lane;
+      int32_t w = 0;
+      uint64_t m = 0ull;
+      if (j < end) {
+        w = col[j];
+        m = lm_next[w] & lanes;
+      }
+      sw[lane] = w;
+      uint32_t c0, c1;
+      lane_columns(m, p0, p1, c0, c1);
+      __syncwarp();
+      while (c0) {
+        const int ja = __ffs(c0) - 1;
+        c0 &= c0 - 1u;
+        const bool hb = c0 != 0u;
+        const int jb = hb ? __ffs(c0) - 1 : ja;
+        if (hb) c0 &= c0 - 1u;
+        const uint64_t xa = coef[(size_t)sw[ja] * 64 + p0];
+        const uint64_t xb = hb ? coef[(size_t)sw[jb] * 64 + p0] : 0ull;
+        acc2_add_nz(a0, xa, e);
+        if (hb) acc2_add_nz(a0, xb, e);
+      }
+      while (c1) {
+        const int ja = __ffs(c1) - 1;
+        c1 &= c1 - 1u;
+        acc2_add_nz(a1, coef[(size_t)sw[ja] * 64 + p1], e);
+      }
+      __syncwarp();
+    }
+    if (p0 >= 0) part[(size_t)s * 64 + p0] = make_uint4(a0.l0, a0.l1, a0.l2, a0.l3);
+    if (p1 >= 0) part[(size_t)s * 64 + p1] = make_uint4(a1.l0, a1.l1, a1.l2, a1.l3);
+  }
+  if (e) atomicOr(err, e);
+}
+
 __global__ void __launch_bounds__(FWD_THREADS, BWD_MIN_BLOCKS)
 k_bwd_heavy_fin_fx(int nh, const int32_t *__restrict__ heavy, const int32_t *__restrict__ hseg0,
                    const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ sigma,
@@ -1145,7 +1351,13 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
                                                  hm.heavy_deg, ctx->pk_maxl, ctx->pk_mincnt);
     }
     const bool heavy_now = hm.nseg && !heavy_done;
-    if (heavy_now) {
+    if (heavy_now && ctx->heavy_lane) {
+      LaunchScope ls(ctx, F_FWD);
+      k_fwd_heavy_lane<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
+          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
+          lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
+          act + l, ws.enable.as<uint64_t>(), ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 1);
+    } else if (heavy_now) {
       LaunchScope ls(ctx, F_FWD);
       k_fwd_heavy<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
           hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
@@ -1233,7 +1445,8 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
       if (hm.nseg && heavy_at(ws, l)) {
         {
           LaunchScope ls(ctx, F_BWD);
-          k_bwd_heavy_seg_fx<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
+          auto kseg = ctx->heavy_lane ? k_bwd_heavy_seg_lane : k_bwd_heavy_seg_fx;
+          kseg<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
               hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
               lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), hm.part2.as<uint4>(),
               ws.wq.as<unsigned>() + 8 * l + 3, ws.err.as<unsigned>(), keep);

@@ -695,6 +695,76 @@ static void do_adaptive_sources(bc_ctx *ctx, const Graph &g, const int32_t *targ
   copy_scan_out(ctx, T, ss, (double)g.n, est, k, S, status);
 }
 
+// ------------------------------------------- blocks of one sharded query --
+// The B x T block of Bader's sum for draws [i0, i0+count) of (seed, qid)
+// (Sec. 4 step 2): out[j*count + i] = delta_{s_{i0+i}}(v_j), computed by the
+// same draw windows and engines as the adaptive loop. Ranks that share one
+// query each compute their own blocks of draws with this and exchange them.
+static void do_target_block(bc_ctx *ctx, const Graph &g, const int32_t *targets, int32_t T, uint64_t seed,
+                            uint64_t qid, int64_t i0, int64_t count, double *out) {
+  Workspace &ws = ctx->ws;
+  const size_t n = (size_t)g.n;
+  cudaStream_t st = ctx->stream;
+  ws.tslot.ensure(n * 4);
+  ws.tdelta.ensure((size_t)std::max(T, 1) * WMAX * 8);
+  {
+    LaunchScope ls(ctx, F_MISC);
+    k_fill_i32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((int64_t)n, -1, ws.tslot.as<int32_t>());
+  }
+  ws.misc.ensure((size_t)std::max(T, 1) * 4 + 64);
+  int32_t *d_targets = dev_upload(ctx, ws.misc, targets, (size_t)T);
+  {
+    LaunchScope ls(ctx, F_MISC);
+    k_set_slots<<<(T + 127) / 128, 128, 0, st>>>(T, d_targets, ws.tslot.as<int32_t>());
+  }
+  KeyMeta &km = key_meta(ctx, g, false);
+  std::vector<double> h((size_t)T * WMAX);
+  for (int64_t a = 0; a < count; a += WMAX) {
+    const int W = (int)std::min<int64_t>(WMAX, count - a);
+    draw_window(ctx, g, km, seed, qid, i0 + a, W);
+    BCG_CUDA(cudaMemsetAsync(ws.tdelta.p, 0, (size_t)T * W * 8, st));
+    Sink sink;
+    sink.tslot = ws.tslot.as<int32_t>();
+    sink.tdelta = ws.tdelta.as<double>();
+    sink.tstride = W;
+    run_window(ctx, g, W, sink);
+    BCG_CUDA(cudaMemcpyAsync(h.data(), ws.tdelta.p, (size_t)T * W * 8, cudaMemcpyDeviceToHost, st));
+    sync(ctx);
+    for (int32_t j = 0; j < T; ++j)
+      std::memcpy(out + (size_t)j * count + a, h.data() + (size_t)j * W, (size_t)W * 8);
+  }
+  check_err_bits(ctx);
+}
+
+// The uniform estimate's exact sums over draws [i0, i0+count) (the sum over
+// sources of Eq. 4, restricted to these draws), added into parts: vertex v's
+// 192-bit fixed-point sum (unit 2^-128) as six 32-bit chunks, chunk q in
+// parts[6v + q]. Chunks in int64 let many such partials be added (by ranks,
+// with a plain integer sum) before the carries are resolved.
+static void do_uniform_partial(bc_ctx *ctx, const Graph &g, uint64_t seed, uint64_t qid, int64_t i0, int64_t count,
+                               int64_t *parts) {
+  Workspace &ws = ctx->ws;
+  const size_t n = (size_t)g.n;
+  ws.acc.ensure(n * sizeof(Acc));
+  BCG_CUDA(cudaMemsetAsync(ws.acc.p, 0, n * sizeof(Acc), ctx->stream));
+  Sink sink;
+  sink.acc = ws.acc.as<Acc>();
+  KeyMeta &km = key_meta(ctx, g, false);
+  for (int64_t a = 0; a < count; a += WMAX) {
+    const int W = (int)std::min<int64_t>(WMAX, count - a);
+    draw_window(ctx, g, km, seed, qid, i0 + a, W);
+    run_window(ctx, g, W, sink);
+  }
+  check_err_bits(ctx);
+  std::vector<Acc> h(n);
+  BCG_CUDA(cudaMemcpyAsync(h.data(), ws.acc.p, n * sizeof(Acc), cudaMemcpyDeviceToHost, ctx->stream));
+  sync(ctx);
+  for (size_t v = 0; v < n; ++v) {
+    const uint64_t w[3] = {h[v].w0, h[v].w1, h[v].w2};
+    for (int q = 0; q < 6; ++q) parts[6 * v + q] += (int64_t)((w[q >> 1] >> (32 * (q & 1))) & 0xFFFFFFFFull);
+  }
+}
+
 // Per-target BFS into [n][Tp] layouts (d(v_j, .) and sigma_{v_j .}). A target
 // whose counts exceed 2^64-1 is recomputed in the extended form: its tsig
 // entries then hold mantissa bits, texp (allocated on first need, [n][Tp])
@@ -1003,9 +1073,51 @@ using namespace bcg;
 
 namespace bcg {
 
+// BC_NORMALIZE: rows sorted, self-loops and duplicate columns dropped (a
+// duplicate edge with lengths keeps the shortest one); the result is written
+// to rp2/col2/w2 (w2 only with lengths).
+static void normalize_csr(int32_t n, const int32_t *row_ptr, const int32_t *col, const uint32_t *wts, int64_t nnz,
+                          std::vector<int32_t> &rp2, std::vector<int32_t> &col2, std::vector<uint32_t> &w2) {
+  if (n < 1) fail(BC_E_INVALID, "n must be >= 1");
+  if (n > (1 << 30)) fail(BC_E_TOO_LARGE, "n too large");
+  if (nnz < 0 || nnz >= ((int64_t)1 << 31)) fail(BC_E_TOO_LARGE, "nnz must be < 2^31");
+  if (row_ptr[0] != 0 || (int64_t)row_ptr[n] != nnz) fail(BC_E_BAD_GRAPH, "row_ptr[0] must be 0 and row_ptr[n] == nnz");
+  if (nnz > 0 && !col) fail(BC_E_INVALID, "col is NULL");
+  rp2.assign((size_t)n + 1, 0);
+  col2.clear();
+  w2.clear();
+  col2.reserve((size_t)nnz);
+  if (wts) w2.reserve((size_t)nnz);
+  std::vector<std::pair<int32_t, uint32_t>> row;
+  for (int32_t v = 0; v < n; ++v) {
+    if (row_ptr[v + 1] < row_ptr[v]) fail(BC_E_BAD_GRAPH, "row_ptr must be non-decreasing");
+    row.clear();
+    for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) {
+      const int32_t w = col[j];
+      if (w < 0 || w >= n) fail(BC_E_BAD_GRAPH, "column out of range");
+      if (w != v) row.emplace_back(w, wts ? wts[j] : 1u);
+    }
+    std::sort(row.begin(), row.end());  // by column, then length: the first of a run is the shortest
+    for (size_t k = 0; k < row.size(); ++k) {
+      if (k > 0 && row[k].first == row[k - 1].first) continue;
+      col2.push_back(row[k].first);
+      if (wts) w2.push_back(row[k].second);
+    }
+    rp2[(size_t)v + 1] = (int32_t)col2.size();
+  }
+}
+
 static void load_graph(bc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col, const uint32_t *wts,
                        int64_t nnz, uint32_t flags, bc_graph *out) {
   if (!out || !row_ptr) fail(BC_E_INVALID, "NULL argument");
+  if (flags & BC_NORMALIZE) {
+    std::vector<int32_t> rp2, col2;
+    std::vector<uint32_t> w2;
+    normalize_csr(n, row_ptr, col, wts, nnz, rp2, col2, w2);
+    load_graph(ctx, n, rp2.data(), col2.data(), wts ? w2.data() : nullptr, (int64_t)col2.size(),
+               flags & ~BC_NORMALIZE, out);
+    return;
+  }
   const bool directed = (flags & BC_DIRECTED) != 0;
   if (directed == ((flags & BC_UNDIRECTED) != 0))
     fail(BC_E_INVALID, "flags need exactly one of BC_UNDIRECTED and BC_DIRECTED");
@@ -1180,6 +1292,7 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
     if (const char *dl = std::getenv("BCG_DEEP_LEVELS")) ctx->deep_levels = std::atoi(dl);
     if (const char *pm = std::getenv("BCG_PK_MAXL")) ctx->pk_maxl = std::atoi(pm);
     if (const char *pc = std::getenv("BCG_PK_MINCNT")) ctx->pk_mincnt = std::atoi(pc);
+    if (const char *hl = std::getenv("BCG_HEAVY_LANE")) ctx->heavy_lane = std::atoi(hl);
     if (const char *mc = std::getenv("BCG_MULTI_CAP")) ctx->multi_cap = std::atoi(mc);
     if (const char *pe = std::getenv("BCG_PAIR_ENGINE")) ctx->pair_engine = std::atoi(pe) == 1 ? 1 : 0;
     if (const char *ws = std::getenv("BCG_W_STEP")) ctx->w_step = std::atoll(ws);
@@ -1469,6 +1582,29 @@ bc_status bc_exact_sum(bc_ctx *ctx, const double *x, int64_t count, double *out)
     throw;
   }
   b.release();
+  BC_GUARD_END
+}
+
+bc_status bc_target_dependencies(bc_ctx *ctx, bc_graph g, const int32_t *targets, int32_t T, uint64_t seed,
+                                 uint64_t qid, int64_t i0, int64_t count, double *out) {
+  BC_GUARD_BEGIN
+  const Graph &gr = get_graph(ctx, g);
+  if (i0 < 0 || count < 0 || count > ((int64_t)1 << 32)) fail(BC_E_INVALID, "need i0 >= 0 and 0 <= count <= 2^32");
+  if (T > 0 && count > 0 && !out) fail(BC_E_INVALID, "out is NULL");
+  validate_targets(gr, targets, T);
+  BCG_CUDA(cudaSetDevice(ctx->device));
+  if (T > 0 && count > 0) do_target_block(ctx, gr, targets, T, seed, qid, i0, count, out);
+  BC_GUARD_END
+}
+
+bc_status bc_uniform_partial(bc_ctx *ctx, bc_graph g, uint64_t seed, uint64_t qid, int64_t i0, int64_t count,
+                             int64_t *parts) {
+  BC_GUARD_BEGIN
+  const Graph &gr = get_graph(ctx, g);
+  if (i0 < 0 || count < 0 || count > ((int64_t)1 << 32)) fail(BC_E_INVALID, "need i0 >= 0 and 0 <= count <= 2^32");
+  if (!parts) fail(BC_E_INVALID, "parts is NULL");
+  BCG_CUDA(cudaSetDevice(ctx->device));
+  if (count > 0) do_uniform_partial(ctx, gr, seed, qid, i0, count, parts);
   BC_GUARD_END
 }
 

@@ -170,11 +170,20 @@ RN_HD double rn_div_u53(double x, uint64_t s) {
     // s = 2^(b-1): exact exponent shift
     return double_of(xb - ((uint64_t)(b - 1) << 52));
   }
-  // seed: rf = RN(1/RN(s)) * 2^b ~ 2^b/s in [1, 2] (relative error < 2^-22);
-  // r0 = rf * 2^63 ~ 2^(63+b)/s, an integer since rf has 24 significant bits
-  const float rf = rcp_f32((float)s) * pow2f(b);
-  const uint64_t r62 = (uint64_t)(rf * pow2f(62));  // exact, in [2^62, 2^63]
-  uint64_t r = r62 >= (1ull << 63) ? ~0ull : (r62 << 1);
+  // seed: the top 32 bits of s, s32 = s >> max(b - 32, 0), converted from a
+  // 32-bit integer (no 64-bit conversion); rf = RN(1/RN(s32)) * 2^min(b, 32)
+  // ~ 2^b/s in [1, 2] (relative error < 2^-22); r0 = rf * 2^63 ~ 2^(63+b)/s,
+  // read off rf's bits: rf = 1.m (24 bits) gives 2^63 + m * 2^40, rf = 2 the
+  // largest 64-bit value
+  const int sh32 = b > 32 ? b - 32 : 0;
+  const float rf = rcp_f32((float)(uint32_t)(s >> sh32)) * pow2f(b - sh32);
+  uint32_t fb;
+#if defined(__CUDA_ARCH__)
+  fb = __float_as_uint(rf);
+#else
+  memcpy(&fb, &rf, 4);
+#endif
+  uint64_t r = (fb >> 23) >= 128u ? ~0ull : ((1ull << 63) | ((uint64_t)(fb & 0x7FFFFFu) << 40));
   // Newton-Raphson: E = 2^(63+b) - s*r (|E| << 2^(63+b)); r += r*E/2^(63+b)
 #pragma unroll
   for (int it = 0; it < 2; ++it) {

@@ -45,7 +45,7 @@ def test_binding_constants_match_header():
     from paper_1608_04472_gb300 import capi as mod
     text = open(HEADER).read()
     defs = dict(re.findall(r"#define\s+(BC_[A-Z_]+)\s+(-?\d+)u?\b", text))
-    names = ["BC_UNDIRECTED", "BC_VALIDATE", "BC_DIRECTED", "BC_STOPPED", "BC_CAPPED"]
+    names = ["BC_UNDIRECTED", "BC_VALIDATE", "BC_DIRECTED", "BC_NORMALIZE", "BC_STOPPED", "BC_CAPPED"]
     for name in names:
         assert name in defs, name
         assert getattr(mod, name) == int(defs[name]), name

@@ -117,7 +117,8 @@ def test_dependencies_er2000(ctx, er2000, width):
 
 @pytest.mark.parametrize("width", WIDTHS)
 def test_dependencies_rmat_s12_with_hubs(ctx, width):
-    # edge factor 64 so the top vertices exceed the heavy-degree split (2048)
+    # edge factor 64: the top vertices exceed the heavy-degree split (256) many
+    # times over, so they are split into several 256-neighbour segments
     g = gg.rmat(12, 64, 0.57, 0.19, 0.19, 3)
     assert g.degrees().max() > 2048
     srcs = np.array([0, 1, 2, 100, 4095, int(np.argmax(g.degrees() == 0))], np.int32)

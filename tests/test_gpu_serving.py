@@ -144,3 +144,55 @@ def test_graph_in_use_and_bad_submissions(ctx, graphs, pkg):
         ctx.submit(hs["er"], pkg.BC_QUERY_SOURCES, targets=[1], c=0.5, cap=10)
     with pytest.raises(pkg.BCError):
         ctx.submit(hs["er"], 99, targets=[1], c=2.0, cap=10)
+
+
+def _served_intervals(ctx, pkg, h, specs):
+    """Submits all queries at once; returns (tickets, [(admit, done)] in seconds
+    on the host clock), from each ticket's queue and run times."""
+    t_sub, tks = [], []
+    for kw in specs:
+        t_sub.append(time.perf_counter())
+        tks.append(ctx.submit(h, pkg.BC_QUERY_PAIRS, **kw))
+    for tk in tks:
+        ctx.poll(tk, -1)
+    iv = []
+    for t0, tk in zip(t_sub, tks):
+        admit = t0 + tk.stats.queue_ms / 1e3
+        iv.append((admit, admit + tk.stats.run_ms / 1e3))
+    return tks, iv
+
+
+def test_admission_by_device_memory(ctx, graphs, pkg):
+    """A pair query holds d(v,.) and sigma_v. for its T targets (T*n*12 bytes +
+    T*64). With a budget that fits one such query, three submitted together run
+    one after another (each admitted only once the previous one has finished and
+    freed its memory); with the default budget they overlap. Results are
+    bit-identical to the queries run alone either way; a query larger than the
+    budget is refused at submit."""
+    g, hs = graphs
+    ba = g["ba"]
+    T = 4
+    need = T * ba.n * 12 + T * 64
+    specs = [dict(targets=gg.degree_targets(ba, T, 30 + i), c=1.0, cap=6000, seed=40 + i, qid=i) for i in range(3)]
+    refs = [ctx.adaptive_pairs(hs["ba"], kw["targets"], kw["c"], kw["cap"], kw["seed"], kw["qid"]) for kw in specs]
+    try:
+        ctx.server_limits(max_active=64, mem_budget_bytes=need + need // 2)
+        tks, iv = _served_intervals(ctx, pkg, hs["ba"], specs)
+        for tk, ref in zip(tks, refs):
+            for key in ["est", "k", "S", "status"]:
+                _same(tk.outputs()[key], ref[key], key)
+        for (a0, d0), (a1, d1) in zip(iv, iv[1:]):
+            assert a1 >= d0 - 2e-3, f"admitted at {a1 - d0:+.4f} s relative to the previous query's end"
+        assert all(tk.stats.queue_ms > 0 for tk in tks[1:])
+        with pytest.raises(pkg.BCError) as e:
+            ctx.submit(hs["ba"], pkg.BC_QUERY_PAIRS, targets=gg.degree_targets(ba, 2 * T, 9), c=1.0, cap=10)
+        assert e.value.code == -2  # BC_E_NOMEM: more than the whole budget
+    finally:
+        # back to the default budget, a quarter of the device's memory
+        torch = pytest.importorskip("torch")
+        ctx.server_limits(max_active=64, mem_budget_bytes=torch.cuda.get_device_properties(0).total_memory // 4)
+    tks, iv = _served_intervals(ctx, pkg, hs["ba"], specs)
+    for tk, ref in zip(tks, refs):
+        for key in ["est", "k", "S", "status"]:
+            _same(tk.outputs()[key], ref[key], key)
+    assert any(a1 < d0 for (a0, d0), (a1, d1) in zip(iv, iv[1:])), "with room for all, the queries should overlap"
