@@ -384,6 +384,49 @@ bc_status bc_scan_block(int32_t T, const double *block, int32_t W, int64_t i0, d
                         double n_scale, double *S, int64_t *k, int32_t *done, double *est, int32_t *status,
                         int32_t *remaining);
 
+/* ------------------------------------------------------------------ tuning -- */
+/*
+ * Launch settings of the engines, kept per graph. None of them changes a
+ * result: every count is an exact integer sum and every sum of dependencies
+ * or coefficients an exact sum rounded once, so only the speed differs.
+ */
+typedef struct bc_tuning {
+  int32_t batch_width;        /* 64: 64 sources share one traversal (level masks); 1: plain kernels */
+  int32_t heavy_degree;       /* vertices of larger degree are split into segments (32 ..) */
+  int32_t segment;            /* neighbours per heavy segment (32 ..) */
+  int32_t packed_max_lanes;   /* light forward: a 32-neighbour chunk over at most this many lanes ... */
+  int32_t packed_min_preds;   /* ... with at least this many predecessors is summed in packed groups
+                                 (packed_max_lanes 0: never) */
+  int32_t bwd_variant;        /* backward (counts <= 2^44): 1 packed lane groups, 0 two lane halves */
+  int32_t heavy_lane;         /* heavy segments: 1 per-lane item loops, 0 a 64-lane step per neighbour */
+  int32_t push_div;           /* forward level top-down (push from the level's vertices, counts pulled
+                                 for the reached ones) when the level's degree sum is <= nnz/push_div;
+                                 bottom-up otherwise; 0: always bottom-up (Sec. 3 step 1 either way) */
+  int32_t deep_levels;        /* the hub's eccentricity above which the graph runs one source per
+                                 persistent CTA instead of level masks */
+  int32_t reserved0;
+  double trial_ms;            /* bc_autotune: the chosen setting's trial time (output only) */
+} bc_tuning;
+
+/* Picks the tuning of graph g by coordinate descent from its current setting:
+ * each knob in turn takes each of a few values, a uniform k-draw estimate
+ * (seed, a fixed query id) is timed with CUDA events on the context's stream
+ * after a short warm-up of the same setting, and the fastest value is kept
+ * (ties keep the current one). Every trial's estimate must equal the first
+ * one bit for bit (else BC_E_DEVICE: a setting changed a result). The result
+ * is kept beside the graph (every later call on g uses it, also through the
+ * query server) and written to *out. 1 <= k <= 2^20. The plain width (1) is
+ * tried only on graphs of at most 2^17 vertices. */
+bc_status bc_autotune(bc_ctx *ctx, bc_graph g, int64_t k, uint64_t seed, bc_tuning *out);
+
+/* The tuning in force for graph g (the context's defaults until one is set). */
+bc_status bc_get_tuning(bc_ctx *ctx, bc_graph g, bc_tuning *out);
+
+/* Sets graph g's tuning (e.g. one cached from an earlier bc_autotune); values
+ * out of the ranges above are BC_E_INVALID. Queries already submitted keep the
+ * setting they were submitted with. */
+bc_status bc_set_tuning(bc_ctx *ctx, bc_graph g, const bc_tuning *t);
+
 /* ------------------------------------------------- allocation-free entry -- */
 /*
  * Not from the paper (it has no counterpart): a variant of bc_source_dependencies

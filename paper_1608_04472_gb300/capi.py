@@ -59,6 +59,18 @@ class bc_query(ctypes.Structure):
                 ("stats", ctypes.POINTER(bc_query_stats))]
 
 
+class bc_tuning(ctypes.Structure):
+    _fields_ = [("batch_width", _i32), ("heavy_degree", _i32), ("segment", _i32), ("packed_max_lanes", _i32),
+                ("packed_min_preds", _i32), ("bwd_variant", _i32), ("heavy_lane", _i32), ("push_div", _i32),
+                ("deep_levels", _i32), ("reserved0", _i32), ("trial_ms", _f64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved0"}
+
+
+TUNING_FIELDS = tuple(name for name, _ in bc_tuning._fields_ if name not in ("reserved0", "trial_ms"))
+
+
 class bc_stats(ctypes.Structure):
     _fields_ = [("launches", _i64), ("samples", _i64), ("batches", _i64), ("dag_edges", _i64),
                 ("reached", _i64),
@@ -98,6 +110,9 @@ _SIGS = {
     "bc_acc_add_rows": (_i32, [_i32, _f64p, _i64, _i64p]),
     "bc_acc_estimate": (_i32, [_i32, _i64p, _i64, _f64p]),
     "bc_scan_block": (_i32, [_i32, _f64p, _i32, _i64, _f64, _f64, _f64, _f64p, _i64p, _i32p, _f64p, _i32p, _i32p]),
+    "bc_autotune": (_i32, [_vp, _i64, _i64, _u64, ctypes.POINTER(bc_tuning)]),
+    "bc_get_tuning": (_i32, [_vp, _i64, ctypes.POINTER(bc_tuning)]),
+    "bc_set_tuning": (_i32, [_vp, _i64, ctypes.POINTER(bc_tuning)]),
     "bc_set_profiling": (_i32, [_vp, _i32]),
     "bc_get_stats": (_i32, [_vp, ctypes.POINTER(bc_stats)]),
     "bc_reset_stats": (_i32, [_vp]),
@@ -456,6 +471,25 @@ def bc_scan_block(block, i0: int, cn: float, threshold_scale: float, n_scale: fl
     return int(rem.value)
 
 
+def bc_autotune(ctx, g: int, k: int = 256, seed: int = 1) -> dict:
+    t = bc_tuning()
+    _ck(ctx, _lib.bc_autotune(ctx, g, int(k), seed, ctypes.byref(t)))
+    return t.as_dict()
+
+
+def bc_get_tuning(ctx, g: int) -> dict:
+    t = bc_tuning()
+    _ck(ctx, _lib.bc_get_tuning(ctx, g, ctypes.byref(t)))
+    return t.as_dict()
+
+
+def bc_set_tuning(ctx, g: int, tuning: dict):
+    t = bc_tuning()
+    for name in TUNING_FIELDS:
+        setattr(t, name, int(tuning[name]))
+    _ck(ctx, _lib.bc_set_tuning(ctx, g, ctypes.byref(t)))
+
+
 def bc_set_profiling(ctx, on: bool):
     _ck(ctx, _lib.bc_set_profiling(ctx, 1 if on else 0))
 
@@ -572,6 +606,15 @@ class Context:
 
     def uniform_partial(self, g, seed, qid, i0, count, parts):
         return bc_uniform_partial(self.ptr, g, seed, qid, i0, count, parts)
+
+    def autotune(self, g, k=256, seed=1):
+        return bc_autotune(self.ptr, g, k, seed)
+
+    def get_tuning(self, g):
+        return bc_get_tuning(self.ptr, g)
+
+    def set_tuning(self, g, tuning):
+        bc_set_tuning(self.ptr, g, tuning)
 
     def set_profiling(self, on: bool):
         bc_set_profiling(self.ptr, on)

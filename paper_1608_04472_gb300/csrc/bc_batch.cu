@@ -136,7 +136,9 @@ __global__ void k_batch_init(int count, const int32_t *__restrict__ sources,
                              uint64_t *__restrict__ lm0, uint64_t *__restrict__ visited,
                              uint64_t *__restrict__ sigma, uint64_t *__restrict__ active0,
                              uint64_t *__restrict__ enable, int32_t *__restrict__ pair_d,
-                             uint64_t *__restrict__ pair_sig) {
+                             uint64_t *__restrict__ pair_sig, const int32_t *__restrict__ rp,
+                             int32_t *__restrict__ list0, unsigned *__restrict__ vcnt0,
+                             unsigned long long *__restrict__ vedges0) {
   const int t = threadIdx.x;
   if (t < 64) {
     pair_d[t] = -1;
@@ -151,11 +153,33 @@ __global__ void k_batch_init(int count, const int32_t *__restrict__ sources,
   if (t < count) {
     const int32_t s = sources[t];
     const uint64_t bit = 1ull << t;
-    atomicOr((unsigned long long *)&lm0[s], (unsigned long long)bit);
+    const unsigned long long old = atomicOr((unsigned long long *)&lm0[s], (unsigned long long)bit);
     atomicOr((unsigned long long *)&visited[s], (unsigned long long)bit);
     sigma[(size_t)s * 64 + t] = 1ull;
     atomicOr((unsigned long long *)active0, (unsigned long long)bit);
+    if (old == 0ull && list0) {  // first lane with this source: it joins the level-0 list
+      list0[atomicAdd(vcnt0, 1u)] = s;
+      atomicAdd(vedges0, (unsigned long long)(rp[s + 1] - rp[s]));
+    }
   }
+}
+
+// Appends the vertices of this warp flagged `first` to a level list (one
+// atomic per warp) and adds their degrees to the level's edge count.
+__device__ __forceinline__ void list_append(bool first, int32_t v, int deg, int32_t *__restrict__ list,
+                                            unsigned *__restrict__ vcnt, unsigned long long *__restrict__ vedges) {
+  if (!list) return;  // level lists off (bottom-up only): nothing to record
+  const int lane = threadIdx.x & 31;
+  const unsigned fb = __ballot_sync(FULL, first);
+  if (!fb) return;
+  unsigned pos0 = 0u;
+  if (lane == 0) pos0 = atomicAdd(vcnt, (unsigned)__popc(fb));
+  pos0 = __shfl_sync(FULL, pos0, 0);
+  if (first) list[pos0 + __popc(fb & ((1u << lane) - 1u))] = v;
+  unsigned long long ds = first ? (unsigned long long)deg : 0ull;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(FULL, ds, off);
+  if (lane == 0) atomicAdd(vedges, ds);
 }
 
 // Zero sigma rows of heavy vertices (their lanes are filled with atomics).
@@ -169,17 +193,27 @@ __global__ void k_zero_heavy_rows(int nh, const int32_t *__restrict__ heavy, uin
 __global__ void k_fwd_level1(int count, const int32_t *__restrict__ sources, const int32_t *__restrict__ rp,
                              const int32_t *__restrict__ col, uint64_t *__restrict__ lm1,
                              uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
-                             uint64_t *__restrict__ active1, unsigned long long *__restrict__ cnt) {
+                             uint64_t *__restrict__ active1, unsigned long long *__restrict__ cnt,
+                             int32_t *__restrict__ list1, unsigned *__restrict__ vcnt1,
+                             unsigned long long *__restrict__ vedges1) {
   const int t = blockIdx.x;
   if (t >= count) return;
   const int32_t s = sources[t];
   const uint64_t bit = 1ull << t;
   const int beg = rp[s], end = rp[s + 1];
-  for (int j = beg + threadIdx.x; j < end; j += blockDim.x) {
-    const int32_t v = col[j];
-    sigma[(size_t)v * 64 + t] = 1ull;
-    atomicOr((unsigned long long *)&lm1[v], (unsigned long long)bit);
-    atomicOr((unsigned long long *)&visited[v], (unsigned long long)bit);
+  for (int jb = beg; jb < end; jb += blockDim.x) {  // block-uniform trip count
+    const int j = jb + (int)threadIdx.x;
+    bool first = false;
+    int32_t v = 0;
+    int dv = 0;
+    if (j < end) {
+      v = col[j];
+      sigma[(size_t)v * 64 + t] = 1ull;
+      first = atomicOr((unsigned long long *)&lm1[v], (unsigned long long)bit) == 0ull;
+      atomicOr((unsigned long long *)&visited[v], (unsigned long long)bit);
+      if (first) dv = rp[v + 1] - rp[v];
+    }
+    list_append(first, v, dv, list1, vcnt1, vedges1);
   }
   if (threadIdx.x == 0 && end > beg) {
     atomicOr((unsigned long long *)active1, (unsigned long long)bit);
@@ -294,7 +328,8 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
             const uint64_t *__restrict__ active_prev, uint64_t *__restrict__ enable,
             uint64_t *__restrict__ active_cur, unsigned *__restrict__ err,
             unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq, int heavy_deg, int pk_maxl,
-            int pk_mincnt) {
+            int pk_mincnt, int32_t *__restrict__ list_next, unsigned *__restrict__ vcnt_next,
+            unsigned long long *__restrict__ vedges_next) {
   __shared__ int32_t lists[FWD_THREADS / 32][32];
   __shared__ int8_t tabs[FWD_THREADS / 32][64];
   const int lane = threadIdx.x & 31;
@@ -317,6 +352,7 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
       if (!work) lm_cur[vl] = 0ull;  // heavy vertices are then filled by their segments
     }
     unsigned todo = __ballot_sync(FULL, work);
+    unsigned found = 0u;  // vertices of this grab that join the next level
     while (todo) {
     const int iv = __ffs(todo) - 1;
     todo &= todo - 1u;
@@ -382,9 +418,11 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
       lm_cur[v] = newm;
       if (newm) visited[v] = vis | newm;
     }
+    if (newm) found |= 1u << iv;
     rch += (unsigned long long)__popcll((long long)newm);
     any_new |= newm;
     }
+    list_append((found >> lane) & 1u, vl, he - hb, list_next, vcnt_next, vedges_next);
   }
   ovf = warp_or64(ovf);
   if (lane == 0 && ovf) atomicOr((unsigned long long *)(enable + 3), (unsigned long long)ovf);
@@ -563,36 +601,161 @@ __global__ void k_fwd_heavy_fin(int nh, const int32_t *__restrict__ heavy,
                                 const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ visited,
                                 uint64_t *__restrict__ active_cur, unsigned long long *__restrict__ cnt,
                                 const uint64_t *__restrict__ sigma, uint64_t *__restrict__ enable,
-                                unsigned *__restrict__ hflag, unsigned long long *__restrict__ hpend) {
-  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+                                unsigned *__restrict__ hflag, unsigned long long *__restrict__ hpend,
+                                const int32_t *__restrict__ rp, int32_t *__restrict__ list_next,
+                                unsigned *__restrict__ vcnt_next, unsigned long long *__restrict__ vedges_next) {
+  // one warp per heavy vertex: the largest count of its new lanes is a warp
+  // maximum over the row (two loads per thread), not a chain of dependent loads
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   const uint64_t en = *enable;
-  uint64_t newm = 0ull, pend = 0ull;
-  if (h < nh) {
+  uint64_t any_new = 0ull, pend_all = 0ull;
+  for (int h = gw; h < nh; h += nw) {
     const int32_t v = heavy[h];
-    newm = lm_cur[v];
-    pend = ~(visited[v] | newm) & en;
-    if (newm) {
-      visited[v] |= newm;
-      atomicAdd(cnt + 1, (unsigned long long)__popcll((long long)newm));
-      uint64_t mx = 0ull, m = newm;
-      while (m) {
-        const int t = __ffsll((long long)m) - 1;
-        m &= m - 1ull;
-        const uint64_t x = sigma[(size_t)v * 64 + t];
-        mx = x > mx ? x : mx;
+    const uint64_t newm = lm_cur[v];
+    const uint64_t *row = sigma + (size_t)v * 64;
+    const uint64_t x0 = ((newm >> lane) & 1ull) ? row[lane] : 0ull;
+    const uint64_t x1 = ((newm >> (lane + 32)) & 1ull) ? row[lane + 32] : 0ull;
+    const uint64_t mx = warp_max64(x0 > x1 ? x0 : x1);
+    if (lane == 0) {
+      const uint64_t vis = visited[v];
+      pend_all |= ~(vis | newm) & en;
+      if (newm) {
+        visited[v] = vis | newm;
+        atomicAdd(cnt + 1, (unsigned long long)__popcll((long long)newm));
+        atomicMax((unsigned long long *)(enable + 2), (unsigned long long)mx);
+        if (list_next) {
+          list_next[atomicAdd(vcnt_next, 1u)] = v;
+          atomicAdd(vedges_next, (unsigned long long)(rp[v + 1] - rp[v]));
+        }
       }
-      atomicMax((unsigned long long *)(enable + 2), (unsigned long long)mx);
     }
+    any_new |= newm;
   }
-  newm = warp_or64(newm);
-  pend = warp_or64(pend);
-  if ((threadIdx.x & 31) == 0) {
-    if (newm) {
-      atomicOr((unsigned long long *)active_cur, (unsigned long long)newm);
+  if (lane == 0) {
+    if (any_new) {
+      atomicOr((unsigned long long *)active_cur, (unsigned long long)any_new);
       atomicOr(hflag, 1u);
     }
-    if (pend) atomicOr(hpend, (unsigned long long)pend);
+    if (pend_all) atomicOr(hpend, (unsigned long long)pend_all);
   }
+}
+
+// ------------------------------------------------------- top-down levels --
+// Sec. 3 step 1 batched over lanes, run top-down for a level whose vertices
+// have few edges: each vertex w of level l pushes its lanes to the neighbours
+// that are not visited in them, which join level l+1 in those lanes
+// (lm_next must be zero before). Each newly reached vertex is listed once.
+__global__ void __launch_bounds__(FWD_THREADS)
+k_fwd_push(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, const int32_t *__restrict__ list_cur,
+           const unsigned *__restrict__ vcnt_cur, const uint64_t *__restrict__ lm_cur_lvl,
+           uint64_t *__restrict__ lm_next, const uint64_t *__restrict__ visited,
+           const uint64_t *__restrict__ active_cur, const uint64_t *__restrict__ enable,
+           int32_t *__restrict__ list_next, unsigned *__restrict__ vcnt_next,
+           unsigned long long *__restrict__ vedges_next, unsigned *__restrict__ wq) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t act = *active_cur & *enable;
+  const int cnt = (int)*vcnt_cur;
+  for (int i = grab(wq, 1); i < cnt; i = grab(wq, 1)) {
+    const int32_t w = list_cur[i];
+    const uint64_t mw = lm_cur_lvl[w] & act;
+    if (!mw) continue;
+    const int beg = rp[w], end = rp[w + 1];
+    for (int base = beg; base < end; base += 32) {
+      const int j = base + lane;
+      bool first = false;
+      int32_t v = 0;
+      int dv = 0;
+      if (j < end) {
+        v = col[j];
+        const uint64_t nl = mw & ~visited[v];
+        if (nl) {
+          first = atomicOr((unsigned long long *)&lm_next[v], (unsigned long long)nl) == 0ull;
+          if (first) dv = rp[v + 1] - rp[v];
+        }
+      }
+      list_append(first, v, dv, list_next, vcnt_next, vedges_next);
+    }
+  }
+}
+
+// Path counts of the vertices a top-down level reached (their new lanes are
+// lm_next[v], complete after k_fwd_push): pulled from the neighbours at level
+// l in those lanes (Def. 3), then visited, the largest count, the overflowed
+// lanes and the level's lane set are updated as by the bottom-up kernels.
+// Counts are exact integer sums, so the direction does not change any value.
+__global__ void __launch_bounds__(FWD_THREADS)
+k_fwd_pull_list(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                const int32_t *__restrict__ list_next, const unsigned *__restrict__ vcnt_next,
+                const uint64_t *__restrict__ lm_cur_lvl, const uint64_t *__restrict__ lm_next,
+                uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma, uint64_t *__restrict__ enable,
+                uint64_t *__restrict__ active_next, unsigned long long *__restrict__ cnt,
+                unsigned *__restrict__ wq, int heavy_deg, unsigned *__restrict__ hflag) {
+  const int lane = threadIdx.x & 31;
+  uint64_t any_new = 0ull, smax = 0ull, ovf = 0ull;
+  unsigned long long tri = 0ull, rch = 0ull;
+  const int nv = (int)*vcnt_next;
+  for (int i = grab(wq, 1); i < nv; i = grab(wq, 1)) {
+    const int32_t v = list_next[i];
+    const uint64_t newm = lm_next[v];
+    const int beg = rp[v], end = rp[v + 1];
+    if (lane == 0 && end - beg > heavy_deg) atomicOr(hflag, 1u);  // the backward's heavy kernels run here
+    uint64_t s0 = 0ull, s1 = 0ull;
+    for (int base = beg; base < end; base += 32) {
+      const int j = base + lane;
+      int32_t w = 0;
+      uint64_t m = 0ull;
+      if (j < end) {
+        w = col[j];
+        m = lm_cur_lvl[w] & newm;
+      }
+      tri += (unsigned long long)__popcll((long long)m);
+      unsigned bal = __ballot_sync(FULL, m != 0ull);
+      while (bal) {
+        uint64_t mk[UNR];
+        int32_t wk[UNR];
+        take(bal, m, w, mk, wk);
+        uint64_t x0[UNR], x1[UNR];
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+          const uint64_t *row = sigma + (size_t)wk[k] * 64;
+          x0[k] = ((mk[k] >> lane) & 1ull) ? row[lane] : 0ull;
+          x1[k] = ((mk[k] >> (lane + 32)) & 1ull) ? row[lane + 32] : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+          const uint64_t t0 = s0 + x0[k];
+          if (t0 < s0) ovf |= 1ull << lane;
+          s0 = t0;
+          const uint64_t t1 = s1 + x1[k];
+          if (t1 < s1) ovf |= 1ull << (lane + 32);
+          s1 = t1;
+        }
+      }
+    }
+    if ((newm >> lane) & 1ull) {
+      sigma[(size_t)v * 64 + lane] = s0;
+      smax = s0 > smax ? s0 : smax;
+    }
+    if ((newm >> (lane + 32)) & 1ull) {
+      sigma[(size_t)v * 64 + 32 + lane] = s1;
+      smax = s1 > smax ? s1 : smax;
+    }
+    if (lane == 0) visited[v] |= newm;
+    rch += (unsigned long long)__popcll((long long)newm);
+    any_new |= newm;
+  }
+  ovf = warp_or64(ovf);
+  if (lane == 0 && ovf) atomicOr((unsigned long long *)(enable + 3), (unsigned long long)ovf);
+  tri = warp_sum64(tri);
+  if (lane == 0 && (tri | rch)) {
+    atomicAdd(cnt, tri);
+    atomicAdd(cnt + 1, rch);
+  }
+  smax = warp_max64(smax);
+  if (lane == 0 && smax > 1ull) atomicMax((unsigned long long *)(enable + 2), (unsigned long long)smax);
+  block_or_to(any_new, active_next);
 }
 
 // Pair lanes: lane i is finished once its destination appears at this level.
@@ -809,16 +972,23 @@ __device__ __forceinline__ void ring_append_c(Ring &R, unsigned &tail, int32_t v
 
 template <class P>
 __global__ void __launch_bounds__(FWD_THREADS)
-k_bwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-            const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
+k_bwd_light(int32_t n, const int32_t *__restrict__ list_l, const unsigned *__restrict__ vcnt_l,
+            const int32_t *__restrict__ rp,
+            const int32_t *__restrict__ col, const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
             uint64_t *__restrict__ sigma, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq,
             int heavy_deg, uint64_t keep) {
   __shared__ Ring rings[FWD_THREADS / 32];
   Ring &R = rings[threadIdx.x >> 5];
   unsigned head = 0u, tail = 0u;
   unsigned e = 0u;
-  for (int base = grab(wq); base < n; base = grab(wq))
-    for (int v = base; v < min(base + GRAB, n); ++v) {
+  // a small level walks its vertex list; a large one scans the vertex ids in
+  // order (adjacent rows, sequential CSR reads), skipping vertices without lanes
+  const int nv = vcnt_l ? (int)*vcnt_l : n;
+  const bool by_list = vcnt_l && (int64_t)nv * 16 <= (int64_t)n;
+  const int total = by_list ? nv : n;
+  for (int base = grab(wq); base < total; base = grab(wq))
+    for (int i = base; i < min(base + GRAB, total); ++i) {
+      const int32_t v = by_list ? list_l[i] : i;
       const uint64_t lanes = lm_cur[v] & keep;
       if (!lanes) continue;
       const int beg = rp[v], end = rp[v + 1];
@@ -977,10 +1147,11 @@ __device__ __forceinline__ void ring_append_fx(Ring &R, unsigned &tail, int32_t 
 }
 
 __global__ void __launch_bounds__(FWD_THREADS, BWD_MIN_BLOCKS)
-k_bwd_light_fx(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-               const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
-               uint64_t *__restrict__ sigma, Sink sink, unsigned *__restrict__ err,
-               unsigned *__restrict__ wq, int heavy_deg, uint64_t keep) {
+k_bwd_light_fx(int32_t n, const int32_t *__restrict__ list_l, const unsigned *__restrict__ vcnt_l,
+               const int32_t *__restrict__ rp,
+               const int32_t *__restrict__ col, const uint64_t *__restrict__ lm_cur,
+               const uint64_t *__restrict__ lm_next, uint64_t *__restrict__ sigma, Sink sink,
+               unsigned *__restrict__ err, unsigned *__restrict__ wq, int heavy_deg, uint64_t keep) {
   __shared__ Ring rings[FWD_THREADS / 32];
   __shared__ int32_t lists[FWD_THREADS / 32][32];
   __shared__ int8_t tabs[FWD_THREADS / 32][64];
@@ -989,8 +1160,14 @@ k_bwd_light_fx(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restr
   int8_t *tab = tabs[threadIdx.x >> 5];
   unsigned head = 0u, tail = 0u;
   unsigned e = 0u;
-  for (int base = grab(wq); base < n; base = grab(wq))
-    for (int v = base; v < min(base + GRAB, n); ++v) {
+  // a small level walks its vertex list; a large one scans the vertex ids in
+  // order (adjacent rows, sequential CSR reads), skipping vertices without lanes
+  const int nv = vcnt_l ? (int)*vcnt_l : n;
+  const bool by_list = vcnt_l && (int64_t)nv * 16 <= (int64_t)n;
+  const int total = by_list ? nv : n;
+  for (int base = grab(wq); base < total; base = grab(wq))
+    for (int i = base; i < min(base + GRAB, total); ++i) {
+      const int32_t v = by_list ? list_l[i] : i;
       const uint64_t lanes = lm_cur[v] & keep;
       if (!lanes) continue;
       const int beg = rp[v], end = rp[v + 1];
@@ -1119,7 +1296,9 @@ k_bwd_heavy_fin_fx(int nh, const int32_t *__restrict__ heavy, const int32_t *__r
                    const uint64_t *__restrict__ lm_cur, uint64_t *__restrict__ sigma,
                    const uint4 *__restrict__ part, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq, uint64_t keep) {
   __shared__ Ring rings[FWD_THREADS / 32];
+  __shared__ int8_t tabs[FWD_THREADS / 32][64];
   Ring &R = rings[threadIdx.x >> 5];
+  int8_t *tab = tabs[threadIdx.x >> 5];
   unsigned head = 0u, tail = 0u;
   unsigned e = 0u;
   for (int h = grab(wq, 1); h < nh; h = grab(wq, 1)) {
@@ -1127,11 +1306,15 @@ k_bwd_heavy_fin_fx(int nh, const int32_t *__restrict__ heavy, const int32_t *__r
       const uint64_t lanes = lm_cur[v] & keep;
       if (!lanes) continue;
       int p0, p1;
-      compact_lanes(lanes, p0, p1);
+      own_lanes(lanes, tab, p0, p1);
       Acc2 a0 = acc2_zero(), a1 = acc2_zero();
-      for (int s = hseg0[h]; s < hseg0[h + 1]; ++s) {
-        if (p0 >= 0) acc2_add_u4(a0, part[(size_t)s * 64 + p0]);
-        if (p1 >= 0) acc2_add_u4(a1, part[(size_t)s * 64 + p1]);
+      // a hub has hundreds of segments: independent loads, four in flight
+      const int sb = hseg0[h], se = hseg0[h + 1];
+      const int q0 = p0 < 0 ? 0 : p0, q1 = p1 < 0 ? 0 : p1;
+#pragma unroll 4
+      for (int s = sb; s < se; ++s) {
+        if (p0 >= 0) acc2_add_u4(a0, part[(size_t)s * 64 + q0]);
+        if (p1 >= 0) acc2_add_u4(a1, part[(size_t)s * 64 + q1]);
       }
       Packed pk;
       pk.glog = 5;
@@ -1179,7 +1362,7 @@ __global__ void k_extract(int32_t n, int count, int maxlevel, const uint64_t *__
 
 // ------------------------------------------------------------------ host --
 struct HeavyMeta {
-  int nh = 0, nseg = 0, heavy_deg = 0;
+  int nh = 0, nseg = 0, heavy_deg = 0, seg = 0;
   DevBuf heavy, hseg0, seg_v, seg_b, seg_e, part, part2;
 };
 static std::map<const int32_t *, HeavyMeta> g_heavy;  // keyed by the graph's device col pointer
@@ -1187,14 +1370,25 @@ static std::mutex g_heavy_mu;
 
 static HeavyMeta &heavy_meta(bc_ctx *ctx, const Graph &g) {
   std::lock_guard<std::mutex> lk(g_heavy_mu);
+  const int want_deg = ctx->heavy_deg > 0 ? ctx->heavy_deg : HEAVY_DEFAULT;
+  const int want_seg = ctx->seg_len > 0 ? ctx->seg_len : SEG_DEFAULT;
   auto it = g_heavy.find(g.rp);
-  if (it != g_heavy.end()) return it->second;
+  if (it != g_heavy.end()) {
+    HeavyMeta &old = it->second;
+    if (old.heavy_deg == want_deg && old.seg == want_seg) return old;
+    // the graph's split changed (a new tuning): rebuild
+    cudaStreamSynchronize(ctx->stream);
+    old.heavy.release(); old.hseg0.release(); old.seg_v.release(); old.seg_b.release();
+    old.seg_e.release(); old.part.release(); old.part2.release();
+    g_heavy.erase(it);
+  }
   HeavyMeta &hm = g_heavy[g.rp];
   std::vector<int32_t> rp(g.n + 1);
   BCG_CUDA(cudaMemcpy(rp.data(), g.rp, sizeof(int32_t) * (g.n + 1), cudaMemcpyDeviceToHost));
   std::vector<int32_t> heavy, hseg0, sv, sb, se;
-  hm.heavy_deg = ctx->heavy_deg > 0 ? ctx->heavy_deg : HEAVY_DEFAULT;
-  const int seg = ctx->seg_len > 0 ? ctx->seg_len : SEG_DEFAULT;
+  hm.heavy_deg = want_deg;
+  hm.seg = want_seg;
+  const int seg = want_seg;
   for (int32_t v = 0; v < g.n; ++v) {
     const int d = rp[v + 1] - rp[v];
     if (d <= hm.heavy_deg) continue;
@@ -1255,14 +1449,10 @@ void batch_ensure(bc_ctx *ctx, const Graph &g) {
   ws.sigma.ensure(n * 64 * 8);
   ws.active.ensure((size_t)(ws.lcap + 2) * 8);
   ws.wq.ensure((size_t)(ws.lcap + 2) * 8 * 4);
+  ws.vlist.ensure((size_t)ws.lcap * n * 4);
+  ws.vcnt.ensure((size_t)(ws.lcap + 2) * 4);
+  ws.vedges.ensure((size_t)(ws.lcap + 2) * 8);
   heavy_meta(ctx, g);
-}
-
-static uint64_t read_u64(bc_ctx *ctx, const uint64_t *dptr) {
-  uint64_t *h = static_cast<uint64_t *>(ctx->ws.pinned);
-  BCG_CUDA(cudaMemcpyAsync(h, dptr, 8, cudaMemcpyDeviceToHost, ctx->stream));
-  BCG_CUDA(cudaStreamSynchronize(ctx->stream));
-  return *h;
 }
 
 // Two device words to the host with one synchronisation.
@@ -1285,6 +1475,16 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
   BCG_CUDA(cudaMemsetAsync(ws.visited.p, 0, n * 8, st));
   BCG_CUDA(cudaMemsetAsync(ws.active.p, 0, (size_t)(ws.lcap + 2) * 8, st));
   BCG_CUDA(cudaMemsetAsync(ws.wq.p, 0, ws.wq.bytes, st));
+  BCG_CUDA(cudaMemsetAsync(ws.vcnt.p, 0, ws.vcnt.bytes, st));
+  BCG_CUDA(cudaMemsetAsync(ws.vedges.p, 0, ws.vedges.bytes, st));
+  // level lists (and their degree sums) are kept only for the direction
+  // switch: a bottom-up-only pass records nothing (the lists cost ~3 % of the
+  // forward on R-MAT s20)
+  ws.lists = ctx->push_div > 0;
+  int32_t *vlist = ws.lists ? ws.vlist.as<int32_t>() : nullptr;
+  unsigned *vcnt = ws.vcnt.as<unsigned>();
+  unsigned long long *vedges = ws.vedges.as<unsigned long long>();
+  auto lst = [&](int lev) -> int32_t * { return vlist ? vlist + (size_t)lev * n : nullptr; };
   {
     LaunchScope ls(ctx, F_INIT);
     if (hm.nh) k_zero_heavy_rows<<<hm.nh, 64, 0, st>>>(hm.nh, hm.heavy.as<int32_t>(), ws.sigma.as<uint64_t>());
@@ -1294,13 +1494,15 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
     k_batch_init<<<1, 64, 0, st>>>(count, ws.sources.as<int32_t>(), ws.lm.as<uint64_t>(),
                                    ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
                                    ws.active.as<uint64_t>(), ws.enable.as<uint64_t>(),
-                                   ws.pair_d.as<int32_t>(), ws.pair_sig.as<uint64_t>());
+                                   ws.pair_d.as<int32_t>(), ws.pair_sig.as<uint64_t>(), g.rp, lst(0), vcnt,
+                                   vedges);
   }
   ctx->samples += count;
   ctx->batches += 1;
   const int blocks = grid_blocks();
   int l = 0;
   bool heavy_done = false;
+  uint64_t fedges = 0ull;  // degree sum of the vertices at the current level (direction test)
   {
     // level 1 straight from the sources' adjacency; heavy sigma rows were zeroed
     // above and only receive stores here, so the atomics-based heavy path is not needed
@@ -1309,7 +1511,7 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
       k_fwd_level1<<<count, 128, 0, st>>>(count, ws.sources.as<int32_t>(), g.rp, g.col,
                                            ws.lm.as<uint64_t>() + n, ws.visited.as<uint64_t>(),
                                            ws.sigma.as<uint64_t>(), ws.active.as<uint64_t>() + 1,
-                                           ws.cnt.as<unsigned long long>());
+                                           ws.cnt.as<unsigned long long>(), lst(1), vcnt + 1, vedges + 1);
     }
     uint64_t cont1;
     if (pairs) {
@@ -1318,9 +1520,9 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
                                      ws.sigma.as<uint64_t>(), ws.enable.as<uint64_t>(), ws.pair_d.as<int32_t>(),
                                      ws.pair_sig.as<uint64_t>(), ws.active.as<uint64_t>() + 1,
                                      ws.enable.as<uint64_t>() + 1);
-      cont1 = read_u64(ctx, ws.enable.as<uint64_t>() + 1);
+      read_u64x2(ctx, ws.enable.as<uint64_t>() + 1, reinterpret_cast<const uint64_t *>(vedges + 1), cont1, fedges);
     } else {
-      cont1 = read_u64(ctx, ws.active.as<uint64_t>() + 1);
+      read_u64x2(ctx, ws.active.as<uint64_t>() + 1, reinterpret_cast<const uint64_t *>(vedges + 1), cont1, fedges);
     }
     ws.last_ovf = 0ull;
     if (!cont1) {  // no vertex at distance 1 (or, for pairs, every destination found)
@@ -1338,19 +1540,48 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
       ws.wq.grow_keep((size_t)(ncap + 2) * 8 * 4, st);
       BCG_CUDA(cudaMemsetAsync(ws.wq.as<unsigned>() + 8 * (ws.lcap + 2), 0, (size_t)(ncap - ws.lcap) * 8 * 4, st));
       BCG_CUDA(cudaMemsetAsync(ws.active.as<uint64_t>() + ws.lcap + 2, 0, (size_t)(ncap - ws.lcap) * 8, st));
+      ws.vlist.grow_keep((size_t)ncap * n * 4, st);
+      ws.vcnt.grow_keep((size_t)(ncap + 2) * 4, st);
+      ws.vedges.grow_keep((size_t)(ncap + 2) * 8, st);
+      BCG_CUDA(cudaMemsetAsync(ws.vcnt.as<unsigned>() + ws.lcap + 2, 0, (size_t)(ncap - ws.lcap) * 4, st));
+      BCG_CUDA(cudaMemsetAsync(ws.vedges.as<unsigned long long>() + ws.lcap + 2, 0, (size_t)(ncap - ws.lcap) * 8, st));
       ws.lcap = ncap;
+      vlist = ws.lists ? ws.vlist.as<int32_t>() : nullptr;
+      vcnt = ws.vcnt.as<unsigned>();
+      vedges = ws.vedges.as<unsigned long long>();
     }
     uint64_t *lm = ws.lm.as<uint64_t>();
     uint64_t *act = ws.active.as<uint64_t>();
-    {
+    unsigned *hw = ws.wq.as<unsigned>() + 8 * (l + 1);  // slot 5: heavy lanes at l+1; 6-7: heavy pending lanes
+    // top-down when the level's vertices have few edges (Beamer's direction
+    // switch, here on the level's degree sum against the graph's edges)
+    const bool push = ws.lists && fedges * (uint64_t)ctx->push_div <= (uint64_t)g.nnz;
+    if (push) {
+      BCG_CUDA(cudaMemsetAsync(lm + (size_t)(l + 1) * n, 0, n * 8, st));
+      {
+        LaunchScope ls(ctx, F_FWD);
+        k_fwd_push<<<blocks, FWD_THREADS, 0, st>>>(g.rp, g.col, lst(l), vcnt + l, lm + (size_t)l * n,
+                                                  lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), act + l,
+                                                  ws.enable.as<uint64_t>(), lst(l + 1), vcnt + l + 1,
+                                                  vedges + l + 1, ws.wq.as<unsigned>() + 8 * l + 0);
+      }
+      LaunchScope ls(ctx, F_FWD);
+      k_fwd_pull_list<<<blocks, FWD_THREADS, 0, st>>>(g.rp, g.col, lst(l + 1), vcnt + l + 1,
+                                                     lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
+                                                     ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
+                                                     ws.enable.as<uint64_t>(), act + l + 1,
+                                                     ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 1,
+                                                     hm.heavy_deg, hw + 5);
+    } else {
       LaunchScope ls(ctx, F_FWD);
       k_fwd_light<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
                                                  ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(), act + l,
                                                  ws.enable.as<uint64_t>(), act + l + 1, ws.err.as<unsigned>(),
                                                  ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 0,
-                                                 hm.heavy_deg, ctx->pk_maxl, ctx->pk_mincnt);
+                                                 hm.heavy_deg, ctx->pk_maxl, ctx->pk_mincnt,
+                                                 lst(l + 1), vcnt + l + 1, vedges + l + 1);
     }
-    const bool heavy_now = hm.nseg && !heavy_done;
+    const bool heavy_now = !push && hm.nseg && !heavy_done;
     if (heavy_now && ctx->heavy_lane) {
       LaunchScope ls(ctx, F_FWD);
       k_fwd_heavy_lane<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
@@ -1365,14 +1596,14 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
           act + l, ws.enable.as<uint64_t>(), ws.err.as<unsigned>(), ws.cnt.as<unsigned long long>(),
           ws.wq.as<unsigned>() + 8 * l + 1);
     }
-    unsigned *hw = ws.wq.as<unsigned>() + 8 * (l + 1);  // slot 5: heavy lanes at l+1; 6-7: heavy pending lanes
     if (heavy_now) {
       LaunchScope ls(ctx, F_FWD);
-      k_fwd_heavy_fin<<<(hm.nh + 255) / 256, 256, 0, st>>>(hm.nh, hm.heavy.as<int32_t>(), lm + (size_t)(l + 1) * n,
+      k_fwd_heavy_fin<<<std::min(blocks, (hm.nh + 7) / 8), 256, 0, st>>>(hm.nh, hm.heavy.as<int32_t>(), lm + (size_t)(l + 1) * n,
                                                           ws.visited.as<uint64_t>(), act + l + 1,
                                                           ws.cnt.as<unsigned long long>(), ws.sigma.as<uint64_t>(),
                                                           ws.enable.as<uint64_t>(), hw + 5,
-                                                          reinterpret_cast<unsigned long long *>(hw + 6));
+                                                          reinterpret_cast<unsigned long long *>(hw + 6), g.rp,
+                                                          lst(l + 1), vcnt + l + 1, vedges + l + 1);
     }
     // Deep traversals also watch the overflowed lanes every level: once every
     // lane has overflowed the integer pass has nothing left to give (and its
@@ -1388,12 +1619,21 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
       cont_word = ws.enable.as<uint64_t>() + 1;
     }
     uint64_t hpend = 0ull;
-    if (watch)
-      read_u64x2(ctx, cont_word, ws.enable.as<uint64_t>() + 3, cont, ovf);
-    else if (heavy_now)
-      read_u64x2(ctx, cont_word, reinterpret_cast<const uint64_t *>(hw + 6), cont, hpend);
-    else
-      cont = read_u64(ctx, cont_word);
+    {
+      // the level's continue word, the overflowed lanes (deep watch) or the
+      // heavy vertices' pending lanes, and the next level's degree sum: one sync
+      uint64_t *h = static_cast<uint64_t *>(ws.pinned);
+      const uint64_t *second = watch ? ws.enable.as<uint64_t>() + 3
+                                     : (heavy_now ? reinterpret_cast<const uint64_t *>(hw + 6) : cont_word);
+      BCG_CUDA(cudaMemcpyAsync(h, cont_word, 8, cudaMemcpyDeviceToHost, st));
+      BCG_CUDA(cudaMemcpyAsync(h + 1, second, 8, cudaMemcpyDeviceToHost, st));
+      BCG_CUDA(cudaMemcpyAsync(h + 2, vedges + l + 1, 8, cudaMemcpyDeviceToHost, st));
+      BCG_CUDA(cudaStreamSynchronize(st));
+      cont = h[0];
+      if (watch) ovf = h[1];
+      else if (heavy_now) hpend = h[1];
+      fedges = h[2];
+    }
     // no heavy vertex is unvisited in a lane that goes on: the heavy kernels
     // have nothing left to do in this batch (the lanes going on only shrink)
     if (heavy_now && !watch && (hpend & cont) == 0ull) heavy_done = true;
@@ -1432,13 +1672,19 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
   cudaStream_t st = ctx->stream;
   const int blocks = grid_blocks();
   uint64_t *lm = ws.lm.as<uint64_t>();
+  // per level: the vertices with lanes there (recorded only with the direction switch on)
+  const int32_t *vlist = ws.lists ? ws.vlist.as<int32_t>() : nullptr;
+  const unsigned *vcnt = ws.lists ? ws.vcnt.as<unsigned>() : nullptr;
+  auto lvl_list = [&](int lev) -> const int32_t * { return vlist ? vlist + (size_t)lev * n : nullptr; };
+  auto lvl_cnt = [&](int lev) -> const unsigned * { return vcnt ? vcnt + lev : nullptr; };
   const bool narrow = ws.last_sigmax <= (1ull << 44);
   if (narrow && ctx->bwd_variant == 1) {
     hm.part2.ensure(std::max<size_t>(hm.nseg, 1) * 64 * sizeof(uint4));
     for (int l = maxlevel; l >= 1; --l) {
       {
         LaunchScope ls(ctx, F_BWD);
-        k_bwd_light_fx<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
+        k_bwd_light_fx<<<blocks, FWD_THREADS, 0, st>>>(g.n, lvl_list(l), lvl_cnt(l), g.rp, g.col,
+                                                      lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
                                                       ws.sigma.as<uint64_t>(), sink, ws.err.as<unsigned>(),
                                                       ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg, keep);
       }
@@ -1464,12 +1710,14 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
       LaunchScope ls(ctx, F_BWD);
       if (narrow)
         k_bwd_light<NarrowAcc><<<blocks, FWD_THREADS, 0, st>>>(
-            g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), sink,
-            ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg, keep);
+            g.n, lvl_list(l), lvl_cnt(l), g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
+            ws.sigma.as<uint64_t>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg,
+            keep);
       else
         k_bwd_light<WideAcc><<<blocks, FWD_THREADS, 0, st>>>(
-            g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), sink,
-            ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg, keep);
+            g.n, lvl_list(l), lvl_cnt(l), g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
+            ws.sigma.as<uint64_t>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg,
+            keep);
     }
     if (hm.nseg && heavy_at(ws, l)) {
       LaunchScope ls(ctx, F_BWD);

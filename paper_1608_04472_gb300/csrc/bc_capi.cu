@@ -1052,7 +1052,7 @@ using namespace bcg;
 
 #define BC_GUARD_BEGIN                               \
   if (!ctx) return BC_E_INVALID;                     \
-  std::lock_guard<std::recursive_mutex> lk(ctx->mu); \
+  bcg::ApiLock lk(ctx);                              \
   try {
 #define BC_GUARD_END                                                   \
   ctx->err = "no error";                                               \
@@ -1293,6 +1293,7 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
     if (const char *pm = std::getenv("BCG_PK_MAXL")) ctx->pk_maxl = std::atoi(pm);
     if (const char *pc = std::getenv("BCG_PK_MINCNT")) ctx->pk_mincnt = std::atoi(pc);
     if (const char *hl = std::getenv("BCG_HEAVY_LANE")) ctx->heavy_lane = std::atoi(hl);
+    if (const char *pd = std::getenv("BCG_PUSH_DIV")) ctx->push_div = std::atoi(pd);
     if (const char *mc = std::getenv("BCG_MULTI_CAP")) ctx->multi_cap = std::atoi(mc);
     if (const char *pe = std::getenv("BCG_PAIR_ENGINE")) ctx->pair_engine = std::atoi(pe) == 1 ? 1 : 0;
     if (const char *ws = std::getenv("BCG_W_STEP")) ctx->w_step = std::atoll(ws);
@@ -1341,7 +1342,7 @@ void bc_destroy(bc_ctx *ctx) {
     }
     ctx->graphs.clear();
     Workspace &ws = ctx->ws;
-    for (DevBuf *b : {&ws.lm, &ws.visited, &ws.sigma, &ws.active, &ws.wq, &ws.enable, &ws.sources, &ws.targets, &ws.pair_d,
+    for (DevBuf *b : {&ws.lm, &ws.vlist, &ws.vcnt, &ws.vedges, &ws.visited, &ws.sigma, &ws.active, &ws.wq, &ws.enable, &ws.sources, &ws.targets, &ws.pair_d,
                       &ws.pair_sig, &ws.pair_exp, &ws.err, &ws.cnt, &ws.acc, &ws.tslot, &ws.tdelta, &ws.scan, &ws.misc, &ws.misc2,
                       &ws.delta_lm, &ws.p_dist, &ws.p_sigma, &ws.p_coef, &ws.p_queue, &ws.p_ctr,
                       &ws.x_dist, &ws.x_m, &ws.x_e, &ws.x_vis, &ws.x_nm, &ws.x_list, &ws.x_lmask, &ws.x_ctr,
@@ -1406,6 +1407,7 @@ bc_status bc_graph_free(bc_ctx *ctx, bc_graph g) {
 bc_status bc_graph_info(bc_ctx *ctx, bc_graph g, int32_t *n, int64_t *nnz) {
   BC_GUARD_BEGIN
   const Graph &gr = get_graph(ctx, g);
+  KnobScope ks(ctx, gr);
   if (n) *n = gr.n;
   if (nnz) *nnz = gr.nnz;
   BC_GUARD_END
@@ -1415,6 +1417,7 @@ bc_status bc_source_dependencies(bc_ctx *ctx, bc_graph g, const int32_t *sources
                                  int32_t *dist_out, uint64_t *sigma_out) {
   BC_GUARD_BEGIN
   const Graph &gr = get_graph(ctx, g);
+  KnobScope ks(ctx, gr);
   if (count < 0) fail(BC_E_INVALID, "count must be >= 0");
   if (count > 0 && (!sources || !delta_out)) fail(BC_E_INVALID, "NULL argument");
   BCG_CUDA(cudaSetDevice(ctx->device));
@@ -1428,6 +1431,7 @@ bc_status bc_source_dependencies_ext(bc_ctx *ctx, bc_graph g, const int32_t *sou
                                      int32_t *sigma_exp_out, int32_t *tier_out) {
   BC_GUARD_BEGIN
   const Graph &gr = get_graph(ctx, g);
+  KnobScope ks(ctx, gr);
   if (count < 0) fail(BC_E_INVALID, "count must be >= 0");
   if (count > 0 && (!sources || !delta_out || !sigma_mant_out || !sigma_exp_out))
     fail(BC_E_INVALID, "NULL argument");
@@ -1443,6 +1447,7 @@ bc_status bc_source_dependencies_weighted(bc_ctx *ctx, bc_graph g, const int32_t
                                           double *sigma_mant_out, int32_t *sigma_exp_out, int32_t *tier_out) {
   BC_GUARD_BEGIN
   const Graph &gr = get_graph(ctx, g);
+  KnobScope ks(ctx, gr);
   if (count < 0) fail(BC_E_INVALID, "count must be >= 0");
   if (count > 0 && (!sources || !delta_out)) fail(BC_E_INVALID, "NULL argument");
   BCG_CUDA(cudaSetDevice(ctx->device));
@@ -1455,6 +1460,7 @@ bc_status bc_source_dependencies_weighted(bc_ctx *ctx, bc_graph g, const int32_t
 bc_status bc_exact(bc_ctx *ctx, bc_graph g, double *bc_out) {
   BC_GUARD_BEGIN
   const Graph &gr = get_graph(ctx, g);
+  KnobScope ks(ctx, gr);
   if (!bc_out) fail(BC_E_INVALID, "bc_out is NULL");
   BCG_CUDA(cudaSetDevice(ctx->device));
   do_exact_or_uniform(ctx, gr, true, gr.n, 0, 0, bc_out);
@@ -1464,6 +1470,7 @@ bc_status bc_exact(bc_ctx *ctx, bc_graph g, double *bc_out) {
 bc_status bc_uniform_sources(bc_ctx *ctx, bc_graph g, int64_t k, uint64_t seed, uint64_t qid, double *est_out) {
   BC_GUARD_BEGIN
   const Graph &gr = get_graph(ctx, g);
+  KnobScope ks(ctx, gr);
   if (!est_out) fail(BC_E_INVALID, "est_out is NULL");
   if (k < 1 || k > ((int64_t)1 << 32)) fail(BC_E_INVALID, "k must be in [1, 2^32]");
   BCG_CUDA(cudaSetDevice(ctx->device));
@@ -1493,6 +1500,7 @@ bc_status bc_adaptive_sources(bc_ctx *ctx, bc_graph g, const int32_t *targets, i
                               int32_t *stop_status) {
   BC_GUARD_BEGIN
   const Graph &gr = get_graph(ctx, g);
+  KnobScope ks(ctx, gr);
   if (!(c >= 1.0) || !(c < 1e300)) fail(BC_E_INVALID, "c must be >= 1 and finite");
   if (cap < 1 || cap > ((int64_t)1 << 32)) fail(BC_E_INVALID, "cap must be in [1, 2^32]");
   if (T > 0 && (!est || !k)) fail(BC_E_INVALID, "NULL output");
@@ -1507,6 +1515,7 @@ bc_status bc_adaptive_pairs(bc_ctx *ctx, bc_graph g, const int32_t *targets, int
                             double *S, int32_t *stop_status) {
   BC_GUARD_BEGIN
   const Graph &gr = get_graph(ctx, g);
+  KnobScope ks(ctx, gr);
   if (gr.n < 2) fail(BC_E_INVALID, "pair sampling needs n >= 2");
   if (gr.directed) fail(BC_E_INVALID, "pair sampling needs an undirected graph");
   if (gr.w) fail(BC_E_INVALID, "pair sampling needs an unweighted graph");
@@ -1589,6 +1598,7 @@ bc_status bc_target_dependencies(bc_ctx *ctx, bc_graph g, const int32_t *targets
                                  uint64_t qid, int64_t i0, int64_t count, double *out) {
   BC_GUARD_BEGIN
   const Graph &gr = get_graph(ctx, g);
+  KnobScope ks(ctx, gr);
   if (i0 < 0 || count < 0 || count > ((int64_t)1 << 32)) fail(BC_E_INVALID, "need i0 >= 0 and 0 <= count <= 2^32");
   if (T > 0 && count > 0 && !out) fail(BC_E_INVALID, "out is NULL");
   validate_targets(gr, targets, T);
@@ -1601,10 +1611,133 @@ bc_status bc_uniform_partial(bc_ctx *ctx, bc_graph g, uint64_t seed, uint64_t qi
                              int64_t *parts) {
   BC_GUARD_BEGIN
   const Graph &gr = get_graph(ctx, g);
+  KnobScope ks(ctx, gr);
   if (i0 < 0 || count < 0 || count > ((int64_t)1 << 32)) fail(BC_E_INVALID, "need i0 >= 0 and 0 <= count <= 2^32");
   if (!parts) fail(BC_E_INVALID, "parts is NULL");
   BCG_CUDA(cudaSetDevice(ctx->device));
   if (count > 0) do_uniform_partial(ctx, gr, seed, qid, i0, count, parts);
+  BC_GUARD_END
+}
+
+static bc_tuning current_tuning(bc_ctx *ctx, const Graph &g) {
+  if (g.tuned) return g.tune;
+  bc_tuning t{};
+  t.batch_width = batch_width(ctx);
+  t.heavy_degree = ctx->heavy_deg > 0 ? ctx->heavy_deg : 256;
+  t.segment = ctx->seg_len > 0 ? ctx->seg_len : 256;
+  t.packed_max_lanes = ctx->pk_maxl;
+  t.packed_min_preds = ctx->pk_mincnt;
+  t.bwd_variant = ctx->bwd_variant;
+  t.heavy_lane = ctx->heavy_lane;
+  t.push_div = ctx->push_div;
+  t.deep_levels = ctx->deep_levels;
+  t.trial_ms = 0.0;
+  return t;
+}
+
+static void check_tuning(const bc_tuning &t) {
+  if (t.batch_width != 1 && t.batch_width != 64) fail(BC_E_INVALID, "batch_width must be 1 or 64");
+  if (t.heavy_degree < 32 || t.segment < 32) fail(BC_E_INVALID, "heavy_degree and segment must be >= 32");
+  if (t.packed_max_lanes < 0 || t.packed_max_lanes > 64 || t.packed_min_preds < 1 || t.packed_min_preds > 32)
+    fail(BC_E_INVALID, "packed_max_lanes in [0, 64], packed_min_preds in [1, 32]");
+  if ((t.bwd_variant != 0 && t.bwd_variant != 1) || (t.heavy_lane != 0 && t.heavy_lane != 1))
+    fail(BC_E_INVALID, "bwd_variant and heavy_lane are 0 or 1");
+  if (t.push_div < 0 || t.deep_levels < 1) fail(BC_E_INVALID, "push_div >= 0 and deep_levels >= 1");
+}
+
+bc_status bc_get_tuning(bc_ctx *ctx, bc_graph g, bc_tuning *out) {
+  BC_GUARD_BEGIN
+  const Graph &gr = get_graph(ctx, g);
+  if (!out) fail(BC_E_INVALID, "out is NULL");
+  *out = current_tuning(ctx, gr);
+  BC_GUARD_END
+}
+
+bc_status bc_set_tuning(bc_ctx *ctx, bc_graph g, const bc_tuning *t) {
+  BC_GUARD_BEGIN
+  get_graph(ctx, g);
+  if (!t) fail(BC_E_INVALID, "t is NULL");
+  check_tuning(*t);
+  Graph &gr = ctx->graphs.find(g)->second;
+  gr.tune = *t;
+  gr.tune.trial_ms = 0.0;
+  gr.tuned = true;
+  BC_GUARD_END
+}
+
+bc_status bc_autotune(bc_ctx *ctx, bc_graph g, int64_t k, uint64_t seed, bc_tuning *out) {
+  BC_GUARD_BEGIN
+  get_graph(ctx, g);
+  if (k < 1 || k > ((int64_t)1 << 20)) fail(BC_E_INVALID, "k must be in [1, 2^20]");
+  BCG_CUDA(cudaSetDevice(ctx->device));
+  Graph &gr = ctx->graphs.find(g)->second;
+  const size_t n = (size_t)gr.n;
+  std::vector<double> ref(n), est(n);
+  bool have_ref = false;
+  cudaEvent_t e0, e1;
+  BCG_CUDA(cudaEventCreate(&e0));
+  BCG_CUDA(cudaEventCreate(&e1));
+  const bc_tuning saved = gr.tune;
+  const bool saved_tuned = gr.tuned;
+  auto trial = [&](const bc_tuning &t) -> double {
+    gr.tune = t;
+    gr.tuned = true;
+    KnobScope ks(ctx, gr);
+    // warm-up of this setting (per-graph metadata of its split, buffers)
+    uniform_one(ctx, gr, std::min<int64_t>(k, 64), seed, 0x7E57ull, est.data());
+    BCG_CUDA(cudaEventRecord(e0, ctx->stream));
+    uniform_one(ctx, gr, k, seed, 0x7E58ull, est.data());
+    BCG_CUDA(cudaEventRecord(e1, ctx->stream));
+    BCG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    BCG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (!have_ref) {
+      ref = est;
+      have_ref = true;
+    } else if (std::memcmp(ref.data(), est.data(), n * sizeof(double)) != 0) {
+      fail(BC_E_DEVICE, "a tuning setting changed an estimate");
+    }
+    return (double)ms;
+  };
+  try {
+    bc_tuning best = current_tuning(ctx, gr);
+    double best_ms = trial(best);
+    auto sweep = [&](int32_t bc_tuning::*field, std::initializer_list<int32_t> values) {
+      for (int32_t v : values) {
+        if (best.*field == v) continue;
+        bc_tuning t = best;
+        t.*field = v;
+        const double ms = trial(t);
+        if (ms < best_ms) {
+          best = t;
+          best_ms = ms;
+        }
+      }
+    };
+    // the traversal's direction and the heavy-vertex split first (largest
+    // effects on R-MAT), then the kernel forms
+    sweep(&bc_tuning::push_div, {0, 8, 32, 128});
+    sweep(&bc_tuning::heavy_degree, {128, 256, 512, 1024});
+    sweep(&bc_tuning::segment, {128, 256, 512});
+    sweep(&bc_tuning::packed_max_lanes, {0, 8, 16, 32});
+    sweep(&bc_tuning::packed_min_preds, {4, 6, 10});
+    sweep(&bc_tuning::bwd_variant, {0, 1});
+    sweep(&bc_tuning::heavy_lane, {0, 1});
+    sweep(&bc_tuning::deep_levels, {16, 32, 64});
+    if (gr.n <= (1 << 17)) sweep(&bc_tuning::batch_width, {1, 64});
+    best.trial_ms = best_ms;
+    gr.tune = best;
+    gr.tuned = true;
+    if (out) *out = best;
+  } catch (...) {
+    gr.tune = saved;
+    gr.tuned = saved_tuned;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   BC_GUARD_END
 }
 

@@ -3,6 +3,7 @@
 // accounting and the per-batch output "sink".
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -59,6 +60,10 @@ struct Graph {
   uint32_t *w = nullptr;
   uint32_t *w_in = nullptr;
   uint64_t w_step = 0;
+  // launch settings of this graph (bc_set_tuning / bc_autotune); unset: the
+  // context's defaults
+  bc_tuning tune{};
+  bool tuned = false;
 };
 
 // Kernel families timed separately when profiling is on.
@@ -107,6 +112,12 @@ struct Workspace {
   DevBuf sigma;    // [n][64] u64 sigma, overwritten by coef (double) in the backward
   DevBuf active;   // [lcap+2] u64 OR of level masks; [0..] per level
   DevBuf wq;       // [2*(lcap+2)] u32 work-queue counters (forward / backward per level)
+  // per level l of the last batched forward: the vertices with lanes at l
+  // (vlist[l*n ..], each once), their count vcnt[l] and degree sum vedges[l]
+  DevBuf vlist;    // [lcap][n] i32
+  DevBuf vcnt;     // [lcap+2] u32
+  DevBuf vedges;   // [lcap+2] u64
+  bool lists = false;  // the last forward recorded level lists (direction switch on)
   DevBuf enable;   // u64 lane enable mask
   DevBuf sources;  // [64] i32
   DevBuf targets;  // [64] i32 pair destinations
@@ -145,6 +156,7 @@ struct bc_ctx {
   cudaStream_t stream2 = nullptr;  // second stream (persistent multi-graph work), made on first use
   int32_t batch_width = 0;
   std::recursive_mutex mu;
+  std::atomic<int> api_waiting{0};  // API calls waiting for mu (the server worker yields to them)
   std::string err = "no error";
   std::map<bc_graph, bcg::Graph> graphs;
   bc_graph next_handle = 1;
@@ -169,6 +181,13 @@ struct bc_ctx {
   // heavy-vertex segments: per-lane item loops (1) or 64-lane steps per neighbour (0);
   // on R-MAT s20 the per-lane loops measured 4 % slower (scattered row loads)
   int32_t heavy_lane = 0;
+  // direction of a forward level: top-down (push from the level's vertex list,
+  // then counts pulled for the discovered vertices only) when the level's
+  // vertices have at most nnz / push_div edges; bottom-up (every vertex with
+  // pending lanes pulls) otherwise; 0 = always bottom-up (the default: on
+  // R-MAT s20 with 64-lane batches the union frontier is rarely small, and the
+  // level lists the switch needs cost more than the top-down levels saved)
+  int32_t push_div = 0;
   // multi-graph split: hub eccentricity above which a graph goes to the
   // persistent kernel, and its CTAs per SM while the batched engine runs beside
   int32_t deep_levels = 32, multi_cap = 4;
@@ -302,5 +321,46 @@ bool plain_pair(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t
 // query server lifetime (bc_serve.cu)
 void server_shutdown(bc_ctx *ctx);
 bool server_uses_graph(bc_ctx *ctx, bc_graph g);
+
+}  // namespace bcg
+
+namespace bcg {
+
+// The context's lock for an API call. Callers count themselves while they
+// wait, so the query server's worker, which takes the lock once per batch,
+// lets them in between batches instead of re-taking it at once (a mutex is not
+// fair: without this a submit or poll could wait for a whole query).
+struct ApiLock {
+  std::unique_lock<std::recursive_mutex> lk;
+  explicit ApiLock(bc_ctx *c) {
+    c->api_waiting.fetch_add(1);
+    lk = std::unique_lock<std::recursive_mutex>(c->mu);
+    c->api_waiting.fetch_sub(1);
+  }
+};
+
+// The graph's tuning applied to the context for the duration of one call
+// (calls on a context are serialised by its mutex), the context's own
+// settings restored afterwards.
+struct KnobScope {
+  bc_ctx *ctx;
+  int32_t bw, hd, sl, pm, pc, bv, hl, pd, dl;
+  KnobScope(bc_ctx *c, const Graph &g) : ctx(c) {
+    bw = c->batch_width; hd = c->heavy_deg; sl = c->seg_len; pm = c->pk_maxl; pc = c->pk_mincnt;
+    bv = c->bwd_variant; hl = c->heavy_lane; pd = c->push_div; dl = c->deep_levels;
+    if (g.tuned) {
+      const bc_tuning &t = g.tune;
+      c->batch_width = t.batch_width; c->heavy_deg = t.heavy_degree; c->seg_len = t.segment;
+      c->pk_maxl = t.packed_max_lanes; c->pk_mincnt = t.packed_min_preds; c->bwd_variant = t.bwd_variant;
+      c->heavy_lane = t.heavy_lane; c->push_div = t.push_div; c->deep_levels = t.deep_levels;
+    }
+  }
+  ~KnobScope() {
+    ctx->batch_width = bw; ctx->heavy_deg = hd; ctx->seg_len = sl; ctx->pk_maxl = pm; ctx->pk_mincnt = pc;
+    ctx->bwd_variant = bv; ctx->heavy_lane = hl; ctx->push_div = pd; ctx->deep_levels = dl;
+  }
+  KnobScope(const KnobScope &) = delete;
+  KnobScope &operator=(const KnobScope &) = delete;
+};
 
 }  // namespace bcg

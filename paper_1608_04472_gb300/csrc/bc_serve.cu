@@ -218,6 +218,7 @@ struct Server {
 
   void loop();
   void admit_locked();
+  void yield_to_api();
   bool prepare(SQuery &q);                    // device state; pairs: per-target BFS
   void run_group(std::vector<std::shared_ptr<SQuery>> &part, std::vector<int> &lanes);
   void finish(SQuery &q);
@@ -235,6 +236,13 @@ void Server::fail_query(SQuery &q, bc_status code, const std::string &msg) {
   q.state = Q_FAILED;
   q.result = code;
   q.err = msg;
+}
+
+// API calls waiting for the context go first (at most 2 ms per batch), so a
+// submit or poll never waits for more than about one batch of the worker.
+void Server::yield_to_api() {
+  const auto t0 = Clock::now();
+  while (ctx->api_waiting.load() > 0 && Clock::now() - t0 < std::chrono::milliseconds(2)) std::this_thread::yield();
 }
 
 void Server::admit_locked() {
@@ -321,6 +329,7 @@ void Server::run_group(std::vector<std::shared_ptr<SQuery>> &part, std::vector<i
   Workspace &ws = ctx->ws;
   cudaStream_t st = ctx->stream;
   const Graph &g = part[0]->g;
+  KnobScope ks(ctx, g);  // the graph's tuning as of the queries' submission
   const int kind = part[0]->kind;
   const int P = (int)part.size();
   std::vector<LaneDraw> ld;
@@ -456,6 +465,7 @@ void Server::loop() {
     }
     // 2. device state for newly admitted queries (pairs: one BFS per target)
     for (auto &q : to_prepare) {
+      yield_to_api();
       std::lock_guard<std::recursive_mutex> g(ctx->mu);
       try {
         prepare(*q);
@@ -488,6 +498,7 @@ void Server::loop() {
       bc_status fcode = BC_OK;
       std::string fmsg;
       {
+        yield_to_api();
         std::lock_guard<std::recursive_mutex> g(ctx->mu);
         try {
           finish(*q);
@@ -573,6 +584,7 @@ void Server::loop() {
     cv_done.notify_all();
     if (part.empty()) continue;
     // 5. one shared batch
+    yield_to_api();
     std::lock_guard<std::recursive_mutex> g(ctx->mu);
     try {
       run_group(part, lanes);
@@ -652,7 +664,7 @@ bc_status bc_submit(bc_ctx *ctx, const bc_query *q, bc_ticket *out) {
   if (!ctx || !q || !out) return BC_E_INVALID;
   auto sq = std::make_shared<SQuery>();
   {
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ApiLock lk(ctx);
     try {
       const Graph &g = get_graph(ctx, q->graph);
       if (q->kind != BC_QUERY_SOURCES && q->kind != BC_QUERY_PAIRS && q->kind != BC_QUERY_UNIFORM)
@@ -704,7 +716,7 @@ bc_status bc_submit(bc_ctx *ctx, const bc_query *q, bc_ticket *out) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if ((int64_t)sq->mem > s->mem_budget) {
-      std::lock_guard<std::recursive_mutex> g(ctx->mu);
+      ApiLock g(ctx);
       ctx->err = "query needs more device memory than the server budget";
       return BC_E_NOMEM;
     }
@@ -737,7 +749,7 @@ bc_status bc_poll(bc_ctx *ctx, bc_ticket t, int64_t timeout_us) {
   s->queries.erase(it);
   lk.unlock();
   if (r != BC_OK) {
-    std::lock_guard<std::recursive_mutex> g(ctx->mu);
+    ApiLock g(ctx);
     ctx->err = msg.empty() ? "query cancelled" : msg;
   }
   return r;
@@ -773,7 +785,7 @@ bc_status bc_server_limits(bc_ctx *ctx, int32_t max_active, int64_t mem_budget_b
   if (!ctx) return BC_E_INVALID;
   Server *s;
   {
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ApiLock lk(ctx);
     s = server_of(ctx);
   }
   {

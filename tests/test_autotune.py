@@ -1,69 +1,46 @@
-"""Host logic of the autotuner (no GPU): coordinate descent from the defaults
-over a fake timing function, the check that knobs never change a result, the
-per-graph cache and the environment it sets while a context is created."""
+"""Host side of the tuner (no GPU): the cache across processes, the graph
+signature, and the binding's copy of the bc_tuning struct against the header
+(field names, order and types)."""
 import os
+import re
 
-import numpy as np
 import pytest
 
 import graphgen as gg
 from paper_1608_04472_gb300 import autotune as at
 
-
-def _fake(times, est=None, log=None):
-    est = np.arange(5.0) if est is None else est
-
-    def runner(s):
-        if log is not None:
-            log.append(dict(s))
-        return times(s), est
-    return runner
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "bc.h")
 
 
-def test_coordinate_descent_picks_the_fastest_value_per_knob():
-    grid = {"A": (1, 2, 3), "B": (10, 20)}
-    # A = 2 is fastest; with A = 2, B = 20 is fastest
-    cost = lambda s: {1: 5.0, 2: 1.0, 3: 4.0}[s["A"]] + (0.5 if s["B"] == 10 else 0.1)
-    log = []
-    res = at.tune(None, None, grid=grid, runner=_fake(cost, log=log))
-    assert res["best"] == {"A": 2, "B": 20}
-    assert res["seconds"] == pytest.approx(1.1)
-    # defaults first, shared setting not rerun: 3 + 2 - 1 trials
-    assert log[0] == {"A": 1, "B": 10} and len(log) == 4 and len(res["trials"]) == 4
+class _FakeCtx:
+    """Records the calls tune_cached makes."""
+
+    def __init__(self):
+        self.calls = []
+
+    def autotune(self, g, k, seed):
+        self.calls.append(("autotune", g, k, seed))
+        return {"batch_width": 64, "heavy_degree": 512, "segment": 256, "packed_max_lanes": 16,
+                "packed_min_preds": 6, "bwd_variant": 1, "heavy_lane": 0, "push_div": 32, "deep_levels": 32,
+                "trial_ms": 3.5}
+
+    def set_tuning(self, g, t):
+        self.calls.append(("set", g, dict(t)))
 
 
-def test_ties_keep_the_smaller_value():
-    res = at.tune(None, None, grid={"A": (3, 1, 2)}, runner=_fake(lambda s: 1.0))
-    assert res["best"] == {"A": 1}
-
-
-def test_a_knob_that_changes_a_result_is_refused():
-    calls = []
-
-    def runner(s):
-        calls.append(s)
-        return 1.0, np.array([1.0, 2.0 if s["A"] == 1 else 2.0000000000000004])
-
-    with pytest.raises(AssertionError):
-        at.tune(None, None, grid={"A": (1, 2)}, runner=runner)
-
-
-def test_empty_grid_entry_is_an_error():
-    with pytest.raises(ValueError):
-        at.tune(None, None, grid={"A": ()}, runner=_fake(lambda s: 1.0))
-
-
-def test_cache_runs_once_per_graph(tmp_path):
+def test_cache_tunes_once_per_graph_and_restores_after(tmp_path):
     g = gg.erdos_renyi(300, 4, 3)
     h = gg.erdos_renyi(300, 4, 4)
     path = str(tmp_path / "tune.json")
-    log = []
-    kw = dict(grid={"A": (1, 2)}, runner=_fake(lambda s: float(s["A"]), log=log))
-    r1 = at.tune_cached(g.row_ptr, g.col, path, **kw)
-    r2 = at.tune_cached(g.row_ptr, g.col, path, **kw)
-    assert r1 == r2 == {"best": {"A": 1}, "seconds": 1.0} and len(log) == 2
-    at.tune_cached(h.row_ptr, h.col, path, **kw)
-    assert len(log) == 4 and len(at.load_cache(path)) == 2
+    c1 = _FakeCtx()
+    r1 = at.tune_cached(c1, 7, g.row_ptr, g.col, path, k=64, seed=2)
+    assert r1["cached"] is False and c1.calls == [("autotune", 7, 64, 2)]
+    c2 = _FakeCtx()  # another process: restored, not tuned
+    r2 = at.tune_cached(c2, 9, g.row_ptr, g.col, path)
+    assert r2["cached"] is True and c2.calls[0][0] == "set" and c2.calls[0][1] == 9
+    assert c2.calls[0][2]["heavy_degree"] == 512 and len(c2.calls) == 1
+    at.tune_cached(c2, 10, h.row_ptr, h.col, path)
+    assert c2.calls[-1][0] == "autotune" and len(at.load_cache(path)) == 2
 
 
 def test_signature_depends_on_the_arrays():
@@ -74,11 +51,12 @@ def test_signature_depends_on_the_arrays():
     assert at.graph_signature(g.row_ptr, g.col) != at.graph_signature(g.row_ptr, col)
 
 
-def test_defaults_come_first_and_the_environment_is_restored(monkeypatch):
-    for name, values in at.DEFAULT_GRID.items():
-        assert len(values) >= 2 and len(set(values)) == len(values), name
-    monkeypatch.setenv("BCG_SEGMENT", "999")
-    monkeypatch.delenv("BCG_HEAVY_DEGREE", raising=False)
-    with at._Env({"BCG_SEGMENT": 512, "BCG_HEAVY_DEGREE": 128}):
-        assert os.environ["BCG_SEGMENT"] == "512" and os.environ["BCG_HEAVY_DEGREE"] == "128"
-    assert os.environ["BCG_SEGMENT"] == "999" and "BCG_HEAVY_DEGREE" not in os.environ
+def test_binding_struct_matches_the_header():
+    from paper_1608_04472_gb300 import capi
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct bc_tuning \{(.*?)\} bc_tuning;", text, re.S).group(1)
+    fields = re.findall(r"^\s*(int32_t|double)\s+(\w+);", body, re.M)
+    declared = [(name, ty) for ty, name in fields]
+    bound = [(name, "double" if t.__name__ == "c_double" else "int32_t") for name, t in capi.bc_tuning._fields_]
+    assert declared == bound
+    assert set(capi.TUNING_FIELDS) == {n for n, _ in declared} - {"reserved0", "trial_ms"}

@@ -151,8 +151,11 @@ def _served_intervals(ctx, pkg, h, specs):
     on the host clock), from each ticket's queue and run times."""
     t_sub, tks = [], []
     for kw in specs:
-        t_sub.append(time.perf_counter())
+        # stamped after the call returns: the call itself may wait for the
+        # context while the server runs a batch, and the library stamps the
+        # submission inside it (the host stamp is then at most microseconds late)
         tks.append(ctx.submit(h, pkg.BC_QUERY_PAIRS, **kw))
+        t_sub.append(time.perf_counter())
     for tk in tks:
         ctx.poll(tk, -1)
     iv = []
@@ -173,7 +176,8 @@ def test_admission_by_device_memory(ctx, graphs, pkg):
     ba = g["ba"]
     T = 4
     need = T * ba.n * 12 + T * 64
-    specs = [dict(targets=gg.degree_targets(ba, T, 30 + i), c=1.0, cap=6000, seed=40 + i, qid=i) for i in range(3)]
+    # long enough (40k pair draws each) to be running still when the next one is submitted
+    specs = [dict(targets=gg.degree_targets(ba, T, 30 + i), c=1.0, cap=40000, seed=40 + i, qid=i) for i in range(3)]
     refs = [ctx.adaptive_pairs(hs["ba"], kw["targets"], kw["c"], kw["cap"], kw["seed"], kw["qid"]) for kw in specs]
     try:
         ctx.server_limits(max_active=64, mem_budget_bytes=need + need // 2)
