@@ -398,7 +398,10 @@ typedef struct bc_tuning {
   int32_t packed_min_preds;   /* ... with at least this many predecessors is summed in packed groups
                                  (packed_max_lanes 0: never) */
   int32_t bwd_variant;        /* backward (counts <= 2^44): 1 packed lane groups, 0 two lane halves */
-  int32_t heavy_lane;         /* heavy segments: 1 per-lane item loops, 0 a 64-lane step per neighbour */
+  int32_t heavy_lane;         /* heavy segments: 0 a 64-lane step per neighbour; 1 per-lane item loops;
+                                 2 the backward's (successor, lane) items spread over all threads with
+                                 exact sums in shared memory; 3 that in both passes; 4 in the forward
+                                 only */
   int32_t push_div;           /* forward level top-down (push from the level's vertices, counts pulled
                                  for the reached ones) when the level's degree sum is <= nnz/push_div;
                                  bottom-up otherwise; 0: always bottom-up (Sec. 3 step 1 either way) */
@@ -411,8 +414,9 @@ typedef struct bc_tuning {
 /* Picks the tuning of graph g by coordinate descent from its current setting:
  * each knob in turn takes each of a few values, a uniform k-draw estimate
  * (seed, a fixed query id) is timed with CUDA events on the context's stream
- * after a short warm-up of the same setting, and the fastest value is kept
- * (ties keep the current one). Every trial's estimate must equal the first
+ * after a short warm-up of the same setting, and a value replaces the
+ * current one only when its trial is at least 2 % faster (trials vary by about
+ * that much). Every trial's estimate must equal the first
  * one bit for bit (else BC_E_DEVICE: a setting changed a result). The result
  * is kept beside the graph (every later call on g uses it, also through the
  * query server) and written to *out. 1 <= k <= 2^20. The plain width (1) is

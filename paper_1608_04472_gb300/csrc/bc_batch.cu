@@ -36,6 +36,7 @@ constexpr int FWD_THREADS = 256;
 // measured 5 % faster than the register-limited four. The forward kernels
 // measured slower that way.
 constexpr int BWD_MIN_BLOCKS = 5;
+constexpr int DENSE_ITEMS = 32 * 64;  // dense item lists: at most 64 lanes for each of 32 neighbours
 
 __device__ __forceinline__ uint64_t warp_or64(uint64_t x) {
   const unsigned lo = __reduce_or_sync(FULL, (unsigned)x);
@@ -587,6 +588,116 @@ k_fwd_heavy_lane(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__r
       if (o1 || old + s1 < old) ovf |= 1ull << p1;
     }
     if (lane == 0) atomicOr((unsigned long long *)&lm_cur[v], (unsigned long long)newm);
+  }
+  ovf = warp_or64(ovf);
+  if (lane == 0 && ovf) atomicOr((unsigned long long *)(enable + 3), (unsigned long long)ovf);
+  tri = warp_sum64(tri);
+  if (lane == 0 && tri) atomicAdd(cnt, tri);
+}
+
+// Adds the count x to lane t's 64-bit sum in shared memory (two 32-bit limbs,
+// the carry of the low limb passed on); a carry out of the high limb (the true
+// sum is 2^64 or more: the lane overflowed) sets the lane's bit in ovf2.
+__device__ __forceinline__ void u64_limbs_atomic_add(uint32_t (*acc)[64], uint32_t *ovf2, int t, uint64_t x) {
+  const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+  uint32_t cy = 0u;
+  if (lo) {
+    const uint32_t old = atomicAdd(&acc[0][t], lo);
+    cy = (old + lo < lo) ? 1u : 0u;
+  }
+  const uint32_t h = hi + cy;
+  bool of = h < cy;  // hi + carry wrapped
+  if (h) {
+    const uint32_t old = atomicAdd(&acc[1][t], h);
+    of |= old + h < h;
+  }
+  if (of) atomicOr(&ovf2[t >> 5], 1u << (t & 31));
+}
+
+// Heavy segments of the forward with the predecessors' (count, lane) items
+// spread over all 32 threads (see k_bwd_heavy_seg_dense); the segment's
+// per-lane sums go to the vertex's count row by 64-bit atomics as in k_fwd_heavy.
+__global__ void __launch_bounds__(FWD_THREADS, 4)
+k_fwd_heavy_dense(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restrict__ seg_b,
+                  const int32_t *__restrict__ seg_e, const int32_t *__restrict__ col,
+                  const uint64_t *__restrict__ lm_prev, uint64_t *__restrict__ lm_cur,
+                  const uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
+                  const uint64_t *__restrict__ active_prev, uint64_t *__restrict__ enable,
+                  unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq) {
+  __shared__ uint32_t accs[FWD_THREADS / 32][2][64];
+  __shared__ uint32_t ovfs[FWD_THREADS / 32][2];
+  __shared__ uint16_t itemss[FWD_THREADS / 32][DENSE_ITEMS];
+  __shared__ int32_t sws[FWD_THREADS / 32][32];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t (*acc)[64] = accs[wid];
+  uint32_t *ovf2 = ovfs[wid];
+  uint16_t *items = itemss[wid];
+  int32_t *sw = sws[wid];
+  const uint64_t act = *active_prev & *enable;
+  unsigned long long tri = 0ull;
+  uint64_t ovf = 0ull;
+  for (int s = grab(wq, 1); s < nseg; s = grab(wq, 1)) {
+    const int32_t v = seg_v[s];
+    const uint64_t pend = ~visited[v] & act;
+    if (!pend) continue;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) (&acc[0][0])[lane + 32 * k] = 0u;
+    if (lane < 2) ovf2[lane] = 0u;
+    __syncwarp();
+    uint64_t newm = 0ull;
+    const int end = seg_e[s];
+    for (int base = seg_b[s]; base < end; base += 32) {
+      const int j = base + lane;
+      int32_t w = 0;
+      uint64_t m = 0ull;
+      if (j < end) {
+        w = col[j];
+        m = lm_prev[w] & pend;
+      }
+      newm |= m;
+      sw[lane] = w;
+      const int c = __popcll((long long)m);
+      tri += (unsigned long long)c;
+      int incl = c;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, off);
+        if (lane >= off) incl += y;
+      }
+      const int N = __shfl_sync(FULL, incl, 31);
+      int k = incl - c;
+      while (m) {
+        const int t = __ffsll((long long)m) - 1;
+        m &= m - 1ull;
+        items[k++] = (uint16_t)((lane << 6) | t);
+      }
+      __syncwarp();
+      for (int r0 = 0; r0 < N; r0 += 32) {
+        const int i = r0 + lane;
+        if (i < N) {
+          const unsigned code = items[i];
+          const int t = (int)(code & 63u);
+          u64_limbs_atomic_add(acc, ovf2, t, sigma[(size_t)sw[code >> 6] * 64 + t]);
+        }
+      }
+      __syncwarp();
+    }
+    newm = warp_or64(newm);
+    if (newm) {
+      unsigned long long *dst = (unsigned long long *)(sigma + (size_t)v * 64);
+      const uint64_t ob = ((uint64_t)ovf2[1] << 32) | ovf2[0];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int t = lane + 32 * h;
+        if ((newm >> t) & 1ull) {
+          const uint64_t x = ((uint64_t)acc[1][t] << 32) | acc[0][t];
+          const unsigned long long old = atomicAdd(dst + t, (unsigned long long)x);
+          if (((ob >> t) & 1ull) || old + x < old) ovf |= 1ull << t;
+        }
+      }
+      if (lane == 0) atomicOr((unsigned long long *)&lm_cur[v], (unsigned long long)newm);
+    }
+    __syncwarp();
   }
   ovf = warp_or64(ovf);
   if (lane == 0 && ovf) atomicOr((unsigned long long *)(enable + 3), (unsigned long long)ovf);
@@ -1235,6 +1346,110 @@ __device__ __forceinline__ void acc2_add_nz(Acc2 &a, uint64_t bits, unsigned &er
   acc2_add4(a, t0, t1, t2, t3);
 }
 
+// Adds the coefficient x (its double bits; 0 is never listed) exactly to lane
+// t's sum in shared memory: four 32-bit limbs acc[0..3][t], value
+// (l3:l2:l1:l0) * 2^-96, the 128-bit window of acc2_add. The mantissa lands on
+// limbs q..q+2 (q from its exponent); each limb is added with a shared-memory
+// atomic and its carry passed to the next limb, so concurrent adds to the same
+// lane sum exactly (integer addition, any order).
+__device__ __forceinline__ void acc_limbs_atomic_add(uint32_t (*acc)[64], int t, uint64_t bits, unsigned &err) {
+  const uint32_t hi = (uint32_t)(bits >> 32), lo = (uint32_t)bits;
+  const int p = (int)(hi >> 20) - 979;  // lowest mantissa bit, in units of 2^-96
+  if ((unsigned)p > 75u) {
+    err |= ERR_RANGE;
+    return;
+  }
+  const uint32_t mh = (hi & 0x000FFFFFu) | 0x00100000u;
+  const int r = p & 31, q = p >> 5;
+  const uint32_t c[3] = {lo << r, __funnelshift_l(lo, mh, r), __funnelshift_l(mh, 0u, r)};
+  uint32_t carry = 0u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int limb = q + k;
+    if (limb > 3) break;  // inside the window the sum never leaves 128 bits
+    const uint32_t x = (k < 3 ? c[k] : 0u) + carry;
+    carry = (k < 3 && x < carry) ? 1u : 0u;  // c[k] + carry wrapped (then x == 0)
+    if (x) {
+      const uint32_t old = atomicAdd(&acc[limb][t], x);
+      carry |= (old + x < x) ? 1u : 0u;
+    }
+    if (k >= 2 && !carry) break;
+  }
+}
+
+// Heavy segments with the successors' (coefficient, lane) items spread over
+// all 32 threads. The items of a 32-neighbour chunk are listed in neighbour
+// order (a successor's lanes are consecutive, so the 32 loads of a round touch
+// two or three coefficient rows); each thread takes one item per round and
+// adds it to the lane's exact sum in shared memory (acc_limbs_atomic_add). No
+// lane slot idles, unlike a 64-lane step per successor, of which a hub-level
+// successor fills about 13.
+__global__ void __launch_bounds__(FWD_THREADS, 4)
+k_bwd_heavy_seg_dense(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restrict__ seg_b,
+                      const int32_t *__restrict__ seg_e, const int32_t *__restrict__ col,
+                      const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
+                      const uint64_t *__restrict__ coef, uint4 *__restrict__ part, unsigned *__restrict__ wq,
+                      unsigned *__restrict__ err, uint64_t keep) {
+  __shared__ uint32_t accs[FWD_THREADS / 32][4][64];
+  __shared__ uint16_t itemss[FWD_THREADS / 32][DENSE_ITEMS];
+  __shared__ int32_t sws[FWD_THREADS / 32][32];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t (*acc)[64] = accs[wid];
+  uint16_t *items = itemss[wid];
+  int32_t *sw = sws[wid];
+  unsigned e = 0u;
+  for (int s = grab(wq, 1); s < nseg; s = grab(wq, 1)) {
+    const int32_t v = seg_v[s];
+    const uint64_t lanes = lm_cur[v] & keep;
+    if (!lanes) continue;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) (&acc[0][0])[lane + 32 * k] = 0u;
+    __syncwarp();
+    const int end = seg_e[s];
+    for (int base = seg_b[s]; base < end; base += 32) {
+      const int j = base + lane;
+      int32_t w = 0;
+      uint64_t m = 0ull;
+      if (j < end) {
+        w = col[j];
+        m = lm_next[w] & lanes;
+      }
+      sw[lane] = w;
+      const int c = __popcll((long long)m);
+      int incl = c;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, off);
+        if (lane >= off) incl += y;
+      }
+      const int N = __shfl_sync(FULL, incl, 31);
+      int k = incl - c;
+      while (m) {  // this neighbour's items: neighbour in bits 6..10, lane in bits 0..5
+        const int t = __ffsll((long long)m) - 1;
+        m &= m - 1ull;
+        items[k++] = (uint16_t)((lane << 6) | t);
+      }
+      __syncwarp();
+      for (int r0 = 0; r0 < N; r0 += 32) {
+        const int i = r0 + lane;
+        if (i < N) {
+          const unsigned code = items[i];
+          const int t = (int)(code & 63u);
+          const uint64_t x = coef[(size_t)sw[code >> 6] * 64 + t];
+          acc_limbs_atomic_add(acc, t, x, e);
+        }
+      }
+      __syncwarp();
+    }
+    if ((lanes >> lane) & 1ull) part[(size_t)s * 64 + lane] = make_uint4(acc[0][lane], acc[1][lane], acc[2][lane], acc[3][lane]);
+    if ((lanes >> (lane + 32)) & 1ull)
+      part[(size_t)s * 64 + lane + 32] =
+          make_uint4(acc[0][lane + 32], acc[1][lane + 32], acc[2][lane + 32], acc[3][lane + 32]);
+    __syncwarp();
+  }
+  if (e) atomicOr(err, e);
+}
+
 __global__ void __launch_bounds__(FWD_THREADS, BWD_MIN_BLOCKS)
 k_bwd_heavy_seg_lane(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__restrict__ seg_b,
                      const int32_t *__restrict__ seg_e, const int32_t *__restrict__ col,
@@ -1582,7 +1797,13 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
                                                  lst(l + 1), vcnt + l + 1, vedges + l + 1);
     }
     const bool heavy_now = !push && hm.nseg && !heavy_done;
-    if (heavy_now && ctx->heavy_lane) {
+    if (heavy_now && (ctx->heavy_lane == 3 || ctx->heavy_lane == 4)) {
+      LaunchScope ls(ctx, F_FWD);
+      k_fwd_heavy_dense<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
+          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
+          lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
+          act + l, ws.enable.as<uint64_t>(), ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 1);
+    } else if (heavy_now && ctx->heavy_lane == 1) {
       LaunchScope ls(ctx, F_FWD);
       k_fwd_heavy_lane<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
           hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
@@ -1691,7 +1912,8 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
       if (hm.nseg && heavy_at(ws, l)) {
         {
           LaunchScope ls(ctx, F_BWD);
-          auto kseg = ctx->heavy_lane ? k_bwd_heavy_seg_lane : k_bwd_heavy_seg_fx;
+          auto kseg = (ctx->heavy_lane == 2 || ctx->heavy_lane == 3) ? k_bwd_heavy_seg_dense
+                                           : (ctx->heavy_lane == 1 ? k_bwd_heavy_seg_lane : k_bwd_heavy_seg_fx);
           kseg<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
               hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
               lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), hm.part2.as<uint4>(),

@@ -178,9 +178,12 @@ struct bc_ctx {
   // light forward: a 32-neighbour chunk with at least pk_mincnt predecessors
   // over at most pk_maxl lanes is summed in packed groups (0 disables)
   int32_t pk_maxl = 16, pk_mincnt = 6;
-  // heavy-vertex segments: per-lane item loops (1) or 64-lane steps per neighbour (0);
-  // on R-MAT s20 the per-lane loops measured 4 % slower (scattered row loads)
-  int32_t heavy_lane = 0;
+  // heavy-vertex segments: 0 a 64-lane step per neighbour in both passes; 1
+  // per-lane item loops (4 % slower on R-MAT s20: scattered row loads); 2 the
+  // backward's items spread over all threads with exact shared-memory sums; 3
+  // that in both passes; 4 in the forward only (the default: the dense forward
+  // measured 3.5 % faster on R-MAT s20, the dense backward 1.6 % slower)
+  int32_t heavy_lane = 4;
   // direction of a forward level: top-down (push from the level's vertex list,
   // then counts pulled for the discovered vertices only) when the level's
   // vertices have at most nnz / push_div edges; bottom-up (every vertex with
