@@ -37,6 +37,10 @@ constexpr int FWD_THREADS = 256;
 // measured slower that way.
 constexpr int BWD_MIN_BLOCKS = 5;
 constexpr int DENSE_ITEMS = 32 * 64;  // dense item lists: at most 64 lanes for each of 32 neighbours
+// Shared-memory lane sums are indexed skew(t) = t + t/32 in rows of DSK words,
+// so lanes t and t + 32 fall in different banks.
+constexpr int DSK = 66;
+__device__ __forceinline__ int skew(int t) { return t + (t >> 5); }
 
 __device__ __forceinline__ uint64_t warp_or64(uint64_t x) {
   const unsigned lo = __reduce_or_sync(FULL, (unsigned)x);
@@ -320,6 +324,26 @@ __device__ __forceinline__ void chunk_packed(uint64_t m, int32_t w, uint64_t cm,
   }
 }
 
+// Adds the count x to lane t's 64-bit sum in shared memory (two 32-bit limbs,
+// the carry of the low limb passed on); a carry out of the high limb (the true
+// sum is 2^64 or more: the lane overflowed) sets the lane's bit in ovf2.
+__device__ __forceinline__ void u64_limbs_atomic_add(uint32_t (*acc)[DSK], uint32_t *ovf2, int t, uint64_t x) {
+  const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+  const int ts = skew(t);
+  uint32_t cy = 0u;
+  if (lo) {
+    const uint32_t old = atomicAdd(&acc[0][ts], lo);
+    cy = (old + lo < lo) ? 1u : 0u;
+  }
+  const uint32_t h = hi + cy;
+  bool of = h < cy;  // hi + carry wrapped
+  if (h) {
+    const uint32_t old = atomicAdd(&acc[1][ts], h);
+    of |= old + h < h;
+  }
+  if (of) atomicOr(&ovf2[t >> 5], 1u << (t & 31));
+}
+
 // --------------------------------------------------------------- forward --
 // One warp per vertex (grid-stride); heavy vertices only get lm_cur[v] = 0 here.
 __global__ void __launch_bounds__(FWD_THREADS)
@@ -595,25 +619,6 @@ k_fwd_heavy_lane(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__r
   if (lane == 0 && tri) atomicAdd(cnt, tri);
 }
 
-// Adds the count x to lane t's 64-bit sum in shared memory (two 32-bit limbs,
-// the carry of the low limb passed on); a carry out of the high limb (the true
-// sum is 2^64 or more: the lane overflowed) sets the lane's bit in ovf2.
-__device__ __forceinline__ void u64_limbs_atomic_add(uint32_t (*acc)[64], uint32_t *ovf2, int t, uint64_t x) {
-  const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
-  uint32_t cy = 0u;
-  if (lo) {
-    const uint32_t old = atomicAdd(&acc[0][t], lo);
-    cy = (old + lo < lo) ? 1u : 0u;
-  }
-  const uint32_t h = hi + cy;
-  bool of = h < cy;  // hi + carry wrapped
-  if (h) {
-    const uint32_t old = atomicAdd(&acc[1][t], h);
-    of |= old + h < h;
-  }
-  if (of) atomicOr(&ovf2[t >> 5], 1u << (t & 31));
-}
-
 // Heavy segments of the forward with the predecessors' (count, lane) items
 // spread over all 32 threads (see k_bwd_heavy_seg_dense); the segment's
 // per-lane sums go to the vertex's count row by 64-bit atomics as in k_fwd_heavy.
@@ -624,12 +629,12 @@ k_fwd_heavy_dense(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__
                   const uint64_t *__restrict__ visited, uint64_t *__restrict__ sigma,
                   const uint64_t *__restrict__ active_prev, uint64_t *__restrict__ enable,
                   unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq) {
-  __shared__ uint32_t accs[FWD_THREADS / 32][2][64];
+  __shared__ uint32_t accs[FWD_THREADS / 32][2][DSK];
   __shared__ uint32_t ovfs[FWD_THREADS / 32][2];
   __shared__ uint16_t itemss[FWD_THREADS / 32][DENSE_ITEMS];
   __shared__ int32_t sws[FWD_THREADS / 32][32];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t (*acc)[64] = accs[wid];
+  uint32_t (*acc)[DSK] = accs[wid];
   uint32_t *ovf2 = ovfs[wid];
   uint16_t *items = itemss[wid];
   int32_t *sw = sws[wid];
@@ -640,8 +645,7 @@ k_fwd_heavy_dense(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__
     const int32_t v = seg_v[s];
     const uint64_t pend = ~visited[v] & act;
     if (!pend) continue;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) (&acc[0][0])[lane + 32 * k] = 0u;
+    for (int k = lane; k < 2 * DSK; k += 32) (&acc[0][0])[k] = 0u;
     if (lane < 2) ovf2[lane] = 0u;
     __syncwarp();
     uint64_t newm = 0ull;
@@ -690,7 +694,7 @@ k_fwd_heavy_dense(int nseg, const int32_t *__restrict__ seg_v, const int32_t *__
       for (int h = 0; h < 2; ++h) {
         const int t = lane + 32 * h;
         if ((newm >> t) & 1ull) {
-          const uint64_t x = ((uint64_t)acc[1][t] << 32) | acc[0][t];
+          const uint64_t x = ((uint64_t)acc[1][skew(t)] << 32) | acc[0][skew(t)];
           const unsigned long long old = atomicAdd(dst + t, (unsigned long long)x);
           if (((ob >> t) & 1ull) || old + x < old) ovf |= 1ull << t;
         }
@@ -1352,7 +1356,7 @@ __device__ __forceinline__ void acc2_add_nz(Acc2 &a, uint64_t bits, unsigned &er
 // limbs q..q+2 (q from its exponent); each limb is added with a shared-memory
 // atomic and its carry passed to the next limb, so concurrent adds to the same
 // lane sum exactly (integer addition, any order).
-__device__ __forceinline__ void acc_limbs_atomic_add(uint32_t (*acc)[64], int t, uint64_t bits, unsigned &err) {
+__device__ __forceinline__ void acc_limbs_atomic_add(uint32_t (*acc)[DSK], int t, uint64_t bits, unsigned &err) {
   const uint32_t hi = (uint32_t)(bits >> 32), lo = (uint32_t)bits;
   const int p = (int)(hi >> 20) - 979;  // lowest mantissa bit, in units of 2^-96
   if ((unsigned)p > 75u) {
@@ -1370,7 +1374,7 @@ __device__ __forceinline__ void acc_limbs_atomic_add(uint32_t (*acc)[64], int t,
     const uint32_t x = (k < 3 ? c[k] : 0u) + carry;
     carry = (k < 3 && x < carry) ? 1u : 0u;  // c[k] + carry wrapped (then x == 0)
     if (x) {
-      const uint32_t old = atomicAdd(&acc[limb][t], x);
+      const uint32_t old = atomicAdd(&acc[limb][skew(t)], x);
       carry |= (old + x < x) ? 1u : 0u;
     }
     if (k >= 2 && !carry) break;
@@ -1390,11 +1394,11 @@ k_bwd_heavy_seg_dense(int nseg, const int32_t *__restrict__ seg_v, const int32_t
                       const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
                       const uint64_t *__restrict__ coef, uint4 *__restrict__ part, unsigned *__restrict__ wq,
                       unsigned *__restrict__ err, uint64_t keep) {
-  __shared__ uint32_t accs[FWD_THREADS / 32][4][64];
+  __shared__ uint32_t accs[FWD_THREADS / 32][4][DSK];
   __shared__ uint16_t itemss[FWD_THREADS / 32][DENSE_ITEMS];
   __shared__ int32_t sws[FWD_THREADS / 32][32];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t (*acc)[64] = accs[wid];
+  uint32_t (*acc)[DSK] = accs[wid];
   uint16_t *items = itemss[wid];
   int32_t *sw = sws[wid];
   unsigned e = 0u;
@@ -1402,8 +1406,7 @@ k_bwd_heavy_seg_dense(int nseg, const int32_t *__restrict__ seg_v, const int32_t
     const int32_t v = seg_v[s];
     const uint64_t lanes = lm_cur[v] & keep;
     if (!lanes) continue;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) (&acc[0][0])[lane + 32 * k] = 0u;
+    for (int k = lane; k < 4 * DSK; k += 32) (&acc[0][0])[k] = 0u;
     __syncwarp();
     const int end = seg_e[s];
     for (int base = seg_b[s]; base < end; base += 32) {
@@ -1441,10 +1444,10 @@ k_bwd_heavy_seg_dense(int nseg, const int32_t *__restrict__ seg_v, const int32_t
       }
       __syncwarp();
     }
-    if ((lanes >> lane) & 1ull) part[(size_t)s * 64 + lane] = make_uint4(acc[0][lane], acc[1][lane], acc[2][lane], acc[3][lane]);
+    const int a0 = skew(lane), a1 = skew(lane + 32);
+    if ((lanes >> lane) & 1ull) part[(size_t)s * 64 + lane] = make_uint4(acc[0][a0], acc[1][a0], acc[2][a0], acc[3][a0]);
     if ((lanes >> (lane + 32)) & 1ull)
-      part[(size_t)s * 64 + lane + 32] =
-          make_uint4(acc[0][lane + 32], acc[1][lane + 32], acc[2][lane + 32], acc[3][lane + 32]);
+      part[(size_t)s * 64 + lane + 32] = make_uint4(acc[0][a1], acc[1][a1], acc[2][a1], acc[3][a1]);
     __syncwarp();
   }
   if (e) atomicOr(err, e);
