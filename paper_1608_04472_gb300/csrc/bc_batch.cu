@@ -1097,17 +1097,32 @@ k_bwd_light(int32_t n, const int32_t *__restrict__ list_l, const unsigned *__res
   unsigned head = 0u, tail = 0u;
   unsigned e = 0u;
   // a small level walks its vertex list; a large one scans the vertex ids in
-  // order (adjacent rows, sequential CSR reads), skipping vertices without lanes
+  // order (adjacent rows, sequential CSR reads). A warp takes 32 vertices at a
+  // time, loads their masks and row bounds at once (one per thread) and walks
+  // only the light ones with lanes at this level.
   const int nv = vcnt_l ? (int)*vcnt_l : n;
   const bool by_list = vcnt_l && (int64_t)nv * 16 <= (int64_t)n;
   const int total = by_list ? nv : n;
-  for (int base = grab(wq); base < total; base = grab(wq))
-    for (int i = base; i < min(base + GRAB, total); ++i) {
-      const int32_t v = by_list ? list_l[i] : i;
-      const uint64_t lanes = lm_cur[v] & keep;
-      if (!lanes) continue;
-      const int beg = rp[v], end = rp[v + 1];
-      if (end - beg > heavy_deg) continue;
+  const int lane_id = threadIdx.x & 31;
+  for (int base = grab(wq, 32); base < total; base = grab(wq, 32)) {
+    const int ii = base + lane_id;
+    int32_t hv = 0;
+    uint64_t hl = 0ull;
+    int hb = 0, he = 0;
+    if (ii < total) {
+      hv = by_list ? list_l[ii] : ii;
+      hl = lm_cur[hv] & keep;
+      if (hl) {
+        hb = rp[hv];
+        he = rp[hv + 1];
+        if (he - hb > heavy_deg) hl = 0ull;  // heavy: its segments' kernels
+      }
+    }
+    for (unsigned todo = __ballot_sync(FULL, hl != 0ull); todo; todo &= todo - 1u) {
+      const int iv = __ffs(todo) - 1;
+      const int32_t v = __shfl_sync(FULL, hv, iv);
+      const uint64_t lanes = __shfl_sync(FULL, hl, iv);
+      const int beg = __shfl_sync(FULL, hb, iv), end = __shfl_sync(FULL, he, iv);
       // thread t owns lanes t and t + 32 (no compaction: cheapest per vertex)
       const int lane = threadIdx.x & 31;
       const int p0 = ((lanes >> lane) & 1ull) ? lane : -1;
@@ -1122,6 +1137,7 @@ k_bwd_light(int32_t n, const int32_t *__restrict__ list_l, const unsigned *__res
         __syncwarp();
       }
     }
+  }
   if (tail != head) ring_round(R, head, (int)(tail - head), sigma, sink, e);
   if (e) atomicOr(err, e);
 }
@@ -1276,17 +1292,32 @@ k_bwd_light_fx(int32_t n, const int32_t *__restrict__ list_l, const unsigned *__
   unsigned head = 0u, tail = 0u;
   unsigned e = 0u;
   // a small level walks its vertex list; a large one scans the vertex ids in
-  // order (adjacent rows, sequential CSR reads), skipping vertices without lanes
+  // order (adjacent rows, sequential CSR reads). A warp takes 32 vertices at a
+  // time, loads their masks and row bounds at once (one per thread) and walks
+  // only the light ones with lanes at this level.
   const int nv = vcnt_l ? (int)*vcnt_l : n;
   const bool by_list = vcnt_l && (int64_t)nv * 16 <= (int64_t)n;
   const int total = by_list ? nv : n;
-  for (int base = grab(wq); base < total; base = grab(wq))
-    for (int i = base; i < min(base + GRAB, total); ++i) {
-      const int32_t v = by_list ? list_l[i] : i;
-      const uint64_t lanes = lm_cur[v] & keep;
-      if (!lanes) continue;
-      const int beg = rp[v], end = rp[v + 1];
-      if (end - beg > heavy_deg) continue;
+  const int lane_id = threadIdx.x & 31;
+  for (int base = grab(wq, 32); base < total; base = grab(wq, 32)) {
+    const int ii = base + lane_id;
+    int32_t hv = 0;
+    uint64_t hl = 0ull;
+    int hb = 0, he = 0;
+    if (ii < total) {
+      hv = by_list ? list_l[ii] : ii;
+      hl = lm_cur[hv] & keep;
+      if (hl) {
+        hb = rp[hv];
+        he = rp[hv + 1];
+        if (he - hb > heavy_deg) hl = 0ull;  // heavy: its segments' kernels
+      }
+    }
+    for (unsigned todo = __ballot_sync(FULL, hl != 0ull); todo; todo &= todo - 1u) {
+      const int iv = __ffs(todo) - 1;
+      const int32_t v = __shfl_sync(FULL, hv, iv);
+      const uint64_t lanes = __shfl_sync(FULL, hl, iv);
+      const int beg = __shfl_sync(FULL, hb, iv), end = __shfl_sync(FULL, he, iv);
       const Packed pk = pack_lanes(lanes, tab);
       Acc2 a0 = acc2_zero(), a1 = acc2_zero();
       gather_packed(beg, end, lanes, lm_next, col, sigma, pk, list, a0, a1, e);
@@ -1298,6 +1329,7 @@ k_bwd_light_fx(int32_t n, const int32_t *__restrict__ list_l, const unsigned *__
         __syncwarp();
       }
     }
+  }
   if (tail != head) ring_round(R, head, (int)(tail - head), sigma, sink, e);
   if (e) atomicOr(err, e);
 }
@@ -1586,11 +1618,15 @@ struct HeavyMeta {
 static std::map<const int32_t *, HeavyMeta> g_heavy;  // keyed by the graph's device col pointer
 static std::mutex g_heavy_mu;
 
-static HeavyMeta &heavy_meta(bc_ctx *ctx, const Graph &g) {
+// The heavy-vertex split of the CSR the forward pulls over (in_csr: the
+// in-neighbour CSR, which is the CSR itself on an undirected graph) or of the
+// out-CSR the backward walks; each is kept per row-pointer array.
+static HeavyMeta &heavy_meta(bc_ctx *ctx, const Graph &g, bool in_csr) {
   std::lock_guard<std::mutex> lk(g_heavy_mu);
   const int want_deg = ctx->heavy_deg > 0 ? ctx->heavy_deg : HEAVY_DEFAULT;
   const int want_seg = ctx->seg_len > 0 ? ctx->seg_len : SEG_DEFAULT;
-  auto it = g_heavy.find(g.rp);
+  const int32_t *grp = in_csr ? g.rp_in : g.rp;
+  auto it = g_heavy.find(grp);
   if (it != g_heavy.end()) {
     HeavyMeta &old = it->second;
     if (old.heavy_deg == want_deg && old.seg == want_seg) return old;
@@ -1600,9 +1636,9 @@ static HeavyMeta &heavy_meta(bc_ctx *ctx, const Graph &g) {
     old.seg_e.release(); old.part.release(); old.part2.release();
     g_heavy.erase(it);
   }
-  HeavyMeta &hm = g_heavy[g.rp];
+  HeavyMeta &hm = g_heavy[grp];
   std::vector<int32_t> rp(g.n + 1);
-  BCG_CUDA(cudaMemcpy(rp.data(), g.rp, sizeof(int32_t) * (g.n + 1), cudaMemcpyDeviceToHost));
+  BCG_CUDA(cudaMemcpy(rp.data(), grp, sizeof(int32_t) * (g.n + 1), cudaMemcpyDeviceToHost));
   std::vector<int32_t> heavy, hseg0, sv, sb, se;
   hm.heavy_deg = want_deg;
   hm.seg = want_seg;
@@ -1670,7 +1706,8 @@ void batch_ensure(bc_ctx *ctx, const Graph &g) {
   ws.vlist.ensure((size_t)ws.lcap * n * 4);
   ws.vcnt.ensure((size_t)(ws.lcap + 2) * 4);
   ws.vedges.ensure((size_t)(ws.lcap + 2) * 8);
-  heavy_meta(ctx, g);
+  heavy_meta(ctx, g, true);
+  heavy_meta(ctx, g, false);
 }
 
 // Two device words to the host with one synchronisation.
@@ -1686,7 +1723,11 @@ static void read_u64x2(bc_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64
 int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mode) {
   Workspace &ws = ctx->ws;
   batch_ensure(ctx, g);
-  HeavyMeta &hm = heavy_meta(ctx, g);
+  // counts are pulled over the in-neighbour CSR (the CSR itself when undirected;
+  // Def. 3 with paths following the edges on a directed graph); level 1 and the
+  // top-down pushes follow the out-edges
+  HeavyMeta &hm = heavy_meta(ctx, g, true);
+  const int32_t *prp = g.rp_in, *pcol = g.col_in;
   const size_t n = (size_t)g.n;
   cudaStream_t st = ctx->stream;
   BCG_CUDA(cudaMemsetAsync(ws.lm.p, 0, 2 * n * 8, st));  // levels 0 and 1
@@ -1784,7 +1825,7 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
                                                   vedges + l + 1, ws.wq.as<unsigned>() + 8 * l + 0);
       }
       LaunchScope ls(ctx, F_FWD);
-      k_fwd_pull_list<<<blocks, FWD_THREADS, 0, st>>>(g.rp, g.col, lst(l + 1), vcnt + l + 1,
+      k_fwd_pull_list<<<blocks, FWD_THREADS, 0, st>>>(prp, pcol, lst(l + 1), vcnt + l + 1,
                                                      lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
                                                      ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
                                                      ws.enable.as<uint64_t>(), act + l + 1,
@@ -1792,7 +1833,7 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
                                                      hm.heavy_deg, hw + 5);
     } else {
       LaunchScope ls(ctx, F_FWD);
-      k_fwd_light<<<blocks, FWD_THREADS, 0, st>>>(g.n, g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
+      k_fwd_light<<<blocks, FWD_THREADS, 0, st>>>(g.n, prp, pcol, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
                                                  ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(), act + l,
                                                  ws.enable.as<uint64_t>(), act + l + 1, ws.err.as<unsigned>(),
                                                  ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 0,
@@ -1803,19 +1844,19 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
     if (heavy_now && (ctx->heavy_lane == 3 || ctx->heavy_lane == 4)) {
       LaunchScope ls(ctx, F_FWD);
       k_fwd_heavy_dense<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
-          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
+          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), pcol,
           lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
           act + l, ws.enable.as<uint64_t>(), ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 1);
     } else if (heavy_now && ctx->heavy_lane == 1) {
       LaunchScope ls(ctx, F_FWD);
       k_fwd_heavy_lane<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
-          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
+          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), pcol,
           lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
           act + l, ws.enable.as<uint64_t>(), ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 1);
     } else if (heavy_now) {
       LaunchScope ls(ctx, F_FWD);
       k_fwd_heavy<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
-          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
+          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), pcol,
           lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
           act + l, ws.enable.as<uint64_t>(), ws.err.as<unsigned>(), ws.cnt.as<unsigned long long>(),
           ws.wq.as<unsigned>() + 8 * l + 1);
@@ -1873,7 +1914,9 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
       // per level: did any heavy vertex get lanes there (level 1 is filled
       // without the heavy kernels: assume yes)
       ws.hlev.assign((size_t)l + 2, 1);
-      if (hm.nseg) {
+      // (a directed graph's backward splits by out-degree, so its heavy
+      // kernels run at every level)
+      if (hm.nseg && !g.directed) {
         std::vector<unsigned> fl((size_t)(l + 2) * 8);
         BCG_CUDA(cudaMemcpyAsync(fl.data(), ws.wq.p, fl.size() * 4, cudaMemcpyDeviceToHost, st));
         BCG_CUDA(cudaStreamSynchronize(st));
@@ -1891,7 +1934,7 @@ static inline bool heavy_at(const Workspace &ws, int l) { return l >= (int)ws.hl
 
 void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink, uint64_t keep) {
   Workspace &ws = ctx->ws;
-  HeavyMeta &hm = heavy_meta(ctx, g);
+  HeavyMeta &hm = heavy_meta(ctx, g, false);  // successors: the out-CSR
   const size_t n = (size_t)g.n;
   cudaStream_t st = ctx->stream;
   const int blocks = grid_blocks();

@@ -637,11 +637,10 @@ static void do_exact_or_uniform(bc_ctx *ctx, const Graph &g, bool exact, int64_t
   BCG_CUDA(cudaMemcpy(out, ws.misc2.p, n * 8, cudaMemcpyDeviceToHost));
 }
 
-// A directed graph reports an unbounded depth, which sends its batches to the
-// lane-major engine: the level-mask engine pulls counts over the out-CSR.
-int graph_depth_hint(bc_ctx *ctx, const Graph &g) {
-  return g.directed ? INT32_MAX : key_meta(ctx, g, false).ecc;
-}
+// The depth that decides between the level-mask engine and one source per
+// persistent CTA: the largest finite distance from the hub (along out-edges on
+// a directed graph; the level-mask engine pulls counts over the in-neighbour CSR).
+int graph_depth_hint(bc_ctx *ctx, const Graph &g) { return key_meta(ctx, g, false).ecc; }
 
 void uniform_one(bc_ctx *ctx, const Graph &g, int64_t k, uint64_t seed, uint64_t qid, double *out) {
   do_exact_or_uniform(ctx, g, false, k, seed, qid, out);
@@ -977,8 +976,7 @@ static void do_source_dependencies(bc_ctx *ctx, const Graph &g, const int32_t *s
     if (sources[i] < 0 || sources[i] >= g.n) fail(BC_E_INVALID, "source out of range");
   ws.delta_lm.ensure(n * 64 * 8);
   DevBuf dd, ddist, dsig, dsm, dse;
-  // a directed graph runs one source at a time on the plain engine
-  const int width = g.directed ? 1 : batch_width(ctx);
+  const int width = batch_width(ctx);
   const int chunk = std::min<int>(64, std::max(1, count));
   const bool want_xf = sm_out || se_out;
   dd.ensure(n * chunk * 8);
@@ -1330,6 +1328,7 @@ void bc_destroy(bc_ctx *ctx) {
     resolve_events(ctx);
     for (auto &kv : ctx->graphs) {
       forget_heavy_meta(kv.second.rp);
+      if (kv.second.directed) forget_heavy_meta(kv.second.rp_in);
       forget_key_meta(kv.second.rp);
       cudaFree(kv.second.rp);
       cudaFree(kv.second.col);
@@ -1391,6 +1390,7 @@ bc_status bc_graph_free(bc_ctx *ctx, bc_graph g) {
   sync(ctx);
   if (multi_plan_uses_graph(ctx, g)) forget_multi_plan(ctx);
   forget_heavy_meta(it->second.rp);
+  if (it->second.directed) forget_heavy_meta(it->second.rp_in);
   forget_key_meta(it->second.rp);
   cudaFree(it->second.rp);
   cudaFree(it->second.col);
