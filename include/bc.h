@@ -350,6 +350,19 @@ bc_status bc_exact_sum(bc_ctx *ctx, const double *x, int64_t count, double *out)
 bc_status bc_target_dependencies(bc_ctx *ctx, bc_graph g, const int32_t *targets, int32_t T, uint64_t seed,
                                  uint64_t qid, int64_t i0, int64_t count, double *out);
 
+/* The block of Algorithm 1's per-draw values for draws [i0, i0+count) of the
+ * stream (seed, qid): out[j*count + i] = the pair value of draw i0+i for
+ * target j -- sigma_{s t}(v_j) / sigma_st when d(s,v_j) + d(v_j,t) = d(s,t)
+ * (Eq. 2) and v_j is neither s nor t, else 0 -- as bc_adaptive_pairs
+ * accumulates them. The T target BFSs (d(v_j, .) and sigma_{v_j .}) are kept
+ * in device memory after the call and reused by the next call with the same
+ * graph and targets (one set per context; freed by bc_graph_free of that graph
+ * or bc_destroy). Undirected unweighted graphs with n >= 2 (BC_E_INVALID
+ * otherwise); targets, count and i0 as bc_target_dependencies; out[T*count]
+ * is caller-owned host memory. */
+bc_status bc_pair_values(bc_ctx *ctx, bc_graph g, const int32_t *targets, int32_t T, uint64_t seed, uint64_t qid,
+                         int64_t i0, int64_t count, double *out);
+
 /* Adds the exact sums over draws [i0, i0+count) of (seed, qid) of the
  * uniform estimate (sum over sampled sources of delta_s(x), Eq. 4 restricted
  * to the draws) into parts[6*n] (caller-owned host memory, in/out): vertex v's

@@ -106,6 +106,7 @@ _SIGS = {
     "bc_draw_pairs": (_i32, [_vp, _u64, _u64, _u64, _i64, _i32, _i32p, _i32p]),
     "bc_exact_sum": (_i32, [_vp, _f64p, _i64, _f64p]),
     "bc_target_dependencies": (_i32, [_vp, _i64, _i32p, _i32, _u64, _u64, _i64, _i64, _f64p]),
+    "bc_pair_values": (_i32, [_vp, _i64, _i32p, _i32, _u64, _u64, _i64, _i64, _f64p]),
     "bc_uniform_partial": (_i32, [_vp, _i64, _u64, _u64, _i64, _i64, _i64p]),
     "bc_acc_add_rows": (_i32, [_i32, _f64p, _i64, _i64p]),
     "bc_acc_estimate": (_i32, [_i32, _i64p, _i64, _f64p]),
@@ -423,6 +424,16 @@ def bc_target_dependencies(ctx, g: int, targets, seed: int, qid: int, i0: int, c
     return out
 
 
+def bc_pair_values(ctx, g: int, targets, seed: int, qid: int, i0: int, count: int) -> np.ndarray:
+    """[T][count] block of Algorithm 1's per-draw pair values for draws i0 .. i0+count-1."""
+    t = _i32arr(targets)
+    out = np.zeros((t.size, max(int(count), 0)), np.float64)
+    tp = t if t.size else np.zeros(1, np.int32)
+    op = out if out.size else np.zeros(1, np.float64)
+    _ck(ctx, _lib.bc_pair_values(ctx, g, _p(tp, _i32p), t.size, seed, qid, i0, int(count), _p(op, _f64p)))
+    return out
+
+
 def bc_uniform_partial(ctx, g: int, seed: int, qid: int, i0: int, count: int, parts: np.ndarray) -> np.ndarray:
     """Adds the exact sums of draws i0 .. i0+count-1 into parts (int64 [n][6], in place)."""
     if parts.dtype != np.int64 or not parts.flags.c_contiguous:
@@ -603,6 +614,9 @@ class Context:
 
     def target_dependencies(self, g, targets, seed, qid, i0, count):
         return bc_target_dependencies(self.ptr, g, targets, seed, qid, i0, count)
+
+    def pair_values(self, g, targets, seed, qid, i0, count):
+        return bc_pair_values(self.ptr, g, targets, seed, qid, i0, count)
 
     def uniform_partial(self, g, seed, qid, i0, count, parts):
         return bc_uniform_partial(self.ptr, g, seed, qid, i0, count, parts)

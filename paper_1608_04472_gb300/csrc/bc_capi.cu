@@ -832,6 +832,115 @@ uint64_t pair_batch(bc_ctx *ctx, const Graph &g, int count) {
   return ovf ? pair_batch_bidir(ctx, g, count) : 0ull;
 }
 
+// d(s,t) and sigma_st of the W pair lanes wsrc -> wdst (Algorithm 1's BFS of
+// the pair): the bidirectional search, or the one-sided BFS 64 lanes at a time.
+static void pair_window(bc_ctx *ctx, const Graph &g, int W, int32_t *wsrc, int32_t *wdst, int32_t *wpd,
+                        uint64_t *wpsig, int32_t *wpexp, int32_t *wpxf) {
+  Workspace &ws = ctx->ws;
+  cudaStream_t st = ctx->stream;
+  if (ctx->pair_engine == 0) {
+    pair_lanes(ctx, g, wsrc, wdst, W, wpd, wpsig, wpexp, wpxf);
+    return;
+  }
+  for (int b = 0; b < W; b += 64) {
+    const int cnt = std::min(64, W - b);
+    BCG_CUDA(cudaMemcpyAsync(ws.sources.p, wsrc + b, (size_t)cnt * 4, cudaMemcpyDeviceToDevice, st));
+    BCG_CUDA(cudaMemcpyAsync(ws.targets.p, wdst + b, (size_t)cnt * 4, cudaMemcpyDeviceToDevice, st));
+    const uint64_t px = pair_batch(ctx, g, cnt);
+    BCG_CUDA(cudaMemcpyAsync(wpd + b, ws.pair_d.p, (size_t)cnt * 4, cudaMemcpyDeviceToDevice, st));
+    BCG_CUDA(cudaMemcpyAsync(wpsig + b, ws.pair_sig.p, (size_t)cnt * 8, cudaMemcpyDeviceToDevice, st));
+    BCG_CUDA(cudaMemcpyAsync(wpexp + b, ws.pair_exp.p, (size_t)cnt * 4, cudaMemcpyDeviceToDevice, st));
+    LaunchScope ls(ctx, F_PAIR);
+    k_mask_flags<<<1, 64, 0, st>>>(cnt, px, wpxf + b);
+  }
+}
+
+// The tables of the targets of the last pair-value block (d(v_j, .) and
+// sigma_{v_j .}, [n][Tp]), kept for the next block of the same query (graph
+// and targets): a rank that computes many blocks of one query runs the T
+// target BFSs once.
+struct PairTables {
+  bc_graph g = 0;
+  std::vector<int32_t> targets;
+  DevBuf tdist, tsig, texp, dtx, dtarg;
+  bool valid = false;
+};
+static std::map<bc_ctx *, PairTables> g_ptab;
+static std::mutex g_ptab_mu;
+
+void forget_pair_tables(bc_ctx *ctx, bc_graph g) {
+  std::lock_guard<std::mutex> lk(g_ptab_mu);
+  auto it = g_ptab.find(ctx);
+  if (it == g_ptab.end() || (g != 0 && it->second.g != g)) return;
+  PairTables &P = it->second;
+  for (DevBuf *b : {&P.tdist, &P.tsig, &P.texp, &P.dtx, &P.dtarg}) b->release();
+  g_ptab.erase(it);
+}
+
+// Algorithm 1's per-draw values for draws [i0, i0+count) of (seed, qid):
+// out[j*count + i] = sigma_{s t}(v_j) / sigma_st (Eq. 2, with the conditions
+// of the pair dependency), the values the adaptive loop sums.
+static void do_pair_block(bc_ctx *ctx, bc_graph gh, const Graph &g, const int32_t *targets, int32_t T,
+                          uint64_t seed, uint64_t qid, int64_t i0, int64_t count, double *out) {
+  cudaStream_t st = ctx->stream;
+  const size_t n = (size_t)g.n;
+  const int Tp = std::max(T, 1);
+  PairTables *Pp;
+  {
+    std::lock_guard<std::mutex> lk(g_ptab_mu);
+    Pp = &g_ptab[ctx];
+  }
+  PairTables &P = *Pp;
+  const std::vector<int32_t> want(targets, targets + T);
+  if (!P.valid || P.g != gh || P.targets != want) {
+    P.valid = false;
+    P.tdist.ensure(n * Tp * 4);
+    P.tsig.ensure(n * Tp * 8);
+    P.dtarg.ensure((size_t)Tp * 4);
+    BCG_CUDA(cudaMemcpyAsync(P.dtarg.p, targets, (size_t)T * 4, cudaMemcpyHostToDevice, st));
+    std::vector<int32_t> tx;
+    P.texp.release();
+    target_bfs(ctx, g, P.dtarg.as<int32_t>(), T, Tp, P.tdist.as<int32_t>(), P.tsig.as<uint64_t>(), P.texp, tx);
+    if (P.texp.p) {
+      P.dtx.ensure((size_t)Tp * 4);
+      BCG_CUDA(cudaMemcpyAsync(P.dtx.p, tx.data(), (size_t)Tp * 4, cudaMemcpyHostToDevice, st));
+    }
+    sync(ctx);
+    P.g = gh;
+    P.targets = want;
+    P.valid = true;
+  }
+  Workspace &ws = ctx->ws;
+  ws.tdelta.ensure((size_t)Tp * WMAX * 8);
+  DevBuf wsrc, wdst, wpd, wpsig, wpexp, wpxf;
+  for (DevBuf *b : {&wsrc, &wdst, &wpd, &wpexp, &wpxf}) b->ensure(WMAX * 4);
+  wpsig.ensure(WMAX * 8);
+  std::vector<double> h((size_t)T * WMAX);
+  for (int64_t a = 0; a < count; a += WMAX) {
+    const int W = (int)std::min<int64_t>(WMAX, count - a);
+    {
+      LaunchScope ls(ctx, F_DRAW);
+      k_draw_pairs<<<(W + 63) / 64, 64, 0, st>>>(seed, qid, (uint64_t)(i0 + a), W, g.n, wsrc.as<int32_t>(),
+                                                 wdst.as<int32_t>());
+    }
+    pair_window(ctx, g, W, wsrc.as<int32_t>(), wdst.as<int32_t>(), wpd.as<int32_t>(), wpsig.as<uint64_t>(),
+                wpexp.as<int32_t>(), wpxf.as<int32_t>());
+    {
+      LaunchScope ls(ctx, F_PAIR);
+      k_pair_values<<<dim3((unsigned)T, (unsigned)((W + 63) / 64)), 64, 0, st>>>(
+          T, W, P.dtarg.as<int32_t>(), wsrc.as<int32_t>(), wdst.as<int32_t>(), wpd.as<int32_t>(),
+          wpsig.as<uint64_t>(), P.tdist.as<int32_t>(), P.tsig.as<uint64_t>(), Tp, P.texp.as<int32_t>(),
+          P.texp.p ? P.dtx.as<int32_t>() : nullptr, wpexp.as<int32_t>(), wpxf.as<int32_t>(), ws.tdelta.as<double>(),
+          W);
+    }
+    BCG_CUDA(cudaMemcpyAsync(h.data(), ws.tdelta.p, (size_t)T * W * 8, cudaMemcpyDeviceToHost, st));
+    sync(ctx);
+    for (int32_t j = 0; j < T; ++j)
+      std::memcpy(out + (size_t)j * count + a, h.data() + (size_t)j * W, (size_t)W * 8);
+  }
+  check_err_bits(ctx);
+}
+
 static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *targets, int32_t T, double c,
                               int64_t cap, uint64_t seed, uint64_t qid, double scale, double *est, int64_t *k,
                               double *S, int32_t *status) {
@@ -872,24 +981,8 @@ static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *target
         k_draw_pairs<<<(W + 63) / 64, 64, 0, st>>>(seed, qid, (uint64_t)i0, W, g.n, wsrc.as<int32_t>(),
                                                    wdst.as<int32_t>());
       }
-      if (ctx->pair_engine == 0) {
-        pair_lanes(ctx, g, wsrc.as<int32_t>(), wdst.as<int32_t>(), W, wpd.as<int32_t>(), wpsig.as<uint64_t>(),
-                   wpexp.as<int32_t>(), wpxf.as<int32_t>());
-      } else {
-        for (int b = 0; b < W; b += 64) {
-          const int cnt = std::min(64, W - b);
-          BCG_CUDA(cudaMemcpyAsync(ws.sources.p, wsrc.as<int32_t>() + b, (size_t)cnt * 4, cudaMemcpyDeviceToDevice, st));
-          BCG_CUDA(cudaMemcpyAsync(ws.targets.p, wdst.as<int32_t>() + b, (size_t)cnt * 4, cudaMemcpyDeviceToDevice, st));
-          const uint64_t px = pair_batch(ctx, g, cnt);
-          BCG_CUDA(cudaMemcpyAsync(wpd.as<int32_t>() + b, ws.pair_d.p, (size_t)cnt * 4, cudaMemcpyDeviceToDevice, st));
-          BCG_CUDA(cudaMemcpyAsync(wpsig.as<uint64_t>() + b, ws.pair_sig.p, (size_t)cnt * 8, cudaMemcpyDeviceToDevice,
-                                   st));
-          BCG_CUDA(cudaMemcpyAsync(wpexp.as<int32_t>() + b, ws.pair_exp.p, (size_t)cnt * 4, cudaMemcpyDeviceToDevice,
-                                   st));
-          LaunchScope ls(ctx, F_PAIR);
-          k_mask_flags<<<1, 64, 0, st>>>(cnt, px, wpxf.as<int32_t>() + b);
-        }
-      }
+      pair_window(ctx, g, W, wsrc.as<int32_t>(), wdst.as<int32_t>(), wpd.as<int32_t>(), wpsig.as<uint64_t>(),
+                  wpexp.as<int32_t>(), wpxf.as<int32_t>());
       if (T > 0) {
         LaunchScope ls(ctx, F_PAIR);
         k_pair_values<<<dim3((unsigned)T, (unsigned)((W + 63) / 64)), 64, 0, st>>>(
@@ -1325,6 +1418,7 @@ void bc_destroy(bc_ctx *ctx) {
     forget_lane_scratch(ctx);
     forget_bidir_scratch(ctx);
     forget_weighted_scratch(ctx);
+    forget_pair_tables(ctx, 0);
     resolve_events(ctx);
     for (auto &kv : ctx->graphs) {
       forget_heavy_meta(kv.second.rp);
@@ -1389,6 +1483,7 @@ bc_status bc_graph_free(bc_ctx *ctx, bc_graph g) {
   if (server_uses_graph(ctx, g)) fail(BC_E_INVALID, "graph is used by a queued or running query");
   sync(ctx);
   if (multi_plan_uses_graph(ctx, g)) forget_multi_plan(ctx);
+  forget_pair_tables(ctx, g);
   forget_heavy_meta(it->second.rp);
   if (it->second.directed) forget_heavy_meta(it->second.rp_in);
   forget_key_meta(it->second.rp);
@@ -1604,6 +1699,21 @@ bc_status bc_target_dependencies(bc_ctx *ctx, bc_graph g, const int32_t *targets
   validate_targets(gr, targets, T);
   BCG_CUDA(cudaSetDevice(ctx->device));
   if (T > 0 && count > 0) do_target_block(ctx, gr, targets, T, seed, qid, i0, count, out);
+  BC_GUARD_END
+}
+
+bc_status bc_pair_values(bc_ctx *ctx, bc_graph g, const int32_t *targets, int32_t T, uint64_t seed, uint64_t qid,
+                         int64_t i0, int64_t count, double *out) {
+  BC_GUARD_BEGIN
+  const Graph &gr = get_graph(ctx, g);
+  KnobScope ks(ctx, gr);
+  if (gr.directed || gr.w) fail(BC_E_INVALID, "pair sampling needs an undirected unweighted graph");
+  if (gr.n < 2) fail(BC_E_INVALID, "pair sampling needs n >= 2");
+  if (i0 < 0 || count < 0 || count > ((int64_t)1 << 32)) fail(BC_E_INVALID, "need i0 >= 0 and 0 <= count <= 2^32");
+  if (T > 0 && count > 0 && !out) fail(BC_E_INVALID, "out is NULL");
+  validate_targets(gr, targets, T);
+  BCG_CUDA(cudaSetDevice(ctx->device));
+  if (T > 0 && count > 0) do_pair_block(ctx, g, gr, targets, T, seed, qid, i0, count, out);
   BC_GUARD_END
 }
 

@@ -76,6 +76,17 @@ def adaptive_sources_sharded(ctx, g: int, targets, c: float, cap: int, seed: int
                             c * n, cap, rank, world, allgather, B)
 
 
+def adaptive_pairs_sharded(ctx, g: int, targets, c: float, cap: int, seed: int, qid: int, rank: int, world: int,
+                           allgather, B: int = 256, threshold_scale: float = 1.0) -> dict:
+    """bc_adaptive_pairs' results for one query computed by `world` ranks
+    (each rank's blocks from bc_pair_values, which keeps the target BFSs of
+    the query between its blocks)."""
+    n, _ = capi.bc_graph_info(ctx.ptr, g)
+    t = np.ascontiguousarray(targets, dtype=np.int32)
+    return adaptive_sharded(lambda i0, cnt: ctx.pair_values(g, t, seed, qid, i0, cnt), t.size,
+                            float(n) * float(n - 1), c * n, cap, rank, world, allgather, B, threshold_scale)
+
+
 def uniform_sources_sharded(ctx, g: int, k: int, seed: int, qid: int, rank: int, world: int, allreduce_sum,
                             B: int = 1024) -> np.ndarray:
     """bc_uniform_sources' estimate for one query computed by `world` ranks."""

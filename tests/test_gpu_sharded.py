@@ -1,9 +1,9 @@
 """The GPU side of one query shared by several ranks: bc_target_dependencies
-blocks and bc_uniform_partial partials computed on the GPU, combined by the
-sharding driver (rank partials summed as integers, blocks scanned in draw
-order), must give bc_adaptive_sources' and bc_uniform_sources' results bit for
-bit, for any block size; the blocks themselves equal the oracle's per-draw
-target dependencies. (The exchange between processes is covered on CPU by
+blocks, bc_pair_values blocks and bc_uniform_partial partials computed on the
+GPU, combined by the sharding driver (rank partials summed as integers, blocks
+scanned in draw order), must give bc_adaptive_sources', bc_adaptive_pairs' and
+bc_uniform_sources' results bit for bit, for any block size; the blocks
+themselves equal the oracle's per-draw target dependencies and pair values. (The exchange between processes is covered on CPU by
 tests/test_sharded_cpu.py.)"""
 import numpy as np
 import pytest
@@ -54,5 +54,56 @@ def test_sharded_matches_single_gpu(ctx, family):
                     ctx.uniform_partial(h, seed, qid + 1, i0, min(B, k - i0), parts[r])
             est = sharded.uniform_sharded(lambda i0, cnt, p: None, g.n, k, 0, 1, lambda a: parts[0] + parts[1] + parts[2])
             assert np.array_equal(est, uni), B
+    finally:
+        ctx.free_graph(h)
+
+
+@pytest.mark.parametrize("family", ["er3000", "ba20000"])
+def test_sharded_pairs_match_single_gpu(ctx, family):
+    from paper_1608_04472_gb300 import sharded
+    g = {"er3000": lambda: gg.erdos_renyi(3000, 8, 2),
+         "ba20000": lambda: gg.barabasi_albert(20000, 4, 3)}[family]()
+    targets = np.unique(np.concatenate([gg.uniform_targets(g.n, 6, 4),
+                                        np.argsort(-g.degrees(), kind="stable")[:3]])).astype(np.int32)
+    c, cap, seed, qid, scale = 1.0, 2500, 13, 9, 500.0
+    h = ctx.load_graph(g.row_ptr, g.col)
+    try:
+        ref = ctx.adaptive_pairs(h, targets, c, cap, seed, qid, scale)
+        assert np.any(ref["status"] == 0) and np.any(ref["status"] == 1)
+        for B in (64, 300):
+            got = sharded.adaptive_pairs_sharded(ctx, h, targets, c, cap, seed, qid, 0, 1, lambda a: [a], B,
+                                                 scale)
+            for key in ("k", "S", "status", "est"):
+                assert np.array_equal(got[key], ref[key]), (B, key)
+        # rank 0's view with three ranks: every rank's blocks computed here and
+        # handed out round by round, as the allgather would
+        ranks, B = 3, 200
+        rounds = (cap + ranks * B - 1) // (ranks * B)
+        blocks = {}
+        for r in range(ranks):
+            for rnd in range(rounds):
+                i0 = rnd * ranks * B + r * B
+                cnt = max(0, min(B, cap - i0))
+                blk = np.zeros((targets.size, B))
+                if cnt:
+                    blk[:, :cnt] = ctx.pair_values(h, targets, seed, qid, i0, cnt)
+                blocks[(r, rnd)] = blk
+        served = [0]
+
+        def allgather(a):
+            out = [blocks[(r, served[0])] for r in range(ranks)]
+            served[0] += 1
+            return out
+        res = sharded.adaptive_sharded(lambda i0, cnt: blocks[(0, i0 // (ranks * B))][:, :cnt], targets.size,
+                                       float(g.n) * float(g.n - 1), c * g.n, cap, 0, ranks, allgather, B, scale)
+        for key in ("k", "S", "status", "est"):
+            assert np.array_equal(res[key], ref[key]), key
+        # a block against the oracle's per-draw pair values
+        blk = ctx.pair_values(h, targets, seed, qid, 1000, 129)
+        want = oracle.pair_sequence_multi(g, targets, seed, qid, 1000, 129)
+        np.testing.assert_array_equal(blk, want)
+        # another target set on the same graph replaces the cached tables
+        other = targets[::-1].copy()
+        np.testing.assert_array_equal(ctx.pair_values(h, other, seed, qid, 1000, 129), want[::-1])
     finally:
         ctx.free_graph(h)

@@ -2,9 +2,10 @@
 the per-block values come from the oracle inside the test (what each rank's GPU
 computes with bc_target_dependencies / bc_uniform_partial), the exchange runs
 over gloo, and the combination goes through the library's host calls
-(bc_scan_block, bc_acc_add_rows, bc_acc_estimate). Bader's k, S, status and est
-and the uniform estimate must be identical at G = 1 and G = 2, for several
-block sizes, and equal to the oracle's own single-threaded runs."""
+(bc_scan_block, bc_acc_add_rows, bc_acc_estimate). Bader's and Algorithm 1's
+k, S, status and est and the uniform estimate must be identical at G = 1 and
+G = 2, for several block sizes, and equal to the oracle's own single-threaded
+runs."""
 import os
 import socket
 
@@ -19,6 +20,7 @@ N_ER, DEG, GSEED = 300, 6, 5
 TARGETS = [0, 7, 150, 299, 42, 123]
 C, CAP, SEED, QID = 1.5, 300, 21, 3
 K_UNI = 90
+PC, PCAP, PSCALE = 1.2, 400, 150.0
 
 
 def _free_port():
@@ -48,7 +50,10 @@ def _run(rank, world, allgather, allreduce_sum, B):
 
     res = sharded.adaptive_sharded(block_fn, t.size, float(g.n), C * g.n, CAP, rank, world, allgather, B)
     est = sharded.uniform_sharded(partial_fn, g.n, K_UNI, rank, world, allreduce_sum, B)
-    return res, est
+    pairs = sharded.adaptive_sharded(lambda i0, cnt: oracle.pair_sequence_multi(g, t, SEED, QID + 2, i0, cnt),
+                                     t.size, float(g.n) * float(g.n - 1), PC * g.n, PCAP, rank, world, allgather, B,
+                                     PSCALE)
+    return res, est, pairs
 
 
 def _worker(rank, world, port, q):
@@ -87,14 +92,18 @@ def test_two_ranks_match_one_rank_and_the_oracle():
     g = gg.erdos_renyi(N_ER, DEG, GSEED)
     ref = oracle.adaptive_sources(g, TARGETS, C, CAP, SEED, QID)
     ref_u = oracle.uniform_sources(g, K_UNI, SEED, QID + 1)
+    ref_p = oracle.adaptive_pairs(g, TARGETS, PC, PCAP, SEED, QID + 2, PSCALE)
     assert np.any(ref["status"] == oracle.STOPPED) and np.any(ref["status"] == oracle.CAPPED)
+    assert np.any(ref_p["status"] == oracle.STOPPED) and np.any(ref_p["status"] == oracle.CAPPED)
     for B in (16, 64, 1024):
-        one, est1 = _single(B)
+        one, est1, p1 = _single(B)
         for rank in range(world):
-            two, est2 = res[rank][B]
+            two, est2, p2 = res[rank][B]
             for key in ("k", "S", "status", "est"):
                 assert np.array_equal(two[key], one[key]), (B, rank, key)
                 assert np.array_equal(one[key], ref[key]), (B, key)
+                assert np.array_equal(p2[key], p1[key]), (B, rank, "pairs", key)
+                assert np.array_equal(p1[key], ref_p[key]), (B, "pairs", key)
             assert np.array_equal(est2, est1) and np.array_equal(est1, ref_u), B
 
 
