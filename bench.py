@@ -65,12 +65,14 @@ def reduce_over_ranks(dist, device, ms: float, samples: float, edges: float):
 
 
 def recorded_traffic():
-    """DRAM bytes per backward launch from the committed ncu summary, or None when
-    the kernel source has changed since the counters were taken."""
+    """DRAM bytes per algorithmic byte of the backward kernels, from the committed
+    ncu summary (a capture of every backward launch of a reduced-cap run on the
+    same graph, divided by that run's own algorithmic bytes), or None when the
+    kernel source has changed since the counters were taken."""
     import hashlib
     try:
         txt = open(os.path.join(ROOT, "profiles", "bwd_traffic_rmat_s20.md")).read()
-        val = float(txt.split("traffic_bytes_per_launch:")[1].split()[0])
+        val = float(txt.split("traffic_per_algorithmic_byte:")[1].split()[0])
         sha = txt.split("sha256/16 = ")[1].split()[0]
         cur = hashlib.sha256(open(os.path.join(ROOT, "paper_1608_04472_gb300", "csrc", "bc_batch.cu"),
                                   "rb").read()).hexdigest()[:16]
@@ -253,7 +255,9 @@ def measure_pairs(pkg, torch, local, stream, caps=(2048, 16384), T=256, n=2_000_
     target runs to the cap, so a run is `cap` pair draws plus one BFS per
     target. Timed at two caps, so that the marginal cost of a pair draw is
     separated from the targets' BFS, for the bidirectional pair search (the
-    default) and the one-sided BFS truncated at t's level (BCG_PAIR_ENGINE=1).
+    default: one pair per CTA), the same search one pair per warp with large
+    balls handed to the CTA form (BCG_PAIR_ENGINE=2) and the one-sided BFS
+    truncated at t's level (BCG_PAIR_ENGINE=1).
     Returns pair draws per second."""
     import graphgen as gg
     g = gg.barabasi_albert(n, 4, 3)
@@ -262,7 +266,7 @@ def measure_pairs(pkg, torch, local, stream, caps=(2048, 16384), T=256, n=2_000_
                        f"caps {caps[0]} and {caps[1]}"}
     prev = os.environ.get("BCG_PAIR_ENGINE")
     try:
-        for engine, name in (("0", "bidirectional"), ("1", "one_sided")):
+        for engine, name in (("0", "bidirectional"), ("2", "bidirectional_warp"), ("1", "one_sided")):
             os.environ["BCG_PAIR_ENGINE"] = engine  # read when the context is made
             ctx = pkg.Context(local, batch_width=64, stream=stream.cuda_stream)
             h = ctx.load_graph(g.row_ptr, g.col)
@@ -297,8 +301,9 @@ def measure_pairs(pkg, torch, local, stream, caps=(2048, 16384), T=256, n=2_000_
                          "profile_cap": caps[1],
                          "family_ms": {k: round(v["ms"], 2) for k, v in st["kernels"].items() if v["launches"]},
                          "family_launches": {k: v["launches"] for k, v in st["kernels"].items() if v["launches"]}}
-            if engine == "0":
+            if engine != "1":
                 out[name]["ball_vertices_per_pair"] = (rk - r1) / (caps[1] - 1)
+                out[name]["pairs_to_cta_search"] = st["pair_fallbacks"]
     finally:
         if prev is None:
             os.environ.pop("BCG_PAIR_ENGINE", None)
@@ -645,10 +650,15 @@ def main():
     dom_ms = kern[dom]["ms"]
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
     kern_names = {"bwd": "backward pass: k_bwd_light_fx + k_bwd_heavy_seg_fx + k_bwd_heavy_fin_fx per level",
-                  "fwd": "forward pass: k_fwd_light + k_fwd_heavy + k_fwd_heavy_fin per level"}
+                  "fwd": "forward pass: k_fwd_light + the heavy-vertex kernels + k_fwd_heavy_fin per level"}
+    ratio = recorded_traffic() if dom == "bwd" else None
+    alg_per_launch = alg_bytes / max(kern[dom]["launches"], 1)
     roofline = {"bound": "hbm", "kernel": kern_names[dom], "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": recorded_traffic() if dom == "bwd" else None, "peak_kind": peak_kind,
+                # ncu DRAM bytes per algorithmic byte (reduced-cap capture, same graph and
+                # kernels) times this run's algorithmic bytes per launch
+                "traffic": ratio * alg_per_launch if ratio is not None else None,
+                "traffic_per_algorithmic_byte": ratio, "peak_kind": peak_kind,
                 "launches": kern[dom]["launches"], "avg_launch_ms": dom_ms / max(kern[dom]["launches"], 1),
                 "alg_bytes_per_launch": alg_bytes / max(kern[dom]["launches"], 1),
                 "dag_edges_per_sample": stats["dag_edges"] / max(lanes_processed, 1),
@@ -679,7 +689,9 @@ def main():
     if rank == 0 and not args.no_plain:
         # plain (one source per launch sequence) vs batched on the same uniform query
         kq = 256
-        ctx.set_batch_width(1)
+        # the graph's tuning overrides the context's width: width 1 goes through it
+        tun = ctx.get_tuning(h)
+        ctx.set_tuning(h, dict(tun, batch_width=1))
         ctx.uniform_sources(h, 8, SEED, 7)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -689,7 +701,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms_plain = e0.elapsed_time(e1)
-        ctx.set_batch_width(64)
+        ctx.set_tuning(h, tun)
         e0.record(stream)
         est_b = ctx.uniform_sources(h, kq, SEED, 77)
         e1.record(stream)

@@ -496,7 +496,8 @@ typedef struct bc_stats {
   int64_t dag_edges;               /* (vertex, successor, lane) triples of the shortest-path DAGs */
   int64_t reached;                 /* (vertex, lane) pairs reached at distance >= 1 */
   int32_t n_kernels;               /* entries used in the arrays below */
-  int32_t reserved0;
+  int32_t pair_fallbacks;          /* pair lanes the one-pair-per-warp search (BCG_PAIR_ENGINE=2) gave up
+                                      on (a ball above half its table) and handed to one pair per CTA */
   char kernel_name[16][32];
   int64_t kernel_launches[16];
   double kernel_ms[16];            /* summed event time per kernel family (profiling on) */

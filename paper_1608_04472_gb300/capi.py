@@ -74,7 +74,7 @@ TUNING_FIELDS = tuple(name for name, _ in bc_tuning._fields_ if name not in ("re
 class bc_stats(ctypes.Structure):
     _fields_ = [("launches", _i64), ("samples", _i64), ("batches", _i64), ("dag_edges", _i64),
                 ("reached", _i64),
-                ("n_kernels", _i32), ("reserved0", _i32), ("kernel_name", (ctypes.c_char * 32) * 16),
+                ("n_kernels", _i32), ("pair_fallbacks", _i32), ("kernel_name", (ctypes.c_char * 32) * 16),
                 ("kernel_launches", _i64 * 16), ("kernel_ms", _f64 * 16)]
 
 
@@ -513,7 +513,8 @@ def bc_get_stats(ctx) -> dict:
         name = bytes(s.kernel_name[i]).split(b"\0", 1)[0].decode()
         kern[name] = dict(launches=int(s.kernel_launches[i]), ms=float(s.kernel_ms[i]))
     return dict(launches=int(s.launches), samples=int(s.samples), batches=int(s.batches),
-                dag_edges=int(s.dag_edges), reached=int(s.reached), kernels=kern)
+                dag_edges=int(s.dag_edges), reached=int(s.reached), pair_fallbacks=int(s.pair_fallbacks),
+                kernels=kern)
 
 
 def bc_reset_stats(ctx):

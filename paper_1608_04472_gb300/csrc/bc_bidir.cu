@@ -259,6 +259,305 @@ k_pair_bidir(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, co
   }
 }
 
+// ------------------------------------------------ one pair per warp ------
+// The same search with one pair per warp and each ball in a small open-
+// addressing hash table of the warp's own (2^lg slots per side) instead of
+// O(n) arrays: no CTA barriers (the warp's lanes step through the levels
+// together, __syncwarp between phases), and scratch proportional to the
+// balls, so many more pairs are in flight at once. A slot's key word holds the
+// vertex and its distance from the side's root, (v << 32) | d, so a vertex and
+// its distance are inserted by one compare-and-swap; the side's list holds the
+// slots in discovery order. Table words written by atomics are read through
+// L2 (__ldcg). A pair whose ball outgrows half of its table, or
+// whose probe finds no free slot, is abandoned (its slots cleared) and listed
+// for the CTA engine above. (Opt-in, BCG_PAIR_ENGINE=2: on BA n = 2M it
+// measured 312k marginal pair draws/s against 486k for one pair per CTA; a
+// warp's 32 lanes take a large level's edges in many more dependent rounds.)
+constexpr int WP_WARPS = 8;                 // warps (pairs) per CTA
+constexpr int WP_HEAVY = 8;                 // frontier vertices above this degree are scanned by the whole warp
+constexpr unsigned long long WP_EMPTY = ~0ull;
+
+__host__ __device__ inline size_t wp_side_bytes(int lg) { return (size_t)21 << lg; }  // 8 + 8 + 4 + 1 bytes per slot
+
+struct WSide {
+  unsigned long long *kd;  // (vertex << 32) | distance; WP_EMPTY when free
+  uint64_t *sg;            // path counts (meaningful where big is 0)
+  int32_t *q;              // slots in discovery order
+  uint8_t *big;            // 1: the count is 2^64 or more
+};
+
+__device__ inline WSide wside_of(unsigned char *base, int lg) {
+  const size_t H = (size_t)1 << lg;
+  WSide w;
+  w.kd = reinterpret_cast<unsigned long long *>(base);
+  w.sg = reinterpret_cast<uint64_t *>(base + 8 * H);
+  w.q = reinterpret_cast<int32_t *>(base + 16 * H);
+  w.big = base + 20 * H;
+  return w;
+}
+
+__device__ __forceinline__ uint32_t wp_hash(int32_t v, int lg) { return ((uint32_t)v * 2654435761u) >> (32 - lg); }
+
+// Slot of v (its distance in *d), or -1 when v is not in the table.
+__device__ __forceinline__ int wp_find(const unsigned long long *kd, int32_t v, int lg, int32_t *d) {
+  const uint32_t mask = (1u << lg) - 1u;
+  uint32_t h = wp_hash(v, lg);
+  for (uint32_t p = 0; p <= mask; ++p) {
+    const unsigned long long e = __ldcg(&kd[h]);
+    if (e == WP_EMPTY) return -1;
+    if ((int32_t)(e >> 32) == v) {
+      *d = (int32_t)(uint32_t)e;
+      return (int)h;
+    }
+    h = (h + 1u) & mask;
+  }
+  return -1;
+}
+
+// Slot of v, inserted with distance dnew if absent (*fresh), else found with
+// its distance in *d; -1 when every slot is taken.
+__device__ __forceinline__ int wp_insert(unsigned long long *kd, int32_t v, int32_t dnew, int lg, int32_t *d,
+                                         bool *fresh) {
+  const uint32_t mask = (1u << lg) - 1u;
+  const unsigned long long want = ((unsigned long long)(uint32_t)v << 32) | (uint32_t)dnew;
+  uint32_t h = wp_hash(v, lg);
+  for (uint32_t p = 0; p <= mask; ++p) {
+    unsigned long long e = __ldcg(&kd[h]);
+    if (e == WP_EMPTY) {
+      e = atomicCAS(&kd[h], WP_EMPTY, want);
+      if (e == WP_EMPTY) {
+        *d = dnew;
+        *fresh = true;
+        return (int)h;
+      }
+    }
+    if ((int32_t)(e >> 32) == v) {
+      *d = (int32_t)(uint32_t)e;
+      *fresh = false;
+      return (int)h;
+    }
+    h = (h + 1u) & mask;
+  }
+  return -1;
+}
+
+// Pair lanes [0, count), taken by warps from *next. Outputs as k_pair_bidir;
+// abandoned pairs are appended to fb_list (*nfb counts them) and their outputs
+// are left for the CTA engine. Tables start empty (keys WP_EMPTY, counts and
+// marks 0) and are left so.
+__global__ void __launch_bounds__(WP_WARPS * 32)
+k_pair_warp(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, const int32_t *__restrict__ src,
+            const int32_t *__restrict__ dst, int count, unsigned *__restrict__ next, unsigned char *__restrict__ tabs,
+            int lg, int32_t *__restrict__ pair_d, uint64_t *__restrict__ pair_sig, int32_t *__restrict__ pair_big,
+            unsigned *__restrict__ nbig, int32_t *__restrict__ fb_list, unsigned *__restrict__ nfb,
+            unsigned long long *__restrict__ visited) {
+  __shared__ int s_tail[WP_WARPS][2];
+  __shared__ int s_full[WP_WARPS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * WP_WARPS + wid;
+  unsigned char *base = tabs + (size_t)gw * 2 * wp_side_bytes(lg);
+  const WSide side0 = wside_of(base, lg), side1 = wside_of(base + wp_side_bytes(lg), lg);
+  const int limit = 1 << (lg - 1);  // abandon a pair once a ball holds half of its table
+  int *tail = s_tail[wid];
+  volatile int *wfull = &s_full[wid];  // the ball reached the limit, or a probe found no slot
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = (int)atomicAdd(next, 1u);
+    item = __shfl_sync(FULL, item, 0);
+    if (item >= count) break;
+    const int32_t s = src[item], t = dst[item];
+    if (lane == 0) {
+      int32_t dd;
+      bool fr;
+      const int a0 = wp_insert(side0.kd, s, 0, lg, &dd, &fr);
+      side0.sg[a0] = 1ull;
+      side0.q[0] = a0;
+      const int a1 = wp_insert(side1.kd, t, 0, lg, &dd, &fr);
+      side1.sg[a1] = 1ull;
+      side1.q[0] = a1;
+      tail[0] = tail[1] = 1;
+      *wfull = 0;
+    }
+    __syncwarp();
+    int fb0 = 0, fb1 = 0, lev0 = 0, lev1 = 0;
+    unsigned long long fe0 = (unsigned long long)(rp[s + 1] - rp[s]), fe1 = (unsigned long long)(rp[t + 1] - rp[t]);
+    bool met = (s == t), big = false, abandon = false;
+    int32_t dmeet = 0;
+    unsigned long long sum = (s == t) ? 1ull : 0ull;
+    while (!met) {
+      const int x = fe1 < fe0 ? 1 : 0;  // the side with the lighter frontier grows
+      const WSide X = x ? side1 : side0, Y = x ? side0 : side1;
+      const int a = x ? lev1 : lev0, fb = x ? fb1 : fb0;
+      const int fe = tail[x];
+      unsigned long long my_edges = 0ull;
+      // once the ball is at the limit the pair is abandoned: the remaining
+      // visits of the level are skipped (a nearly full table would make
+      // every further probe long)
+      auto visit = [&](int32_t w, uint64_t sv, bool bv) {
+        if (*wfull) return;
+        int32_t dw;
+        bool fresh;
+        const int sl = wp_insert(X.kd, w, a + 1, lg, &dw, &fresh);
+        if (sl < 0) {
+          *wfull = 1;
+          return;
+        }
+        if (fresh) {
+          const int p = atomicAdd(&tail[x], 1);
+          X.q[p] = sl;
+          if (p + 1 >= limit) *wfull = 1;
+          my_edges += (unsigned long long)(rp[w + 1] - rp[w]);
+        }
+        if (dw == a + 1) {  // v is in P(w)
+          const unsigned long long old = atomicAdd((unsigned long long *)&X.sg[sl], (unsigned long long)sv);
+          if (bv || old + sv < old) X.big[sl] = 1;
+        }
+      };
+      for (int cb = fb; cb < fe; cb += 32) {
+        if (__any_sync(FULL, *wfull != 0)) break;  // the same decision in every lane
+        const int k = cb + lane;
+        int32_t v = -1;
+        int beg = 0, end = 0;
+        uint64_t sv = 0ull;
+        bool bv = false;
+        if (k < fe) {
+          const int sl = X.q[k];
+          v = (int32_t)(__ldcg(&X.kd[sl]) >> 32);
+          beg = rp[v];
+          end = rp[v + 1];
+          sv = __ldcg(&X.sg[sl]);
+          bv = X.big[sl] != 0;
+        }
+        const bool heavy = v >= 0 && end - beg > WP_HEAVY;
+        if (v >= 0 && !heavy)
+          for (int j = beg; j < end && !*wfull; ++j) visit(col[j], sv, bv);
+        for (unsigned hb = __ballot_sync(FULL, heavy); hb; hb &= hb - 1u) {
+          const int kl = __ffs(hb) - 1;
+          const int hbeg = __shfl_sync(FULL, beg, kl), hend = __shfl_sync(FULL, end, kl);
+          const uint64_t hsv = __shfl_sync(FULL, sv, kl);
+          const bool hbv = __shfl_sync(FULL, (int)bv, kl) != 0;
+          for (int j = hbeg + lane; j < hend && !*wfull; j += 32) visit(col[j], hsv, hbv);
+        }
+      }
+      __syncwarp();
+      const int ne = tail[x];
+      if (*wfull) {  // read after the warp barrier: the same in every lane
+        abandon = true;
+        break;
+      }
+      for (int o = 16; o > 0; o >>= 1) my_edges += __shfl_xor_sync(FULL, my_edges, o);
+      if (ne == fe) break;  // side x's component is exhausted without meeting: t unreachable
+      // vertices of the new level inside the other ball: the balls meet there
+      bool found = false, lbig = false;
+      int32_t ldm = 0;
+      unsigned long long lsum = 0ull;
+      for (int k = fe + lane; k < ne; k += 32) {
+        const int sl = X.q[k];
+        const int32_t w = (int32_t)(__ldcg(&X.kd[sl]) >> 32);
+        int32_t dy;
+        const int sy = wp_find(Y.kd, w, lg, &dy);
+        if (sy >= 0) {
+          found = true;
+          ldm = a + 1 + dy;  // the same for every meeting vertex
+          if (X.big[sl] || Y.big[sy]) {
+            lbig = true;
+          } else {
+            const uint64_t sw = __ldcg(&X.sg[sl]), y = __ldcg(&Y.sg[sy]);
+            const uint64_t lo = sw * y;
+            if (__umul64hi(sw, y) != 0ull) {
+              lbig = true;
+            } else {
+              const unsigned long long o = lsum;
+              lsum += lo;
+              if (lsum < o) lbig = true;
+            }
+          }
+        }
+      }
+      const unsigned fmask = __ballot_sync(FULL, found);
+      if (fmask) {
+        met = true;
+        dmeet = __shfl_sync(FULL, ldm, __ffs(fmask) - 1);
+        big = __any_sync(FULL, lbig);
+        for (int o = 16; o > 0; o >>= 1) {
+          const unsigned long long y = __shfl_xor_sync(FULL, lsum, o);
+          const unsigned long long z = lsum + y;
+          if (z < lsum) big = true;
+          lsum = z;
+        }
+        big = __any_sync(FULL, big);
+        sum = lsum;
+      }
+      if (x) {
+        fb1 = fe;
+        lev1 = a + 1;
+        fe1 = my_edges;
+      } else {
+        fb0 = fe;
+        lev0 = a + 1;
+        fe0 = my_edges;
+      }
+      __syncwarp();
+    }
+    __syncwarp();
+    const int t0 = tail[0], t1 = tail[1];
+    if (lane == 0) {
+      if (abandon) {
+        fb_list[atomicAdd(nfb, 1u)] = item;
+      } else {
+        pair_d[item] = met ? dmeet : -1;
+        pair_sig[item] = (met && !big) ? (uint64_t)sum : 0ull;
+        pair_big[item] = (met && big) ? 1 : 0;
+        if (met && big) atomicAdd(nbig, 1u);
+        if (visited) atomicAdd(visited, (unsigned long long)(t0 + t1));
+      }
+    }
+    // leave the tables as found
+    for (int k = lane; k < t0; k += 32) {
+      const int sl = side0.q[k];
+      side0.kd[sl] = WP_EMPTY;
+      side0.sg[sl] = 0ull;
+      side0.big[sl] = 0;
+    }
+    for (int k = lane; k < t1; k += 32) {
+      const int sl = side1.q[k];
+      side1.kd[sl] = WP_EMPTY;
+      side1.sg[sl] = 0ull;
+      side1.big[sl] = 0;
+    }
+    __syncwarp();
+  }
+}
+
+// Fresh warp tables: per side, keys WP_EMPTY, counts and marks 0.
+__global__ void k_init_wtabs(unsigned long long *__restrict__ p, long long words, int lg) {
+  const long long side_words = (long long)(wp_side_bytes(lg) / 8), key_words = 1ll << lg;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < words; k += (long long)gridDim.x * blockDim.x)
+    p[k] = (k % side_words) < key_words ? WP_EMPTY : 0ull;
+}
+
+__global__ void k_scatter_fallback(int c, const int32_t *__restrict__ idx, const int32_t *__restrict__ pd_in,
+                                   const uint64_t *__restrict__ ps_in, const int32_t *__restrict__ pb_in,
+                                   int32_t *__restrict__ pd, uint64_t *__restrict__ ps, int32_t *__restrict__ pb) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < c) {
+    const int32_t i = idx[k];
+    pd[i] = pd_in[k];
+    ps[i] = ps_in[k];
+    pb[i] = pb_in[k];
+  }
+}
+
+__global__ void k_gather_fallback(int c, const int32_t *__restrict__ idx, const int32_t *__restrict__ src,
+                                  const int32_t *__restrict__ dst, int32_t *__restrict__ s_out,
+                                  int32_t *__restrict__ t_out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < c) {
+    s_out[k] = src[idx[k]];
+    t_out[k] = dst[idx[k]];
+  }
+}
+
 // Fresh scratch: in each CTA block of `per` ints the first `dints` (the two
 // distance arrays) are -1, the rest 0.
 __global__ void k_init_bscr(int32_t *__restrict__ p, long long total, long long per, long long dints) {
@@ -299,6 +598,10 @@ struct BidirState {
   DevBuf scratch, next, idx, src, dst, pd, psig, pexp, pxf;
   int32_t nmax = 0;
   int ncta = 0;
+  // one-pair-per-warp engine: tables, counters, abandoned pairs and their
+  // compact inputs and outputs for the CTA engine
+  DevBuf wtabs, wctr, wfb, fsrc, fdst, fpd, fps, fpb;
+  int wlg = 0, wctas = 0;
 };
 static std::map<bc_ctx *, BidirState> g_bidir;
 static std::mutex g_bidir_mu;
@@ -313,12 +616,13 @@ void forget_bidir_scratch(bc_ctx *ctx) {
   auto it = g_bidir.find(ctx);
   if (it == g_bidir.end()) return;
   BidirState &B = it->second;
-  for (DevBuf *b : {&B.scratch, &B.next, &B.idx, &B.src, &B.dst, &B.pd, &B.psig, &B.pexp, &B.pxf}) b->release();
+  for (DevBuf *b : {&B.scratch, &B.next, &B.idx, &B.src, &B.dst, &B.pd, &B.psig, &B.pexp, &B.pxf, &B.wtabs, &B.wctr,
+                    &B.wfb, &B.fsrc, &B.fdst, &B.fpd, &B.fps, &B.fpb})
+    b->release();
   g_bidir.erase(it);
 }
 
-// Resident CTAs of k_pair_bidir over all SMs, within a quarter of the free
-// device memory (at most 32 GB) of scratch.
+// Resident CTAs of k_pair_bidir over all SMs, within the scratch budget.
 static int bidir_ctas(int count, size_t per) {
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
@@ -327,21 +631,13 @@ static int bidir_ctas(int count, size_t per) {
     cudaGetLastError();
     occ = 1;
   }
-  size_t fr = 0, tot = 0;
-  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
-    cudaGetLastError();
-    fr = (size_t)32 << 30;
-  }
-  const size_t budget = std::min<size_t>(fr / 4, (size_t)32 << 30);
-  return std::max(1, std::min({count, sms * occ, (int)std::max<size_t>(1, budget / per)}));
+  return std::max(1, std::min({count, sms * occ, (int)std::max<size_t>(1, cta_scratch_budget() / per)}));
 }
 
-std::vector<int32_t> pair_lanes(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dst, int count,
-                                int32_t *pd, uint64_t *psig, int32_t *pexp, int32_t *pxf) {
-  std::vector<int32_t> bigs;
-  if (count < 1) return bigs;
-  if (g.directed) fail(BC_E_INVALID, "pair sampling needs an undirected graph");
-  BidirState &B = bidir_state(ctx);
+// The CTA engine over pair lanes [0, count); returns how many have
+// sigma_st >= 2^64 (flagged in pbig).
+static unsigned cta_pairs(bc_ctx *ctx, const Graph &g, BidirState &B, const int32_t *d_src, const int32_t *d_dst,
+                          int count, int32_t *pd, uint64_t *psig, int32_t *pbig) {
   cudaStream_t st = ctx->stream;
   const int32_t nmax = std::max(B.nmax, g.n);
   const size_t stride = bscr_stride(nmax);
@@ -363,19 +659,98 @@ std::vector<int32_t> pair_lanes(bc_ctx *ctx, const Graph &g, const int32_t *d_sr
   const int ncta = std::min(count, B.ncta);
   B.next.ensure(32);
   BCG_CUDA(cudaMemsetAsync(B.next.p, 0, 32, st));
-  BCG_CUDA(cudaMemsetAsync(pexp, 0, (size_t)count * 4, st));
   {
     LaunchScope ls(ctx, F_PAIR);
     k_pair_bidir<<<ncta, BT, 0, st>>>(g.rp, g.col, d_src, d_dst, count, B.next.as<unsigned>(),
-                                      B.scratch.as<unsigned char>(), stride, nmax, pd, psig, pxf,
+                                      B.scratch.as<unsigned char>(), stride, nmax, pd, psig, pbig,
                                       B.next.as<unsigned>() + 1, ctx->ws.cnt.as<unsigned long long>() + 1);
   }
   unsigned *h = static_cast<unsigned *>(ctx->ws.pinned);
   BCG_CUDA(cudaMemcpyAsync(h, B.next.as<unsigned>() + 1, 4, cudaMemcpyDeviceToHost, st));
   BCG_CUDA(cudaStreamSynchronize(st));
+  return h[0];
+}
+
+// The warp engine over pair lanes [0, count), the pairs it abandons by the
+// CTA engine; returns how many lanes have sigma_st >= 2^64.
+static unsigned warp_pairs(bc_ctx *ctx, const Graph &g, BidirState &B, const int32_t *d_src, const int32_t *d_dst,
+                           int count, int32_t *pd, uint64_t *psig, int32_t *pbig) {
+  cudaStream_t st = ctx->stream;
+  const int lg = ctx->pair_hash_lg;
+  const size_t per_warp = 2 * wp_side_bytes(lg);
+  if (B.wlg != lg || !B.wtabs.p) {
+    B.wtabs.release();
+    B.wlg = 0;
+    int dev = 0, sms = 0, occ = 0;
+    BCG_CUDA(cudaGetDevice(&dev));
+    BCG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_warp, WP_WARPS * 32, 0) != cudaSuccess || occ < 1) {
+      cudaGetLastError();
+      occ = 1;
+    }
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      cudaGetLastError();
+      fr = (size_t)16 << 30;
+    }
+    const size_t budget = std::min<size_t>(fr / 4, (size_t)16 << 30);
+    const int ctas = std::max(1, std::min(sms * occ, (int)(budget / (per_warp * WP_WARPS))));
+    B.wtabs.ensure(per_warp * WP_WARPS * (size_t)ctas);
+    {
+      LaunchScope ls(ctx, F_MISC);
+      k_init_wtabs<<<1024, 256, 0, st>>>(B.wtabs.as<unsigned long long>(), (long long)(B.wtabs.bytes / 8), lg);
+    }
+    B.wlg = lg;
+    B.wctas = ctas;
+  }
+  B.wctr.ensure(32);
+  B.wfb.ensure((size_t)count * 4);
+  BCG_CUDA(cudaMemsetAsync(B.wctr.p, 0, 32, st));
+  const int ncta = std::min(B.wctas, (count + WP_WARPS - 1) / WP_WARPS);
+  unsigned *ctr = B.wctr.as<unsigned>();  // [0] next lane, [1] lanes >= 2^64, [2] abandoned
+  {
+    LaunchScope ls(ctx, F_PAIR);
+    k_pair_warp<<<ncta, WP_WARPS * 32, 0, st>>>(g.rp, g.col, d_src, d_dst, count, ctr, B.wtabs.as<unsigned char>(),
+                                                lg, pd, psig, pbig, ctr + 1, B.wfb.as<int32_t>(), ctr + 2,
+                                                ctx->ws.cnt.as<unsigned long long>() + 1);
+  }
+  unsigned *h = static_cast<unsigned *>(ctx->ws.pinned);
+  BCG_CUDA(cudaMemcpyAsync(h, ctr + 1, 8, cudaMemcpyDeviceToHost, st));
+  BCG_CUDA(cudaStreamSynchronize(st));
+  unsigned nbig = h[0];
+  const int nfb = (int)h[1];
+  ctx->pair_fallbacks += nfb;
+  if (nfb > 0) {
+    for (DevBuf *b : {&B.fsrc, &B.fdst, &B.fpd, &B.fpb}) b->ensure((size_t)nfb * 4);
+    B.fps.ensure((size_t)nfb * 8);
+    const unsigned nb = (unsigned)((nfb + 255) / 256);
+    {
+      LaunchScope ls(ctx, F_PAIR);
+      k_gather_fallback<<<nb, 256, 0, st>>>(nfb, B.wfb.as<int32_t>(), d_src, d_dst, B.fsrc.as<int32_t>(),
+                                            B.fdst.as<int32_t>());
+    }
+    nbig += cta_pairs(ctx, g, B, B.fsrc.as<int32_t>(), B.fdst.as<int32_t>(), nfb, B.fpd.as<int32_t>(),
+                      B.fps.as<uint64_t>(), B.fpb.as<int32_t>());
+    LaunchScope ls(ctx, F_PAIR);
+    k_scatter_fallback<<<nb, 256, 0, st>>>(nfb, B.wfb.as<int32_t>(), B.fpd.as<int32_t>(), B.fps.as<uint64_t>(),
+                                           B.fpb.as<int32_t>(), pd, psig, pbig);
+  }
+  return nbig;
+}
+
+std::vector<int32_t> pair_lanes(bc_ctx *ctx, const Graph &g, const int32_t *d_src, const int32_t *d_dst, int count,
+                                int32_t *pd, uint64_t *psig, int32_t *pexp, int32_t *pxf) {
+  std::vector<int32_t> bigs;
+  if (count < 1) return bigs;
+  if (g.directed) fail(BC_E_INVALID, "pair sampling needs an undirected graph");
+  BidirState &B = bidir_state(ctx);
+  cudaStream_t st = ctx->stream;
+  BCG_CUDA(cudaMemsetAsync(pexp, 0, (size_t)count * 4, st));
+  const unsigned nbig = ctx->pair_engine == 2 ? warp_pairs(ctx, g, B, d_src, d_dst, count, pd, psig, pxf)
+                                              : cta_pairs(ctx, g, B, d_src, d_dst, count, pd, psig, pxf);
   ctx->samples += count;
   ctx->batches += 1;
-  if (h[0] == 0u) return bigs;
+  if (nbig == 0u) return bigs;
   // sigma_st >= 2^64 on a few lanes: the extended form from the one-sided
   // engines, 64 lanes at a time (ws.sources / ws.targets / ws.pair_* as scratch)
   std::vector<int32_t> flags((size_t)count);

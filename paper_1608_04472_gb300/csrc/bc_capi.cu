@@ -341,14 +341,123 @@ __global__ void k_validate(int32_t n, const int32_t *__restrict__ rp, const int3
 
 // Key of a vertex for grouping sampled sources: its distance from the graph's
 // highest-degree vertex (capped at 254), 255 when unreachable from it.
-__global__ void k_make_key(int32_t n, const int32_t *__restrict__ dist, uint8_t *__restrict__ key,
-                           int *__restrict__ maxd) {
+// Source keys (Sec. 3's per-sample step is the same for every source; only
+// which sources share a 64-lane batch changes the work): the distances of each
+// vertex to K landmarks, projected on their first principal component and
+// quantised to 8 bits, so that sources with similar BFS level structure sort
+// next to each other. Landmark 0 is the hub; landmark i+1 is the vertex reached
+// from the hub that is farthest from landmarks 0..i (smallest index on ties).
+
+// Row l of the landmark distances as bytes (254 caps a distance, 255: not
+// reached) and the running minimum over landmarks (-1: not reached from the
+// hub). The first row also gives the hub's eccentricity.
+__global__ void k_land_row(int32_t n, const int32_t *__restrict__ dist, uint8_t *__restrict__ row,
+                           int32_t *__restrict__ mind, int first, int *__restrict__ maxd) {
   const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < n) {
-    const int32_t d = dist[v];
-    key[v] = d < 0 ? 255 : (uint8_t)(d > 254 ? 254 : d);
+  if (v >= n) return;
+  const int32_t d = dist[v];
+  row[v] = d < 0 ? 255 : (uint8_t)(d > 254 ? 254 : d);
+  if (first) {
+    mind[v] = d;
     if (d > 0) atomicMax(maxd, d);
+  } else if (mind[v] >= 0 && d >= 0 && d < mind[v]) {
+    mind[v] = d;
   }
+}
+
+// (mind << 32) | ~v, maximised over the vertices: the farthest vertex, the
+// smallest index among equals.
+__global__ void k_land_far(int32_t n, const int32_t *__restrict__ mind, unsigned long long *__restrict__ best) {
+  const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long x = 0;
+  if (v < n && mind[v] >= 0) x = ((unsigned long long)mind[v] << 32) | (uint32_t)~(uint32_t)v;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = y > x ? y : x;
+  }
+  if ((threadIdx.x & 31) == 0 && x) atomicMax(best, x);
+}
+
+constexpr int KEY_LM_MAX = 16;
+constexpr int KEY_CHUNK = 2048;
+
+// Integer moments of the landmark distances over the vertices reached from the
+// hub: sums[0] = their count, sums[1+i] = sum of d_i, then sum of d_i d_j for
+// i <= j (row-major upper triangle). A block stages a chunk of the K rows in
+// shared memory and thread t owns moment t over the chunk.
+__global__ void __launch_bounds__(160) k_land_moments(int32_t n, int K, const uint8_t *__restrict__ rows,
+                                                      unsigned long long *__restrict__ sums) {
+  __shared__ uint8_t sh[KEY_LM_MAX][KEY_CHUNK];
+  const int64_t v0 = (int64_t)blockIdx.x * KEY_CHUNK;
+  const int64_t left = (int64_t)n - v0;
+  const int cnt = left < KEY_CHUNK ? (int)left : KEY_CHUNK;
+  for (int idx = threadIdx.x; idx < K * KEY_CHUNK; idx += blockDim.x) {
+    const int i = idx / KEY_CHUNK, c = idx % KEY_CHUNK;
+    sh[i][c] = c < cnt ? rows[(size_t)i * n + v0 + c] : (uint8_t)255;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  const int nmom = 1 + K + K * (K + 1) / 2;
+  if (t >= nmom) return;
+  int a = -1, b = -1;  // moment t: count (a = b = -1), sum d_a (b = -1), sum d_a d_b
+  if (t >= 1 && t <= K) {
+    a = t - 1;
+  } else if (t > K) {
+    int r = t - 1 - K;
+    a = 0;
+    while (r >= K - a) {
+      r -= K - a;
+      ++a;
+    }
+    b = a + r;
+  }
+  unsigned long long acc = 0;
+  for (int c = 0; c < cnt; ++c) {
+    if (sh[0][c] == 255) continue;
+    if (a < 0)
+      acc += 1;
+    else if (b < 0)
+      acc += sh[a][c];
+    else
+      acc += (unsigned)sh[a][c] * (unsigned)sh[b][c];
+  }
+  if (acc) atomicAdd(&sums[t], acc);
+}
+
+__device__ __forceinline__ int ordered_float(float f) {
+  const int b = __float_as_int(f);
+  return b >= 0 ? b : b ^ 0x7FFFFFFF;
+}
+
+// p(v) = sum_i w_i (d_i(v) - mu_i) for vertices reached from the hub, and the
+// range of p as order-preserving integers (range[0] min, range[1] max).
+__global__ void k_land_project(int32_t n, int K, const uint8_t *__restrict__ rows, const float *__restrict__ wmu,
+                               float *__restrict__ proj, int *__restrict__ range) {
+  const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  if (rows[v] == 255) return;
+  float p = 0.f;
+  for (int i = 0; i < K; ++i) p = fmaf(wmu[i], (float)rows[(size_t)i * n + v] - wmu[KEY_LM_MAX + i], p);
+  proj[v] = p;
+  const int o = ordered_float(p);
+  atomicMin(&range[0], o);
+  atomicMax(&range[1], o);
+}
+
+__global__ void k_land_key(int32_t n, const uint8_t *__restrict__ row0, const float *__restrict__ proj,
+                           const int *__restrict__ range, uint8_t *__restrict__ key) {
+  const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  if (row0[v] == 255) {
+    key[v] = 255;
+    return;
+  }
+  const int lo_o = range[0], hi_o = range[1];
+  const float lo = __int_as_float(lo_o >= 0 ? lo_o : lo_o ^ 0x7FFFFFFF);
+  const float hi = __int_as_float(hi_o >= 0 ? hi_o : hi_o ^ 0x7FFFFFFF);
+  int q = 0;
+  if (hi > lo) q = (int)((proj[v] - lo) / (hi - lo) * 255.f);
+  key[v] = (uint8_t)(q < 0 ? 0 : (q > 254 ? 254 : q));
 }
 
 // Counting sort of a window of W <= 1024 drawn sources by key (one block).
@@ -482,8 +591,9 @@ static void copy_scan_out(bc_ctx *ctx, int32_t T, const ScanState &st, double sc
 
 // ---------------------------------------------------------------- drivers ---
 
-// Per-graph source keys (distance from the hub) and, for exact BC, all
-// vertices ordered by key; computed on first use with one BFS from the hub.
+// Per-graph source keys (landmark projection, above) and, for exact BC, all
+// vertices ordered by key; computed on first use from K BFSs (K = 16, or
+// BCG_KEY_LANDMARKS; 1 gives the hub distance alone, rescaled).
 struct KeyMeta {
   DevBuf key, order;
   int32_t ecc = 0;  // largest finite distance from the hub
@@ -500,38 +610,135 @@ void forget_key_meta(const int32_t *rp) {
   g_keys.erase(it);
 }
 
+static int key_landmarks() {
+  int K = KEY_LM_MAX;
+  if (const char *e = std::getenv("BCG_KEY_LANDMARKS")) K = std::atoi(e);
+  return std::max(1, std::min(KEY_LM_MAX, K));
+}
+
+// The leading eigenvector of the K x K covariance of the landmark distances
+// (power iteration from the all-ones vector; a fixed number of steps, so the
+// key does not depend on anything but the graph).
+static std::vector<double> leading_component(int K, const std::vector<unsigned long long> &m) {
+  const double cnt = (double)m[0];
+  std::vector<double> mu(K), C((size_t)K * K);
+  for (int i = 0; i < K; ++i) mu[i] = (double)m[1 + i] / cnt;
+  int t = 1 + K;
+  for (int i = 0; i < K; ++i)
+    for (int j = i; j < K; ++j, ++t) C[(size_t)i * K + j] = C[(size_t)j * K + i] = (double)m[t] / cnt - mu[i] * mu[j];
+  std::vector<double> w(K, 1.0 / std::sqrt((double)K)), y(K);
+  for (int it = 0; it < 200; ++it) {
+    double nn = 0.0;
+    for (int i = 0; i < K; ++i) {
+      double a = 0.0;
+      for (int j = 0; j < K; ++j) a += C[(size_t)i * K + j] * w[j];
+      y[i] = a;
+      nn += a * a;
+    }
+    if (!(nn > 0.0)) break;
+    nn = std::sqrt(nn);
+    for (int i = 0; i < K; ++i) w[i] = y[i] / nn;
+  }
+  w.insert(w.end(), mu.begin(), mu.end());
+  return w;
+}
+
+static void build_key(bc_ctx *ctx, const Graph &g, KeyMeta &km) {
+  Workspace &ws = ctx->ws;
+  cudaStream_t st = ctx->stream;
+  const size_t n = (size_t)g.n;
+  const int K = key_landmarks();
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  const int64_t s0 = ctx->samples, b0 = ctx->batches;
+  DevBuf dist, mind, rows, proj, small;
+  auto release_all = [&] {
+    for (DevBuf *b : {&dist, &mind, &rows, &proj, &small}) b->release();
+  };
+  try {
+    dist.ensure(n * 4 + 8);
+    mind.ensure(n * 4);
+    rows.ensure(n * K);
+    // small: [0] landmark, [8] max distance, [16] farthest (u64), [32] range, [64] w|mu, [256] moments
+    small.ensure(256 + 8 * 160);
+    char *sm = small.as<char>();
+    int32_t *d_src = reinterpret_cast<int32_t *>(sm);
+    int *d_maxd = reinterpret_cast<int *>(sm + 8);
+    unsigned long long *d_far = reinterpret_cast<unsigned long long *>(sm + 16);
+    int *d_range = reinterpret_cast<int *>(sm + 32);
+    float *d_wmu = reinterpret_cast<float *>(sm + 64);  // w[16] | mu[16]
+    unsigned long long *d_mom = reinterpret_cast<unsigned long long *>(sm + 256);
+    BCG_CUDA(cudaMemsetAsync(sm, 0, small.bytes, st));
+    int32_t L = g.hub;
+    int Kused = 0;
+    for (int i = 0; i < K; ++i) {
+      BCG_CUDA(cudaMemcpyAsync(d_src, &L, 4, cudaMemcpyHostToDevice, st));
+      plain_distances(ctx, g, d_src, dist.as<int32_t>());  // any depth
+      {
+        LaunchScope ls(ctx, F_MISC);
+        k_land_row<<<nb, 256, 0, st>>>(g.n, dist.as<int32_t>(), rows.as<uint8_t>() + (size_t)i * n,
+                                       mind.as<int32_t>(), i == 0, d_maxd);
+      }
+      ++Kused;
+      if (i == 0) {
+        BCG_CUDA(cudaMemcpyAsync(ws.pinned, d_maxd, 4, cudaMemcpyDeviceToHost, st));
+        sync(ctx);
+        km.ecc = *static_cast<int32_t *>(ws.pinned);
+      }
+      // deep graphs run one source per persistent CTA, where batches do not
+      // share traversals: the hub distance alone
+      if (i + 1 == K || km.ecc > 64) break;
+      {
+        LaunchScope ls(ctx, F_MISC);
+        BCG_CUDA(cudaMemsetAsync(d_far, 0, 8, st));
+        k_land_far<<<nb, 256, 0, st>>>(g.n, mind.as<int32_t>(), d_far);
+        BCG_CUDA(cudaMemcpyAsync(ws.pinned, d_far, 8, cudaMemcpyDeviceToHost, st));
+      }
+      sync(ctx);
+      const unsigned long long far = *static_cast<unsigned long long *>(ws.pinned);
+      if ((far >> 32) == 0) break;  // every vertex reached from the hub is a landmark
+      L = (int32_t)~(uint32_t)(far & 0xFFFFFFFFull);
+    }
+    const int nmom = 1 + Kused + Kused * (Kused + 1) / 2;
+    {
+      LaunchScope ls(ctx, F_MISC);
+      k_land_moments<<<(unsigned)((n + KEY_CHUNK - 1) / KEY_CHUNK), 160, 0, st>>>(g.n, Kused, rows.as<uint8_t>(),
+                                                                                 d_mom);
+    }
+    std::vector<unsigned long long> mom(nmom);
+    BCG_CUDA(cudaMemcpyAsync(mom.data(), d_mom, (size_t)nmom * 8, cudaMemcpyDeviceToHost, st));
+    sync(ctx);
+    const std::vector<double> wmu = leading_component(Kused, mom);
+    float hw[2 * KEY_LM_MAX] = {};
+    for (int i = 0; i < Kused; ++i) {
+      hw[i] = (float)wmu[i];
+      hw[KEY_LM_MAX + i] = (float)wmu[Kused + i];
+    }
+    const int hr[2] = {0x7FFFFFFF, (int)0x80000000};
+    BCG_CUDA(cudaMemcpyAsync(d_wmu, hw, sizeof(hw), cudaMemcpyHostToDevice, st));
+    BCG_CUDA(cudaMemcpyAsync(d_range, hr, 8, cudaMemcpyHostToDevice, st));
+    proj.ensure(n * 4);
+    km.key.ensure(n);
+    {
+      LaunchScope ls(ctx, F_MISC);
+      k_land_project<<<nb, 256, 0, st>>>(g.n, Kused, rows.as<uint8_t>(), d_wmu, proj.as<float>(), d_range);
+      k_land_key<<<nb, 256, 0, st>>>(g.n, rows.as<uint8_t>(), proj.as<float>(), d_range, km.key.as<uint8_t>());
+    }
+    sync(ctx);
+  } catch (...) {
+    cudaStreamSynchronize(st);
+    release_all();
+    throw;
+  }
+  ctx->samples = s0;
+  ctx->batches = b0;
+  release_all();
+}
+
 static KeyMeta &key_meta(bc_ctx *ctx, const Graph &g, bool need_order) {
   std::lock_guard<std::mutex> lk(g_keys_mu);
   KeyMeta &km = g_keys[g.rp];
-  Workspace &ws = ctx->ws;
   const size_t n = (size_t)g.n;
-  if (!km.key.p) {
-    km.key.ensure(n);
-    const int32_t hub = g.hub;
-    const int64_t s0 = ctx->samples, b0 = ctx->batches;
-    DevBuf dist;
-    dist.ensure(n * 4 + 8);  // distances, the largest one, the hub (ws.sources may hold a batch)
-    try {
-      int32_t *d_hub = dist.as<int32_t>() + n + 1;
-      BCG_CUDA(cudaMemcpyAsync(d_hub, &hub, 4, cudaMemcpyHostToDevice, ctx->stream));
-      plain_distances(ctx, g, d_hub, dist.as<int32_t>());  // any depth
-      ctx->samples = s0;
-      ctx->batches = b0;
-      {
-        LaunchScope ls(ctx, F_MISC);
-        int *d_maxd = reinterpret_cast<int *>(dist.as<int32_t>() + n);
-        BCG_CUDA(cudaMemsetAsync(d_maxd, 0, 4, ctx->stream));
-        k_make_key<<<(g.n + 255) / 256, 256, 0, ctx->stream>>>(g.n, dist.as<int32_t>(), km.key.as<uint8_t>(), d_maxd);
-        BCG_CUDA(cudaMemcpyAsync(ws.pinned, d_maxd, 4, cudaMemcpyDeviceToHost, ctx->stream));
-      }
-      sync(ctx);
-      km.ecc = *static_cast<int32_t *>(ws.pinned);
-    } catch (...) {
-      dist.release();
-      throw;
-    }
-    dist.release();
-  }
+  if (!km.key.p) build_key(ctx, g, km);
   if (need_order && !km.order.p) {
     std::vector<uint8_t> key(n);
     BCG_CUDA(cudaMemcpy(key.data(), km.key.p, n, cudaMemcpyDeviceToHost));
@@ -819,7 +1026,7 @@ void target_bfs(bc_ctx *ctx, const Graph &g, const int32_t *d_targets, int T, in
 // decides the form of sigma_st exactly (R11).
 uint64_t pair_batch(bc_ctx *ctx, const Graph &g, int count) {
   Workspace &ws = ctx->ws;
-  if (ctx->pair_engine == 0) return pair_batch_bidir(ctx, g, count);
+  if (ctx->pair_engine != 1) return pair_batch_bidir(ctx, g, count);
   uint64_t ovf;
   if (batch_width(ctx) == 1) {
     ovf = plain_pair(ctx, g, ws.sources.as<int32_t>(), ws.targets.as<int32_t>()) ? 1ull : 0ull;
@@ -838,7 +1045,7 @@ static void pair_window(bc_ctx *ctx, const Graph &g, int W, int32_t *wsrc, int32
                         uint64_t *wpsig, int32_t *wpexp, int32_t *wpxf) {
   Workspace &ws = ctx->ws;
   cudaStream_t st = ctx->stream;
-  if (ctx->pair_engine == 0) {
+  if (ctx->pair_engine != 1) {
     pair_lanes(ctx, g, wsrc, wdst, W, wpd, wpsig, wpexp, wpxf);
     return;
   }
@@ -854,6 +1061,11 @@ static void pair_window(bc_ctx *ctx, const Graph &g, int W, int32_t *wsrc, int32
     k_mask_flags<<<1, 64, 0, st>>>(cnt, px, wpxf + b);
   }
 }
+
+// Pair draws per window of Algorithm 1's loop: up to 4096 (the one-pair-per-
+// warp search keeps that many pairs in flight at once) while the window's
+// T x W values stay small, else 1024.
+static int pair_window_max(int32_t T) { return T <= 4096 ? 4096 : WMAX; }
 
 // The tables of the targets of the last pair-value block (d(v_j, .) and
 // sigma_{v_j .}, [n][Tp]), kept for the next block of the same query (graph
@@ -885,6 +1097,7 @@ static void do_pair_block(bc_ctx *ctx, bc_graph gh, const Graph &g, const int32_
   cudaStream_t st = ctx->stream;
   const size_t n = (size_t)g.n;
   const int Tp = std::max(T, 1);
+  const int pwmax = pair_window_max(T);
   PairTables *Pp;
   {
     std::lock_guard<std::mutex> lk(g_ptab_mu);
@@ -911,13 +1124,13 @@ static void do_pair_block(bc_ctx *ctx, bc_graph gh, const Graph &g, const int32_
     P.valid = true;
   }
   Workspace &ws = ctx->ws;
-  ws.tdelta.ensure((size_t)Tp * WMAX * 8);
+  ws.tdelta.ensure((size_t)Tp * pwmax * 8);
   DevBuf wsrc, wdst, wpd, wpsig, wpexp, wpxf;
-  for (DevBuf *b : {&wsrc, &wdst, &wpd, &wpexp, &wpxf}) b->ensure(WMAX * 4);
-  wpsig.ensure(WMAX * 8);
-  std::vector<double> h((size_t)T * WMAX);
-  for (int64_t a = 0; a < count; a += WMAX) {
-    const int W = (int)std::min<int64_t>(WMAX, count - a);
+  for (DevBuf *b : {&wsrc, &wdst, &wpd, &wpexp, &wpxf}) b->ensure(pwmax * 4);
+  wpsig.ensure(pwmax * 8);
+  std::vector<double> h((size_t)T * pwmax);
+  for (int64_t a = 0; a < count; a += pwmax) {
+    const int W = (int)std::min<int64_t>(pwmax, count - a);
     {
       LaunchScope ls(ctx, F_DRAW);
       k_draw_pairs<<<(W + 63) / 64, 64, 0, st>>>(seed, qid, (uint64_t)(i0 + a), W, g.n, wsrc.as<int32_t>(),
@@ -948,6 +1161,7 @@ static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *target
   const size_t n = (size_t)g.n;
   cudaStream_t st = ctx->stream;
   const int Tp = std::max(T, 1);
+  const int pwmax = pair_window_max(T);
   // Per-target BFS (distance and sigma from every target), layout [n][Tp].
   DevBuf tdist, tsig, texp, dtx, wsrc, wdst, wpd, wpsig, wpexp, wpxf;
   tdist.ensure(n * Tp * 4);
@@ -963,19 +1177,19 @@ static void do_adaptive_pairs(bc_ctx *ctx, const Graph &g, const int32_t *target
       BCG_CUDA(cudaMemcpyAsync(dtx.p, tx.data(), (size_t)Tp * 4, cudaMemcpyHostToDevice, st));
       d_tx = dtx.as<int32_t>();
     }
-    ws.tdelta.ensure((size_t)Tp * WMAX * 8);
+    ws.tdelta.ensure((size_t)Tp * pwmax * 8);
     ScanState ss = make_scan(ctx, T);
     const double cn = c * (double)g.n;
     const int width = batch_width(ctx);
-    for (DevBuf *b : {&wsrc, &wdst, &wpd, &wpexp, &wpxf}) b->ensure(WMAX * 4);
-    wpsig.ensure(WMAX * 8);
+    for (DevBuf *b : {&wsrc, &wdst, &wpd, &wpexp, &wpxf}) b->ensure(pwmax * 4);
+    wpsig.ensure(pwmax * 8);
     int32_t remaining = T;
     // windows of draws as in Bader's loop (64 .. 1024, growing with the draws
     // made; one draw at a time with the plain width); the stop scan walks each
     // window in draw order
     for (int64_t i0 = 0; i0 < cap && remaining > 0;) {
       const int64_t want = width == 1 ? 1 : std::max<int64_t>(64, i0 / 2);
-      const int W = (int)std::min<int64_t>(std::min<int64_t>(WMAX, want), cap - i0);
+      const int W = (int)std::min<int64_t>(std::min<int64_t>(pwmax, want), cap - i0);
       {
         LaunchScope ls(ctx, F_DRAW);
         k_draw_pairs<<<(W + 63) / 64, 64, 0, st>>>(seed, qid, (uint64_t)i0, W, g.n, wsrc.as<int32_t>(),
@@ -1386,7 +1600,11 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
     if (const char *hl = std::getenv("BCG_HEAVY_LANE")) ctx->heavy_lane = std::atoi(hl);
     if (const char *pd = std::getenv("BCG_PUSH_DIV")) ctx->push_div = std::atoi(pd);
     if (const char *mc = std::getenv("BCG_MULTI_CAP")) ctx->multi_cap = std::atoi(mc);
-    if (const char *pe = std::getenv("BCG_PAIR_ENGINE")) ctx->pair_engine = std::atoi(pe) == 1 ? 1 : 0;
+    if (const char *pe = std::getenv("BCG_PAIR_ENGINE")) {
+      const int e = std::atoi(pe);
+      ctx->pair_engine = (e == 1 || e == 2) ? e : 0;
+    }
+    if (const char *ph = std::getenv("BCG_PAIR_HASH")) ctx->pair_hash_lg = std::max(6, std::min(24, std::atoi(ph)));
     if (const char *ws = std::getenv("BCG_W_STEP")) ctx->w_step = std::atoll(ws);
     BCG_CUDA(cudaMallocHost(&ctx->ws.pinned, 4096));
     ctx->ws.enable.ensure(64);   // [0] lane enable mask, [1] pair continuation word
@@ -1872,6 +2090,7 @@ bc_status bc_get_stats(bc_ctx *ctx, bc_stats *out) {
     out->reached = (int64_t)c2[1];
   }
   out->n_kernels = F_NFAM;
+  out->pair_fallbacks = (int32_t)std::min<int64_t>(ctx->pair_fallbacks, INT32_MAX);
   for (int f = 0; f < F_NFAM; ++f) {
     std::strncpy(out->kernel_name[f], kFamilyName[f], 31);
     out->kernel_launches[f] = ctx->fam_launches[f];
@@ -1884,6 +2103,7 @@ bc_status bc_reset_stats(bc_ctx *ctx) {
   BC_GUARD_BEGIN
   sync(ctx);
   ctx->launches = ctx->samples = ctx->batches = 0;
+  ctx->pair_fallbacks = 0;
   BCG_CUDA(cudaMemset(ctx->ws.cnt.p, 0, 16));
   for (int f = 0; f < F_NFAM; ++f) {
     ctx->fam_launches[f] = 0;

@@ -205,7 +205,12 @@ __device__ __forceinline__ Acc acc2_widen(const Acc2 &a) {
 // Counts below 2^53 (every count of the narrow backward path) go through the
 // integer-only forms of bc_rn.h, which round exactly as the FP64 instructions
 // do but keep the slow FP64 pipe free; larger counts use the FP64 instructions.
-constexpr uint64_t EXACT53 = 1ull << 53;
+// BCG_RN_INT=0 at compile time takes the FP64 instructions throughout (the
+// same results; for measuring what the integer forms save).
+#ifndef BCG_RN_INT
+#define BCG_RN_INT 1
+#endif
+constexpr uint64_t EXACT53 = BCG_RN_INT ? (1ull << 53) : 0ull;
 
 __device__ __forceinline__ double sigma_to_double(uint64_t s) {
   if (s == 0ull) return 0.0;
@@ -219,12 +224,28 @@ __device__ __forceinline__ double delta_rn(uint64_t sigma, double sum) {
 
 // RN(RN(1 + delta) / RN(sigma)), delta >= 0 normal or zero, sigma >= 1.
 __device__ __forceinline__ double coef_of(double delta, uint64_t sigma) {
-  const double x = bcrn::rn_one_plus(delta);
+  const double x = BCG_RN_INT ? bcrn::rn_one_plus(delta) : __dadd_rn(1.0, delta);
   if ((sigma & (sigma - 1ull)) == 0ull) {  // power of two: exact scaling
     const int k = 63 - __clzll((long long)sigma);
     return __longlong_as_double((long long)((uint64_t)__double_as_longlong(x) - ((uint64_t)k << 52)));
   }
   return sigma < EXACT53 ? bcrn::rn_div_u53(x, sigma) : __ddiv_rn(x, sigma_to_double(sigma));
+}
+
+// The same two values by the FP64 instructions. The one-source-per-CTA
+// engines (lane-major, weighted) take these: they issue few FP64 operations
+// per memory access, and there the integer forms measured 4.5 % slower.
+__device__ __forceinline__ double delta_rn_fp(uint64_t sigma, double sum) {
+  return __dmul_rn(__ull2double_rn(sigma), sum);
+}
+
+__device__ __forceinline__ double coef_of_fp(double delta, uint64_t sigma) {
+  const double x = __dadd_rn(1.0, delta);
+  if ((sigma & (sigma - 1ull)) == 0ull) {  // power of two: exact scaling
+    const int k = 63 - __clzll((long long)sigma);
+    return __longlong_as_double((long long)((uint64_t)__double_as_longlong(x) - ((uint64_t)k << 52)));
+  }
+  return __ddiv_rn(x, __ull2double_rn(sigma));
 }
 
 }  // namespace bcg

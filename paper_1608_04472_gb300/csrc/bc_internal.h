@@ -5,6 +5,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <string>
@@ -194,15 +195,38 @@ struct bc_ctx {
   // multi-graph split: hub eccentricity above which a graph goes to the
   // persistent kernel, and its CTAs per SM while the batched engine runs beside
   int32_t deep_levels = 32, multi_cap = 4;
-  // pair lanes of Algorithm 1: 0 = bidirectional search (bc_bidir.cu), 1 = the
-  // one-sided BFS from s truncated at t's level (kept for comparison)
+  // pair lanes of Algorithm 1: 0 = bidirectional search, one pair per CTA
+  // (bc_bidir.cu); 2 = the same search one pair per warp with hash-table
+  // balls, pairs with large balls handed to one pair per CTA (measured slower,
+  // kept for comparison); 1 = the one-sided BFS from s truncated at t's level
+  // (kept for comparison)
   int32_t pair_engine = 0;
+  // log2 of the slots of each side's table in the one-pair-per-warp search
+  int32_t pair_hash_lg = 14;
+  int64_t pair_fallbacks = 0;  // pairs that search handed to the CTA form
   // weighted graphs: near-far threshold increment for graphs loaded later
   // (0 = a sixth of the graph's mean edge length)
   long long w_step = 0;
 };
 
 namespace bcg {
+
+// Device memory for the per-CTA scratch of the one-source-per-CTA engines
+// (lane-major, weighted, one pair per CTA): a quarter of the free memory, at
+// most 32 GB; with BCG_SCRATCH_GB set, half of the free memory, at most that.
+inline size_t cta_scratch_budget() {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    fr = (size_t)32 << 30;
+  }
+  if (const char *e = std::getenv("BCG_SCRATCH_GB")) {
+    const long long gb = std::atoll(e);
+    if (gb > 0) return std::min<size_t>(fr / 2, (size_t)gb << 30);
+  }
+  return std::min<size_t>(fr / 4, (size_t)32 << 30);
+}
+
 
 // Launch accounting: call before and after each kernel launch.
 struct LaunchScope {

@@ -265,8 +265,8 @@ __device__ void multi_source(const MGraph &G, int32_t s, const MScratch &S, unsi
         }
         if (coop) a = acc_warp_sum(a);
         const uint64_t sg = S.sig[v];
-        delta = delta_rn(sg, acc_round(a));
-        if (!coop || lane == 0) S.coef[v] = coef_of(delta, sg);
+        delta = delta_rn_fp(sg, acc_round(a));
+        if (!coop || lane == 0) S.coef[v] = coef_of_fp(delta, sg);
       }
       if (!coop || lane == 0) deliver(v, delta);
     });
@@ -580,19 +580,8 @@ static void build_plan(bc_ctx *ctx, MultiPlan &P, const std::vector<const Graph 
   cuda_check(ie, "cudaGraphInstantiate");
 }
 
-// Lane-major scratch budget: a quarter of the free device memory, at most 32 GB
-// (on the 8.4 M-vertex grid a CTA needs ~300 MB; 64 lanes then run at once).
-static size_t lane_budget() {
-  size_t fr = 0, tot = 0;
-  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
-    cudaGetLastError();
-    fr = (size_t)32 << 30;
-  }
-  return std::min<size_t>(fr / 4, (size_t)32 << 30);
-}
-
 static int lane_ctas(int count, size_t per) {
-  return std::max(1, std::min({count, multi_ctas(0), (int)std::max<size_t>(1, lane_budget() / per)}));
+  return std::max(1, std::min({count, multi_ctas(0), (int)std::max<size_t>(1, cta_scratch_budget() / per)}));
 }
 
 // Per-context scratch of the lane-major path (grown on demand).

@@ -381,8 +381,8 @@ __device__ void w_source(const WGraph &G, int32_t s, const WScr &S, WShared &sh,
         }
         if (coop) a = acc_warp_sum(a);
         const uint64_t sg = S.sig[v];
-        delta = delta_rn(sg, acc_round(a));
-        if (!coop || lane == 0) S.coef[v] = coef_of(delta, sg);
+        delta = delta_rn_fp(sg, acc_round(a));
+        if (!coop || lane == 0) S.coef[v] = coef_of_fp(delta, sg);
       }
       if (!coop || lane == 0) deliver(v, delta);
     });
@@ -509,13 +509,7 @@ static int w_ctas_max(size_t per) {
     cudaGetLastError();
     occ = 1;
   }
-  size_t fr = 0, tot = 0;
-  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
-    cudaGetLastError();
-    fr = (size_t)32 << 30;
-  }
-  const size_t budget = std::min<size_t>(fr / 4, (size_t)32 << 30);
-  return std::max(1, std::min(sms * occ, (int)std::max<size_t>(1, budget / per)));
+  return std::max(1, std::min(sms * occ, (int)std::max<size_t>(1, cta_scratch_budget() / per)));
 }
 
 // Scratch for every resident CTA (partials included), laid out for nmax.

@@ -6,8 +6,10 @@ whose hubs are expanded by whole CTAs; a sparse graph
 with many unreachable pairs and isolated vertices; tiny graphs (adjacent
 pairs); a 90x90 grid where many sigma_st exceed 2^64 (extended form) and others
 lie below 2^64 while counts elsewhere at the same depth do not (R11 for pairs).
-The one-sided engine (BCG_PAIR_ENGINE=1), the plain width and the served query
-must agree too."""
+The one-sided engine (BCG_PAIR_ENGINE=1), the one-pair-per-warp search
+(BCG_PAIR_ENGINE=2), the plain width and the served query must agree too, and
+so must the one-pair-per-warp search when small tables (BCG_PAIR_HASH) make it
+hand most pairs, or some of them, to the CTA search."""
 import numpy as np
 import pytest
 
@@ -42,7 +44,7 @@ def _same(got, ref, what):
         assert np.array_equal(got[key], ref[key]), (what, key, got[key][:8], ref[key][:8])
 
 
-@pytest.mark.parametrize("engine", ["0", "1"])
+@pytest.mark.parametrize("engine", ["0", "1", "2"])
 def test_small_world_windows(pkg, monkeypatch, engine):
     monkeypatch.setenv("BCG_PAIR_ENGINE", engine)
     g = gg.barabasi_albert(20000, 4, 41)
@@ -54,9 +56,12 @@ def test_small_world_windows(pkg, monkeypatch, engine):
     assert np.all(ref["k"] == 3000)  # every target ran through windows of up to 1024 draws
 
 
-def test_hub_vertices_expanded_by_the_whole_cta(pkg):
+@pytest.mark.parametrize("engine", ["0", "2"])
+def test_hub_vertices_expanded_by_the_whole_cta(pkg, monkeypatch, engine):
     # R-MAT s13 has 27 vertices of degree above 512 (up to 2,204): frontiers
-    # holding them are expanded by all threads of the CTA
+    # holding them are expanded by all threads of the CTA (engine 0) or by the
+    # whole warp (engine 2)
+    monkeypatch.setenv("BCG_PAIR_ENGINE", engine)
     g = gg.rmat(13, 16, 0.57, 0.19, 0.19, 46)
     assert int(np.diff(g.row_ptr).max()) > 2000
     targets = gg.degree_targets(g, 12, 47)
@@ -103,7 +108,7 @@ def test_tiny_graphs(pkg, make):
     _same(got, ref, "tiny")
 
 
-@pytest.mark.parametrize("engine,width", [("0", 64), ("1", 64), ("0", 1)])
+@pytest.mark.parametrize("engine,width", [("0", 64), ("1", 64), ("2", 64), ("0", 1)])
 def test_grid_with_counts_beyond_2_to_64(pkg, monkeypatch, engine, width):
     # about 3 in 10 draws have sigma_st >= 2^64 (extended form); about 1 in 10
     # have sigma_st < 2^64 while other counts at depth <= d(s,t) from s exceed
@@ -116,3 +121,21 @@ def test_grid_with_counts_beyond_2_to_64(pkg, monkeypatch, engine, width):
     got, _ = _run(pkg, g, targets, 1.0, cap, 5, 9, width=width)
     _same(got, ref, f"engine {engine} width {width}")
     assert np.sum(ref["S"] > 0) >= 5
+
+
+@pytest.mark.parametrize("lg", ["6", "9"])
+def test_warp_search_hands_large_balls_to_the_cta_search(pkg, monkeypatch, lg):
+    # 2^6 slots per side: nearly every pair outgrows its table (32 vertices);
+    # 2^9: some do. Either way the results are the oracle's.
+    monkeypatch.setenv("BCG_PAIR_ENGINE", "2")
+    monkeypatch.setenv("BCG_PAIR_HASH", lg)
+    g = gg.barabasi_albert(20000, 4, 41)
+    targets = gg.degree_targets(g, 16, 42)
+    ref = oracle.adaptive_pairs(g, targets, 1.0, 2000, 4, 9)
+    with pkg.Context(0, batch_width=64) as ctx:
+        h = ctx.load_graph(g.row_ptr, g.col)
+        ctx.reset_stats()
+        got = ctx.adaptive_pairs(h, targets, 1.0, 2000, 4, 9)
+        fb = ctx.stats()["pair_fallbacks"]
+    _same(got, ref, f"hash 2^{lg}")
+    assert fb > (1000 if lg == "6" else 0), fb
