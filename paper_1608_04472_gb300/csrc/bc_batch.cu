@@ -21,6 +21,7 @@
 // Vertices of degree > HEAVY are split into SEG-long neighbour segments, each
 // handled by one warp; partial results are combined exactly afterwards.
 #include <algorithm>
+#include <cstdlib>
 
 #include "bc_internal.h"
 
@@ -1091,25 +1092,26 @@ k_bwd_light(int32_t n, const int32_t *__restrict__ list_l, const unsigned *__res
             const int32_t *__restrict__ rp,
             const int32_t *__restrict__ col, const uint64_t *__restrict__ lm_cur, const uint64_t *__restrict__ lm_next,
             uint64_t *__restrict__ sigma, Sink sink, unsigned *__restrict__ err, unsigned *__restrict__ wq,
-            int heavy_deg, uint64_t keep) {
+            int heavy_deg, uint64_t keep, int gsz) {
   __shared__ Ring rings[FWD_THREADS / 32];
   Ring &R = rings[threadIdx.x >> 5];
   unsigned head = 0u, tail = 0u;
   unsigned e = 0u;
   // a small level walks its vertex list; a large one scans the vertex ids in
-  // order (adjacent rows, sequential CSR reads). A warp takes 32 vertices at a
-  // time, loads their masks and row bounds at once (one per thread) and walks
-  // only the light ones with lanes at this level.
+  // order (adjacent rows, sequential CSR reads). A warp takes gsz <= 32
+  // vertices at a time, loads their masks and row bounds at once (one per
+  // thread) and walks only the light ones with lanes at this level (smaller
+  // takes on small graphs spread a level over more warps).
   const int nv = vcnt_l ? (int)*vcnt_l : n;
   const bool by_list = vcnt_l && (int64_t)nv * 16 <= (int64_t)n;
   const int total = by_list ? nv : n;
   const int lane_id = threadIdx.x & 31;
-  for (int base = grab(wq, 32); base < total; base = grab(wq, 32)) {
+  for (int base = grab(wq, gsz); base < total; base = grab(wq, gsz)) {
     const int ii = base + lane_id;
     int32_t hv = 0;
     uint64_t hl = 0ull;
     int hb = 0, he = 0;
-    if (ii < total) {
+    if (lane_id < gsz && ii < total) {
       hv = by_list ? list_l[ii] : ii;
       hl = lm_cur[hv] & keep;
       if (hl) {
@@ -1282,7 +1284,7 @@ k_bwd_light_fx(int32_t n, const int32_t *__restrict__ list_l, const unsigned *__
                const int32_t *__restrict__ rp,
                const int32_t *__restrict__ col, const uint64_t *__restrict__ lm_cur,
                const uint64_t *__restrict__ lm_next, uint64_t *__restrict__ sigma, Sink sink,
-               unsigned *__restrict__ err, unsigned *__restrict__ wq, int heavy_deg, uint64_t keep) {
+               unsigned *__restrict__ err, unsigned *__restrict__ wq, int heavy_deg, uint64_t keep, int gsz) {
   __shared__ Ring rings[FWD_THREADS / 32];
   __shared__ int32_t lists[FWD_THREADS / 32][32];
   __shared__ int8_t tabs[FWD_THREADS / 32][64];
@@ -1292,19 +1294,20 @@ k_bwd_light_fx(int32_t n, const int32_t *__restrict__ list_l, const unsigned *__
   unsigned head = 0u, tail = 0u;
   unsigned e = 0u;
   // a small level walks its vertex list; a large one scans the vertex ids in
-  // order (adjacent rows, sequential CSR reads). A warp takes 32 vertices at a
-  // time, loads their masks and row bounds at once (one per thread) and walks
-  // only the light ones with lanes at this level.
+  // order (adjacent rows, sequential CSR reads). A warp takes gsz <= 32
+  // vertices at a time, loads their masks and row bounds at once (one per
+  // thread) and walks only the light ones with lanes at this level (smaller
+  // takes on small graphs spread a level over more warps).
   const int nv = vcnt_l ? (int)*vcnt_l : n;
   const bool by_list = vcnt_l && (int64_t)nv * 16 <= (int64_t)n;
   const int total = by_list ? nv : n;
   const int lane_id = threadIdx.x & 31;
-  for (int base = grab(wq, 32); base < total; base = grab(wq, 32)) {
+  for (int base = grab(wq, gsz); base < total; base = grab(wq, gsz)) {
     const int ii = base + lane_id;
     int32_t hv = 0;
     uint64_t hl = 0ull;
     int hb = 0, he = 0;
-    if (ii < total) {
+    if (lane_id < gsz && ii < total) {
       hv = by_list ? list_l[ii] : ii;
       hl = lm_cur[hv] & keep;
       if (hl) {
@@ -1929,6 +1932,21 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
   }
 }
 
+// Vertices a warp of the light backward kernels takes at a time: 32 on large
+// graphs (measured best on R-MAT s20), fewer on small ones, where a level's
+// vertices would otherwise sit with too few warps (ER n = 100k, 256 samples:
+// backward 3.86 ms taking 32, 2.41 ms taking 16, 2.22 ms taking 8, 2.33 ms
+// taking 4). BCG_BWD_GRAB overrides.
+static int bwd_grab(int32_t n) {
+  static const int env = [] {
+    const char *e = std::getenv("BCG_BWD_GRAB");
+    const int v = e ? std::atoi(e) : 0;
+    return (v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32) ? v : 0;
+  }();
+  if (env) return env;
+  return n >= (1 << 19) ? 32 : (n >= (1 << 17) ? 16 : 8);
+}
+
 // Whether a heavy vertex has lanes at level l in the last forward pass.
 static inline bool heavy_at(const Workspace &ws, int l) { return l >= (int)ws.hlev.size() || ws.hlev[l]; }
 
@@ -1953,7 +1971,8 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
         k_bwd_light_fx<<<blocks, FWD_THREADS, 0, st>>>(g.n, lvl_list(l), lvl_cnt(l), g.rp, g.col,
                                                       lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
                                                       ws.sigma.as<uint64_t>(), sink, ws.err.as<unsigned>(),
-                                                      ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg, keep);
+                                                      ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg, keep,
+                                                      bwd_grab(g.n));
       }
       if (hm.nseg && heavy_at(ws, l)) {
         {
@@ -1980,12 +1999,12 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
         k_bwd_light<NarrowAcc><<<blocks, FWD_THREADS, 0, st>>>(
             g.n, lvl_list(l), lvl_cnt(l), g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
             ws.sigma.as<uint64_t>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg,
-            keep);
+            keep, bwd_grab(g.n));
       else
         k_bwd_light<WideAcc><<<blocks, FWD_THREADS, 0, st>>>(
             g.n, lvl_list(l), lvl_cnt(l), g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
             ws.sigma.as<uint64_t>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg,
-            keep);
+            keep, bwd_grab(g.n));
     }
     if (hm.nseg && heavy_at(ws, l)) {
       LaunchScope ls(ctx, F_BWD);
