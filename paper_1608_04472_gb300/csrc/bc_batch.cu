@@ -355,7 +355,7 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
             uint64_t *__restrict__ active_cur, unsigned *__restrict__ err,
             unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq, int heavy_deg, int pk_maxl,
             int pk_mincnt, int32_t *__restrict__ list_next, unsigned *__restrict__ vcnt_next,
-            unsigned long long *__restrict__ vedges_next) {
+            unsigned long long *__restrict__ vedges_next, int gsz) {
   __shared__ int32_t lists[FWD_THREADS / 32][32];
   __shared__ int8_t tabs[FWD_THREADS / 32][64];
   const int lane = threadIdx.x & 31;
@@ -363,14 +363,14 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
   uint64_t any_new = 0ull, smax = 0ull;
   unsigned long long tri = 0ull, rch = 0ull;
   uint64_t ovf = 0ull;  // lanes whose counts exceeded 2^64-1 here
-  // a warp takes 32 vertices; each thread loads one vertex's header, and only
-  // vertices with unvisited active lanes and light degree are walked
-  for (int base = grab(wq, 32); base < n; base = grab(wq, 32)) {
+  // a warp takes gsz <= 32 vertices; each thread loads one vertex's header,
+  // and only vertices with unvisited active lanes and light degree are walked
+  for (int base = grab(wq, gsz); base < n; base = grab(wq, gsz)) {
     const int vl = base + lane;
     int hb = 0, he = 0;
     uint64_t hv = 0ull;
     bool work = false;
-    if (vl < n) {
+    if (lane < gsz && vl < n) {
       hb = rp[vl];
       he = rp[vl + 1];
       hv = visited[vl];
@@ -1695,6 +1695,30 @@ static int grid_blocks() {
   return g_num_sms * 8;
 }
 
+// Vertices a warp of the light kernels takes at a time. Fewer than 32 spread a
+// level's vertices over more warps, which matters most on small graphs (ER
+// n = 100k, 256 samples: backward 3.86 / 2.41 / 2.22 / 2.33 ms taking 32 / 16
+// / 8 / 4, forward 1.72 / 1.38 / 1.31 / 1.41 ms) and still pays on R-MAT s20
+// (17,437 vs 17,074 samples/s taking 16 instead of 32).
+// BCG_BWD_GRAB / BCG_FWD_GRAB override.
+static int env_grab(const char *name) {
+  const char *e = std::getenv(name);
+  const int v = e ? std::atoi(e) : 0;
+  return (v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32) ? v : 0;
+}
+
+static int light_grab(int32_t n) { return n >= (1 << 17) ? 16 : 8; }
+
+static int bwd_grab(int32_t n) {
+  static const int env = env_grab("BCG_BWD_GRAB");
+  return env ? env : light_grab(n);
+}
+
+static int fwd_grab(int32_t n) {
+  static const int env = env_grab("BCG_FWD_GRAB");
+  return env ? env : light_grab(n);
+}
+
 void batch_ensure(bc_ctx *ctx, const Graph &g) {
   Workspace &ws = ctx->ws;
   const size_t n = (size_t)g.n;
@@ -1841,7 +1865,7 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
                                                  ws.enable.as<uint64_t>(), act + l + 1, ws.err.as<unsigned>(),
                                                  ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 0,
                                                  hm.heavy_deg, ctx->pk_maxl, ctx->pk_mincnt,
-                                                 lst(l + 1), vcnt + l + 1, vedges + l + 1);
+                                                 lst(l + 1), vcnt + l + 1, vedges + l + 1, fwd_grab(g.n));
     }
     const bool heavy_now = !push && hm.nseg && !heavy_done;
     if (heavy_now && (ctx->heavy_lane == 3 || ctx->heavy_lane == 4)) {
@@ -1932,21 +1956,6 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
   }
 }
 
-// Vertices a warp of the light backward kernels takes at a time: 32 on large
-// graphs (measured best on R-MAT s20), fewer on small ones, where a level's
-// vertices would otherwise sit with too few warps (ER n = 100k, 256 samples:
-// backward 3.86 ms taking 32, 2.41 ms taking 16, 2.22 ms taking 8, 2.33 ms
-// taking 4). BCG_BWD_GRAB overrides.
-static int bwd_grab(int32_t n) {
-  static const int env = [] {
-    const char *e = std::getenv("BCG_BWD_GRAB");
-    const int v = e ? std::atoi(e) : 0;
-    return (v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32) ? v : 0;
-  }();
-  if (env) return env;
-  return n >= (1 << 19) ? 32 : (n >= (1 << 17) ? 16 : 8);
-}
-
 // Whether a heavy vertex has lanes at level l in the last forward pass.
 static inline bool heavy_at(const Workspace &ws, int l) { return l >= (int)ws.hlev.size() || ws.hlev[l]; }
 
@@ -1963,9 +1972,41 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
   auto lvl_list = [&](int lev) -> const int32_t * { return vlist ? vlist + (size_t)lev * n : nullptr; };
   auto lvl_cnt = [&](int lev) -> const unsigned * { return vcnt ? vcnt + lev : nullptr; };
   const bool narrow = ws.last_sigmax <= (1ull << 44);
+  // A level's heavy-segment kernel and its light kernel touch disjoint data
+  // (segment partials vs the light vertices' slots; both read only level l+1's
+  // coefficients), so the segments run on the side stream beside the light
+  // kernel and the finisher joins them: each kernel's tail overlaps the other.
+  const bool overlap = ctx->bwd_overlap && hm.nseg;
+  if (overlap && !ctx->side) {
+    BCG_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    BCG_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    BCG_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+  }
+  cudaStream_t sst = overlap ? ctx->side : st;
+  auto fork = [&] {
+    if (!overlap) return;
+    BCG_CUDA(cudaEventRecord(ctx->ev_fork, st));
+    BCG_CUDA(cudaStreamWaitEvent(sst, ctx->ev_fork, 0));
+  };
+  auto join = [&] {
+    if (!overlap) return;
+    BCG_CUDA(cudaEventRecord(ctx->ev_join, sst));
+    BCG_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+  };
   if (narrow && ctx->bwd_variant == 1) {
     hm.part2.ensure(std::max<size_t>(hm.nseg, 1) * 64 * sizeof(uint4));
     for (int l = maxlevel; l >= 1; --l) {
+      const bool hv = hm.nseg && heavy_at(ws, l);
+      if (hv) {
+        fork();
+        LaunchScope ls(ctx, F_BWD, sst);
+        auto kseg = (ctx->heavy_lane == 2 || ctx->heavy_lane == 3) ? k_bwd_heavy_seg_dense
+                                         : (ctx->heavy_lane == 1 ? k_bwd_heavy_seg_lane : k_bwd_heavy_seg_fx);
+        kseg<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, sst>>>(
+            hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
+            lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), hm.part2.as<uint4>(),
+            ws.wq.as<unsigned>() + 8 * l + 3, ws.err.as<unsigned>(), keep);
+      }
       {
         LaunchScope ls(ctx, F_BWD);
         k_bwd_light_fx<<<blocks, FWD_THREADS, 0, st>>>(g.n, lvl_list(l), lvl_cnt(l), g.rp, g.col,
@@ -1974,16 +2015,8 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
                                                       ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg, keep,
                                                       bwd_grab(g.n));
       }
-      if (hm.nseg && heavy_at(ws, l)) {
-        {
-          LaunchScope ls(ctx, F_BWD);
-          auto kseg = (ctx->heavy_lane == 2 || ctx->heavy_lane == 3) ? k_bwd_heavy_seg_dense
-                                           : (ctx->heavy_lane == 1 ? k_bwd_heavy_seg_lane : k_bwd_heavy_seg_fx);
-          kseg<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
-              hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
-              lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), hm.part2.as<uint4>(),
-              ws.wq.as<unsigned>() + 8 * l + 3, ws.err.as<unsigned>(), keep);
-        }
+      if (hv) {
+        join();
         LaunchScope ls(ctx, F_BWD);
         k_bwd_heavy_fin_fx<<<std::min(blocks, (hm.nh + 7) / 8), FWD_THREADS, 0, st>>>(
             hm.nh, hm.heavy.as<int32_t>(), hm.hseg0.as<int32_t>(), lm + (size_t)l * n, ws.sigma.as<uint64_t>(),
@@ -1993,6 +2026,16 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
     return;
   }
   for (int l = maxlevel; l >= 1; --l) {
+    const bool hv = hm.nseg && heavy_at(ws, l);
+    if (hv) {
+      fork();
+      LaunchScope ls(ctx, F_BWD, sst);
+      auto kseg = narrow ? k_bwd_heavy_seg<NarrowAcc> : k_bwd_heavy_seg<WideAcc>;
+      kseg<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, sst>>>(
+          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
+          lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), hm.part.as<Acc>(),
+          ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 3, keep);
+    }
     {
       LaunchScope ls(ctx, F_BWD);
       if (narrow)
@@ -2006,13 +2049,9 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
             ws.sigma.as<uint64_t>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 2, hm.heavy_deg,
             keep, bwd_grab(g.n));
     }
-    if (hm.nseg && heavy_at(ws, l)) {
+    if (hv) {
+      join();
       LaunchScope ls(ctx, F_BWD);
-      auto kseg = narrow ? k_bwd_heavy_seg<NarrowAcc> : k_bwd_heavy_seg<WideAcc>;
-      kseg<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
-          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
-          lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.sigma.as<uint64_t>(), hm.part.as<Acc>(),
-          ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 3, keep);
       k_bwd_heavy_fin<<<std::min(blocks, (hm.nh + 7) / 8), FWD_THREADS, 0, st>>>(
           hm.nh, hm.heavy.as<int32_t>(), hm.hseg0.as<int32_t>(), lm + (size_t)l * n, ws.sigma.as<uint64_t>(),
           hm.part.as<Acc>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 4, keep);

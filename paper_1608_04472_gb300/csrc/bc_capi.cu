@@ -66,7 +66,7 @@ void DevBuf::release() {
   bytes = 0;
 }
 
-LaunchScope::LaunchScope(bc_ctx *c, int f) : ctx(c), fam(f) {
+LaunchScope::LaunchScope(bc_ctx *c, int f, cudaStream_t st) : ctx(c), fam(f), s(st ? st : c->stream) {
   if (ctx->profiling) {
     for (cudaEvent_t *e : {&e0, &e1}) {
       if (!ctx->event_pool.empty()) {
@@ -76,7 +76,7 @@ LaunchScope::LaunchScope(bc_ctx *c, int f) : ctx(c), fam(f) {
         cudaEventCreate(e);
       }
     }
-    cudaEventRecord(e0, ctx->stream);
+    cudaEventRecord(e0, s);
   }
 }
 
@@ -84,7 +84,7 @@ LaunchScope::~LaunchScope() {
   ctx->launches += 1;
   ctx->fam_launches[fam] += 1;
   if (e0) {
-    cudaEventRecord(e1, ctx->stream);
+    cudaEventRecord(e1, s);
     ctx->pending_events.push_back({fam, {e0, e1}});
   }
 }
@@ -1604,6 +1604,7 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
       const int e = std::atoi(pe);
       ctx->pair_engine = (e == 1 || e == 2) ? e : 0;
     }
+    if (const char *bo = std::getenv("BCG_BWD_OVERLAP")) ctx->bwd_overlap = std::atoi(bo) != 0;
     if (const char *ph = std::getenv("BCG_PAIR_HASH")) ctx->pair_hash_lg = std::max(6, std::min(24, std::atoi(ph)));
     if (const char *ws = std::getenv("BCG_W_STEP")) ctx->w_step = std::atoll(ws);
     BCG_CUDA(cudaMallocHost(&ctx->ws.pinned, 4096));
@@ -1663,6 +1664,9 @@ void bc_destroy(bc_ctx *ctx) {
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   }
   delete ctx;
 }

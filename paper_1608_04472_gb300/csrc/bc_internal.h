@@ -155,6 +155,11 @@ struct bc_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaStream_t stream2 = nullptr;  // second stream (persistent multi-graph work), made on first use
+  // the backward pass runs a level's heavy-segment kernel on this stream beside
+  // the light kernel on the main one (fork and join events), made on first use
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int32_t bwd_overlap = 1;
   int32_t batch_width = 0;
   std::recursive_mutex mu;
   std::atomic<int> api_waiting{0};  // API calls waiting for mu (the server worker yields to them)
@@ -232,8 +237,9 @@ inline size_t cta_scratch_budget() {
 struct LaunchScope {
   bc_ctx *ctx;
   int fam;
+  cudaStream_t s;  // the stream the kernel goes to (the context's by default)
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  LaunchScope(bc_ctx *c, int f);
+  LaunchScope(bc_ctx *c, int f, cudaStream_t st = nullptr);
   ~LaunchScope();
 };
 void resolve_events(bc_ctx *ctx);  // after a stream sync
