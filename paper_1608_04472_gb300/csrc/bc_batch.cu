@@ -194,6 +194,13 @@ __global__ void k_zero_heavy_rows(int nh, const int32_t *__restrict__ heavy, uin
   if (h < nh && threadIdx.x < 64) sigma[(size_t)heavy[h] * 64 + threadIdx.x] = 0ull;
 }
 
+// Clear the next level's masks of the heavy vertices (before their segments
+// OR into them), when the light kernel of the level runs beside them.
+__global__ void k_zero_heavy_lm(int nh, const int32_t *__restrict__ heavy, uint64_t *__restrict__ lm_cur) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h < nh) lm_cur[heavy[h]] = 0ull;
+}
+
 // Level 1 directly: the vertices at distance 1 from s_t are its neighbours, each
 // with exactly one shortest path (sigma = 1). One block per lane.
 __global__ void k_fwd_level1(int count, const int32_t *__restrict__ sources, const int32_t *__restrict__ rp,
@@ -355,7 +362,7 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
             uint64_t *__restrict__ active_cur, unsigned *__restrict__ err,
             unsigned long long *__restrict__ cnt, unsigned *__restrict__ wq, int heavy_deg, int pk_maxl,
             int pk_mincnt, int32_t *__restrict__ list_next, unsigned *__restrict__ vcnt_next,
-            unsigned long long *__restrict__ vedges_next, int gsz) {
+            unsigned long long *__restrict__ vedges_next, int gsz, int zero_heavy) {
   __shared__ int32_t lists[FWD_THREADS / 32][32];
   __shared__ int8_t tabs[FWD_THREADS / 32][64];
   const int lane = threadIdx.x & 31;
@@ -375,7 +382,9 @@ k_fwd_light(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
       he = rp[vl + 1];
       hv = visited[vl];
       work = ((~hv & act) != 0ull) && he > hb && he - hb <= heavy_deg;
-      if (!work) lm_cur[vl] = 0ull;  // heavy vertices are then filled by their segments
+      // heavy vertices are filled by their segments: their rows are cleared
+      // here, or (zero_heavy = 0) by k_zero_heavy_lm on the heavy kernels' stream
+      if (!work && (zero_heavy || he - hb <= heavy_deg)) lm_cur[vl] = 0ull;
     }
     unsigned todo = __ballot_sync(FULL, work);
     unsigned found = 0u;  // vertices of this grab that join the next level
@@ -1719,6 +1728,14 @@ static int fwd_grab(int32_t n) {
   return env ? env : light_grab(n);
 }
 
+// The context's side stream and its fork / join events, made on first use.
+static void side_stream(bc_ctx *ctx) {
+  if (ctx->side) return;
+  BCG_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+  BCG_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+  BCG_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+}
+
 void batch_ensure(bc_ctx *ctx, const Graph &g) {
   Workspace &ws = ctx->ws;
   const size_t n = (size_t)g.n;
@@ -1842,60 +1859,85 @@ int batch_forward(bc_ctx *ctx, const Graph &g, int count, bool pairs, OvfMode mo
     // top-down when the level's vertices have few edges (Beamer's direction
     // switch, here on the level's degree sum against the graph's edges)
     const bool push = ws.lists && fedges * (uint64_t)ctx->push_div <= (uint64_t)g.nnz;
-    if (push) {
-      BCG_CUDA(cudaMemsetAsync(lm + (size_t)(l + 1) * n, 0, n * 8, st));
-      {
-        LaunchScope ls(ctx, F_FWD);
-        k_fwd_push<<<blocks, FWD_THREADS, 0, st>>>(g.rp, g.col, lst(l), vcnt + l, lm + (size_t)l * n,
-                                                  lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), act + l,
-                                                  ws.enable.as<uint64_t>(), lst(l + 1), vcnt + l + 1,
-                                                  vedges + l + 1, ws.wq.as<unsigned>() + 8 * l + 0);
-      }
-      LaunchScope ls(ctx, F_FWD);
-      k_fwd_pull_list<<<blocks, FWD_THREADS, 0, st>>>(prp, pcol, lst(l + 1), vcnt + l + 1,
-                                                     lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
-                                                     ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
-                                                     ws.enable.as<uint64_t>(), act + l + 1,
-                                                     ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 1,
-                                                     hm.heavy_deg, hw + 5);
-    } else {
-      LaunchScope ls(ctx, F_FWD);
-      k_fwd_light<<<blocks, FWD_THREADS, 0, st>>>(g.n, prp, pcol, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
-                                                 ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(), act + l,
-                                                 ws.enable.as<uint64_t>(), act + l + 1, ws.err.as<unsigned>(),
-                                                 ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 0,
-                                                 hm.heavy_deg, ctx->pk_maxl, ctx->pk_mincnt,
-                                                 lst(l + 1), vcnt + l + 1, vedges + l + 1, fwd_grab(g.n));
-    }
     const bool heavy_now = !push && hm.nseg && !heavy_done;
-    if (heavy_now && (ctx->heavy_lane == 3 || ctx->heavy_lane == 4)) {
-      LaunchScope ls(ctx, F_FWD);
-      k_fwd_heavy_dense<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
-          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), pcol,
-          lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
-          act + l, ws.enable.as<uint64_t>(), ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 1);
-    } else if (heavy_now && ctx->heavy_lane == 1) {
-      LaunchScope ls(ctx, F_FWD);
-      k_fwd_heavy_lane<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
-          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), pcol,
-          lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
-          act + l, ws.enable.as<uint64_t>(), ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 1);
-    } else if (heavy_now) {
-      LaunchScope ls(ctx, F_FWD);
-      k_fwd_heavy<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, st>>>(
-          hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), pcol,
-          lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
-          act + l, ws.enable.as<uint64_t>(), ws.err.as<unsigned>(), ws.cnt.as<unsigned long long>(),
-          ws.wq.as<unsigned>() + 8 * l + 1);
-    }
-    if (heavy_now) {
-      LaunchScope ls(ctx, F_FWD);
-      k_fwd_heavy_fin<<<std::min(blocks, (hm.nh + 7) / 8), 256, 0, st>>>(hm.nh, hm.heavy.as<int32_t>(), lm + (size_t)(l + 1) * n,
-                                                          ws.visited.as<uint64_t>(), act + l + 1,
-                                                          ws.cnt.as<unsigned long long>(), ws.sigma.as<uint64_t>(),
-                                                          ws.enable.as<uint64_t>(), hw + 5,
-                                                          reinterpret_cast<unsigned long long *>(hw + 6), g.rp,
-                                                          lst(l + 1), vcnt + l + 1, vedges + l + 1);
+    // With heavy work at this level, the heavy vertices' kernels (clear their
+    // rows, segments, finisher) run on the side stream beside the light kernel:
+    // the two write disjoint rows and read only level l's masks and counts, and
+    // the level ends with a join. Without the side stream the light kernel
+    // clears the heavy rows itself and runs first.
+    const bool fov = heavy_now && ctx->fwd_overlap;
+    if (fov) side_stream(ctx);
+    const cudaStream_t hst = fov ? ctx->side : st;
+    auto heavy_chain = [&] {
+      if (fov) {
+        LaunchScope ls(ctx, F_FWD, hst, false);
+        k_zero_heavy_lm<<<(hm.nh + 255) / 256, 256, 0, hst>>>(hm.nh, hm.heavy.as<int32_t>(),
+                                                              lm + (size_t)(l + 1) * n);
+      }
+      if (ctx->heavy_lane == 3 || ctx->heavy_lane == 4) {
+        LaunchScope ls(ctx, F_FWD, hst, false);
+        k_fwd_heavy_dense<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, hst>>>(
+            hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), pcol,
+            lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
+            act + l, ws.enable.as<uint64_t>(), ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 1);
+      } else if (ctx->heavy_lane == 1) {
+        LaunchScope ls(ctx, F_FWD, hst, false);
+        k_fwd_heavy_lane<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, hst>>>(
+            hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), pcol,
+            lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
+            act + l, ws.enable.as<uint64_t>(), ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 1);
+      } else {
+        LaunchScope ls(ctx, F_FWD, hst, false);
+        k_fwd_heavy<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, hst>>>(
+            hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), pcol,
+            lm + (size_t)l * n, lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
+            act + l, ws.enable.as<uint64_t>(), ws.err.as<unsigned>(), ws.cnt.as<unsigned long long>(),
+            ws.wq.as<unsigned>() + 8 * l + 1);
+      }
+      LaunchScope ls(ctx, F_FWD, hst, false);
+      k_fwd_heavy_fin<<<std::min(blocks, (hm.nh + 7) / 8), 256, 0, hst>>>(
+          hm.nh, hm.heavy.as<int32_t>(), lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), act + l + 1,
+          ws.cnt.as<unsigned long long>(), ws.sigma.as<uint64_t>(), ws.enable.as<uint64_t>(), hw + 5,
+          reinterpret_cast<unsigned long long *>(hw + 6), g.rp, lst(l + 1), vcnt + l + 1, vedges + l + 1);
+    };
+    {
+      // the level's time on the main stream (after the join) is the family's time
+      LaunchScope level_scope(ctx, F_FWD, st, true, false);
+      if (fov) {
+        BCG_CUDA(cudaEventRecord(ctx->ev_fork, st));
+        BCG_CUDA(cudaStreamWaitEvent(hst, ctx->ev_fork, 0));
+        heavy_chain();
+      }
+      if (push) {
+        BCG_CUDA(cudaMemsetAsync(lm + (size_t)(l + 1) * n, 0, n * 8, st));
+        {
+          LaunchScope ls(ctx, F_FWD, st, false);
+          k_fwd_push<<<blocks, FWD_THREADS, 0, st>>>(g.rp, g.col, lst(l), vcnt + l, lm + (size_t)l * n,
+                                                    lm + (size_t)(l + 1) * n, ws.visited.as<uint64_t>(), act + l,
+                                                    ws.enable.as<uint64_t>(), lst(l + 1), vcnt + l + 1,
+                                                    vedges + l + 1, ws.wq.as<unsigned>() + 8 * l + 0);
+        }
+        LaunchScope ls(ctx, F_FWD, st, false);
+        k_fwd_pull_list<<<blocks, FWD_THREADS, 0, st>>>(prp, pcol, lst(l + 1), vcnt + l + 1,
+                                                       lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
+                                                       ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(),
+                                                       ws.enable.as<uint64_t>(), act + l + 1,
+                                                       ws.cnt.as<unsigned long long>(),
+                                                       ws.wq.as<unsigned>() + 8 * l + 1, hm.heavy_deg, hw + 5);
+      } else {
+        LaunchScope ls(ctx, F_FWD, st, false);
+        k_fwd_light<<<blocks, FWD_THREADS, 0, st>>>(g.n, prp, pcol, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
+                                                   ws.visited.as<uint64_t>(), ws.sigma.as<uint64_t>(), act + l,
+                                                   ws.enable.as<uint64_t>(), act + l + 1, ws.err.as<unsigned>(),
+                                                   ws.cnt.as<unsigned long long>(), ws.wq.as<unsigned>() + 8 * l + 0,
+                                                   hm.heavy_deg, ctx->pk_maxl, ctx->pk_mincnt, lst(l + 1),
+                                                   vcnt + l + 1, vedges + l + 1, fwd_grab(g.n), fov ? 0 : 1);
+      }
+      if (heavy_now && !fov) heavy_chain();
+      if (fov) {
+        BCG_CUDA(cudaEventRecord(ctx->ev_join, hst));
+        BCG_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+      }
     }
     // Deep traversals also watch the overflowed lanes every level: once every
     // lane has overflowed the integer pass has nothing left to give (and its
@@ -1977,12 +2019,11 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
   // coefficients), so the segments run on the side stream beside the light
   // kernel and the finisher joins them: each kernel's tail overlaps the other.
   const bool overlap = ctx->bwd_overlap && hm.nseg;
-  if (overlap && !ctx->side) {
-    BCG_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
-    BCG_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-    BCG_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
-  }
+  if (overlap) side_stream(ctx);
   cudaStream_t sst = overlap ? ctx->side : st;
+  // the family's time is the pass's time on the main stream (the side stream's
+  // kernels are joined into it): the overlapping launches are counted, not timed
+  LaunchScope pass(ctx, F_BWD, st, true, false);
   auto fork = [&] {
     if (!overlap) return;
     BCG_CUDA(cudaEventRecord(ctx->ev_fork, st));
@@ -1999,7 +2040,7 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
       const bool hv = hm.nseg && heavy_at(ws, l);
       if (hv) {
         fork();
-        LaunchScope ls(ctx, F_BWD, sst);
+        LaunchScope ls(ctx, F_BWD, sst, false);
         auto kseg = (ctx->heavy_lane == 2 || ctx->heavy_lane == 3) ? k_bwd_heavy_seg_dense
                                          : (ctx->heavy_lane == 1 ? k_bwd_heavy_seg_lane : k_bwd_heavy_seg_fx);
         kseg<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, sst>>>(
@@ -2008,7 +2049,7 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
             ws.wq.as<unsigned>() + 8 * l + 3, ws.err.as<unsigned>(), keep);
       }
       {
-        LaunchScope ls(ctx, F_BWD);
+        LaunchScope ls(ctx, F_BWD, st, false);
         k_bwd_light_fx<<<blocks, FWD_THREADS, 0, st>>>(g.n, lvl_list(l), lvl_cnt(l), g.rp, g.col,
                                                       lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
                                                       ws.sigma.as<uint64_t>(), sink, ws.err.as<unsigned>(),
@@ -2017,7 +2058,7 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
       }
       if (hv) {
         join();
-        LaunchScope ls(ctx, F_BWD);
+        LaunchScope ls(ctx, F_BWD, st, false);
         k_bwd_heavy_fin_fx<<<std::min(blocks, (hm.nh + 7) / 8), FWD_THREADS, 0, st>>>(
             hm.nh, hm.heavy.as<int32_t>(), hm.hseg0.as<int32_t>(), lm + (size_t)l * n, ws.sigma.as<uint64_t>(),
             hm.part2.as<uint4>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 4, keep);
@@ -2029,7 +2070,7 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
     const bool hv = hm.nseg && heavy_at(ws, l);
     if (hv) {
       fork();
-      LaunchScope ls(ctx, F_BWD, sst);
+      LaunchScope ls(ctx, F_BWD, sst, false);
       auto kseg = narrow ? k_bwd_heavy_seg<NarrowAcc> : k_bwd_heavy_seg<WideAcc>;
       kseg<<<std::min(blocks, (hm.nseg + 7) / 8), FWD_THREADS, 0, sst>>>(
           hm.nseg, hm.seg_v.as<int32_t>(), hm.seg_b.as<int32_t>(), hm.seg_e.as<int32_t>(), g.col,
@@ -2037,7 +2078,7 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
           ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 3, keep);
     }
     {
-      LaunchScope ls(ctx, F_BWD);
+      LaunchScope ls(ctx, F_BWD, st, false);
       if (narrow)
         k_bwd_light<NarrowAcc><<<blocks, FWD_THREADS, 0, st>>>(
             g.n, lvl_list(l), lvl_cnt(l), g.rp, g.col, lm + (size_t)l * n, lm + (size_t)(l + 1) * n,
@@ -2051,7 +2092,7 @@ void batch_backward(bc_ctx *ctx, const Graph &g, int maxlevel, const Sink &sink,
     }
     if (hv) {
       join();
-      LaunchScope ls(ctx, F_BWD);
+      LaunchScope ls(ctx, F_BWD, st, false);
       k_bwd_heavy_fin<<<std::min(blocks, (hm.nh + 7) / 8), FWD_THREADS, 0, st>>>(
           hm.nh, hm.heavy.as<int32_t>(), hm.hseg0.as<int32_t>(), lm + (size_t)l * n, ws.sigma.as<uint64_t>(),
           hm.part.as<Acc>(), sink, ws.err.as<unsigned>(), ws.wq.as<unsigned>() + 8 * l + 4, keep);

@@ -66,8 +66,9 @@ void DevBuf::release() {
   bytes = 0;
 }
 
-LaunchScope::LaunchScope(bc_ctx *c, int f, cudaStream_t st) : ctx(c), fam(f), s(st ? st : c->stream) {
-  if (ctx->profiling) {
+LaunchScope::LaunchScope(bc_ctx *c, int f, cudaStream_t st, bool timed, bool counted)
+    : ctx(c), fam(f), s(st ? st : c->stream), counted_(counted) {
+  if (ctx->profiling && timed) {
     for (cudaEvent_t *e : {&e0, &e1}) {
       if (!ctx->event_pool.empty()) {
         *e = ctx->event_pool.back();
@@ -81,8 +82,10 @@ LaunchScope::LaunchScope(bc_ctx *c, int f, cudaStream_t st) : ctx(c), fam(f), s(
 }
 
 LaunchScope::~LaunchScope() {
-  ctx->launches += 1;
-  ctx->fam_launches[fam] += 1;
+  if (counted_) {
+    ctx->launches += 1;
+    ctx->fam_launches[fam] += 1;
+  }
   if (e0) {
     cudaEventRecord(e1, s);
     ctx->pending_events.push_back({fam, {e0, e1}});
@@ -1605,6 +1608,7 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
       ctx->pair_engine = (e == 1 || e == 2) ? e : 0;
     }
     if (const char *bo = std::getenv("BCG_BWD_OVERLAP")) ctx->bwd_overlap = std::atoi(bo) != 0;
+    if (const char *fo = std::getenv("BCG_FWD_OVERLAP")) ctx->fwd_overlap = std::atoi(fo) != 0;
     if (const char *ph = std::getenv("BCG_PAIR_HASH")) ctx->pair_hash_lg = std::max(6, std::min(24, std::atoi(ph)));
     if (const char *ws = std::getenv("BCG_W_STEP")) ctx->w_step = std::atoll(ws);
     BCG_CUDA(cudaMallocHost(&ctx->ws.pinned, 4096));

@@ -159,7 +159,7 @@ struct bc_ctx {
   // the light kernel on the main one (fork and join events), made on first use
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  int32_t bwd_overlap = 1;
+  int32_t bwd_overlap = 1, fwd_overlap = 1;
   int32_t batch_width = 0;
   std::recursive_mutex mu;
   std::atomic<int> api_waiting{0};  // API calls waiting for mu (the server worker yields to them)
@@ -239,8 +239,12 @@ struct LaunchScope {
   int fam;
   cudaStream_t s;  // the stream the kernel goes to (the context's by default)
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  LaunchScope(bc_ctx *c, int f, cudaStream_t st = nullptr);
+  // counted = false: time the scope (a phase of several launches) without
+  // counting a launch; timed = false: count the launch, leave the time to an
+  // enclosing phase scope
+  LaunchScope(bc_ctx *c, int f, cudaStream_t st = nullptr, bool timed = true, bool counted = true);
   ~LaunchScope();
+  bool counted_;
 };
 void resolve_events(bc_ctx *ctx);  // after a stream sync
 
