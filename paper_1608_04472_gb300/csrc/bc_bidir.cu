@@ -36,8 +36,10 @@
 
 namespace bcg {
 
-constexpr int BT = 256;  // threads per CTA
-constexpr int BWARPS = BT / 32;
+// threads per CTA: a template parameter of the CTA search, 256 by default;
+// 128 (BCG_PAIR_CTA_THREADS=128) keeps twice the pairs in flight per SM at the
+// same registers, each level taken by half the threads, and measured slower on
+// BA n = 2M (501k vs 523k marginal pair draws/s with memory for every CTA)
 constexpr int BHEAVY = 32;   // vertices above this degree are handled by a whole warp
 constexpr int BHUGE = 512;   // ... and above this one by the whole CTA
 constexpr int BHUGE_CAP = 64;  // CTA-wide vertices per pass (the rest fall back to a warp)
@@ -76,9 +78,10 @@ __device__ inline BScr bscr_of(unsigned char *base, int32_t nmax) {
 // (lane, 32), huge ones (degree > BHUGE, up to BHUGE_CAP of them) by the whole
 // CTA after the others (thread, BT). Called by every thread of the CTA; ends
 // with a CTA barrier. s_huge / s_nhuge: shared scratch, *s_nhuge = 0 on entry.
-template <class F>
+template <int BT, class F>
 __device__ __forceinline__ void for_list(const int32_t *__restrict__ q, const int32_t *__restrict__ rp, int b, int e,
                                          int32_t *s_huge, int *s_nhuge, F fn) {
+  constexpr int BWARPS = BT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int cb = b + warp * 32; cb < e; cb += BWARPS * 32) {
     const int idx = cb + lane;
@@ -118,7 +121,8 @@ __device__ __forceinline__ void for_list(const int32_t *__restrict__ q, const in
 // lane: pair_d = d(s,t) (-1 unreachable), pair_sig = sigma_st (0 when
 // unreachable or when pair_big = 1, i.e. sigma_st >= 2^64; *nbig counts those).
 // *visited (may be null) accumulates the vertices of both balls.
-__global__ void __launch_bounds__(BT, 4)
+template <int BT>
+__global__ void __launch_bounds__(BT, 1024 / BT)
 k_pair_bidir(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, const int32_t *__restrict__ src,
              const int32_t *__restrict__ dst, int count, unsigned *__restrict__ next, unsigned char *__restrict__ scratch,
              size_t stride, int32_t nmax, int32_t *__restrict__ pair_d, uint64_t *__restrict__ pair_sig,
@@ -177,7 +181,7 @@ k_pair_bidir(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, co
       // frontier's edges (exact integer sums in any order; a carry out of 64
       // bits or a marked predecessor marks the vertex)
       unsigned long long my_edges = 0ull;
-      for_list(qX, rp, fb, fe, s_huge, &s_nhuge, [&](int32_t v, int beg, int end, int off, int step) {
+      for_list<BT>(qX, rp, fb, fe, s_huge, &s_nhuge, [&](int32_t v, int beg, int end, int off, int step) {
         const uint64_t sv = sX[v];
         const bool bv = bX[v] != 0;
         for (int j = beg + off; j < end; j += step) {
@@ -597,7 +601,7 @@ __global__ void k_scatter_pairs(int c, const int32_t *__restrict__ idx, const in
 struct BidirState {
   DevBuf scratch, next, idx, src, dst, pd, psig, pexp, pxf;
   int32_t nmax = 0;
-  int ncta = 0;
+  int ncta = 0, threads = 0;
   // one-pair-per-warp engine: tables, counters, abandoned pairs and their
   // compact inputs and outputs for the CTA engine
   DevBuf wtabs, wctr, wfb, fsrc, fdst, fpd, fps, fpb;
@@ -623,15 +627,18 @@ void forget_bidir_scratch(bc_ctx *ctx) {
 }
 
 // Resident CTAs of k_pair_bidir over all SMs, within the scratch budget.
-static int bidir_ctas(int count, size_t per) {
+static int bidir_ctas(int count, size_t per, int threads) {
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_bidir, BT, 0) != cudaSuccess || occ < 1) {
+  const cudaError_t oe = threads == 128
+                             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_bidir<128>, 128, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_bidir<256>, 256, 0);
+  if (oe != cudaSuccess || occ < 1) {
     cudaGetLastError();
     occ = 1;
   }
-  return std::max(1, std::min({count, sms * occ, (int)std::max<size_t>(1, cta_scratch_budget() / per)}));
+  return std::max(1, std::min({count, sms * occ, (int)std::max<size_t>(1, cta_scratch_budget(true) / per)}));
 }
 
 // The CTA engine over pair lanes [0, count); returns how many have
@@ -641,12 +648,13 @@ static unsigned cta_pairs(bc_ctx *ctx, const Graph &g, BidirState &B, const int3
   cudaStream_t st = ctx->stream;
   const int32_t nmax = std::max(B.nmax, g.n);
   const size_t stride = bscr_stride(nmax);
-  if (nmax != B.nmax) {
+  const int threads = ctx->pair_cta_threads;
+  if (nmax != B.nmax || threads != B.threads) {
     // a new layout, sized once for every resident CTA: all distances -1
     B.scratch.release();
     B.nmax = 0;
     B.ncta = 0;
-    const int full = bidir_ctas(1 << 30, stride);
+    const int full = bidir_ctas(1 << 30, stride, threads);
     B.scratch.ensure(stride * (size_t)full);
     {
       LaunchScope ls(ctx, F_MISC);
@@ -655,15 +663,17 @@ static unsigned cta_pairs(bc_ctx *ctx, const Graph &g, BidirState &B, const int3
     }
     B.nmax = nmax;
     B.ncta = full;
+    B.threads = threads;
   }
   const int ncta = std::min(count, B.ncta);
   B.next.ensure(32);
   BCG_CUDA(cudaMemsetAsync(B.next.p, 0, 32, st));
   {
     LaunchScope ls(ctx, F_PAIR);
-    k_pair_bidir<<<ncta, BT, 0, st>>>(g.rp, g.col, d_src, d_dst, count, B.next.as<unsigned>(),
-                                      B.scratch.as<unsigned char>(), stride, nmax, pd, psig, pbig,
-                                      B.next.as<unsigned>() + 1, ctx->ws.cnt.as<unsigned long long>() + 1);
+    auto kern = threads == 128 ? k_pair_bidir<128> : k_pair_bidir<256>;
+    kern<<<ncta, threads, 0, st>>>(g.rp, g.col, d_src, d_dst, count, B.next.as<unsigned>(),
+                                   B.scratch.as<unsigned char>(), stride, nmax, pd, psig, pbig,
+                                   B.next.as<unsigned>() + 1, ctx->ws.cnt.as<unsigned long long>() + 1);
   }
   unsigned *h = static_cast<unsigned *>(ctx->ws.pinned);
   BCG_CUDA(cudaMemcpyAsync(h, B.next.as<unsigned>() + 1, 4, cudaMemcpyDeviceToHost, st));

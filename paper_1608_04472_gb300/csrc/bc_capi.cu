@@ -1609,6 +1609,7 @@ bc_status bc_create(bc_ctx **out, int device, const bc_options *opt) {
     }
     if (const char *bo = std::getenv("BCG_BWD_OVERLAP")) ctx->bwd_overlap = std::atoi(bo) != 0;
     if (const char *fo = std::getenv("BCG_FWD_OVERLAP")) ctx->fwd_overlap = std::atoi(fo) != 0;
+    if (const char *pt = std::getenv("BCG_PAIR_CTA_THREADS")) ctx->pair_cta_threads = std::atoi(pt) == 128 ? 128 : 256;
     if (const char *ph = std::getenv("BCG_PAIR_HASH")) ctx->pair_hash_lg = std::max(6, std::min(24, std::atoi(ph)));
     if (const char *ws = std::getenv("BCG_W_STEP")) ctx->w_step = std::atoll(ws);
     BCG_CUDA(cudaMallocHost(&ctx->ws.pinned, 4096));

@@ -208,6 +208,8 @@ struct bc_ctx {
   int32_t pair_engine = 0;
   // log2 of the slots of each side's table in the one-pair-per-warp search
   int32_t pair_hash_lg = 14;
+  // threads per CTA of the one-pair-per-CTA search (128 or 256)
+  int32_t pair_cta_threads = 256;
   int64_t pair_fallbacks = 0;  // pairs that search handed to the CTA form
   // weighted graphs: near-far threshold increment for graphs loaded later
   // (0 = a sixth of the graph's mean edge length)
@@ -217,9 +219,12 @@ struct bc_ctx {
 namespace bcg {
 
 // Device memory for the per-CTA scratch of the one-source-per-CTA engines
-// (lane-major, weighted, one pair per CTA): a quarter of the free memory, at
-// most 32 GB; with BCG_SCRATCH_GB set, half of the free memory, at most that.
-inline size_t cta_scratch_budget() {
+// (lane-major, weighted: a quarter of the free memory, at most 32 GB) and of
+// the one-pair-per-CTA search (a third, at most 64 GB: on BA n = 2M every
+// resident CTA then has its 68 MB, 523k vs 477k pair draws/s at 32 GB; the
+// weighted engine measured the same with more CTAs); with BCG_SCRATCH_GB set,
+// half of the free memory, at most that.
+inline size_t cta_scratch_budget(bool pairs = false) {
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
     cudaGetLastError();
@@ -229,7 +234,7 @@ inline size_t cta_scratch_budget() {
     const long long gb = std::atoll(e);
     if (gb > 0) return std::min<size_t>(fr / 2, (size_t)gb << 30);
   }
-  return std::min<size_t>(fr / 4, (size_t)32 << 30);
+  return pairs ? std::min<size_t>(fr / 3, (size_t)64 << 30) : std::min<size_t>(fr / 4, (size_t)32 << 30);
 }
 
 

@@ -82,3 +82,46 @@ def test_missing_library_fails_loudly(tmp_path):
     code = "import paper_1608_04472_gb300 as p\ntry:\n    p.Context\nexcept ImportError:\n    print('LOUD')\n"
     r = subprocess.run([sys.executable, "-c", code], cwd=tmp_path, capture_output=True, text=True)
     assert "LOUD" in r.stdout, r.stdout + r.stderr
+
+
+def _c_layout(text, name):
+    """Field (name, offset, size) of `typedef struct name {...} name;` in the
+    header, with natural alignment (every type here is 1, 4 or 8 bytes)."""
+    import re
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    sizes = {"int32_t": 4, "uint32_t": 4, "int64_t": 8, "uint64_t": 8, "double": 8, "char": 1, "bc_graph": 8}
+    out, off = [], 0
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        m = re.match(r"(?:const\s+)?(\w+)\s+(.*)", decl)
+        base, names = m.group(1), m.group(2)
+        for item in names.split(","):
+            item = item.strip()
+            ptr = item.startswith("*")
+            nm = re.match(r"\**\s*(\w+)", item).group(1)
+            dims = [int(d) for d in re.findall(r"\[(\d+)\]", item)]
+            el = 8 if (ptr or base == "void") else sizes[base]
+            count = 1
+            for d in dims:
+                count *= d
+            off = (off + el - 1) // el * el
+            out.append((nm, off, el * count))
+            off += el * count
+    return out
+
+
+@pytest.mark.parametrize("name", ["bc_options", "bc_query_stats", "bc_query", "bc_tuning", "bc_stats"])
+def test_binding_structs_match_the_header_layout(name):
+    """Every struct the binding mirrors has the header's fields, in order, at
+    the same offsets and sizes."""
+    import ctypes
+    from paper_1608_04472_gb300 import capi
+    text = open(os.path.join(ROOT, "include", "bc.h")).read()
+    declared = _c_layout(text, name)
+    cls = getattr(capi, name)
+    bound = [(f, getattr(cls, f).offset, getattr(cls, f).size) for f, _ in cls._fields_]
+    assert bound == declared
+    assert ctypes.sizeof(cls) >= declared[-1][1] + declared[-1][2]
