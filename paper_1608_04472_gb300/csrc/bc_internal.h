@@ -220,10 +220,10 @@ namespace bcg {
 
 // Device memory for the per-CTA scratch of the one-source-per-CTA engines
 // (lane-major, weighted: a quarter of the free memory, at most 32 GB) and of
-// the one-pair-per-CTA search (a third, at most 64 GB: on BA n = 2M every
-// resident CTA then has its 68 MB, 523k vs 477k pair draws/s at 32 GB; the
-// weighted engine measured the same with more CTAs); with BCG_SCRATCH_GB set,
-// half of the free memory, at most that.
+// the one-pair-per-CTA search (a third, at most 96 GB: on BA n = 2M its 8
+// resident CTAs per SM then all have their 68 MB, 592k vs 524k pair draws/s
+// with 32 GB; the weighted engine measured the same with more CTAs); with
+// BCG_SCRATCH_GB set, half of the free memory, at most that.
 inline size_t cta_scratch_budget(bool pairs = false) {
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
@@ -234,7 +234,7 @@ inline size_t cta_scratch_budget(bool pairs = false) {
     const long long gb = std::atoll(e);
     if (gb > 0) return std::min<size_t>(fr / 2, (size_t)gb << 30);
   }
-  return pairs ? std::min<size_t>(fr / 3, (size_t)64 << 30) : std::min<size_t>(fr / 4, (size_t)32 << 30);
+  return pairs ? std::min<size_t>(fr / 3, (size_t)96 << 30) : std::min<size_t>(fr / 4, (size_t)32 << 30);
 }
 
 
