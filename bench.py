@@ -237,6 +237,32 @@ def cpu_multicore(g, budget_s=10.0):
             "sample": f"{done} per-sample Brandes steps (source draws of R-MAT s20), one per thread"}
 
 
+def cpu_small_configs(budget_s=3.0):
+    """The single-threaded oracle on the two small workloads it also runs in
+    full in the tests: per-sample Brandes steps on ER n=2000 (average degree 8,
+    seed 1) and Algorithm 1 pair draws on BA n=20,000 (4 edges per new vertex,
+    seed 3; one BFS from s per draw and target)."""
+    import graphgen as gg
+    import oracle
+    out = {}
+    er = gg.erdos_renyi(2000, 8, 1)
+    oracle.dependencies(er, 0)
+    t0, k = time.perf_counter(), 0
+    while time.perf_counter() - t0 < budget_s and k < 20000:
+        oracle.dependencies(er, oracle.draw_source(SEED, 997, k, er.n))
+        k += 1
+    out["er2000_samples_per_s"] = k / (time.perf_counter() - t0)
+    ba = gg.barabasi_albert(20000, 4, 3)
+    t = int(gg.degree_targets(ba, 1, 3)[0])
+    t0, k = time.perf_counter(), 0
+    while time.perf_counter() - t0 < budget_s and k < 20000:
+        oracle.pair_sequence(ba, t, SEED, 996, k, 16)
+        k += 16
+    out["ba20k_pair_draws_per_s"] = k / (time.perf_counter() - t0)
+    out["cores"] = 1
+    return out
+
+
 def oracle_pair_rate(g, targets, draws=4):
     """The oracle's marginal cost of a pair draw of Algorithm 1 (one BFS from s)
     on one host core: a run of `draws` draws minus a run of one, same stream."""
@@ -755,6 +781,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(g, targets)
         out["cpu_multicore"] = cpu_multicore(g)
+        out["cpu_small_configs"] = cpu_small_configs()
     ctx.close()
     if rank == 0:
         print(json.dumps(out))
