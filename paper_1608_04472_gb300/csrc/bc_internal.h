@@ -46,8 +46,6 @@ struct Graph {
   int64_t nnz = 0;
   int32_t max_deg = 0;
   int32_t hub = 0;                 // a vertex of maximum degree
-  uint8_t *key = nullptr;          // device [n]: min(d(hub, v), 254), 255 if unreachable (lazy)
-  int32_t *order = nullptr;        // device [n]: all vertices sorted by key (lazy, exact BC)
   int32_t *rp = nullptr;   // device row_ptr[n+1] (out-neighbours)
   int32_t *col = nullptr;  // device col[nnz]
   // in-neighbour CSR, over which path counts are pulled: a separate device copy
