@@ -392,3 +392,33 @@ def test_ba20k_pairs_full_run():
     for key in ["k", "status", "S", "est"]:
         _assert_same(res[key], ref[key], key)
     assert np.all(res["status"] == pkg.BC_STOPPED)
+
+
+@pytest.mark.parametrize("shape", ["edgeless", "matching", "star", "two_stars"])
+def test_source_key_degenerate_graphs(ctx, shape):
+    """Graphs where the source key's landmarks run out early (every vertex
+    reached from the hub is a landmark), its distances have no spread (zero
+    covariance) or most vertices are not reached from the hub (key 255): the
+    uniform estimate, exact BC and Bader's loop equal the oracle's."""
+    n = 60
+    if shape == "edgeless":
+        u, v = np.zeros(0, np.int32), np.zeros(0, np.int32)
+    elif shape == "matching":
+        u, v = np.arange(0, 40, 2, dtype=np.int32), np.arange(1, 40, 2, dtype=np.int32)
+    elif shape == "star":
+        u, v = np.zeros(n - 1, np.int32), np.arange(1, n, dtype=np.int32)
+    else:
+        u = np.concatenate([np.zeros(29, np.int32), np.full(29, 30, np.int32)])
+        v = np.concatenate([np.arange(1, 30, dtype=np.int32), np.arange(31, 60, dtype=np.int32)])
+    g = gg.from_edges(n, u, v)
+    h = ctx.load_graph(g.row_ptr, g.col)
+    try:
+        _assert_same(ctx.uniform_sources(h, 300, 4, 6), oracle.uniform_sources(g, 300, 4, 6), "uniform")
+        _assert_same(ctx.exact(h), oracle.exact_bc(g), "exact")
+        targets = [0, 1, 30, 59]
+        res = ctx.adaptive_sources(h, targets, 1.5, 400, 4, 7)
+        ref = oracle.adaptive_sources(g, targets, 1.5, 400, 4, 7)
+        for key in ("k", "S", "status", "est"):
+            _assert_same(res[key], ref[key], key)
+    finally:
+        ctx.free_graph(h)
