@@ -277,8 +277,8 @@ k_pair_bidir(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, co
 // L2 (__ldcg). A pair whose ball outgrows half of its table, or
 // whose probe finds no free slot, is abandoned (its slots cleared) and listed
 // for the CTA engine above. (Opt-in, BCG_PAIR_ENGINE=2: on BA n = 2M it
-// measured 312k marginal pair draws/s against 486k for one pair per CTA; a
-// warp's 32 lanes take a large level's edges in many more dependent rounds.)
+// measured 312k marginal pair draws/s against 486k-592k for one pair per CTA;
+// a warp's 32 lanes take a large level's edges in many more dependent rounds.)
 constexpr int WP_WARPS = 8;                 // warps (pairs) per CTA
 constexpr int WP_HEAVY = 8;                 // frontier vertices above this degree are scanned by the whole warp
 constexpr unsigned long long WP_EMPTY = ~0ull;
