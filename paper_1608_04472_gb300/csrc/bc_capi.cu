@@ -381,14 +381,15 @@ __global__ void k_land_far(int32_t n, const int32_t *__restrict__ mind, unsigned
   if ((threadIdx.x & 31) == 0 && x) atomicMax(best, x);
 }
 
-constexpr int KEY_LM_MAX = 16;
-constexpr int KEY_CHUNK = 2048;
+constexpr int KEY_LM_MAX = 32;
+constexpr int KEY_CHUNK = 1024;
+constexpr int KEY_MOM_THREADS = 576;  // >= 1 + K + K(K+1)/2 = 561 moments for K = 32
 
 // Integer moments of the landmark distances over the vertices reached from the
 // hub: sums[0] = their count, sums[1+i] = sum of d_i, then sum of d_i d_j for
 // i <= j (row-major upper triangle). A block stages a chunk of the K rows in
 // shared memory and thread t owns moment t over the chunk.
-__global__ void __launch_bounds__(160) k_land_moments(int32_t n, int K, const uint8_t *__restrict__ rows,
+__global__ void __launch_bounds__(KEY_MOM_THREADS) k_land_moments(int32_t n, int K, const uint8_t *__restrict__ rows,
                                                       unsigned long long *__restrict__ sums) {
   __shared__ uint8_t sh[KEY_LM_MAX][KEY_CHUNK];
   const int64_t v0 = (int64_t)blockIdx.x * KEY_CHUNK;
@@ -595,7 +596,7 @@ static void copy_scan_out(bc_ctx *ctx, int32_t T, const ScanState &st, double sc
 // ---------------------------------------------------------------- drivers ---
 
 // Per-graph source keys (landmark projection, above) and, for exact BC, all
-// vertices ordered by key; computed on first use from K BFSs (K = 16, or
+// vertices ordered by key; computed on first use from K BFSs (K = 32, or
 // BCG_KEY_LANDMARKS; 1 gives the hub distance alone, rescaled).
 struct KeyMeta {
   DevBuf key, order;
@@ -661,15 +662,15 @@ static void build_key(bc_ctx *ctx, const Graph &g, KeyMeta &km) {
     dist.ensure(n * 4 + 8);
     mind.ensure(n * 4);
     rows.ensure(n * K);
-    // small: [0] landmark, [8] max distance, [16] farthest (u64), [32] range, [64] w|mu, [256] moments
-    small.ensure(256 + 8 * 160);
+    // small: [0] landmark, [8] max distance, [16] farthest (u64), [32] range, [64] w|mu, [512] moments
+    small.ensure(512 + 8 * KEY_MOM_THREADS);
     char *sm = small.as<char>();
     int32_t *d_src = reinterpret_cast<int32_t *>(sm);
     int *d_maxd = reinterpret_cast<int *>(sm + 8);
     unsigned long long *d_far = reinterpret_cast<unsigned long long *>(sm + 16);
     int *d_range = reinterpret_cast<int *>(sm + 32);
-    float *d_wmu = reinterpret_cast<float *>(sm + 64);  // w[16] | mu[16]
-    unsigned long long *d_mom = reinterpret_cast<unsigned long long *>(sm + 256);
+    float *d_wmu = reinterpret_cast<float *>(sm + 64);  // w[KEY_LM_MAX] | mu[KEY_LM_MAX]
+    unsigned long long *d_mom = reinterpret_cast<unsigned long long *>(sm + 512);
     BCG_CUDA(cudaMemsetAsync(sm, 0, small.bytes, st));
     int32_t L = g.hub;
     int Kused = 0;
@@ -704,7 +705,8 @@ static void build_key(bc_ctx *ctx, const Graph &g, KeyMeta &km) {
     const int nmom = 1 + Kused + Kused * (Kused + 1) / 2;
     {
       LaunchScope ls(ctx, F_MISC);
-      k_land_moments<<<(unsigned)((n + KEY_CHUNK - 1) / KEY_CHUNK), 160, 0, st>>>(g.n, Kused, rows.as<uint8_t>(),
+      k_land_moments<<<(unsigned)((n + KEY_CHUNK - 1) / KEY_CHUNK), KEY_MOM_THREADS, 0, st>>>(g.n, Kused,
+                                                                                           rows.as<uint8_t>(),
                                                                                  d_mom);
     }
     std::vector<unsigned long long> mom(nmom);
